@@ -1,0 +1,512 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints, closed forms (Bardeen's critical curve moved to finite r0, the
+Schwarzschild photon sphere and deflection integral, straight lines in flat
+space, Keplerian redshift), invariants of the exact flow (H = 0, Carter
+constant), and the Runge-Kutta order conditions. A plausible slip in the
+oracle (a dropped term, a wrong sign or index, a transposed operand) fails at
+least one of them.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_00086_gb300 import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+R0 = 1000.0
+
+
+# ---------------------------------------------------------------------------
+# Metric (Sec. 4.3): closed-form properties of the Kerr line element
+# ---------------------------------------------------------------------------
+
+def _points(seed=0, n=40):
+    rng = np.random.default_rng(seed)
+    for _ in range(n):
+        a = rng.uniform(0.0, 0.999)
+        rh = 1.0 + math.sqrt(1.0 - a * a)
+        r = rh * 1.05 + rng.uniform(0.0, 30.0)
+        th = rng.uniform(0.05, math.pi - 0.05)
+        yield a, r, th
+
+
+def test_metric_closed_forms():
+    for a, r, th in _points():
+        g = oracle.metric_cov(a, r, th)
+        s, c = math.sin(th), math.cos(th)
+        Sigma = r * r + a * a * c * c
+        # sqrt(-det g) = Sigma sin(theta) for Kerr in Boyer-Lindquist form.
+        assert np.linalg.det(g) == pytest.approx(-(Sigma * s) ** 2, rel=1e-11)
+        # frame-dragging rate -g_tphi/g_phph = 2 a r / ((r^2+a^2)^2 - a^2 Delta sin^2)
+        Delta = r * r - 2 * r + a * a
+        omega = 2 * a * r / ((r * r + a * a) ** 2 - a * a * Delta * s * s)
+        assert -g[0, 3] / g[3, 3] == pytest.approx(omega, rel=1e-12, abs=1e-300)
+        # symmetric, and only (t,phi) mixes
+        assert np.allclose(g, g.T, rtol=0, atol=0)
+        assert g[0, 1] == g[0, 2] == g[1, 2] == g[1, 3] == g[2, 3] == 0.0
+    # Schwarzschild limit
+    r, th = 7.3, 1.1
+    g = oracle.metric_cov(0.0, r, th)
+    expect = np.diag([-(1 - 2 / r), 1 / (1 - 2 / r), r * r, (r * math.sin(th)) ** 2])
+    assert np.allclose(g, expect, rtol=1e-15, atol=0)
+    # ergosphere: g_tt = 0 at r = 1 + sqrt(1 - a^2 cos^2)
+    a, th = 0.9, 0.7
+    r_erg = 1 + math.sqrt(1 - (a * math.cos(th)) ** 2)
+    assert abs(oracle.metric_cov(a, r_erg, th)[0, 0]) < 1e-14
+    # flat space (M = 0): Minkowski in spherical coordinates
+    g = oracle.metric_cov(0.0, 5.0, 0.4, M=0.0)
+    assert np.allclose(g, np.diag([-1, 1, 25, 25 * math.sin(0.4) ** 2]), rtol=1e-15, atol=0)
+
+
+def test_inverse_metric_is_inverse():
+    for a, r, th in _points(1):
+        g = oracle.metric_cov(a, r, th)
+        gi = oracle.metric_con(a, r, th)
+        assert np.allclose(gi @ g, np.eye(4), rtol=0, atol=1e-12)
+    # g^rr vanishes on the horizon
+    a = 0.7
+    rh = 1 + math.sqrt(1 - a * a)
+    assert abs(oracle.metric_con(a, rh, 1.0)[1, 1]) < 1e-15
+
+
+def _fd(f, x, h):
+    # fourth-order central difference
+    return (-f(x + 2 * h) + 8 * f(x + h) - 8 * f(x - h) + f(x - 2 * h)) / (12 * h)
+
+
+def test_inverse_metric_derivatives():
+    for a, r, th in _points(2, 25):
+        dr, dth = oracle.metric_con_derivs(a, r, th)
+        fr = _fd(lambda rr: oracle.metric_con(a, rr, th), r, 1e-3 * r)
+        ft = _fd(lambda tt: oracle.metric_con(a, r, tt), th, 1e-3)
+        scale_r = np.abs(fr).max()
+        scale_t = np.abs(ft).max() + 1e-300
+        assert np.abs(dr - fr).max() <= 1e-8 * scale_r
+        assert np.abs(dth - ft).max() <= 1e-8 * max(scale_t, 1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Equations of motion (Sec. 2.1): the RHS is the Hamiltonian vector field
+# ---------------------------------------------------------------------------
+
+def test_rhs_is_hamiltonian_vector_field():
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        a = rng.uniform(0, 0.99)
+        r = 1.2 * (1 + math.sqrt(1 - a * a)) + rng.uniform(0, 20)
+        th = rng.uniform(0.2, math.pi - 0.2)
+        y = np.array([0.0, r, th, 0.3, rng.normal(), rng.normal() * 3])
+        E, L = rng.uniform(0.5, 1.5), rng.normal() * 4  # off-shell on purpose: H != 0
+
+        def H(yy=y, EE=E, LL=L):
+            return oracle.hamiltonian(a, yy, EE, LL)
+
+        def d_state(k, h):
+            return _fd(lambda v: H(np.where(np.arange(6) == k, v, y)), y[k], h)
+
+        dy = oracle.rhs(a, y, E, L)
+        dH_dE = _fd(lambda v: H(y, v, L), E, 1e-4)
+        dH_dL = _fd(lambda v: H(y, E, v), L, 1e-4)
+        expect = np.array([
+            -dH_dE,                 # t'  = dH/dp_t = -dH/dE
+            d_state(4, 1e-4),       # r'  = dH/dp_r
+            d_state(5, 1e-4),       # th' = dH/dp_th
+            dH_dL,                  # ph' = dH/dp_ph
+            -d_state(1, 1e-4 * r),  # p_r'  = -dH/dr
+            -d_state(2, 1e-4),      # p_th' = -dH/dth
+        ])
+        assert np.allclose(dy, expect, rtol=1e-7, atol=1e-9 * np.abs(expect).max())
+
+
+# ---------------------------------------------------------------------------
+# Initial data (Sec. 2.3) against the values the paper prints (Sec. 3.1)
+# ---------------------------------------------------------------------------
+
+def _golden_ics():
+    with open(os.path.join(GOLDEN, "paper_single_orbit_ics.json")) as f:
+        return json.load(f)
+
+
+def test_printed_initial_conditions():
+    gold = _golden_ics()
+    a, r0 = gold["spacetime"]["a"], gold["observer"]["r0"]
+    for ray in gold["rays"]:
+        st = oracle.init_ray(a, r0, 90.0, ray["x"], ray["y"])
+        p_t, p_r, p_th, p_ph = -st[6], st[4], st[5], st[7]
+        # six printed decimals; p_r printed one unit off in the sixth place
+        assert p_t == pytest.approx(ray["p_t"], abs=2e-6)
+        assert p_r == pytest.approx(ray["p_r"], abs=2e-6)
+        assert p_th == pytest.approx(ray["p_theta"], abs=1e-6)
+        assert p_ph == pytest.approx(ray["p_phi"], abs=1e-6)
+        assert abs(oracle.hamiltonian(a, st[:6], st[6], st[7])) < 1e-15
+
+
+def test_initial_data_is_null_everywhere():
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        a = rng.uniform(0, 0.998)
+        inc = rng.uniform(3, 90)
+        x, y = rng.uniform(-25, 25, 2)
+        st = oracle.init_ray(a, rng.uniform(100, 2000), inc, x, y)
+        assert abs(oracle.hamiltonian(a, st[:6], st[6], st[7])) < 1e-14
+        assert st[4] < 0  # ingoing
+
+
+# ---------------------------------------------------------------------------
+# Capture flags: Bardeen's critical curve (Sec. 3.2) moved to finite r0
+# ---------------------------------------------------------------------------
+
+def _captured_by_radial_potential(a, st):
+    """Exact test: the ingoing ray is captured iff R(r) > 0 on [r_H, r0], with
+    R = (r^2 + a^2 - a xi)^2 - Delta (eta + (xi - a)^2), xi = L/E,
+    eta = Q/E^2, Q the Carter constant."""
+    r0, th0, p_th, E, L = st[1], st[2], st[5], st[6], st[7]
+    xi = L / E
+    eta = (p_th ** 2 + math.cos(th0) ** 2 * (L ** 2 / math.sin(th0) ** 2 - a * a * E * E)) / E ** 2
+    # R(r) = r^4 + (a^2 - xi^2 - eta) r^2 + 2 (eta + (xi - a)^2) r - a^2 eta
+    coeffs = [1.0, 0.0, a * a - xi * xi - eta, 2.0 * (eta + (xi - a) ** 2), -a * a * eta]
+    rh = 1 + math.sqrt(1 - a * a)
+    roots = np.roots(coeffs)
+    real = [z.real for z in roots if abs(z.imag) < 1e-7 * max(1.0, abs(z))]
+    return not any(rh < z < r0 for z in real)
+
+
+def _band_mask(flags):
+    """True where the 3x3 neighbourhood of a pixel has mixed flags."""
+    f = flags.astype(int)
+    ny, nx = f.shape
+    pad = np.pad(f, 1, mode="edge")
+    lo = np.full_like(f, 2)
+    hi = np.full_like(f, -1)
+    for dj in range(3):
+        for di in range(3):
+            w = pad[dj:dj + ny, di:di + nx]
+            lo = np.minimum(lo, w)
+            hi = np.maximum(hi, w)
+    return lo != hi
+
+
+@pytest.mark.parametrize("a,inc", [(0.0, 60.0), (0.5, 17.0), (0.9, 90.0), (0.998, 60.0),
+                                   (0.998, 90.0)])
+def test_capture_flags_match_critical_curve(a, inc):
+    n = 24
+    ext = (-8.0, 8.0, -8.0, 8.0)
+    res = oracle.trace_pixels(a, R0, inc, ext, n, n)
+    flags = np.zeros((n, n), bool)
+    for j in range(n):
+        for i in range(n):
+            x = ext[0] + (i + 0.5) * (ext[1] - ext[0]) / n
+            y = ext[2] + (j + 0.5) * (ext[3] - ext[2]) / n
+            flags[j, i] = _captured_by_radial_potential(a, oracle.init_ray(a, R0, inc, x, y))
+    got = (res["status"] == oracle.STATUS_CAPTURED).reshape(n, n)
+    assert set(np.unique(res["status"])) <= {oracle.STATUS_CAPTURED, oracle.STATUS_ESCAPED}
+    keep = ~_band_mask(flags)
+    assert keep.sum() > 0.6 * n * n
+    assert np.array_equal(got[keep], flags[keep])
+
+
+def test_worked_orbits_fates():
+    """The two printed initial conditions (Sec. 3.1) end as the equations say."""
+    gold = _golden_ics()
+    a, r0 = gold["spacetime"]["a"], gold["observer"]["r0"]
+    for ray in gold["rays"]:
+        st = oracle.init_ray(a, r0, 90.0, ray["x"], ray["y"])
+        captured = _captured_by_radial_potential(a, st)
+        assert captured == (ray["fate_from_equations"] == "captured")
+        res = oracle.trace_states(a, r0, st[None, :6], [st[6]], [st[7]])
+        want = oracle.STATUS_CAPTURED if captured else oracle.STATUS_ESCAPED
+        assert res["status"][0] == want
+
+
+def test_schwarzschild_shadow_radius():
+    """Config 'Schwarzschild shadow 64x64': captured iff rho < 3 sqrt(3) sqrt(1 - 2/r0)."""
+    cam = workloads.schwarzschild_shadow_64()
+    n = cam["nx"]
+    res = oracle.trace_pixels(cam["a"], cam["r_obs"], cam["incl_deg"], cam["extent"], n, n,
+                              tol=cam["tol"])
+    x0, x1, y0, y1 = cam["extent"]
+    xs = x0 + (np.arange(n) + 0.5) * (x1 - x0) / n
+    ys = y0 + (np.arange(n) + 0.5) * (y1 - y0) / n
+    rho = np.hypot(xs[None, :], ys[:, None])
+    rho_c = 3 * math.sqrt(3) * math.sqrt(1 - 2 / cam["r_obs"])
+    expect = rho < rho_c
+    got = (res["status"] == oracle.STATUS_CAPTURED).reshape(n, n)
+    keep = ~_band_mask(expect)
+    assert np.array_equal(got[keep], expect[keep])
+    # terminal surfaces located by bisection
+    cap = res["status"] == oracle.STATUS_CAPTURED
+    esc = res["status"] == oracle.STATUS_ESCAPED
+    assert np.allclose(res["r"][cap], 1.01 * 2.0, rtol=1e-12)
+    assert np.allclose(res["r"][esc], 1.1 * cam["r_obs"], rtol=1e-12)
+
+
+def test_schwarzschild_critical_impact_parameter():
+    """Bisection in rho on the oracle converges to 3 sqrt(3) sqrt(1 - 2/r0)."""
+    inc = 85.0
+    lo, hi = 5.0, 5.4
+    for _ in range(24):
+        mid = 0.5 * (lo + hi)
+        st = oracle.init_ray(0.0, R0, inc, -mid, 0.0)
+        res = oracle.trace_states(0.0, R0, st[None, :6], [st[6]], [st[7]])
+        if res["status"][0] == oracle.STATUS_CAPTURED:
+            lo = mid
+        else:
+            hi = mid
+    assert 0.5 * (lo + hi) == pytest.approx(3 * math.sqrt(3) * math.sqrt(1 - 2 / R0), abs=2e-6)
+
+
+# ---------------------------------------------------------------------------
+# Photon sphere and deflection (Schwarzschild), straight lines (flat space)
+# ---------------------------------------------------------------------------
+
+def test_photon_sphere_orbit():
+    """r = 3, p_r = 0, b = 3 sqrt(3): a circular photon orbit with dphi/dt = 1/(3 sqrt 3)."""
+    b = 3 * math.sqrt(3)
+    st = np.array([[0.0, 3.0, math.pi / 2, 0.0, 0.0, 0.0]])
+    res = oracle.trace_states(0.0, R0, st, [1.0], [b], max_steps=60)
+    assert res["status"][0] == oracle.STATUS_MAXSTEP
+    assert res["r"][0] == pytest.approx(3.0, abs=1e-8)
+    assert res["phi"][0] / res["t"][0] == pytest.approx(1 / b, rel=1e-9)
+    assert res["t"][0] > 20.0
+
+
+def _cartesian_frame(th, ph):
+    er = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+    et = np.array([math.cos(th) * math.cos(ph), math.cos(th) * math.sin(ph), -math.sin(th)])
+    ep = np.array([-math.sin(ph), math.cos(ph), 0.0])
+    return er, et, ep
+
+
+def _initial_direction(x, y, r0, th0):
+    """Unit spatial direction of the ray in the observer's orthonormal frame:
+    (P^r, P^theta, P^phi) = (-sqrt(1 - (x^2+y^2)/r0^2), y/r0, -x/r0)."""
+    er, et, ep = _cartesian_frame(th0, 0.0)
+    v = -math.sqrt(1 - (x * x + y * y) / r0 ** 2) * er + (y / r0) * et + (-x / r0) * ep
+    return er, v
+
+
+def _angles(u):
+    th = math.acos(max(-1.0, min(1.0, u[2])))
+    ph = math.atan2(u[1], u[0]) % (2 * math.pi)
+    return th, ph
+
+
+def _ang_close(got_th, got_ph, th, ph, tol):
+    assert abs(got_th - th) < tol
+    d = (got_ph - ph + math.pi) % (2 * math.pi) - math.pi
+    assert abs(d) < tol
+
+
+def test_flat_space_straight_lines():
+    rng = np.random.default_rng(5)
+    r0, inc = 1000.0, 70.0
+    th0 = math.radians(inc)
+    pts = rng.uniform(-400, 400, size=(12, 2))
+    for x, y in pts:
+        st = oracle.init_ray(0.0, r0, inc, x, y, M=0.0)
+        res = oracle.trace_states(0.0, r0, st[None, :6], [st[6]], [st[7]], M=0.0)
+        assert res["status"][0] == oracle.STATUS_ESCAPED
+        n0, v = _initial_direction(x, y, r0, th0)
+        X0 = r0 * n0
+        r_esc = 1.1 * r0
+        bdot = X0 @ v
+        s = -bdot + math.sqrt(bdot * bdot - r0 * r0 + r_esc * r_esc)
+        Xf = X0 + s * v
+        th, ph = _angles(Xf / np.linalg.norm(Xf))
+        _ang_close(res["theta"][0], res["phi"][0] % (2 * math.pi), th, ph, 1e-9)
+        assert res["max_abs_H"][0] < 1e-9  # truncation error at tol 1e-10
+
+
+def _deflection_sweep(b, r0, r_esc):
+    """Swept orbital angle from r0 in to the turning point and out to r_esc
+    (Schwarzschild, M = 1): with u = 1/r the orbit equation reads
+    (du/dphi)^2 = G(u) = 1/b^2 - u^2 + 2 u^3, so the sweep is the sum of the
+    two integrals of du / sqrt(G) from 1/r0 and from 1/r_esc up to the
+    turning point u_t, the smallest positive root of G."""
+    import mpmath as mp
+    mp.mp.dps = 40
+    b = mp.mpf(b)
+    roots = mp.polyroots([2, -1, 0, 1 / (b * b)], maxsteps=400, extraprec=120)
+    u_t = min(mp.re(z) for z in roots if abs(mp.im(z)) < mp.mpf(10) ** -30 and mp.re(z) > 0)
+
+    def f(u):
+        return 1 / mp.sqrt(1 / (b * b) - u * u + 2 * u ** 3)
+
+    total = mp.quad(f, [1 / mp.mpf(r0), u_t]) + mp.quad(f, [1 / mp.mpf(r_esc), u_t])
+    return float(mp.re(total))
+
+
+def test_schwarzschild_deflection():
+    r0, inc = 1000.0, 85.0
+    th0 = math.radians(inc)
+    for x, y in [(-6.5, 0.7), (7.0, -3.0), (0.4, 8.9), (-9.0, -9.5), (5.6, 1.1)]:
+        st = oracle.init_ray(0.0, r0, inc, x, y)
+        res = oracle.trace_states(0.0, r0, st[None, :6], [st[6]], [st[7]])
+        assert res["status"][0] == oracle.STATUS_ESCAPED
+        b = math.hypot(x, y) / math.sqrt(1 - 2 / r0)
+        Phi = _deflection_sweep(b, r0, 1.1 * r0)
+        n0, v = _initial_direction(x, y, r0, th0)
+        nrm = np.cross(n0, v)
+        nrm /= np.linalg.norm(nrm)
+        # rotate n0 by Phi about the orbit normal (Rodrigues)
+        uf = n0 * math.cos(Phi) + np.cross(nrm, n0) * math.sin(Phi)
+        th, ph = _angles(uf)
+        _ang_close(res["theta"][0], res["phi"][0] % (2 * math.pi), th, ph, 1e-8)
+
+
+# ---------------------------------------------------------------------------
+# Invariants along oracle rays
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("a,inc", [(0.9, 60.0), (0.998, 17.0), (0.5, 90.0)])
+def test_carter_constant_and_H(a, inc):
+    n = 16
+    res = oracle.trace_pixels(a, R0, inc, (-8, 8, -8, 8), n, n)
+    rel = res["max_carter_drift"] / np.maximum(np.abs(res["carter0"]), 1.0)
+    assert rel.max() < 1e-8
+    esc = res["status"] == oracle.STATUS_ESCAPED
+    # |H| of escaped rays stays near the per-step tolerance (1e-10)
+    assert res["max_abs_H"][esc].max() < 2e-9
+
+
+def test_H_scales_with_tolerance():
+    cam = workloads.schwarzschild_shadow_64()
+    pix = np.arange(0, 64 * 64, 37)
+    out = {}
+    for tol in (1e-10, 1e-11):
+        res = oracle.trace_pixels(0.0, R0, 85.0, cam["extent"], 64, 64, pixels=pix, tol=tol)
+        esc = res["status"] == oracle.STATUS_ESCAPED
+        out[tol] = res["max_abs_H"][esc].max()
+    assert out[1e-11] < 1e-10
+    assert out[1e-11] < out[1e-10] / 5
+
+
+# ---------------------------------------------------------------------------
+# Thin Keplerian disk (Sec. 5)
+# ---------------------------------------------------------------------------
+
+def test_schwarzschild_disk_redshift_closed_form():
+    cam = workloads.schwarzschild_disk(side=40)
+    n = cam["nx"]
+    res = oracle.trace_pixels(0.0, R0, cam["incl_deg"], cam["extent"], n, n, disk=True,
+                              r_in=cam["r_in"], r_out=cam["r_out"],
+                              cell_phase_deg=cam["cell_phase_deg"])
+    disk = res["status"] == oracle.STATUS_DISK
+    assert disk.sum() > 0.1 * n * n
+    r = res["r_hit"][disk]
+    assert r.min() >= 6.0 and r.max() <= 20.0
+    assert np.abs(res["theta"][disk] - math.pi / 2).max() < 1e-12
+    E, L = res["E"][disk], res["L"][disk]
+    # u^t = 1/sqrt(1 - 3/r), Omega = r^-3/2
+    g_expect = np.sqrt(1 - 3 / r) / (E - L * r ** -1.5)
+    assert np.allclose(res["g"][disk], g_expect, rtol=1e-13)
+    assert np.allclose(res["intensity"][disk], g_expect ** 3 / r ** 2, rtol=1e-12)
+    # rays that miss the disk follow exactly the shadow-mode trajectory
+    sh = oracle.trace_pixels(0.0, R0, cam["incl_deg"], cam["extent"], n, n,
+                             cell_phase_deg=cam["cell_phase_deg"])
+    miss = ~disk
+    for key in ("status", "r", "theta", "phi", "max_abs_H", "accepted"):
+        assert np.array_equal(res[key][miss], sh[key][miss]), key
+
+
+def test_kerr_disk_redshift_closed_form():
+    a = 0.9
+    r_in = oracle.isco(a)
+    res = oracle.trace_pixels(a, R0, 60.0, (-25, 25, -25, 25), 24, 24, disk=True, r_in=r_in,
+                              r_out=20.0)
+    disk = res["status"] == oracle.STATUS_DISK
+    assert disk.sum() > 50
+    r, E, L = res["r_hit"][disk], res["E"][disk], res["L"][disk]
+    # Bardeen-Press-Teukolsky prograde circular orbit: u^t and Omega in closed form
+    ut = (r ** 1.5 + a) / (r ** 0.75 * np.sqrt(r ** 1.5 - 3 * r ** 0.5 + 2 * a))
+    Om = 1 / (r ** 1.5 + a)
+    assert np.allclose(res["g"][disk], 1 / (ut * (E - Om * L)), rtol=1e-12)
+
+
+def test_redshift_special_cases():
+    # L = 0 ray hitting a Schwarzschild disk: g = sqrt(1 - 3/r) / E
+    for r in (6.0, 9.5, 20.0):
+        g, I = oracle.disk_observables(0.0, r, 0.97, 0.0)
+        assert g == pytest.approx(math.sqrt(1 - 3 / r) / 0.97, rel=1e-14)
+        assert I == pytest.approx(g ** 3 / r ** 2, rel=1e-14)
+
+
+def test_isco():
+    """ISCO closed form: extremum of the circular-orbit energy; a=0 -> 6, a=1 -> 1."""
+    from scipy.optimize import minimize_scalar
+    assert oracle.isco(0.0) == pytest.approx(6.0, abs=1e-13)
+    assert oracle.isco(1.0) == pytest.approx(1.0, abs=1e-6)
+    for a in (0.3, 0.5, 0.9, 0.998):
+        def energy(r):
+            return (r ** 1.5 - 2 * r ** 0.5 + a) / (r ** 0.75 * math.sqrt(r ** 1.5 - 3 * r ** 0.5 + 2 * a))
+        rg = oracle.isco(a)
+        opt = minimize_scalar(energy, bracket=(rg * 0.9, rg, rg * 1.5), tol=1e-12)
+        assert opt.x == pytest.approx(rg, rel=1e-5)
+
+
+# ---------------------------------------------------------------------------
+# Cash-Karp 4(5) (Sec. 3.1)
+# ---------------------------------------------------------------------------
+
+def _order_conditions(A, b, c, order):
+    """Butcher order conditions up to `order` (17 for order 5); returns residuals."""
+    Ac = A @ c
+    Ac2 = A @ (c * c)
+    AAc = A @ Ac
+    conds = [
+        (1, b.sum(), 1),
+        (2, b @ c, Fraction(1, 2)),
+        (3, b @ c ** 2, Fraction(1, 3)), (3, b @ Ac, Fraction(1, 6)),
+        (4, b @ c ** 3, Fraction(1, 4)), (4, b @ (c * Ac), Fraction(1, 8)),
+        (4, b @ Ac2, Fraction(1, 12)), (4, b @ AAc, Fraction(1, 24)),
+        (5, b @ c ** 4, Fraction(1, 5)), (5, b @ (c * c * Ac), Fraction(1, 10)),
+        (5, b @ (c * Ac2), Fraction(1, 15)), (5, b @ (c * AAc), Fraction(1, 30)),
+        (5, b @ (Ac * Ac), Fraction(1, 20)), (5, b @ (A @ c ** 3), Fraction(1, 20)),
+        (5, b @ (A @ (c * Ac)), Fraction(1, 40)), (5, b @ (A @ Ac2), Fraction(1, 60)),
+        (5, b @ (A @ AAc), Fraction(1, 120)),
+    ]
+    return [(o, float(v) - float(t)) for o, v, t in conds if o <= order]
+
+
+def test_cash_karp_tableau_order_conditions():
+    c, A, b5, b4 = oracle.ck_tableau()
+    assert np.allclose(A.sum(axis=1), c, atol=1e-15)
+    assert np.allclose(np.triu(A), 0.0)
+    res5 = _order_conditions(A, b5, c, 5)
+    assert len(res5) == 17
+    assert max(abs(r) for _, r in res5) < 1e-14
+    res4 = _order_conditions(A, b4, c, 5)
+    assert max(abs(r) for o, r in res4 if o <= 4) < 1e-14
+    assert max(abs(r) for o, r in res4 if o == 5) > 1e-4  # the embedded pair is 4th order
+
+
+def test_cash_karp_convergence_order():
+    """Fixed-step integration of a flat-space ray: global error of the
+    propagated solution falls as h^5."""
+    r0, th0 = 10.0, 1.0
+    x, y = 3.0, -2.0
+    st = oracle.init_ray(0.0, r0, math.degrees(th0), x, y, M=0.0)
+    n0, v = _initial_direction(x, y, r0, th0)
+    lam = 12.0
+    Xf = r0 * n0 + lam * v  # E = 1: the affine parameter is the Euclidean length
+    r_ex = np.linalg.norm(Xf)
+    th_ex, ph_ex = _angles(Xf / r_ex)
+    errs = []
+    for nsteps in (80, 160, 320):
+        yv = st[:6].copy()
+        h = lam / nsteps
+        for _ in range(nsteps):
+            yv, _d = oracle.ck_step(0.0, yv, st[6], st[7], h, M=0.0)
+        errs.append(max(abs(yv[1] - r_ex), abs(yv[2] - th_ex),
+                        abs((yv[3] - ph_ex + math.pi) % (2 * math.pi) - math.pi)))
+    orders = [math.log2(e1 / e2) for e1, e2 in zip(errs, errs[1:])]
+    # pre-asymptotic at the coarse end, ~5.0 once h is small enough
+    assert 4.6 < orders[0] < 6.2
+    assert 4.7 < orders[1] < 5.3
