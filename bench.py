@@ -1,0 +1,352 @@
+"""Benchmark: Kerr shadow / Einstein-ring renders, rays per second.
+
+One step = one pass of the whole hot path (initial data, Cash-Karp
+integration of Hamilton's equations, stopping surfaces, observables) over the
+twelve 1024x1024 renders of the Kerr set: spin a in {0, 0.5, 0.9, 0.998} x
+inclination in {17, 60, 90} deg, r_obs = 1000, image plane [-8, 8]^2,
+tol 1e-10, seeded 10-degree checkerboard, FP64. By default the twelve renders
+go through ONE persistent batched launch (osiris_trace_batch).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0). With N > 1 (torchrun) every rank renders its
+own copy of the set (weak scaling) and the time is the max over ranks.
+`--impl reference` times the CPU oracle (the only other implementation of the
+method here) on a bounded pixel sample of the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD_NAME = ("kerr_shadow_ring: 12 renders (a in {0,0.5,0.9,0.998} x incl in {17,60,90} deg), "
+                 "r_obs=1000, 1024x1024 cell centres on [-8,8]^2, Cash-Karp tol 1e-10, "
+                 "r_cap=1.01 r_H, r_esc=1.1 r_obs, seeded 10-deg checkerboard")
+METRIC = "rays/s (Kerr shadow+ring renders, FP64 Cash-Karp)"
+UNIT = "rays/s"
+# Algorithmic FP64 operations (FMA = 2, add/mul = 1, sincos and reciprocal = 1
+# each) of one evaluation of the separated Hamilton equations, and of one
+# Cash-Karp attempt besides its six evaluations (stage sums, fifth-order sum,
+# error estimate, error norm, step clamp).
+F_RHS = 59
+F_STEP = 258
+# Bytes per ray of the shadow outputs copied back in the end-to-end timing:
+# status 1, r/theta/phi/max|H| 4x8, steps 4, cell_i/cell_j 2x2, parity 1.
+SHADOW_BYTES_PER_RAY = 42
+ORACLE_SAMPLE_STRIDE = 128  # CPU baseline: every 128th pixel of each render
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="osiris", choices=["osiris", "reference"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--kernel", default="batch", choices=["batch", "persistent", "plain"])
+    p.add_argument("--side", type=int, default=1024)
+    p.add_argument("--block", type=int, default=0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": float(max(power))}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_pixels(rd, stride):
+    n = rd["nx"] * rd["ny"]
+    return np.arange(stride // 2, n, stride, dtype=np.int64)
+
+
+def run_oracle_sample(renders, stride):
+    import oracle
+    cores = os.cpu_count() or 1
+    n = 0
+    t0 = time.perf_counter()
+    for rd in renders:
+        pix = oracle_sample_pixels(rd, stride)
+        oracle.trace_pixels(rd["a"], rd["r_obs"], rd["incl_deg"], rd["extent"], rd["nx"],
+                            rd["ny"], pixels=pix, nthreads=cores, tol=rd["tol"],
+                            cell_deg=rd["cell_deg"], cell_phase_deg=rd["cell_phase_deg"])
+        n += pix.size
+    dt = time.perf_counter() - t0
+    return n, dt, cores
+
+
+def reference_arm(args, renders):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    stride = ORACLE_SAMPLE_STRIDE
+    for _ in range(args.warmup):
+        run_oracle_sample(renders, stride)
+    tot_n, tot_t, cores = 0, 0.0, 1
+    for _ in range(args.steps):
+        n, dt, cores = run_oracle_sample(renders, stride)
+        tot_n += n
+        tot_t += dt
+    value = tot_n / tot_t
+    sample = ("every %dth pixel of each of the 12 renders (%d rays per step), all host cores"
+              % (stride, tot_n // max(1, args.steps)))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    from paper_2202_00086_gb300 import workloads
+    renders = workloads.kerr_shadow_ring_set(args.side)
+    if args.impl == "reference":
+        return reference_arm(args, renders)
+
+    import torch
+    import paper_2202_00086_gb300 as osr
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    precision = osr.MIXED if args.precision == "mixed" else osr.FP64
+    tol = 1e-10
+    cams = [osr.Camera.from_render(rd) for rd in renders]
+    n_rays = sum(c.n_rays for c in cams)
+    outs = [osr.alloc_outputs(c.n_rays) for c in cams]
+    ws = torch.empty(osr.workspace_bytes(len(cams)), dtype=torch.uint8, device="cuda")
+    stats = osr.new_stats()
+    stream = torch.cuda.current_stream()
+    launches = [0]
+    common = dict(tol=tol, precision=precision, block_size=args.block, workspace=ws,
+                  cell_deg=renders[0]["cell_deg"], cell_phase_deg=renders[0]["cell_phase_deg"])
+
+    def step(st=None):
+        if args.kernel == "batch":
+            reqs = [{"camera": c, "out": o} for c, o in zip(cams, outs)]
+            osr.trace_batch(reqs, stats=st, **common)
+            launches[0] += 1
+        else:
+            for c, o in zip(cams, outs):
+                osr.trace(c, out=o, persistent=(args.kernel == "persistent"), stats=st, **common)
+                launches[0] += 1
+
+    # L2 flush buffer (larger than the 129 MB L2), written between timed steps
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # FP64 / FP32 FMA throughput probe (roofline denominators), same process
+    probe_out = torch.empty(152 * 8 * 256, dtype=torch.float64, device="cuda")
+    peaks = {}
+    for prec, iters, name in ((osr.FP64, 4096, "fp64"), (osr.MIXED, 65536, "fp32")):
+        osr.fma_probe(prec, probe_out.numel(), iters, probe_out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fl = sum(osr.fma_probe(prec, probe_out.numel(), iters, probe_out) for _ in range(5))
+        e1.record()
+        torch.cuda.synchronize()
+        peaks[name] = fl / (e0.elapsed_time(e1) * 1e-3) / 1e12
+
+    # ---- timed region: K steps, per-step CUDA events, L2 flushed between ----
+    clocks = ClockSampler(local)
+    stats.zero_()
+    launches[0] = 0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        ev[k][0].record(stream)
+        step(stats)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    barrier()
+    clk = clocks.stop()
+    kernel_launches = launches[0]
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    s = osr.decode_stats(stats)
+
+    # ---- end to end through the C interface with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        host = [osr.alloc_outputs(c.n_rays, device="cpu", pin_memory=True) for c in cams]
+        h2d = osr.workspace_bytes(len(cams)) - 256 if args.kernel == "batch" else 0
+        d2h = SHADOW_BYTES_PER_RAY * n_rays
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            step()
+            for c, o, h in zip(cams, outs, host):
+                osr.copy_outputs_to_host(o, h, c.n_rays)
+            torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        tt = torch.tensor([te], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt.item())
+        e2e = {"value": world * n_rays * args.steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, dt, cores = run_oracle_sample(renders, ORACLE_SAMPLE_STRIDE)
+        cpu = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "every %dth pixel of each of the 12 renders (%d rays), one pass"
+                         % (ORACLE_SAMPLE_STRIDE, n)}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    value = world * n_rays * args.steps / (ms_max * 1e-3)
+    attempts = s["accepted"] + s["rejected"] + s["root_steps"]
+    flops = s["rhs_evals"] * F_RHS + attempts * F_STEP
+    per_launch_ms = ms / max(1, kernel_launches)
+    achieved = flops / max(1, kernel_launches) / (per_launch_ms * 1e-3) / 1e12
+    peak = peaks["fp64"] if precision == osr.FP64 else peaks["fp32"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if precision == osr.FP64 else "f64+f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "rays_per_step_per_gpu": n_rays,
+                   "kernel": args.kernel, "precision": args.precision,
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "wall_s_timed": t_wall},
+        "rhs_evals_per_s": world * s["rhs_evals"] / (ms_max * 1e-3),
+        "steps_per_ray": {"accepted": s["accepted"] / (n_rays * args.steps),
+                          "rejected": s["rejected"] / (n_rays * args.steps),
+                          "locate": s["root_steps"] / (n_rays * args.steps)},
+        "status_counts_per_step": {k: s[k] // args.steps for k in
+                                   ("status_captured", "status_escaped", "status_maxstep",
+                                    "status_error")},
+        "max_abs_H": s["max_abs_H"],
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "FMA probe measured in this process (FP64 pipe)"
+                                    if precision == osr.FP64 else
+                                    "FMA probe measured in this process (FP32 pipe)",
+                     "flops_per_launch": flops / max(1, kernel_launches),
+                     "f_rhs": F_RHS, "f_step": F_STEP},
+        "fma_probe_tflops": peaks,
+        "clocks": clk,
+        "gpu_launches": kernel_launches,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

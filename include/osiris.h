@@ -1,0 +1,228 @@
+/*
+ * osiris.h -- C interface of the GB300 backward ray tracer for null geodesics
+ * in Kerr space-time (Velasquez-Cadavid et al., "OSIRIS: A New Code for Ray
+ * Tracing Around Compact Objects", arXiv:2202.00086).
+ *
+ * Conventions shared by every call
+ *   - Geometrized units with the black-hole mass M = 1 (Sec. 1, last paragraph).
+ *   - Boyer-Lindquist coordinates (t, r, theta, phi) and signature (-,+,+,+)
+ *     (Sec. 4.3, Eq. Kerr).
+ *   - One image-plane pixel = one backward null geodesic (Sec. 2.2). Pixel
+ *     (i, j), 0 <= i < nx, 0 <= j < ny, sits at the cell centre
+ *       x_i = x_min + (i + 1/2) (x_max - x_min) / nx,
+ *       y_j = y_min + (j + 1/2) (y_max - y_min) / ny,
+ *     and its outputs live at linear index j * nx + i.
+ *   - Output arrays are caller-owned DEVICE pointers (any may be NULL when
+ *     not wanted). The library never frees them.
+ *   - Every launch is asynchronous on the caller's CUDA stream (a
+ *     cudaStream_t passed as void*; NULL = the legacy default stream).
+ *   - Return value 0 = OSIRIS_OK, negative = error (see osiris_strerror).
+ *     Argument errors are detected on the host before anything is launched.
+ *     No C++ exception crosses this interface.
+ */
+#ifndef OSIRIS_H
+#define OSIRIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define OSIRIS_OK 0
+#define OSIRIS_EINVAL (-1)   /* an argument is out of its documented range */
+#define OSIRIS_ECUDA (-2)    /* a CUDA runtime call failed */
+#define OSIRIS_ENOMEM (-3)   /* a caller-provided workspace is too small */
+#define OSIRIS_ETIMEOUT (-4) /* a bounded wait ran out */
+
+/* ---- per-ray status (the fate of the backward ray; Sec. 4.1, Sec. 5) ---- */
+#define OSIRIS_STATUS_NONE 0     /* not traced */
+#define OSIRIS_STATUS_CAPTURED 1 /* reached r < r_cap_factor * r_H */
+#define OSIRIS_STATUS_ESCAPED 2  /* reached the celestial sphere r > r_esc_factor * r_obs */
+#define OSIRIS_STATUS_DISK 3     /* hit the equatorial disk r_in <= r <= r_out */
+#define OSIRIS_STATUS_MAXSTEP 4  /* step budget exhausted */
+#define OSIRIS_STATUS_ERROR 5    /* state became non-finite */
+
+/* ---- precision of the integrator -------------------------------------- */
+#define OSIRIS_FP64 0  /* every operation in double precision */
+#define OSIRIS_MIXED 1 /* FP32 stage evaluations, FP64 state and controller */
+
+/* ---- counters written to osiris_trace_opts.stats (uint64 each) --------- */
+#define OSIRIS_STAT_RAYS 0          /* rays finished */
+#define OSIRIS_STAT_ACCEPTED 1      /* accepted Cash-Karp steps */
+#define OSIRIS_STAT_REJECTED 2      /* rejected Cash-Karp steps */
+#define OSIRIS_STAT_ROOT_STEPS 3    /* steps spent locating stopping surfaces */
+#define OSIRIS_STAT_RHS_EVALS 4     /* evaluations of Hamilton's equations */
+#define OSIRIS_STAT_STATUS0 5       /* 5..10: rays per status code 0..5 */
+#define OSIRIS_STAT_MAX_ABS_H 11    /* max |H| over all rays, as IEEE-754 bits */
+#define OSIRIS_STAT_FP64_STEPS 12   /* mixed precision: steps taken in FP64 */
+#define OSIRIS_STATS_LEN 16
+
+/* Opaque camera: space-time, observer and image plane. Host memory only. */
+typedef struct osiris_camera osiris_camera;
+
+/* Integration options. Fill with osiris_default_opts, then override. */
+typedef struct {
+    double tol;            /* per-step tolerance of the embedded error estimate
+                              (error norm: max over r, theta, phi, p_r, p_theta of
+                              |y5 - y4| / (tol (1 + max(|y_n|, |y_n+1|)))), > 0 */
+    int64_t max_steps;     /* cap on accepted + rejected steps per ray, >= 1 */
+    int32_t precision;     /* OSIRIS_FP64 or OSIRIS_MIXED */
+    int32_t persistent;    /* 0: one ray per thread; 1: persistent grid that
+                              refills lanes from a device ray queue (needs
+                              workspace) */
+    double r_cap_factor;   /* captured when r < r_cap_factor * r_H, > 1 */
+    double r_esc_factor;   /* escaped when r > r_esc_factor * r_obs, > 1 */
+    double cell_deg;       /* celestial checkerboard cell, degrees, (0, 180] */
+    double cell_phase_deg; /* longitude offset of the checkerboard, degrees */
+    int32_t block_size;    /* threads per block, multiple of 32 in [32, 512];
+                              0 = library default */
+    int32_t blocks_per_sm; /* persistent grid: blocks per SM; 0 = occupancy limit */
+    uint64_t* stats;       /* optional DEVICE array of OSIRIS_STATS_LEN counters;
+                              the call adds to them (zero it first) */
+    void* workspace;       /* DEVICE scratch, >= osiris_workspace_bytes(n) bytes,
+                              256-byte aligned; required when persistent != 0 or
+                              for osiris_trace_batch. Not shared between calls
+                              that may run at the same time. */
+    size_t workspace_bytes;
+} osiris_trace_opts;
+
+/* Per-ray outputs: DEVICE arrays with one entry per ray (NULL = not wanted).
+ * Shadow/lensing outputs (Sec. 3.2, Sec. 4):
+ *   status      fate (OSIRIS_STATUS_*)
+ *   r,theta,phi final Boyer-Lindquist position; on the stopping surface for
+ *               CAPTURED / ESCAPED / DISK; theta and phi are not wrapped
+ *   max_abs_H   max |H| over the initial point, every accepted point and the
+ *               final point (Sec. 3.1, Error = |H_num|)
+ *   steps       accepted Cash-Karp steps
+ *   cell_i/j    ESCAPED: checkerboard cell (theta folded into [0, pi], phi
+ *               wrapped into [0, 2pi) after adding the phase); else -1
+ *   parity      ESCAPED: (cell_i + cell_j) mod 2; else 0
+ * Disk outputs (Sec. 5), DISK rays only (0 elsewhere):
+ *   g           redshift nu_obs / nu_em, nu_obs = 1 in the observer's frame
+ *   intensity   g^3 r_hit^-2
+ *   r_hit       radius of the first crossing inside [r_in, r_out] */
+typedef struct {
+    uint8_t* status;
+    double* r;
+    double* theta;
+    double* phi;
+    double* max_abs_H;
+    uint32_t* steps;
+    int16_t* cell_i;
+    int16_t* cell_j;
+    uint8_t* parity;
+    double* g;
+    double* intensity;
+    double* r_hit;
+} osiris_outputs;
+
+/* Sets the defaults: tol 1e-10, max_steps 1e6, FP64, non-persistent,
+ * r_cap_factor 1.01, r_esc_factor 1.1, 10-degree cells, phase 0, library
+ * block size, no stats, no workspace. */
+void osiris_default_opts(osiris_trace_opts* opts);
+
+/* Create a camera (Sec. 2.3, Eq. momentums; observer at t0 = 0, phi0 = 0):
+ *   a          spin, 0 <= a < 1
+ *   r_obs      observer radius, > 10 r_H
+ *   incl_deg   observer polar angle theta0 in degrees, (0, 180)
+ *   x/y_min/max image-plane extent (x_min < x_max, y_min < y_max); every
+ *              corner must satisfy x^2 + y^2 < r_obs^2
+ *   nx, ny     resolution, >= 1 each
+ * The observer is a zero angular momentum observer; a pixel (x, y) gets
+ *   p_theta = y sqrt(g_thth)/r_obs, L = p_phi = -x sqrt(g_phph)/r_obs,
+ *   E = -p_t = 1/A_t + x g_tphi/(r_obs sqrt(g_phph)),
+ *   p_r = -sqrt(g_rr (1 - (x^2 + y^2)/r_obs^2)),
+ * with A_t = sqrt(g_phph / (g_tphi^2 - g_tt g_phph)) and the metric at
+ * (r_obs, theta0). Host-only: no device work, no allocation on the device.
+ * On success *out owns host memory released by osiris_destroy_camera. */
+int osiris_init_camera(osiris_camera** out, double a, double r_obs, double incl_deg,
+                       double x_min, double x_max, double y_min, double y_max, int32_t nx,
+                       int32_t ny);
+
+void osiris_destroy_camera(osiris_camera* cam);
+
+/* Number of rays (nx * ny) of a camera. */
+int64_t osiris_camera_rays(const osiris_camera* cam);
+
+/* Shadow and lensing render (Sec. 3.2, Sec. 4): trace every pixel of the
+ * camera until capture, escape, the step cap or a non-finite state. Rays are
+ * integrated with Hamilton's equations (Sec. 2.1) by adaptive Cash-Karp 4(5)
+ * steps (Sec. 3.1); the capture and escape surfaces are located inside the
+ * last step. Outputs hold osiris_camera_rays(cam) entries. */
+int osiris_trace(const osiris_camera* cam, const osiris_trace_opts* opts,
+                 const osiris_outputs* out, void* cuda_stream);
+
+/* Thin-disk render (Sec. 5): as osiris_trace, and a ray also stops at its
+ * first crossing of the equatorial plane with r_in <= r <= r_out, where a
+ * Keplerian disk (Omega = 1 / (r^3/2 + a)) gives the redshift g and the
+ * intensity g^3 r^-2. Requires r_cap_factor * r_H < r_in < r_out < r_esc. */
+int osiris_render_disk(const osiris_camera* cam, double r_in, double r_out,
+                       const osiris_trace_opts* opts, const osiris_outputs* out,
+                       void* cuda_stream);
+
+/* One render of a batch. */
+typedef struct {
+    const osiris_camera* camera;
+    int32_t disk;        /* 0: shadow/lensing, 1: thin disk */
+    double r_in, r_out;  /* disk radii (disk = 1) */
+    double tol;          /* per-request tolerance; <= 0 takes opts->tol */
+    osiris_outputs out;  /* DEVICE outputs of this request */
+} osiris_request;
+
+/* Bytes of DEVICE workspace that osiris_trace_batch needs for n requests
+ * (also enough for osiris_trace / osiris_render_disk with persistent = 1
+ * when n = 1). */
+size_t osiris_workspace_bytes(int32_t n_requests);
+
+/* Batched uneven renders in ONE persistent launch: the rays of all requests
+ * form one device queue; lanes that finish a ray take the next one, whatever
+ * its request. Each request's outputs are those of the corresponding single
+ * call. opts->workspace must hold osiris_workspace_bytes(n) bytes; the
+ * request table is copied into it on the stream (the host array may be
+ * reused when the call returns). 1 <= n_requests <= 65536. */
+int osiris_trace_batch(const osiris_request* reqs, int32_t n_requests,
+                       const osiris_trace_opts* opts, void* cuda_stream);
+
+/* Test hook: trace n rays from explicit initial data instead of pixels.
+ * states: DEVICE array of n rows (t, r, theta, phi, p_r, p_theta) (t unused);
+ * E, L: DEVICE arrays of n constants (p_t = -E, p_phi = L). r_obs sets the
+ * escape radius. disk = 1 adds the disk of osiris_render_disk. Outputs hold
+ * n entries. */
+int osiris_trace_states(double a, double r_obs, const double* states, const double* E,
+                        const double* L, int64_t n, int32_t disk, double r_in, double r_out,
+                        const osiris_trace_opts* opts, const osiris_outputs* out,
+                        void* cuda_stream);
+
+/* Copy n entries of every non-NULL field of dev (DEVICE) to the same field of
+ * host (HOST, preferably pinned), asynchronously on the stream. Fields that
+ * are NULL in either struct are skipped. */
+int osiris_copy_outputs_to_host(const osiris_outputs* dev, const osiris_outputs* host,
+                                int64_t n, void* cuda_stream);
+
+/* Prograde ISCO radius (Bardeen, Press & Teukolsky 1972) for the disk inner
+ * edge r_in = r_isco(a) (Sec. 5 uses r_in = r_isco). Host-only. */
+double osiris_isco(double a);
+
+/* Horizon radius r_H = 1 + sqrt(1 - a^2) (Sec. 4.3). Host-only. */
+double osiris_horizon(double a);
+
+/* Throughput probe for the roofline denominators: launches one kernel of
+ * n_threads threads, each running 8 independent fused multiply-add chains
+ * of `iters` iterations in FP64 (precision = OSIRIS_FP64) or FP32
+ * (OSIRIS_MIXED), and stores one value per thread in dev_out (DEVICE,
+ * n_threads doubles). *flops receives the floating-point operations of the
+ * launch (2 per FMA). n_threads must be a multiple of 256. */
+int osiris_fma_probe(int32_t precision, int64_t n_threads, int32_t iters, double* dev_out,
+                     double* flops, void* cuda_stream);
+
+/* Human-readable text for a return code. */
+const char* osiris_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OSIRIS_H */

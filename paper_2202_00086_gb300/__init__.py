@@ -1,0 +1,290 @@
+"""Python binding of libosiris.so, the GB300 backward ray tracer for null
+geodesics in Kerr space-time (Velasquez-Cadavid et al., "OSIRIS",
+arXiv:2202.00086).
+
+Argument marshalling only: every step of the path (initial data, Hamilton's
+equations, Cash-Karp steps, stopping surfaces, observables) runs in the CUDA
+kernels of the library. PyTorch provides device memory and streams. There is
+no CPU fallback: if the library is missing the calls raise.
+
+The names follow the C interface in include/osiris.h.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libosiris.so")
+
+OK, EINVAL, ECUDA, ENOMEM, ETIMEOUT = 0, -1, -2, -3, -4
+STATUS_NONE, STATUS_CAPTURED, STATUS_ESCAPED, STATUS_DISK, STATUS_MAXSTEP, STATUS_ERROR = range(6)
+FP64, MIXED = 0, 1
+STATS_LEN = 16
+STAT_NAMES = ["rays", "accepted", "rejected", "root_steps", "rhs_evals", "status_none",
+              "status_captured", "status_escaped", "status_disk", "status_maxstep",
+              "status_error", "max_abs_H_bits", "fp64_steps"]
+
+_P = ctypes.POINTER
+_d = ctypes.c_double
+_vp = ctypes.c_void_p
+
+
+class TraceOpts(ctypes.Structure):
+    _fields_ = [("tol", _d), ("max_steps", ctypes.c_int64), ("precision", ctypes.c_int32),
+                ("persistent", ctypes.c_int32), ("r_cap_factor", _d), ("r_esc_factor", _d),
+                ("cell_deg", _d), ("cell_phase_deg", _d), ("block_size", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("stats", _vp), ("workspace", _vp),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+OUTPUT_FIELDS = [("status", torch.uint8), ("r", torch.float64), ("theta", torch.float64),
+                 ("phi", torch.float64), ("max_abs_H", torch.float64), ("steps", torch.int32),
+                 ("cell_i", torch.int16), ("cell_j", torch.int16), ("parity", torch.uint8),
+                 ("g", torch.float64), ("intensity", torch.float64), ("r_hit", torch.float64)]
+SHADOW_FIELDS = ["status", "r", "theta", "phi", "max_abs_H", "steps", "cell_i", "cell_j",
+                 "parity"]
+DISK_FIELDS = SHADOW_FIELDS + ["g", "intensity", "r_hit"]
+
+
+class Outputs(ctypes.Structure):
+    _fields_ = [(name, _vp) for name, _ in OUTPUT_FIELDS]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("camera", _vp), ("disk", ctypes.c_int32), ("r_in", _d), ("r_out", _d),
+                ("tol", _d), ("out", Outputs)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libosiris.so. Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libosiris.so is not built (%s); run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        L.osiris_default_opts.argtypes = [_P(TraceOpts)]
+        L.osiris_init_camera.argtypes = [_P(_vp), _d, _d, _d, _d, _d, _d, _d, ctypes.c_int32,
+                                         ctypes.c_int32]
+        L.osiris_destroy_camera.argtypes = [_vp]
+        L.osiris_camera_rays.argtypes = [_vp]
+        L.osiris_camera_rays.restype = ctypes.c_int64
+        L.osiris_trace.argtypes = [_vp, _P(TraceOpts), _P(Outputs), _vp]
+        L.osiris_render_disk.argtypes = [_vp, _d, _d, _P(TraceOpts), _P(Outputs), _vp]
+        L.osiris_workspace_bytes.argtypes = [ctypes.c_int32]
+        L.osiris_workspace_bytes.restype = ctypes.c_size_t
+        L.osiris_trace_batch.argtypes = [_P(Request), ctypes.c_int32, _P(TraceOpts), _vp]
+        L.osiris_trace_states.argtypes = [_d, _d, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32,
+                                          _d, _d, _P(TraceOpts), _P(Outputs), _vp]
+        L.osiris_copy_outputs_to_host.argtypes = [_P(Outputs), _P(Outputs), ctypes.c_int64, _vp]
+        L.osiris_isco.argtypes = [_d]
+        L.osiris_isco.restype = _d
+        L.osiris_horizon.argtypes = [_d]
+        L.osiris_horizon.restype = _d
+        L.osiris_fma_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _vp,
+                                       _P(_d), _vp]
+        L.osiris_strerror.argtypes = [ctypes.c_int]
+        L.osiris_strerror.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+class OsirisError(RuntimeError):
+    def __init__(self, code, what):
+        msg = lib().osiris_strerror(code).decode()
+        super().__init__("%s failed: %s (%d)" % (what, msg, code))
+        self.code = code
+
+
+def _check(code, what):
+    if code != OK:
+        raise OsirisError(code, what)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return _vp(stream.cuda_stream)
+
+
+class Camera:
+    """Observer at (r_obs, incl_deg), image plane extent (x_min, x_max, y_min,
+    y_max) with nx x ny pixels (osiris_init_camera)."""
+
+    def __init__(self, a, r_obs, incl_deg, extent, nx, ny):
+        h = _vp()
+        x0, x1, y0, y1 = (float(v) for v in extent)
+        _check(lib().osiris_init_camera(ctypes.byref(h), float(a), float(r_obs),
+                                        float(incl_deg), x0, x1, y0, y1, int(nx), int(ny)),
+               "osiris_init_camera")
+        self._h = h
+        self.a, self.r_obs, self.incl_deg = float(a), float(r_obs), float(incl_deg)
+        self.extent, self.nx, self.ny = (x0, x1, y0, y1), int(nx), int(ny)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def n_rays(self):
+        return self.nx * self.ny
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.osiris_destroy_camera(h)
+            self._h = None
+
+    @classmethod
+    def from_render(cls, rd):
+        return cls(rd["a"], rd["r_obs"], rd["incl_deg"], rd["extent"], rd["nx"], rd["ny"])
+
+
+def workspace_bytes(n_requests=1):
+    return int(lib().osiris_workspace_bytes(int(n_requests)))
+
+
+def make_opts(tol=1e-10, max_steps=1_000_000, precision=FP64, persistent=False,
+              r_cap_factor=1.01, r_esc_factor=1.1, cell_deg=10.0, cell_phase_deg=0.0,
+              block_size=0, blocks_per_sm=0, stats=None, workspace=None):
+    o = TraceOpts()
+    lib().osiris_default_opts(ctypes.byref(o))
+    o.tol, o.max_steps = float(tol), int(max_steps)
+    o.precision = int(precision)
+    o.persistent = 1 if persistent else 0
+    o.r_cap_factor, o.r_esc_factor = float(r_cap_factor), float(r_esc_factor)
+    o.cell_deg, o.cell_phase_deg = float(cell_deg), float(cell_phase_deg)
+    o.block_size, o.blocks_per_sm = int(block_size), int(blocks_per_sm)
+    o.stats = stats.data_ptr() if stats is not None else None
+    if workspace is not None:
+        o.workspace = workspace.data_ptr()
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    return o
+
+
+def alloc_outputs(n, device="cuda", fields=SHADOW_FIELDS, pin_memory=False):
+    """Dict of output tensors (one entry per ray) for the given fields."""
+    dt = dict(OUTPUT_FIELDS)
+    if str(device) == "cpu":
+        return {f: torch.empty(n, dtype=dt[f], pin_memory=pin_memory) for f in fields}
+    return {f: torch.empty(n, dtype=dt[f], device=device) for f in fields}
+
+
+def outputs_struct(d):
+    o = Outputs()
+    for name, _ in OUTPUT_FIELDS:
+        t = d.get(name) if d else None
+        setattr(o, name, t.data_ptr() if t is not None else None)
+    return o
+
+
+def new_stats(device="cuda"):
+    return torch.zeros(STATS_LEN, dtype=torch.int64, device=device)
+
+
+def trace(camera, out=None, stream=None, **opts):
+    """Shadow / lensing render of every pixel (osiris_trace)."""
+    if out is None:
+        out = alloc_outputs(camera.n_rays)
+    o = make_opts(**opts)
+    os_ = outputs_struct(out)
+    _check(lib().osiris_trace(camera.handle, ctypes.byref(o), ctypes.byref(os_),
+                              _stream_handle(stream)), "osiris_trace")
+    return out
+
+
+def render_disk(camera, r_in, r_out, out=None, stream=None, **opts):
+    """Thin Keplerian disk render (osiris_render_disk)."""
+    if out is None:
+        out = alloc_outputs(camera.n_rays, fields=DISK_FIELDS)
+    o = make_opts(**opts)
+    os_ = outputs_struct(out)
+    _check(lib().osiris_render_disk(camera.handle, float(r_in), float(r_out), ctypes.byref(o),
+                                    ctypes.byref(os_), _stream_handle(stream)),
+           "osiris_render_disk")
+    return out
+
+
+def trace_batch(requests, stream=None, **opts):
+    """One persistent launch over many renders (osiris_trace_batch).
+
+    requests: list of dicts with keys camera, disk (bool), r_in, r_out, tol
+    (<= 0: opts tol), out (dict of device tensors). opts must include a
+    workspace tensor of at least workspace_bytes(len(requests)) bytes."""
+    n = len(requests)
+    arr = (Request * n)()
+    for k, q in enumerate(requests):
+        arr[k].camera = q["camera"].handle
+        arr[k].disk = 1 if q.get("disk") else 0
+        arr[k].r_in = float(q.get("r_in") or 0.0)
+        arr[k].r_out = float(q.get("r_out") or 0.0)
+        arr[k].tol = float(q.get("tol") or 0.0)
+        arr[k].out = outputs_struct(q["out"])
+    o = make_opts(**opts)
+    _check(lib().osiris_trace_batch(arr, n, ctypes.byref(o), _stream_handle(stream)),
+           "osiris_trace_batch")
+    return requests
+
+
+def trace_states(a, r_obs, states, E, L, out=None, disk=False, r_in=0.0, r_out=0.0,
+                 stream=None, **opts):
+    """Trace rays from explicit device initial data (osiris_trace_states)."""
+    n = int(E.numel())
+    assert states.is_cuda and states.dtype == torch.float64 and states.is_contiguous()
+    assert E.is_cuda and L.is_cuda and E.dtype == torch.float64 and L.dtype == torch.float64
+    if out is None:
+        out = alloc_outputs(n, fields=DISK_FIELDS if disk else SHADOW_FIELDS)
+    o = make_opts(**opts)
+    os_ = outputs_struct(out)
+    _check(lib().osiris_trace_states(float(a), float(r_obs), states.data_ptr(), E.data_ptr(),
+                                     L.data_ptr(), n, 1 if disk else 0, float(r_in),
+                                     float(r_out), ctypes.byref(o), ctypes.byref(os_),
+                                     _stream_handle(stream)), "osiris_trace_states")
+    return out
+
+
+def copy_outputs_to_host(dev, host, n, stream=None):
+    """Asynchronous device-to-host copy of every field present in both dicts."""
+    d = outputs_struct(dev)
+    h = outputs_struct(host)
+    _check(lib().osiris_copy_outputs_to_host(ctypes.byref(d), ctypes.byref(h), int(n),
+                                             _stream_handle(stream)),
+           "osiris_copy_outputs_to_host")
+    return host
+
+
+def isco(a):
+    return float(lib().osiris_isco(float(a)))
+
+
+def horizon(a):
+    return float(lib().osiris_horizon(float(a)))
+
+
+def fma_probe(precision, n_threads, iters, out, stream=None):
+    """Launch the FMA throughput probe; returns the launch's flop count."""
+    fl = _d()
+    _check(lib().osiris_fma_probe(int(precision), int(n_threads), int(iters), out.data_ptr(),
+                                  ctypes.byref(fl), _stream_handle(stream)), "osiris_fma_probe")
+    return fl.value
+
+
+def decode_stats(stats):
+    """Counters of a stats tensor as a dict (max |H| decoded from its bits)."""
+    v = stats.detach().cpu().tolist()
+    out = {name: int(v[k]) for k, name in enumerate(STAT_NAMES)}
+    out["max_abs_H"] = ctypes.cast(ctypes.pointer(ctypes.c_int64(v[11])),
+                                   _P(_d)).contents.value
+    return out
+
+
+def resolve_r_in(render_dict):
+    """r_in of a workload render, with the ISCO marker resolved by the library."""
+    r_in = render_dict.get("r_in")
+    if r_in == "isco":
+        return isco(render_dict["a"])
+    return r_in

@@ -1,0 +1,356 @@
+// Host side of the C interface declared in include/osiris.h: argument
+// validation, the per-camera constants of the initial data (Sec. 2.3), and
+// the launches. No allocation happens here: outputs and workspace belong to
+// the caller.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "osiris_internal.h"
+
+using osiris_impl::Kernel;
+using osiris_impl::KernelArgs;
+using osiris_impl::ReqDev;
+
+struct osiris_camera {
+  double a, r0, incl_deg, th0;
+  double x_min, x_max, y_min, y_max;
+  int32_t nx, ny;
+  // observer terms of the initial momenta
+  double inv_At, e_x, l_x, pth_y, grr;
+};
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kDefaultBlock = 128;
+
+bool is_fin(double v) { return std::isfinite(v); }
+
+double horizon(double a) { return 1.0 + std::sqrt(1.0 - a * a); }
+
+int check_opts(const osiris_trace_opts* o) {
+  if (!o) return OSIRIS_EINVAL;
+  if (!(o->tol > 0.0) || !is_fin(o->tol)) return OSIRIS_EINVAL;
+  if (o->max_steps < 1) return OSIRIS_EINVAL;
+  if (o->precision != OSIRIS_FP64 && o->precision != OSIRIS_MIXED) return OSIRIS_EINVAL;
+  if (!(o->r_cap_factor > 1.0) || !is_fin(o->r_cap_factor)) return OSIRIS_EINVAL;
+  if (!(o->r_esc_factor > 1.0) || !is_fin(o->r_esc_factor)) return OSIRIS_EINVAL;
+  if (!(o->cell_deg > 0.0 && o->cell_deg <= 180.0)) return OSIRIS_EINVAL;
+  if (!is_fin(o->cell_phase_deg)) return OSIRIS_EINVAL;
+  if (o->block_size != 0 &&
+      (o->block_size < 32 || o->block_size > 256 || o->block_size % 32 != 0))
+    return OSIRIS_EINVAL;
+  if (o->blocks_per_sm < 0) return OSIRIS_EINVAL;
+  if (o->workspace && (reinterpret_cast<uintptr_t>(o->workspace) & 255u)) return OSIRIS_EINVAL;
+  return OSIRIS_OK;
+}
+
+int check_disk(double a, double r_cap_factor, double r_esc, double r_in, double r_out) {
+  if (!is_fin(r_in) || !is_fin(r_out)) return OSIRIS_EINVAL;
+  if (!(r_in > r_cap_factor * horizon(a))) return OSIRIS_EINVAL;
+  if (!(r_in < r_out) || !(r_out < r_esc)) return OSIRIS_EINVAL;
+  return OSIRIS_OK;
+}
+
+// Fields common to pixel and explicit-state requests.
+void fill_common(ReqDev& R, double a, double r0, const osiris_trace_opts* o, double tol,
+                 int disk, double r_in, double r_out, const osiris_outputs* out) {
+  R.a = a;
+  R.r0 = r0;
+  R.r_cap = o->r_cap_factor * horizon(a);
+  R.r_esc = o->r_esc_factor * r0;
+  R.disk = disk ? 1 : 0;
+  R.r_in = disk ? r_in : 0.0;
+  R.r_out = disk ? r_out : 0.0;
+  R.tol = tol > 0.0 ? tol : o->tol;
+  R.h0 = 0.01 * r0;
+  R.max_steps = o->max_steps;
+  R.cell_rad = o->cell_deg * kPi / 180.0;
+  R.phase_rad = o->cell_phase_deg * kPi / 180.0;
+  R.n_th_cells = static_cast<int32_t>(std::ceil(180.0 / o->cell_deg - 1e-9));
+  R.n_ph_cells = static_cast<int32_t>(std::ceil(360.0 / o->cell_deg - 1e-9));
+  R.out = *out;
+}
+
+void fill_camera(ReqDev& R, const osiris_camera* c) {
+  R.th0 = c->th0;
+  R.x_min = c->x_min;
+  R.x_span = c->x_max - c->x_min;
+  R.y_min = c->y_min;
+  R.y_span = c->y_max - c->y_min;
+  R.nx = c->nx;
+  R.ny = c->ny;
+  R.inv_At = c->inv_At;
+  R.e_x = c->e_x;
+  R.l_x = c->l_x;
+  R.pth_y = c->pth_y;
+  R.grr = c->grr;
+  R.explicit_states = 0;
+  R.states = R.E = R.L = nullptr;
+  R.n_rays = static_cast<int64_t>(c->nx) * c->ny;
+}
+
+int cuda_rc(int e) { return e == 0 ? OSIRIS_OK : OSIRIS_ECUDA; }
+
+int sm_count(int* n) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return OSIRIS_ECUDA;
+  if (cudaDeviceGetAttribute(n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return OSIRIS_ECUDA;
+  return OSIRIS_OK;
+}
+
+// Launch the trace kernel for the requests in args (args.reqs / single).
+int launch(KernelArgs& args, const osiris_trace_opts* o, void* stream) {
+  if (args.total_rays == 0) return OSIRIS_OK;
+  const int block = o->block_size ? o->block_size : kDefaultBlock;
+  const bool persistent = o->persistent != 0 || args.reqs != nullptr;
+  auto launcher = (o->precision == OSIRIS_MIXED) ? osiris_impl::launch_trace_mixed
+                                                 : osiris_impl::launch_trace_fp64;
+  if (!persistent) {
+    const int64_t grid = (args.total_rays + block - 1) / block;
+    if (grid > 0x7fffffff) return OSIRIS_EINVAL;
+    args.queue = nullptr;
+    return cuda_rc(launcher(args, Kernel::kPlain, static_cast<int>(grid), block, stream));
+  }
+  if (!o->workspace || o->workspace_bytes < osiris_impl::kQueueBytes) return OSIRIS_ENOMEM;
+  int sms = 0;
+  if (int rc = sm_count(&sms)) return rc;
+  int per_sm = o->blocks_per_sm;
+  if (per_sm == 0) {
+    auto occ = (o->precision == OSIRIS_MIXED) ? osiris_impl::occupancy_mixed
+                                              : osiris_impl::occupancy_fp64;
+    if (occ(Kernel::kPersistent, block, &per_sm) != 0 || per_sm < 1) return OSIRIS_ECUDA;
+  }
+  int64_t grid = static_cast<int64_t>(sms) * per_sm;
+  const int64_t needed = (args.total_rays + block - 1) / block;
+  if (grid > needed) grid = needed;
+  args.queue = static_cast<unsigned long long*>(o->workspace);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(args.queue, 0, sizeof(unsigned long long), s) != cudaSuccess)
+    return OSIRIS_ECUDA;
+  return cuda_rc(launcher(args, Kernel::kPersistent, static_cast<int>(grid), block, stream));
+}
+
+int run_camera(const osiris_camera* cam, int disk, double r_in, double r_out,
+               const osiris_trace_opts* o, const osiris_outputs* out, void* stream) {
+  if (!cam || !out) return OSIRIS_EINVAL;
+  if (int rc = check_opts(o)) return rc;
+  const double r_esc = o->r_esc_factor * cam->r0;
+  if (disk)
+    if (int rc = check_disk(cam->a, o->r_cap_factor, r_esc, r_in, r_out)) return rc;
+  KernelArgs args;
+  std::memset(&args, 0, sizeof(args));
+  ReqDev& R = args.single;
+  fill_common(R, cam->a, cam->r0, o, o->tol, disk, r_in, r_out, out);
+  fill_camera(R, cam);
+  R.ray_begin = 0;
+  args.reqs = nullptr;
+  args.n_req = 1;
+  args.total_rays = R.n_rays;
+  args.stats = reinterpret_cast<unsigned long long*>(o->stats);
+  return launch(args, o, stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+void osiris_default_opts(osiris_trace_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-10;
+  o->max_steps = 1000000;
+  o->precision = OSIRIS_FP64;
+  o->persistent = 0;
+  o->r_cap_factor = 1.01;
+  o->r_esc_factor = 1.1;
+  o->cell_deg = 10.0;
+  o->cell_phase_deg = 0.0;
+}
+
+int osiris_init_camera(osiris_camera** out, double a, double r_obs, double incl_deg,
+                       double x_min, double x_max, double y_min, double y_max, int32_t nx,
+                       int32_t ny) {
+  if (!out) return OSIRIS_EINVAL;
+  *out = nullptr;
+  if (!(a >= 0.0 && a < 1.0)) return OSIRIS_EINVAL;
+  if (!is_fin(r_obs) || !(r_obs > 10.0 * horizon(a))) return OSIRIS_EINVAL;
+  if (!(incl_deg > 0.0 && incl_deg < 180.0)) return OSIRIS_EINVAL;
+  if (!is_fin(x_min) || !is_fin(x_max) || !is_fin(y_min) || !is_fin(y_max)) return OSIRIS_EINVAL;
+  if (!(x_min < x_max) || !(y_min < y_max)) return OSIRIS_EINVAL;
+  if (nx < 1 || ny < 1) return OSIRIS_EINVAL;
+  const double xm = std::fmax(std::fabs(x_min), std::fabs(x_max));
+  const double ym = std::fmax(std::fabs(y_min), std::fabs(y_max));
+  if (!(xm * xm + ym * ym < r_obs * r_obs)) return OSIRIS_EINVAL;
+
+  osiris_camera* c = new (std::nothrow) osiris_camera;
+  if (!c) return OSIRIS_ENOMEM;
+  c->a = a;
+  c->r0 = r_obs;
+  c->incl_deg = incl_deg;
+  c->th0 = incl_deg * kPi / 180.0;
+  c->x_min = x_min;
+  c->x_max = x_max;
+  c->y_min = y_min;
+  c->y_max = y_max;
+  c->nx = nx;
+  c->ny = ny;
+  // Metric at the observer (Eq. Kerr), with the identity
+  // g_tphi^2 - g_tt g_phph = Delta sin^2(theta) for A_t of Eq. matrix.
+  const double r = r_obs, s = std::sin(c->th0), co = std::cos(c->th0);
+  const double s2 = s * s;
+  const double Sigma = r * r + a * a * co * co;
+  const double Delta = r * r - 2.0 * r + a * a;
+  const double rho2 = r * r + a * a;
+  const double g_tph = -2.0 * a * r * s2 / Sigma;
+  const double g_phph = s2 * (rho2 * rho2 - a * a * Delta * s2) / Sigma;
+  const double sq_phph = std::sqrt(g_phph);
+  c->inv_At = std::sqrt(Delta * s2 / g_phph);
+  c->e_x = g_tph / (r * sq_phph);
+  c->l_x = -sq_phph / r;
+  c->pth_y = std::sqrt(Sigma) / r;
+  c->grr = Sigma / Delta;
+  *out = c;
+  return OSIRIS_OK;
+}
+
+void osiris_destroy_camera(osiris_camera* cam) { delete cam; }
+
+int64_t osiris_camera_rays(const osiris_camera* cam) {
+  return cam ? static_cast<int64_t>(cam->nx) * cam->ny : 0;
+}
+
+int osiris_trace(const osiris_camera* cam, const osiris_trace_opts* opts,
+                 const osiris_outputs* out, void* cuda_stream) {
+  return run_camera(cam, 0, 0.0, 0.0, opts, out, cuda_stream);
+}
+
+int osiris_render_disk(const osiris_camera* cam, double r_in, double r_out,
+                       const osiris_trace_opts* opts, const osiris_outputs* out,
+                       void* cuda_stream) {
+  return run_camera(cam, 1, r_in, r_out, opts, out, cuda_stream);
+}
+
+size_t osiris_workspace_bytes(int32_t n_requests) {
+  if (n_requests < 1) n_requests = 1;
+  return osiris_impl::kQueueBytes + sizeof(ReqDev) * static_cast<size_t>(n_requests);
+}
+
+int osiris_trace_batch(const osiris_request* reqs, int32_t n, const osiris_trace_opts* o,
+                       void* cuda_stream) {
+  if (!reqs || n < 1 || n > 65536) return OSIRIS_EINVAL;
+  if (int rc = check_opts(o)) return rc;
+  if (!o->workspace || o->workspace_bytes < osiris_workspace_bytes(n)) return OSIRIS_ENOMEM;
+  std::vector<ReqDev> table(static_cast<size_t>(n));
+  int64_t begin = 0;
+  for (int32_t k = 0; k < n; ++k) {
+    const osiris_request& q = reqs[k];
+    if (!q.camera) return OSIRIS_EINVAL;
+    if (q.tol < 0.0 || !is_fin(q.tol)) return OSIRIS_EINVAL;
+    const double r_esc = o->r_esc_factor * q.camera->r0;
+    if (q.disk)
+      if (int rc = check_disk(q.camera->a, o->r_cap_factor, r_esc, q.r_in, q.r_out)) return rc;
+    ReqDev& R = table[k];
+    std::memset(&R, 0, sizeof(R));
+    fill_common(R, q.camera->a, q.camera->r0, o, q.tol, q.disk, q.r_in, q.r_out, &q.out);
+    fill_camera(R, q.camera);
+    R.ray_begin = begin;
+    begin += R.n_rays;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  char* ws = static_cast<char*>(o->workspace);
+  ReqDev* dev_table = reinterpret_cast<ReqDev*>(ws + osiris_impl::kQueueBytes);
+  if (cudaMemcpyAsync(dev_table, table.data(), sizeof(ReqDev) * table.size(),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return OSIRIS_ECUDA;
+  KernelArgs args;
+  std::memset(&args, 0, sizeof(args));
+  args.reqs = dev_table;
+  args.n_req = n;
+  args.total_rays = begin;
+  args.stats = reinterpret_cast<unsigned long long*>(o->stats);
+  return launch(args, o, cuda_stream);
+}
+
+int osiris_trace_states(double a, double r_obs, const double* states, const double* E,
+                        const double* L, int64_t n, int32_t disk, double r_in, double r_out,
+                        const osiris_trace_opts* o, const osiris_outputs* out,
+                        void* cuda_stream) {
+  if (!out || n < 0) return OSIRIS_EINVAL;
+  if (n > 0 && (!states || !E || !L)) return OSIRIS_EINVAL;
+  if (!(a >= 0.0 && a < 1.0) || !is_fin(r_obs) || !(r_obs > 0.0)) return OSIRIS_EINVAL;
+  if (int rc = check_opts(o)) return rc;
+  if (disk)
+    if (int rc = check_disk(a, o->r_cap_factor, o->r_esc_factor * r_obs, r_in, r_out)) return rc;
+  KernelArgs args;
+  std::memset(&args, 0, sizeof(args));
+  ReqDev& R = args.single;
+  fill_common(R, a, r_obs, o, o->tol, disk, r_in, r_out, out);
+  R.explicit_states = 1;
+  R.states = states;
+  R.E = E;
+  R.L = L;
+  R.nx = 1;
+  R.ny = 1;
+  R.n_rays = n;
+  R.ray_begin = 0;
+  args.n_req = 1;
+  args.total_rays = n;
+  args.stats = reinterpret_cast<unsigned long long*>(o->stats);
+  return launch(args, o, cuda_stream);
+}
+
+int osiris_copy_outputs_to_host(const osiris_outputs* dev, const osiris_outputs* host, int64_t n,
+                                void* cuda_stream) {
+  if (!dev || !host || n < 0) return OSIRIS_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  auto cp = [&](void* h, const void* d, size_t elem) -> bool {
+    if (!h || !d || n == 0) return true;
+    return cudaMemcpyAsync(h, d, elem * static_cast<size_t>(n), cudaMemcpyDeviceToHost, s) ==
+           cudaSuccess;
+  };
+  bool ok = cp(host->status, dev->status, 1) && cp(host->r, dev->r, 8) &&
+            cp(host->theta, dev->theta, 8) && cp(host->phi, dev->phi, 8) &&
+            cp(host->max_abs_H, dev->max_abs_H, 8) && cp(host->steps, dev->steps, 4) &&
+            cp(host->cell_i, dev->cell_i, 2) && cp(host->cell_j, dev->cell_j, 2) &&
+            cp(host->parity, dev->parity, 1) && cp(host->g, dev->g, 8) &&
+            cp(host->intensity, dev->intensity, 8) && cp(host->r_hit, dev->r_hit, 8);
+  return ok ? OSIRIS_OK : OSIRIS_ECUDA;
+}
+
+double osiris_isco(double a) {
+  // Bardeen, Press & Teukolsky (1972), prograde orbit, M = 1.
+  const double z1 =
+      1.0 + std::cbrt(1.0 - a * a) * (std::cbrt(1.0 + a) + std::cbrt(1.0 - a));
+  const double z2 = std::sqrt(3.0 * a * a + z1 * z1);
+  return 3.0 + z2 - std::sqrt((3.0 - z1) * (3.0 + z1 + 2.0 * z2));
+}
+
+double osiris_horizon(double a) { return horizon(a); }
+
+int osiris_fma_probe(int32_t precision, int64_t n_threads, int32_t iters, double* dev_out,
+                     double* flops, void* cuda_stream) {
+  if (!dev_out || n_threads < 256 || n_threads % 256 != 0 || iters < 1) return OSIRIS_EINVAL;
+  if (n_threads / 256 > 0x7fffffff) return OSIRIS_EINVAL;
+  if (precision != OSIRIS_FP64 && precision != OSIRIS_MIXED) return OSIRIS_EINVAL;
+  if (flops) *flops = 2.0 * 8.0 * static_cast<double>(iters) * static_cast<double>(n_threads);
+  return cuda_rc(osiris_impl::launch_fma_probe(precision, n_threads, iters, dev_out, cuda_stream));
+}
+
+const char* osiris_strerror(int code) {
+  switch (code) {
+    case OSIRIS_OK: return "ok";
+    case OSIRIS_EINVAL: return "invalid argument";
+    case OSIRIS_ECUDA: return "CUDA runtime error";
+    case OSIRIS_ENOMEM: return "workspace too small or missing";
+    case OSIRIS_ETIMEOUT: return "timed out";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

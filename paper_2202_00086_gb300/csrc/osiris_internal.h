@@ -1,0 +1,66 @@
+// Internal layout shared by the host API (osiris_api.cu) and the trace
+// kernels (trace_*.cu). Not part of the public interface.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "osiris.h"
+
+namespace osiris_impl {
+
+// One render (or one explicit-state batch) as the kernels see it. Lives in
+// kernel parameter space for single renders and in the workspace for
+// batches. Every quantity the kernels need per ray is precomputed on the host.
+struct alignas(16) ReqDev {
+  // space-time (M = 1)
+  double a;
+  // observer and image plane (Sec. 2.3)
+  double r0, th0;
+  double x_min, x_span, y_min, y_span;  // centre of pixel i: x_min + (i + 1/2) x_span / nx
+  int32_t nx, ny;
+  // observer terms of the initial momenta:
+  //   E = inv_At + x e_x,  L = x l_x,  p_theta = y pth_y,
+  //   p_r = -sqrt(grr (1 - (x^2 + y^2) / r0^2))
+  double inv_At, e_x, l_x, pth_y, grr;
+  // stopping surfaces (Sec. 4.1, Sec. 5)
+  double r_cap, r_esc, r_in, r_out;
+  int32_t disk;
+  int32_t explicit_states;  // 1: rays start from states / E / L (test hook)
+  const double* states;     // n x 6 rows (t, r, theta, phi, p_r, p_theta)
+  const double* E;
+  const double* L;
+  // integrator
+  double tol, h0;
+  int64_t max_steps;
+  // celestial checkerboard
+  double cell_rad, phase_rad;
+  int32_t n_th_cells, n_ph_cells;
+  // position in the launch's global ray queue
+  int64_t ray_begin, n_rays;
+  osiris_outputs out;
+};
+
+// Kernel arguments (passed as a __grid_constant__ parameter).
+struct KernelArgs {
+  const ReqDev* reqs;              // device table (batch); nullptr -> use `single`
+  int32_t n_req;
+  int64_t total_rays;
+  unsigned long long* queue;       // persistent grids: next ray index (device)
+  unsigned long long* stats;       // optional OSIRIS_STATS_LEN counters (device)
+  ReqDev single;
+};
+
+constexpr size_t kQueueBytes = 256;  // workspace head: the ray counter
+
+enum class Kernel { kPlain, kPersistent };
+
+// Launchers implemented in the kernel translation units. They return a
+// cudaError_t value as int (0 = success).
+int launch_trace_fp64(const KernelArgs& args, Kernel kind, int grid, int block, void* stream);
+int launch_trace_mixed(const KernelArgs& args, Kernel kind, int grid, int block, void* stream);
+int occupancy_fp64(Kernel kind, int block, int* blocks_per_sm);
+int occupancy_mixed(Kernel kind, int block, int* blocks_per_sm);
+int launch_fma_probe(int precision, int64_t n_threads, int iters, double* out, void* stream);
+
+}  // namespace osiris_impl

@@ -1,0 +1,260 @@
+// Device side of the backward ray tracer: Hamilton's equations for null
+// geodesics in Kerr space-time (Sec. 2.1, Sec. 4.3), adaptive Cash-Karp 4(5)
+// steps (Sec. 3.1), the |H| constraint error, stopping surfaces (Sec. 4.1,
+// Sec. 5) and the per-ray observables.
+//
+// Execution model (one ray per lane):
+//   Every lane of a warp runs the same loop body each iteration: ONE
+//   Cash-Karp attempt from its current state with its own step length.
+//   What the lane does with the result depends on its mode:
+//     INTEGRATE  accept/reject under the error controller; an accepted step
+//                that crosses a stopping surface switches the lane to LOCATE
+//     LOCATE     the attempt is a trial step length inside the bracket of the
+//                crossing (Illinois-modified regula falsi); on convergence the
+//                ray finishes (or, for an equatorial crossing outside the
+//                disk, resumes integrating)
+//     IDLE       no ray (finished; persistent grids refill it from the queue)
+//   So surface location and refills never serialise a warp behind one lane:
+//   the expensive part (six evaluations of the equations of motion) is the
+//   same instruction stream for every lane.
+#pragma once
+
+#include <cstdint>
+
+#include "osiris_internal.h"
+
+namespace osiris_impl {
+
+// ---------------------------------------------------------------------------
+// Cash-Karp 4(5) tableau (Cash & Karp 1990, the RKCK45 scheme of Sec. 3.1).
+// ---------------------------------------------------------------------------
+namespace ck {
+constexpr double A21 = 1.0 / 5.0;
+constexpr double A31 = 3.0 / 40.0, A32 = 9.0 / 40.0;
+constexpr double A41 = 3.0 / 10.0, A42 = -9.0 / 10.0, A43 = 6.0 / 5.0;
+constexpr double A51 = -11.0 / 54.0, A52 = 5.0 / 2.0, A53 = -70.0 / 27.0, A54 = 35.0 / 27.0;
+constexpr double A61 = 1631.0 / 55296.0, A62 = 175.0 / 512.0, A63 = 575.0 / 13824.0,
+                 A64 = 44275.0 / 110592.0, A65 = 253.0 / 4096.0;
+// fifth-order weights (propagated solution); stages 2 and 5 have weight 0
+constexpr double B1 = 37.0 / 378.0, B3 = 250.0 / 621.0, B4 = 125.0 / 594.0,
+                 B6 = 512.0 / 1771.0;
+// fifth minus embedded fourth order (error estimate weights), exact rationals
+constexpr double D1 = -277.0 / 64512.0, D3 = 6925.0 / 370944.0, D4 = -6925.0 / 202752.0,
+                 D5 = -277.0 / 14336.0, D6 = 277.0 / 7084.0;
+}  // namespace ck
+
+// pi/2 split in two doubles: (PIO2_HI - theta) + PIO2_LO has the sign of
+// cos(theta) for theta in (-pi/2, 3pi/2), and equals it to first order near
+// the equator.
+constexpr double PIO2_HI = 1.5707963267948966;
+constexpr double PIO2_LO = 6.123233995736766e-17;
+constexpr double TWO_PI = 6.283185307179586;
+constexpr double PI_D = 3.141592653589793;
+
+enum : int { MODE_IDLE = 0, MODE_INTEGRATE = 1, MODE_LOCATE = 2 };
+enum : int { SURF_EQUATOR = 0, SURF_CAPTURE = 1, SURF_ESCAPE = 2 };
+
+struct State {  // evolved coordinates and momenta (t does not feed back; not integrated)
+  double r, th, ph, pr, pth;
+};
+
+// Per-ray constants of the Hamiltonian.
+struct RayK {
+  double a, a2, aE, aL, E, L;
+};
+
+// ---------------------------------------------------------------------------
+// Hamilton's equations in separated form.
+//
+// With p_t = -E, p_phi = L, the Kerr Hamiltonian H = 1/2 g^{mu nu} p_mu p_nu
+// (Eq. ligH) on the inverse of the metric of Eq. Kerr can be written
+//   H = N / (2 Sigma),
+//   N = Delta p_r^2 + p_theta^2 + W^2 - P^2 / Delta,
+//   P = (r^2 + a^2) E - a L,   W = L / sin(theta) - a E sin(theta).
+// Its exact derivatives (no use of H = 0, so the flow is the paper's flow
+// everywhere, also off the constraint surface) give, with u = P / Delta,
+//   r'       =  Delta p_r / Sigma
+//   theta'   =  p_theta / Sigma
+//   phi'     =  (W / sin + a u) / Sigma
+//   p_r'     =  [ r N / Sigma - (r - 1)(p_r^2 + u^2) + 2 r E u ] / Sigma
+//   p_theta' =  cos [ W (L / sin^2 + a E) - a^2 sin N / Sigma ] / Sigma
+// which are the component equations of Sec. 2.1 after the common factors
+// are collected. One reciprocal of Delta Sigma sin(theta) yields all three
+// reciprocals. twoH receives 2H = N / Sigma at the evaluation point.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void rhs64(const RayK& K, double r, double th, double pr, double pth,
+                                      double& dr, double& dth, double& dph, double& dpr,
+                                      double& dpth, double& twoH) {
+  double s, c;
+  sincos(th, &s, &c);
+  const double r2 = r * r;
+  const double Delta = fma(r, r - 2.0, K.a2);
+  const double Sigma = fma(K.a2 * c, c, r2);
+  const double P = fma(r2 + K.a2, K.E, -K.aL);
+  const double DS = Delta * Sigma;
+  const double inv = __drcp_rn(DS * s);
+  const double iSig = (Delta * s) * inv;
+  const double iDel = (Sigma * s) * inv;
+  const double is = DS * inv;
+  const double W = fma(K.L, is, -K.aE * s);
+  const double u = P * iDel;
+  const double Dpr = Delta * pr;
+  const double N = fma(Dpr, pr, fma(pth, pth, fma(W, W, -P * u)));
+  const double NiS = N * iSig;
+  dr = Dpr * iSig;
+  dth = pth * iSig;
+  dph = fma(W, is, K.a * u) * iSig;
+  dpr = iSig * (fma(r, NiS, 2.0 * r * K.E * u) - (r - 1.0) * fma(u, u, pr * pr));
+  dpth = (c * iSig) * fma(W, fma(K.L, is * is, K.aE), -(K.a2 * s) * NiS);
+  twoH = NiS;
+}
+
+// 2H at a state (used once per ray for the terminal point).
+__device__ __forceinline__ double twoH64(const RayK& K, const State& y) {
+  double a0, a1, a2, a3, a4, h2;
+  rhs64(K, y.r, y.th, y.pr, y.pth, a0, a1, a2, a3, a4, h2);
+  return h2;
+}
+
+// One Cash-Karp attempt of length h from y (FP64 everywhere): o = fifth-order
+// result, d = fifth minus fourth order. phi is cyclic, so its stage values
+// are never needed; only its increment is accumulated.
+__device__ __forceinline__ void ck_step64(const RayK& K, const State& y, double h, State& o,
+                                          State& d, double& twoH) {
+  using namespace ck;
+  double k1r, k1t, k1p, k1pr, k1pt;
+  rhs64(K, y.r, y.th, y.pr, y.pth, k1r, k1t, k1p, k1pr, k1pt, twoH);
+  double k2r, k2t, k2p, k2pr, k2pt, hd;
+  rhs64(K, fma(h, A21 * k1r, y.r), fma(h, A21 * k1t, y.th), fma(h, A21 * k1pr, y.pr),
+        fma(h, A21 * k1pt, y.pth), k2r, k2t, k2p, k2pr, k2pt, hd);
+#define OSIRIS_S3(c) fma(h, fma(A32, k2##c, A31 * k1##c), y_##c)
+  double k3r, k3t, k3p, k3pr, k3pt;
+  {
+    const double y_r = y.r, y_t = y.th, y_pr = y.pr, y_pt = y.pth;
+    rhs64(K, OSIRIS_S3(r), OSIRIS_S3(t), OSIRIS_S3(pr), OSIRIS_S3(pt), k3r, k3t, k3p, k3pr, k3pt,
+          hd);
+  }
+#undef OSIRIS_S3
+#define OSIRIS_S4(c) fma(h, fma(A43, k3##c, fma(A42, k2##c, A41 * k1##c)), y_##c)
+  double k4r, k4t, k4p, k4pr, k4pt;
+  {
+    const double y_r = y.r, y_t = y.th, y_pr = y.pr, y_pt = y.pth;
+    rhs64(K, OSIRIS_S4(r), OSIRIS_S4(t), OSIRIS_S4(pr), OSIRIS_S4(pt), k4r, k4t, k4p, k4pr, k4pt,
+          hd);
+  }
+#undef OSIRIS_S4
+#define OSIRIS_S5(c) \
+  fma(h, fma(A54, k4##c, fma(A53, k3##c, fma(A52, k2##c, A51 * k1##c))), y_##c)
+  double k5r, k5t, k5p, k5pr, k5pt;
+  {
+    const double y_r = y.r, y_t = y.th, y_pr = y.pr, y_pt = y.pth;
+    rhs64(K, OSIRIS_S5(r), OSIRIS_S5(t), OSIRIS_S5(pr), OSIRIS_S5(pt), k5r, k5t, k5p, k5pr, k5pt,
+          hd);
+  }
+#undef OSIRIS_S5
+#define OSIRIS_S6(c) \
+  fma(h, fma(A65, k5##c, fma(A64, k4##c, fma(A63, k3##c, fma(A62, k2##c, A61 * k1##c)))), y_##c)
+  double k6r, k6t, k6p, k6pr, k6pt;
+  {
+    const double y_r = y.r, y_t = y.th, y_pr = y.pr, y_pt = y.pth;
+    rhs64(K, OSIRIS_S6(r), OSIRIS_S6(t), OSIRIS_S6(pr), OSIRIS_S6(pt), k6r, k6t, k6p, k6pr, k6pt,
+          hd);
+  }
+#undef OSIRIS_S6
+#define OSIRIS_Y5(c) fma(B6, k6##c, fma(B4, k4##c, fma(B3, k3##c, B1 * k1##c)))
+#define OSIRIS_DL(c) fma(D6, k6##c, fma(D5, k5##c, fma(D4, k4##c, fma(D3, k3##c, D1 * k1##c))))
+  o.r = fma(h, OSIRIS_Y5(r), y.r);
+  o.th = fma(h, OSIRIS_Y5(t), y.th);
+  o.ph = fma(h, OSIRIS_Y5(p), y.ph);
+  o.pr = fma(h, OSIRIS_Y5(pr), y.pr);
+  o.pth = fma(h, OSIRIS_Y5(pt), y.pth);
+  d.r = h * OSIRIS_DL(r);
+  d.th = h * OSIRIS_DL(t);
+  d.ph = h * OSIRIS_DL(p);
+  d.pr = h * OSIRIS_DL(pr);
+  d.pth = h * OSIRIS_DL(pt);
+#undef OSIRIS_Y5
+#undef OSIRIS_DL
+}
+
+// True when x is +-inf or NaN (exponent bits all set); integer test only.
+__device__ __forceinline__ bool not_finite(double x) {
+  return ((__double2hiint(x) >> 20) & 0x7ff) == 0x7ff;
+}
+
+__device__ __forceinline__ bool state_not_finite(const State& s) {
+  return not_finite(s.r) | not_finite(s.th) | not_finite(s.ph) | not_finite(s.pr) |
+         not_finite(s.pth);
+}
+
+// Error test of one component: accept needs |d| <= tol (1 + max(|y|, |o|));
+// the ratio (for the step-size controller only) is formed in FP32.
+__device__ __forceinline__ void err_component(double y, double o, double d, double tol,
+                                              bool& ok, float& err) {
+  const double scale = tol * (1.0 + fmax(fabs(y), fabs(o)));
+  const double ad = fabs(d);
+  ok = ok && (ad <= scale);
+  err = fmaxf(err, __fdividef((float)ad, (float)scale));
+}
+
+// Value whose sign tells which side of a stopping surface a state is on;
+// the crossing is where it changes sign.
+__device__ __forceinline__ double surface_value(int kind, const State& s, double r_cap,
+                                                double r_esc) {
+  if (kind == SURF_EQUATOR) return (PIO2_HI - s.th) + PIO2_LO;  // sign of cos(theta)
+  if (kind == SURF_CAPTURE) return s.r - r_cap;
+  return s.r - r_esc;
+}
+
+__device__ __forceinline__ bool crosses_equator(const State& y0, const State& y1) {
+  const double c0 = (PIO2_HI - y0.th) + PIO2_LO;
+  const double c1 = (PIO2_HI - y1.th) + PIO2_LO;
+  return (c0 > 0.0 && c1 <= 0.0) || (c0 < 0.0 && c1 >= 0.0);
+}
+
+__device__ __forceinline__ const ReqDev* request_of(const KernelArgs& A, int k) {
+  return A.reqs ? (A.reqs + k) : &A.single;
+}
+
+// Request owning global ray g (largest k with ray_begin <= g).
+__device__ __forceinline__ int find_request(const KernelArgs& A, int64_t g) {
+  if (A.reqs == nullptr) return 0;
+  int lo = 0, hi = A.n_req - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&A.reqs[mid].ray_begin) <= g)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// Per-lane totals folded into the stats counters when the lane retires.
+struct LaneStats {
+  unsigned long long rays = 0, acc = 0, rej = 0, root = 0, rhs = 0, fp64_steps = 0;
+  unsigned long long status[6] = {0, 0, 0, 0, 0, 0};
+  double max_abs_H = 0.0;
+};
+
+__device__ __forceinline__ void flush_stats(const KernelArgs& A, LaneStats& S) {
+  if (A.stats == nullptr) return;
+  const unsigned FULL = 0xffffffffu;
+  unsigned long long v[12] = {S.rays, S.acc, S.rej, S.root, S.rhs, S.status[0], S.status[1],
+                              S.status[2], S.status[3], S.status[4], S.status[5], S.fp64_steps};
+  double mh = S.max_abs_H;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int q = 0; q < 12; ++q) v[q] += __shfl_xor_sync(FULL, v[q], off);
+    mh = fmax(mh, __shfl_xor_sync(FULL, mh, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    for (int q = 0; q < 11; ++q)
+      if (v[q]) atomicAdd(A.stats + q, v[q]);
+    if (v[11]) atomicAdd(A.stats + OSIRIS_STAT_FP64_STEPS, v[11]);
+    atomicMax(A.stats + OSIRIS_STAT_MAX_ABS_H, (unsigned long long)__double_as_longlong(mh));
+  }
+}
+
+}  // namespace osiris_impl

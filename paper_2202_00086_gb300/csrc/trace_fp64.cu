@@ -1,0 +1,66 @@
+// FP64 trace kernels: every operation of the integrator in double precision.
+#include <cuda_runtime.h>
+
+#include "trace_kernel.cuh"
+
+namespace osiris_impl {
+
+struct StepperFP64 {
+  static __device__ __forceinline__ bool attempt(const RayK& K, const State& y, double h,
+                                                 State& o, State& d, double& twoH) {
+    ck_step64(K, y, h, o, d, twoH);
+    return true;
+  }
+  static __device__ __forceinline__ double twoH(const RayK& K, const State& y) {
+    return twoH64(K, y);
+  }
+};
+
+constexpr int kMaxBlock = 256;
+
+__global__ void __launch_bounds__(kMaxBlock) trace_fp64_plain(const __grid_constant__ KernelArgs A) {
+  trace_body<StepperFP64, false>(A);
+}
+
+__global__ void __launch_bounds__(kMaxBlock) trace_fp64_persistent(const __grid_constant__ KernelArgs A) {
+  trace_body<StepperFP64, true>(A);
+}
+
+int launch_trace_fp64(const KernelArgs& args, Kernel kind, int grid, int block, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (kind == Kernel::kPersistent)
+    trace_fp64_persistent<<<grid, block, 0, s>>>(args);
+  else
+    trace_fp64_plain<<<grid, block, 0, s>>>(args);
+  return (int)cudaGetLastError();
+}
+
+int occupancy_fp64(Kernel kind, int block, int* blocks_per_sm) {
+  const void* fn = (kind == Kernel::kPersistent) ? (const void*)trace_fp64_persistent
+                                                 : (const void*)trace_fp64_plain;
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, 0);
+}
+
+// Roofline probe: 8 independent FMA chains per thread.
+template <typename T>
+__global__ void __launch_bounds__(256) fma_probe_kernel(double* out, T b, T c, int iters) {
+  T a0 = (T)threadIdx.x * (T)1e-3, a1 = a0 + (T)1, a2 = a0 + (T)2, a3 = a0 + (T)3;
+  T a4 = a0 + (T)4, a5 = a0 + (T)5, a6 = a0 + (T)6, a7 = a0 + (T)7;
+  for (int i = 0; i < iters; ++i) {
+    a0 = fma(a0, b, c); a1 = fma(a1, b, c); a2 = fma(a2, b, c); a3 = fma(a3, b, c);
+    a4 = fma(a4, b, c); a5 = fma(a5, b, c); a6 = fma(a6, b, c); a7 = fma(a7, b, c);
+  }
+  out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = (double)(a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7);
+}
+
+int launch_fma_probe(int precision, int64_t n_threads, int iters, double* out, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int grid = (int)(n_threads / 256);
+  if (precision == OSIRIS_FP64)
+    fma_probe_kernel<double><<<grid, 256, 0, s>>>(out, 0.999999, 1e-7, iters);
+  else
+    fma_probe_kernel<float><<<grid, 256, 0, s>>>(out, 0.999999f, 1e-7f, iters);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace osiris_impl

@@ -1,0 +1,280 @@
+// The trace kernel: one ray per lane, uniform Cash-Karp attempts, stopping
+// surfaces located inside the step, per-ray epilogue, and (persistent grids)
+// lane refill from a device ray queue. Instantiated per precision by
+// trace_fp64.cu and trace_mixed.cu through the Stepper policy:
+//   Stepper::attempt(K, y, h, o, d, twoH) -> one Cash-Karp attempt
+//   Stepper::twoH(K, y)                   -> 2H at a state (FP64)
+#pragma once
+
+#include "trace_device.cuh"
+
+namespace osiris_impl {
+
+template <class Stepper, bool PERSISTENT>
+__device__ __forceinline__ void trace_body(const KernelArgs& A) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+
+  int mode = MODE_IDLE;
+  bool drained = !PERSISTENT;
+  LaneStats S;
+
+  // ray identity and constants
+  int req = 0;
+  int64_t local = 0;
+  RayK K;
+  double r_cap = 0, r_esc = 0, r_in = 0, r_out = 0, tol = 0;
+  int disk = 0;
+  int64_t max_steps = 0;
+  // integration state
+  State y;
+  double h = 0, max_abs_H = 0;
+  unsigned n_acc = 0, n_rej = 0;
+  // surface location (LOCATE)
+  int kind = 0, side = 0, iters = 0;
+  double lo = 0, hi = 0, flo = 0, fhi = 0, h_try = 0, h_step = 0;
+  State yF, yE;  // state at the upper bracket end; end of the accepted step
+
+  auto start_ray = [&](int64_t g) {
+    req = find_request(A, g);
+    const ReqDev* R = request_of(A, req);
+    local = g - R->ray_begin;
+    const double a = R->a;
+    K.a = a;
+    K.a2 = a * a;
+    if (R->explicit_states) {
+      const double* st = R->states + 6 * local;
+      y.r = st[1];
+      y.th = st[2];
+      y.ph = st[3];
+      y.pr = st[4];
+      y.pth = st[5];
+      K.E = R->E[local];
+      K.L = R->L[local];
+    } else {
+      // pixel centre, then the initial momenta of Sec. 2.3 (Eq. momentums)
+      const int64_t i = local % R->nx, j = local / R->nx;
+      const double x = R->x_min + ((double)i + 0.5) * R->x_span / R->nx;
+      const double yy = R->y_min + ((double)j + 0.5) * R->y_span / R->ny;
+      const double Pth = yy / R->r0, Pph = -x / R->r0;
+      K.E = R->inv_At + x * R->e_x;
+      K.L = x * R->l_x;
+      y.r = R->r0;
+      y.th = R->th0;
+      y.ph = 0.0;
+      y.pth = yy * R->pth_y;
+      y.pr = -sqrt(R->grr * (1.0 - Pth * Pth - Pph * Pph));
+    }
+    K.aE = a * K.E;
+    K.aL = a * K.L;
+    r_cap = R->r_cap;
+    r_esc = R->r_esc;
+    r_in = R->r_in;
+    r_out = R->r_out;
+    disk = R->disk;
+    tol = R->tol;
+    max_steps = R->max_steps;
+    h = R->h0;
+    max_abs_H = 0.0;
+    n_acc = n_rej = 0;
+    mode = MODE_INTEGRATE;
+  };
+
+  // Write the ray's outputs and retire the lane.
+  auto finish = [&](int status, const State& f) {
+    const ReqDev* R = request_of(A, req);
+    if (status != OSIRIS_STATUS_ERROR) {
+      max_abs_H = fmax(max_abs_H, fabs(0.5 * Stepper::twoH(K, f)));
+      S.rhs += 1;
+    }
+    const osiris_outputs& O = R->out;
+    if (O.status) O.status[local] = (uint8_t)status;
+    if (O.r) O.r[local] = f.r;
+    if (O.theta) O.theta[local] = f.th;
+    if (O.phi) O.phi[local] = f.ph;
+    if (O.max_abs_H) O.max_abs_H[local] = max_abs_H;
+    if (O.steps) O.steps[local] = n_acc;
+    int ci = -1, cj = -1, par = 0;
+    if (status == OSIRIS_STATUS_ESCAPED) {
+      // celestial checkerboard: fold theta into [0, pi], wrap phi into [0, 2pi)
+      double t = fmod(f.th, TWO_PI);
+      if (t < 0.0) t += TWO_PI;
+      double p = f.ph;
+      if (t > PI_D) {
+        t = TWO_PI - t;
+        p += PI_D;
+      }
+      double q = fmod(p + R->phase_rad, TWO_PI);
+      if (q < 0.0) q += TWO_PI;
+      ci = (int)floor(t / R->cell_rad);
+      cj = (int)floor(q / R->cell_rad);
+      ci = min(max(ci, 0), R->n_th_cells - 1);
+      cj = ((cj % R->n_ph_cells) + R->n_ph_cells) % R->n_ph_cells;
+      par = (ci + cj) & 1;
+    }
+    if (O.cell_i) O.cell_i[local] = (int16_t)ci;
+    if (O.cell_j) O.cell_j[local] = (int16_t)cj;
+    if (O.parity) O.parity[local] = (uint8_t)par;
+    double g = 0.0, I = 0.0, rh = 0.0;
+    if (status == OSIRIS_STATUS_DISK) {
+      // Keplerian disk (Sec. 5): Omega = 1/(r^3/2 + a); u^t from the
+      // normalisation g_ab u^a u^b = -1 in the equatorial plane;
+      // g = 1/(u^t (E - Omega L)); I = g^3 / r^2.
+      const double r = f.r, a = K.a;
+      const double Om = 1.0 / fma(r, sqrt(r), a);
+      const double gtt = -(1.0 - 2.0 / r);
+      const double gtp = -2.0 * a / r;
+      const double gpp = r * r + a * a + 2.0 * a * a / r;
+      const double inv_ut = sqrt(-gtt - 2.0 * Om * gtp - Om * Om * gpp);
+      g = inv_ut / (K.E - Om * K.L);
+      I = g * g * g / (r * r);
+      rh = r;
+    }
+    if (O.g) O.g[local] = g;
+    if (O.intensity) O.intensity[local] = I;
+    if (O.r_hit) O.r_hit[local] = rh;
+    S.rays += 1;
+    S.status[status] += 1;
+    S.acc += n_acc;
+    S.rej += n_rej;
+    S.max_abs_H = fmax(S.max_abs_H, max_abs_H);
+    mode = MODE_IDLE;
+  };
+
+  // Start locating the crossing of `surf` inside the accepted step y -> o.
+  auto begin_locate = [&](int surf, double hs, const State& o) {
+    kind = surf;
+    lo = 0.0;
+    hi = hs;
+    flo = surface_value(surf, y, r_cap, r_esc);
+    fhi = surface_value(surf, o, r_cap, r_esc);
+    yF = o;
+    side = 0;
+    iters = 0;
+    h_try = (lo * fhi - hi * flo) / (fhi - flo);
+    if (!(h_try > lo && h_try < hi)) h_try = 0.5 * (lo + hi);
+    mode = MODE_LOCATE;
+  };
+
+  // After an accepted step without a disk hit: capture and escape tests on
+  // the step end o (in this order), else continue from o.
+  auto after_accept = [&](double hs, const State& o) {
+    if (o.r < r_cap) {
+      begin_locate(SURF_CAPTURE, hs, o);
+    } else if (o.r > r_esc) {
+      begin_locate(SURF_ESCAPE, hs, o);
+    } else {
+      y = o;
+      mode = MODE_INTEGRATE;
+      if ((int64_t)(n_acc + n_rej) >= max_steps) finish(OSIRIS_STATUS_MAXSTEP, y);
+    }
+  };
+
+  if (!PERSISTENT) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < A.total_rays) start_ray(g);
+  }
+
+  for (;;) {
+    if (PERSISTENT) {
+      const bool need = (mode == MODE_IDLE) && !drained;
+      const unsigned m = __ballot_sync(FULL, need);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(A.queue, (unsigned long long)__popc(m));
+        base = __shfl_sync(FULL, base, leader);
+        if (need) {
+          const unsigned long long g = base + __popc(m & ((1u << lane) - 1u));
+          if (g < (unsigned long long)A.total_rays)
+            start_ray((int64_t)g);
+          else
+            drained = true;
+        }
+      }
+    }
+    if (!__any_sync(FULL, mode != MODE_IDLE)) break;
+    if (mode == MODE_IDLE) continue;
+
+    const double hs = (mode == MODE_LOCATE) ? h_try : fmin(h, 0.1 * y.r);
+    State o, d;
+    double twoH;
+    const bool fp64_step = Stepper::attempt(K, y, hs, o, d, twoH);
+    S.rhs += 6;
+    S.fp64_steps += fp64_step ? 1 : 0;
+
+    if (mode == MODE_INTEGRATE) {
+      max_abs_H = fmax(max_abs_H, fabs(0.5 * twoH));
+      if (state_not_finite(o) || state_not_finite(d)) {
+        finish(OSIRIS_STATUS_ERROR, y);
+        continue;
+      }
+      bool ok = true;
+      float err = 0.0f;
+      err_component(y.r, o.r, d.r, tol, ok, err);
+      err_component(y.th, o.th, d.th, tol, ok, err);
+      err_component(y.ph, o.ph, d.ph, tol, ok, err);
+      err_component(y.pr, o.pr, d.pr, tol, ok, err);
+      err_component(y.pth, o.pth, d.pth, tol, ok, err);
+      if (ok) {
+        ++n_acc;
+        // step-size controller (FP32 is enough to size the next step):
+        // min(5, max(0.2, 0.9 err^-1/5))
+        const float grow = fminf(5.0f, fmaxf(0.2f, 0.9f * exp2f(-0.2f * log2f(err))));
+        h = hs * (double)grow;
+        h_step = hs;
+        yE = o;
+        if (disk && crosses_equator(y, o))
+          begin_locate(SURF_EQUATOR, hs, o);
+        else
+          after_accept(hs, o);
+      } else {
+        ++n_rej;
+        const float shrink = fmaxf(0.1f, 0.9f * exp2f(-0.25f * log2f(err)));
+        h = hs * (double)shrink;
+        if ((int64_t)(n_acc + n_rej) >= max_steps) finish(OSIRIS_STATUS_MAXSTEP, y);
+      }
+    } else {  // MODE_LOCATE: Illinois-modified regula falsi on the step length
+      S.root += 1;
+      ++iters;
+      if (state_not_finite(o)) {
+        finish(OSIRIS_STATUS_ERROR, y);
+        continue;
+      }
+      const double f = surface_value(kind, o, r_cap, r_esc);
+      const bool to_lo = (f != 0.0) && ((f > 0.0) == (flo > 0.0));
+      if (to_lo) {
+        lo = hs;
+        flo = f;
+        if (side == -1) fhi *= 0.5;
+        side = -1;
+      } else {
+        hi = hs;
+        fhi = f;
+        yF = o;
+        if (side == +1) flo *= 0.5;
+        side = +1;
+      }
+      const double ftol = (kind == SURF_EQUATOR) ? 1e-15 : 1e-14 * (kind == SURF_CAPTURE ? r_cap : r_esc);
+      const bool done = (f == 0.0) || (!to_lo && fabs(f) <= ftol) || (hi - lo <= 4e-16 * hi) ||
+                        iters >= 64;
+      if (!done) {
+        h_try = (lo * fhi - hi * flo) / (fhi - flo);
+        if (!(h_try > lo && h_try < hi)) h_try = 0.5 * (lo + hi);
+      } else if (kind == SURF_CAPTURE) {
+        finish(OSIRIS_STATUS_CAPTURED, yF);
+      } else if (kind == SURF_ESCAPE) {
+        finish(OSIRIS_STATUS_ESCAPED, yF);
+      } else if (yF.r >= r_in && yF.r <= r_out) {
+        finish(OSIRIS_STATUS_DISK, yF);
+      } else {
+        // equatorial crossing outside the disk: the accepted step stands;
+        // run the capture / escape tests on its end point
+        after_accept(h_step, yE);
+      }
+    }
+  }
+  flush_stats(A, S);
+}
+
+}  // namespace osiris_impl

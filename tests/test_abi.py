@@ -1,0 +1,81 @@
+"""CPU-side checks of the C interface: the library builds, loads and exports
+every entry point include/osiris.h declares; host-only calls and argument
+validation work without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def osr():
+    from paper_2202_00086_gb300 import build
+    build.build()
+    import paper_2202_00086_gb300 as m
+    return m
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(osiris_\w+)\s*\(", src))
+    return names
+
+
+def test_exports_every_declared_symbol(osr):
+    names = _declared_functions()
+    assert {"osiris_init_camera", "osiris_trace", "osiris_render_disk"} <= names
+    lib = ctypes.CDLL(osr.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+def test_host_helpers(osr):
+    import oracle
+    for a in (0.0, 0.5, 0.9, 0.998):
+        assert osr.isco(a) == pytest.approx(oracle.isco(a), rel=1e-14)
+        assert osr.horizon(a) == pytest.approx(1 + (1 - a * a) ** 0.5, rel=1e-15)
+
+
+@pytest.mark.parametrize("args", [
+    (1.0, 1000.0, 60.0, (-8, 8, -8, 8), 8, 8),      # a >= 1
+    (0.5, 15.0, 60.0, (-8, 8, -8, 8), 8, 8),        # r_obs <= 10 r_H
+    (0.5, 1000.0, 0.0, (-8, 8, -8, 8), 8, 8),       # on the axis
+    (0.5, 1000.0, 60.0, (8, -8, -8, 8), 8, 8),      # empty extent
+    (0.5, 1000.0, 60.0, (-8, 8, -8, 8), 0, 8),      # no pixels
+    (0.5, 30.0, 60.0, (-25, 25, -25, 25), 8, 8),    # corner outside the sky
+])
+def test_camera_validation(osr, args):
+    with pytest.raises(osr.OsirisError) as e:
+        osr.Camera(*args)
+    assert e.value.code == osr.EINVAL
+
+
+def test_trace_validation_before_launch(osr):
+    cam = osr.Camera(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 8, 8)
+    out = osr.Outputs()
+    for bad in (dict(tol=-1.0), dict(max_steps=0), dict(precision=7), dict(r_cap_factor=1.0),
+                dict(cell_deg=0.0), dict(block_size=48)):
+        o = osr.make_opts(**bad)
+        rc = osr.lib().osiris_trace(cam.handle, ctypes.byref(o), ctypes.byref(out), None)
+        assert rc == osr.EINVAL, bad
+    o = osr.make_opts()
+    rc = osr.lib().osiris_render_disk(cam.handle, 30.0, 20.0, ctypes.byref(o), ctypes.byref(out),
+                                      None)
+    assert rc == osr.EINVAL
+    rc = osr.lib().osiris_trace_batch(None, 0, ctypes.byref(o), None)
+    assert rc == osr.EINVAL
+    assert osr.workspace_bytes(10) > osr.workspace_bytes(1) >= 256
+
+
+def test_oracle_library_loads():
+    import oracle
+    lib = oracle.lib()
+    for n in ("oracle_trace_pixels", "oracle_trace_states", "oracle_init_ray"):
+        assert hasattr(lib, n)
