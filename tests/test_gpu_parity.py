@@ -125,7 +125,7 @@ def test_explicit_states_hook():
         assert np.allclose(g, ref[key], rtol=1e-8, atol=1e-8), key
     # photon sphere: r stays at 3 while the step cap runs out
     b = 3 * math.sqrt(3)
-    s = torch.tensor([[0.0, 3.0, math.pi / 2, 0.0, 0.0, 0.0]], device="cuda")
+    s = torch.tensor([[0.0, 3.0, math.pi / 2, 0.0, 0.0, 0.0]], device="cuda", dtype=torch.float64)
     o = osr.trace_states(0.0, 1000.0, s, torch.ones(1, device="cuda", dtype=torch.float64),
                          torch.full((1,), b, device="cuda", dtype=torch.float64), max_steps=60)
     torch.cuda.synchronize()
