@@ -186,6 +186,36 @@ size_t osiris_workspace_bytes(int32_t n_requests);
 int osiris_trace_batch(const osiris_request* reqs, int32_t n_requests,
                        const osiris_trace_opts* opts, void* cuda_stream);
 
+/* Most requests osiris_trace_batch_static takes in one call. */
+#define OSIRIS_STATIC_MAX_REQUESTS 256
+
+/* Allocation-free variant of osiris_trace_batch. The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory themselves, e.g. a plug-in inside a host application that
+ * owns every device allocation, a process running under a device-memory
+ * quota where a fresh allocation may fail at a bad moment, or a render loop
+ * that must not call cudaMalloc/cudaFree because those calls can synchronize
+ * the whole device.
+ * Instead of opts->workspace (ignored here, as is opts->workspace_bytes), the
+ * queue counter and request table live in a fixed array in device memory
+ * that the library reserves when it is loaded on a device: 256 bytes plus
+ * room for OSIRIS_STATIC_MAX_REQUESTS requests (about 90 KB). Every GPU that
+ * loads the library holds that array until the process exits. The caller
+ * still owns the cameras and every output array, as with osiris_trace_batch,
+ * and the outputs are the same.
+ *   - n_requests must be in [1, OSIRIS_STATIC_MAX_REQUESTS]; more returns
+ *     OSIRIS_EINVAL before anything is launched.
+ *   - The first call on a device looks up the device address of the array
+ *     (once per device, with that device current); make that first call
+ *     before any stream capture begins.
+ *   - All calls share the one array, which keeps the last call's contents;
+ *     each call resets the queue counter and rewrites the request table on
+ *     its stream. Calls whose work may overlap on the GPU (different streams
+ *     without ordering between them) race on the array: serialize them.
+ *   - No cudaMalloc, cudaFree or other allocating routine is called. */
+int osiris_trace_batch_static(const osiris_request* reqs, int32_t n_requests,
+                              const osiris_trace_opts* opts, void* cuda_stream);
+
 /* Test hook: trace n rays from explicit initial data instead of pixels.
  * states: DEVICE array of n rows (t, r, theta, phi, p_r, p_theta) (t unused);
  * E, L: DEVICE arrays of n constants (p_t = -E, p_phi = L). r_obs sets the

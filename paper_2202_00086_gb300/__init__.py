@@ -230,6 +230,28 @@ def trace_batch(requests, stream=None, **opts):
     return requests
 
 
+def trace_batch_static(requests, stream=None, **opts):
+    """osiris_trace_batch_static: like trace_batch, but the queue and request
+    table live in the library's fixed device array, so no workspace tensor
+    is needed (any `workspace` option is ignored). At most
+    OSIRIS_STATIC_MAX_REQUESTS (256) requests per call."""
+    L = lib()
+    fn = L.osiris_trace_batch_static
+    fn.argtypes = [_P(Request), ctypes.c_int32, _P(TraceOpts), _vp]
+    n = len(requests)
+    arr = (Request * max(1, n))()
+    for k, q in enumerate(requests):
+        arr[k].camera = q["camera"].handle
+        arr[k].disk = 1 if q.get("disk") else 0
+        arr[k].r_in = float(q.get("r_in") or 0.0)
+        arr[k].r_out = float(q.get("r_out") or 0.0)
+        arr[k].tol = float(q.get("tol") or 0.0)
+        arr[k].out = outputs_struct(q["out"])
+    o = make_opts(**opts)
+    _check(fn(arr, n, ctypes.byref(o), _stream_handle(stream)), "osiris_trace_batch_static")
+    return requests
+
+
 def trace_states(a, r_obs, states, E, L, out=None, disk=False, r_in=0.0, r_out=0.0,
                  stream=None, **opts):
     """Trace rays from explicit device initial data (osiris_trace_states)."""

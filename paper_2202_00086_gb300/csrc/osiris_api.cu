@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -354,3 +355,84 @@ const char* osiris_strerror(int code) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free batched trace (osiris_trace_batch_static): the workspace of
+// osiris_trace_batch is replaced by one fixed array in device memory.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kStaticMaxDevices = 64;
+constexpr size_t kStaticBytes =
+    osiris_impl::kQueueBytes + sizeof(ReqDev) * static_cast<size_t>(OSIRIS_STATIC_MAX_REQUESTS);
+
+// Queue counter (first 256 bytes) and request table; one copy per device.
+__device__ __align__(256) unsigned char g_static_workspace[kStaticBytes];
+
+std::mutex g_static_mutex;                      // guards the two arrays below
+void* g_static_address[kStaticMaxDevices] = {};  // device address, per device
+ReqDev g_static_table[OSIRIS_STATIC_MAX_REQUESTS];  // host staging of the table
+
+// Device address of g_static_workspace on the current device, looked up once
+// per device. Host code must not use the symbol itself as an address.
+int static_workspace_address(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return OSIRIS_ECUDA;
+  if (dev < 0 || dev >= kStaticMaxDevices) return OSIRIS_EINVAL;
+  if (g_static_address[dev] == nullptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_workspace) != cudaSuccess || p == nullptr)
+      return OSIRIS_ECUDA;
+    g_static_address[dev] = p;
+  }
+  *out = g_static_address[dev];
+  return OSIRIS_OK;
+}
+
+}  // namespace
+
+extern "C" int osiris_trace_batch_static(const osiris_request* reqs, int32_t n,
+                                         const osiris_trace_opts* opts, void* cuda_stream) {
+  if (!reqs || !opts || n < 1 || n > OSIRIS_STATIC_MAX_REQUESTS) return OSIRIS_EINVAL;
+  osiris_trace_opts o = *opts;
+  o.workspace = nullptr;
+  o.workspace_bytes = 0;
+  if (int rc = check_opts(&o)) return rc;
+
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  int64_t begin = 0;
+  for (int32_t k = 0; k < n; ++k) {
+    const osiris_request& q = reqs[k];
+    if (!q.camera) return OSIRIS_EINVAL;
+    if (q.tol < 0.0 || !is_fin(q.tol)) return OSIRIS_EINVAL;
+    if (q.disk)
+      if (int rc = check_disk(q.camera->a, o.r_cap_factor, o.r_esc_factor * q.camera->r0, q.r_in,
+                              q.r_out))
+        return rc;
+    ReqDev& R = g_static_table[k];
+    std::memset(&R, 0, sizeof(R));
+    fill_common(R, q.camera->a, q.camera->r0, &o, q.tol, q.disk, q.r_in, q.r_out, &q.out);
+    fill_camera(R, q.camera);
+    R.ray_begin = begin;
+    begin += R.n_rays;
+  }
+  void* base = nullptr;
+  if (int rc = static_workspace_address(&base)) return rc;
+  char* ws = static_cast<char*>(base);
+  ReqDev* dev_table = reinterpret_cast<ReqDev*>(ws + osiris_impl::kQueueBytes);
+  // Pageable source: the call returns once the table has been staged, so the
+  // host table may be refilled by the next call.
+  if (cudaMemcpyAsync(dev_table, g_static_table, sizeof(ReqDev) * static_cast<size_t>(n),
+                      cudaMemcpyHostToDevice, static_cast<cudaStream_t>(cuda_stream)) !=
+      cudaSuccess)
+    return OSIRIS_ECUDA;
+  KernelArgs args;
+  std::memset(&args, 0, sizeof(args));
+  args.reqs = dev_table;
+  args.n_req = n;
+  args.total_rays = begin;
+  args.stats = reinterpret_cast<unsigned long long*>(o.stats);
+  o.workspace = base;  // launch() clears the queue counter at its head
+  o.workspace_bytes = kStaticBytes;
+  return launch(args, &o, cuda_stream);
+}
