@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="osiris", choices=["osiris", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "df64"])
     p.add_argument("--kernel", default="batch", choices=["batch", "persistent", "plain"])
     p.add_argument("--side", type=int, default=1024)
     p.add_argument("--block", type=int, default=0)
@@ -203,7 +203,7 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    precision = osr.MIXED if args.precision == "mixed" else osr.FP64
+    precision = {"fp64": osr.FP64, "mixed": osr.MIXED, "df64": osr.DF64}[args.precision]
     tol = 1e-10
     cams = [osr.Camera.from_render(rd) for rd in renders]
     n_rays = sum(c.n_rays for c in cams)
@@ -316,7 +316,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if precision == osr.FP64 else "f64+f32", "data": "synthetic",
+        "dtype": {osr.FP64: "f64", osr.MIXED: "f64+f32", osr.DF64: "f64+df64"}[precision],
+        "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "rays_per_step_per_gpu": n_rays,
                    "kernel": args.kernel, "precision": args.precision,
                    "l2": "flushed between timed steps (256 MB write)",

@@ -47,7 +47,12 @@ extern "C" {
 
 /* ---- precision of the integrator -------------------------------------- */
 #define OSIRIS_FP64 0  /* every operation in double precision */
-#define OSIRIS_MIXED 1 /* FP32 stage evaluations, FP64 state and controller */
+#define OSIRIS_MIXED 1 /* FP32 stage evaluations, FP64 state and controller;
+                          FP64 steps near the horizon (r < 4) and at polar
+                          turning points; for tolerances of 1e-7 and looser */
+#define OSIRIS_DF64 2  /* stage evaluations in double-float (pairs of FP32,
+                          48-bit significand) on the FP32 pipe; FP64 state
+                          and controller */
 
 /* ---- counters written to osiris_trace_opts.stats (uint64 each) --------- */
 #define OSIRIS_STAT_RAYS 0          /* rays finished */
@@ -69,7 +74,7 @@ typedef struct {
                               (error norm: max over r, theta, phi, p_r, p_theta of
                               |y5 - y4| / (tol (1 + max(|y_n|, |y_n+1|)))), > 0 */
     int64_t max_steps;     /* cap on accepted + rejected steps per ray, >= 1 */
-    int32_t precision;     /* OSIRIS_FP64 or OSIRIS_MIXED */
+    int32_t precision;     /* OSIRIS_FP64, OSIRIS_MIXED or OSIRIS_DF64 */
     int32_t persistent;    /* 0: one ray per thread; 1: persistent grid that
                               refills lanes from a device ray queue (needs
                               workspace) */
@@ -77,7 +82,7 @@ typedef struct {
     double r_esc_factor;   /* escaped when r > r_esc_factor * r_obs, > 1 */
     double cell_deg;       /* celestial checkerboard cell, degrees, (0, 180] */
     double cell_phase_deg; /* longitude offset of the checkerboard, degrees */
-    int32_t block_size;    /* threads per block, multiple of 32 in [32, 512];
+    int32_t block_size;    /* threads per block, multiple of 32 in [32, 256];
                               0 = library default */
     int32_t blocks_per_sm; /* persistent grid: blocks per SM; 0 = occupancy limit */
     uint64_t* stats;       /* optional DEVICE array of OSIRIS_STATS_LEN counters;

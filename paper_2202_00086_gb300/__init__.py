@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libosiris.so")
 
 OK, EINVAL, ECUDA, ENOMEM, ETIMEOUT = 0, -1, -2, -3, -4
 STATUS_NONE, STATUS_CAPTURED, STATUS_ESCAPED, STATUS_DISK, STATUS_MAXSTEP, STATUS_ERROR = range(6)
-FP64, MIXED = 0, 1
+FP64, MIXED, DF64 = 0, 1, 2
 STATS_LEN = 16
 STAT_NAMES = ["rays", "accepted", "rejected", "root_steps", "rhs_evals", "status_none",
               "status_captured", "status_escaped", "status_disk", "status_maxstep",

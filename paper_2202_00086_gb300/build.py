@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libosiris.so")
-SOURCES = ["osiris_api.cu", "trace_fp64.cu", "trace_mixed.cu"]
+SOURCES = ["osiris_api.cu", "trace_fp64.cu", "trace_mixed.cu", "trace_df64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

@@ -37,7 +37,8 @@ int check_opts(const osiris_trace_opts* o) {
   if (!o) return OSIRIS_EINVAL;
   if (!(o->tol > 0.0) || !is_fin(o->tol)) return OSIRIS_EINVAL;
   if (o->max_steps < 1) return OSIRIS_EINVAL;
-  if (o->precision != OSIRIS_FP64 && o->precision != OSIRIS_MIXED) return OSIRIS_EINVAL;
+  if (o->precision != OSIRIS_FP64 && o->precision != OSIRIS_MIXED && o->precision != OSIRIS_DF64)
+    return OSIRIS_EINVAL;
   if (!(o->r_cap_factor > 1.0) || !is_fin(o->r_cap_factor)) return OSIRIS_EINVAL;
   if (!(o->r_esc_factor > 1.0) || !is_fin(o->r_esc_factor)) return OSIRIS_EINVAL;
   if (!(o->cell_deg > 0.0 && o->cell_deg <= 180.0)) return OSIRIS_EINVAL;
@@ -110,8 +111,9 @@ int launch(KernelArgs& args, const osiris_trace_opts* o, void* stream) {
   if (args.total_rays == 0) return OSIRIS_OK;
   const int block = o->block_size ? o->block_size : kDefaultBlock;
   const bool persistent = o->persistent != 0 || args.reqs != nullptr;
-  auto launcher = (o->precision == OSIRIS_MIXED) ? osiris_impl::launch_trace_mixed
-                                                 : osiris_impl::launch_trace_fp64;
+  auto launcher = (o->precision == OSIRIS_MIXED)  ? osiris_impl::launch_trace_mixed
+                  : (o->precision == OSIRIS_DF64) ? osiris_impl::launch_trace_df64
+                                                  : osiris_impl::launch_trace_fp64;
   if (!persistent) {
     const int64_t grid = (args.total_rays + block - 1) / block;
     if (grid > 0x7fffffff) return OSIRIS_EINVAL;
@@ -123,8 +125,9 @@ int launch(KernelArgs& args, const osiris_trace_opts* o, void* stream) {
   if (int rc = sm_count(&sms)) return rc;
   int per_sm = o->blocks_per_sm;
   if (per_sm == 0) {
-    auto occ = (o->precision == OSIRIS_MIXED) ? osiris_impl::occupancy_mixed
-                                              : osiris_impl::occupancy_fp64;
+    auto occ = (o->precision == OSIRIS_MIXED)  ? osiris_impl::occupancy_mixed
+               : (o->precision == OSIRIS_DF64) ? osiris_impl::occupancy_df64
+                                               : osiris_impl::occupancy_fp64;
     if (occ(Kernel::kPersistent, block, &per_sm) != 0 || per_sm < 1) return OSIRIS_ECUDA;
   }
   int64_t grid = static_cast<int64_t>(sms) * per_sm;

@@ -1,0 +1,406 @@
+// Double-float trace kernels. Every Cash-Karp attempt of the integration runs
+// in df64 arithmetic (pairs of FP32, 48-bit significand) on the FP32 pipe,
+// which on GB300 is ~70x the FP64 pipe: the six evaluations of Hamilton's
+// equations, the stage sums, the increment, the error estimate, the error
+// test and the stopping-surface tests. The state between steps is a df64
+// vector too. FP64 is used only once per ray (initial data, the terminal
+// state and its |H|, the observables) and inside surface location.
+//
+// Stage sums. With d_j = k_j - k_1 (j >= 2), the Cash-Karp combinations are
+//   stage input  y_i = y + c_i h k_1 + h sum_j a_ij d_j      (sum_j a_ij = c_i)
+//   increment        = h k_1 + h sum_i b_i d_i                (sum_i b_i = 1)
+//   error estimate   = h sum_i (b_i - b*_i) d_i               (sum = 0)
+// The increment and the error estimate are formed in df64 with df64 weights
+// (the error estimate cancels to O(h^5) and needs the extra digits). In a
+// stage input the part h sum_j a_ij d_j is O(h/T) smaller than the stage's
+// step (T: time scale of the solution) and reaches the result only through
+// one more factor h/T, so it is summed in FP32.
+//
+// The six stages run as a loop with one copy of the evaluation of Hamilton's
+// equations (the df64 code of six inlined copies overflows the instruction
+// cache); the stage differences live in small per-thread arrays.
+#include <cuda_runtime.h>
+
+#include "df64.cuh"
+#include "trace_kernel.cuh"
+
+namespace osiris_impl {
+
+struct RayDF {
+  df a, a2, aE, aL, E, L, twoE;
+};
+
+__device__ __forceinline__ RayDF to_df(const RayK& K) {
+  RayDF k;
+  k.a = df_from_double(K.a);
+  k.a2 = df_from_double(K.a2);
+  k.aE = df_from_double(K.aE);
+  k.aL = df_from_double(K.aL);
+  k.E = df_from_double(K.E);
+  k.L = df_from_double(K.L);
+  k.twoE = df_scale(k.E, 2.0f);
+  return k;
+}
+
+struct StateDF {
+  df r, th, ph, pr, pth;
+};
+
+__device__ __forceinline__ StateDF to_df(const State& s) {
+  StateDF d;
+  d.r = df_from_double(s.r);
+  d.th = df_from_double(s.th);
+  d.ph = df_from_double(s.ph);
+  d.pr = df_from_double(s.pr);
+  d.pth = df_from_double(s.pth);
+  return d;
+}
+
+__device__ __forceinline__ State to_double(const StateDF& d) {
+  State s;
+  s.r = df_to_double(d.r);
+  s.th = df_to_double(d.th);
+  s.ph = df_to_double(d.ph);
+  s.pr = df_to_double(d.pr);
+  s.pth = df_to_double(d.pth);
+  return s;
+}
+
+// a < b for normalised df values
+__device__ __forceinline__ bool df_lt(df a, df b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+
+// Sign of cos(theta) through pi/2 - theta (exact to df64 precision).
+__device__ __forceinline__ float df_side(df th) {
+  const df t = df_sub(mk(dfc::P1, dfc::P2), th);
+  return t.hi != 0.0f ? t.hi : t.lo;
+}
+
+__device__ __forceinline__ bool df_not_finite(float x) {
+  return ((__float_as_uint(x) >> 23) & 0xffu) == 0xffu;
+}
+
+// Hamilton's equations in the separated form of rhs64 (trace_device.cuh),
+// every operation in df64.
+__device__ __forceinline__ void rhs_df(const RayDF& K, df r, df th, df pr, df pth, df& dr,
+                                       df& dth, df& dph, df& dpr, df& dpth, float& twoH) {
+  df s, c;
+  df_sincos(th, s, c);
+  const df r2 = df_sqr(r);
+  const df Delta = df_add(df_mul(r, df_add_f(r, -2.0f)), K.a2);
+  const df Sigma = df_add(r2, df_mul(K.a2, df_sqr(c)));
+  const df P = df_sub(df_mul(df_add(r2, K.a2), K.E), K.aL);
+  const df DS = df_mul(Delta, Sigma);
+  const df inv = df_rcp(df_mul(DS, s));
+  const df iSig = df_mul(df_mul(Delta, s), inv);
+  const df iDel = df_mul(df_mul(Sigma, s), inv);
+  const df is = df_mul(DS, inv);
+  const df W = df_sub(df_mul(K.L, is), df_mul(K.aE, s));
+  const df u = df_mul(P, iDel);
+  const df Dpr = df_mul(Delta, pr);
+  const df N = df_add(df_add(df_mul(Dpr, pr), df_sqr(pth)), df_sub(df_sqr(W), df_mul(P, u)));
+  const df NiS = df_mul(N, iSig);
+  dr = df_mul(Dpr, iSig);
+  dth = df_mul(pth, iSig);
+  dph = df_mul(df_add(df_mul(W, is), df_mul(K.a, u)), iSig);
+  const df t1 = df_add(df_mul(r, NiS), df_mul(df_mul(r, K.twoE), u));
+  const df t2 = df_mul(df_add_f(r, -1.0f), df_add(df_sqr(u), df_sqr(pr)));
+  dpr = df_mul(iSig, df_sub(t1, t2));
+  const df t3 = df_mul(W, df_add(df_mul(K.L, df_sqr(is)), K.aE));
+  const df t4 = df_mul(df_mul(K.a2, s), NiS);
+  dpth = df_mul(df_mul(c, iSig), df_sub(t3, t4));
+  twoH = NiS.hi;
+}
+
+// Cash-Karp coefficients for the df64 stepper. Stage s = 0..5 is the
+// tableau's stage s + 1.
+__constant__ float kA[6][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 0},
+    {0, 9.0f / 40.0f, 0, 0, 0, 0},
+    {0, -9.0f / 10.0f, 6.0f / 5.0f, 0, 0, 0},
+    {0, 5.0f / 2.0f, -70.0f / 27.0f, 35.0f / 27.0f, 0, 0},
+    {0, 175.0f / 512.0f, 575.0f / 13824.0f, 44275.0f / 110592.0f, 253.0f / 4096.0f, 0}};
+// c_s as df (1/5, 3/10, 3/5 are not FP32 numbers; 1 and 7/8 are)
+__constant__ float kCH[6] = {0.0f, 0.20000000298023224f, 0.30000001192092896f,
+                             0.6000000238418579f, 1.0f, 0.875f};
+__constant__ float kCL[6] = {0.0f, -2.9802322831784522e-09f, -1.1920929132713809e-08f,
+                             -2.3841858265427618e-08f, 0.0f, 0.0f};
+
+namespace dfk {
+// fifth-order weights b_3, b_4, b_6 (b_2 = b_5 = 0) as df
+constexpr float B3H = 0.4025764763355255f, B3L = 1.3197485770888306e-08f;
+constexpr float B4H = 0.21043771505355835f, B4L = -4.615847704059206e-09f;
+constexpr float B6H = 0.2891021966934204f, B6L = 5.452259976834739e-09f;
+// b_i - b*_i for i = 3..6 (i = 2 is zero) as df
+constexpr float D3H = 0.018668586388230324f, D3L = -2.943724985993157e-10f;
+constexpr float D4H = -0.03415502607822418f, D4L = -7.525838841004884e-10f;
+constexpr float D5H = -0.01932198740541935f, D5L = 7.982765004577175e-10f;
+constexpr float D6H = 0.03910220041871071f, D6L = 1.726969678372825e-09f;
+}  // namespace dfk
+
+// One Cash-Karp attempt of length h from y, all in df64: o = fifth-order
+// result, d = fifth minus fourth order (FP32 is enough for the error test).
+__device__ __forceinline__ void ck_step_df(const RayDF& K, const StateDF& y, df h, StateDF& o,
+                                           float d[5], float& twoH) {
+  using namespace dfk;
+  df k1[5];
+  rhs_df(K, y.r, y.th, y.pr, y.pth, k1[0], k1[1], k1[2], k1[3], k1[4], twoH);
+  df hk1[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) hk1[c] = df_mul(h, k1[c]);
+  const df y4[4] = {y.r, y.th, y.pr, y.pth};
+  const float hf = h.hi;
+  float dv[6][4];  // d_s in FP32, components (r, theta, p_r, p_theta)
+  df ev[6][5];     // d_s in df64, components (r, theta, phi, p_r, p_theta)
+#pragma unroll 1
+  for (int s = 1; s < 6; ++s) {
+    const df cs = mk(kCH[s], kCL[s]);
+    df in[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int kc = c < 2 ? c : c + 1;  // skip phi in k
+      float fs = 0.0f;
+      for (int t = 1; t < s; ++t) fs = fmaf(kA[s][t], dv[t][c], fs);
+      in[c] = df_add_f(df_add(y4[c], df_mul(hk1[kc], cs)), __fmul_rn(hf, fs));
+    }
+    df k[5];
+    float unused;
+    rhs_df(K, in[0], in[1], in[2], in[3], k[0], k[1], k[2], k[3], k[4], unused);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) ev[s][c] = df_sub(k[c], k1[c]);
+    dv[s][0] = ev[s][0].hi;
+    dv[s][1] = ev[s][1].hi;
+    dv[s][2] = ev[s][3].hi;
+    dv[s][3] = ev[s][4].hi;
+  }
+  df inc[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    const df bs = df_add(df_mul(ev[5][c], mk(B6H, B6L)),
+                         df_add(df_mul(ev[3][c], mk(B4H, B4L)), df_mul(ev[2][c], mk(B3H, B3L))));
+    inc[c] = df_add(hk1[c], df_mul(h, bs));
+    const df ds =
+        df_add(df_add(df_mul(ev[5][c], mk(D6H, D6L)), df_mul(ev[4][c], mk(D5H, D5L))),
+               df_add(df_mul(ev[3][c], mk(D4H, D4L)), df_mul(ev[2][c], mk(D3H, D3L))));
+    d[c] = df_mul(h, ds).hi;
+  }
+  o.r = df_add(y.r, inc[0]);
+  o.th = df_add(y.th, inc[1]);
+  o.ph = df_add(y.ph, inc[2]);
+  o.pr = df_add(y.pr, inc[3]);
+  o.pth = df_add(y.pth, inc[4]);
+}
+
+// The lane state machine of trace_body (trace_kernel.cuh) with a df64 state:
+// same modes, same order of tests, same controller; the INTEGRATE path issues
+// no FP64 instruction. Surface location keeps its bracket in FP64.
+template <bool PERSISTENT>
+__device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
+  const unsigned FULL = 0xffffffffu;
+  int mode = MODE_IDLE;
+  bool drained = !PERSISTENT;
+  LaneStats S;
+
+  RayInfo I;
+  RayDF KD;
+  df r_cap, r_esc;
+  float tol = 0.0f;
+  StateDF y;
+  float h = 0.0f, max_abs_H = 0.0f;
+  unsigned n_acc = 0, n_rej = 0;
+  int kind = 0, side = 0, iters = 0;
+  double lo = 0, hi = 0, flo = 0, fhi = 0, h_try = 0, h_step = 0;
+  StateDF yF, yE;
+
+  auto start_ray = [&](int64_t g) {
+    State y0;
+    load_ray(A, g, I, y0);
+    y = to_df(y0);
+    KD = to_df(I.K);
+    r_cap = df_from_double(I.r_cap);
+    r_esc = df_from_double(I.r_esc);
+    tol = (float)I.tol;
+    h = (float)I.h0;
+    max_abs_H = 0.0f;
+    n_acc = n_rej = 0;
+    mode = MODE_INTEGRATE;
+  };
+
+  auto finish = [&](int status, const StateDF& fd) {
+    const State f = to_double(fd);
+    double mh = (double)max_abs_H;
+    if (status != OSIRIS_STATUS_ERROR) {
+      mh = fmax(mh, fabs(0.5 * twoH64(I.K, f)));
+      S.rhs += 1;
+    }
+    write_outputs(A, I, status, f, mh, n_acc, n_rej, S);
+    mode = MODE_IDLE;
+  };
+
+  // FP64 value whose sign tells the side of the surface (see surface_value)
+  auto surf = [&](int k, const StateDF& s) -> double {
+    if (k == SURF_EQUATOR) return (PIO2_HI - df_to_double(s.th)) + PIO2_LO;
+    if (k == SURF_CAPTURE) return df_to_double(s.r) - I.r_cap;
+    return df_to_double(s.r) - I.r_esc;
+  };
+
+  auto begin_locate = [&](int k, double hs, const StateDF& o) {
+    kind = k;
+    lo = 0.0;
+    hi = hs;
+    flo = surf(k, y);
+    fhi = surf(k, o);
+    yF = o;
+    side = 0;
+    iters = 0;
+    h_try = (lo * fhi - hi * flo) / (fhi - flo);
+    if (!(h_try > lo && h_try < hi)) h_try = 0.5 * (lo + hi);
+    mode = MODE_LOCATE;
+  };
+
+  auto after_accept = [&](double hs, const StateDF& o) {
+    if (df_lt(o.r, r_cap)) {
+      begin_locate(SURF_CAPTURE, hs, o);
+    } else if (df_lt(r_esc, o.r)) {
+      begin_locate(SURF_ESCAPE, hs, o);
+    } else {
+      y = o;
+      mode = MODE_INTEGRATE;
+      if ((int64_t)(n_acc + n_rej) >= I.max_steps) finish(OSIRIS_STATUS_MAXSTEP, y);
+    }
+  };
+
+  if (!PERSISTENT) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < A.total_rays) start_ray(g);
+  }
+
+  for (;;) {
+    if (PERSISTENT) {
+      const int64_t g = refill(A, (mode == MODE_IDLE) && !drained);
+      if (g >= 0)
+        start_ray(g);
+      else if (g == -2)
+        drained = true;
+    }
+    if (!__any_sync(FULL, mode != MODE_IDLE)) break;
+    if (mode == MODE_IDLE) continue;
+
+    const float hs_f = fminf(h, 0.1f * y.r.hi);
+    const df hd = (mode == MODE_LOCATE) ? df_from_double(h_try) : mk(hs_f, 0.0f);
+    StateDF o;
+    float d[5];
+    float twoH;
+    ck_step_df(KD, y, hd, o, d, twoH);
+    S.rhs += 6;
+
+    if (mode == MODE_INTEGRATE) {
+      max_abs_H = fmaxf(max_abs_H, fabsf(0.5f * twoH));
+      const float ys[5] = {y.r.hi, y.th.hi, y.ph.hi, y.pr.hi, y.pth.hi};
+      const float os[5] = {o.r.hi, o.th.hi, o.ph.hi, o.pr.hi, o.pth.hi};
+      bool bad = false, ok = true;
+      float err = 0.0f;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        bad |= df_not_finite(os[c]) | df_not_finite(d[c]);
+        const float scale = tol * (1.0f + fmaxf(fabsf(ys[c]), fabsf(os[c])));
+        const float ad = fabsf(d[c]);
+        ok = ok && (ad <= scale);
+        err = fmaxf(err, __fdividef(ad, scale));
+      }
+      if (bad) {
+        finish(OSIRIS_STATUS_ERROR, y);
+        continue;
+      }
+      if (ok) {
+        ++n_acc;
+        const float grow = fminf(5.0f, fmaxf(0.2f, 0.9f * exp2f(-0.2f * log2f(err))));
+        h = hs_f * grow;
+        h_step = (double)hs_f;
+        yE = o;
+        if (I.disk && ((df_side(y.th) > 0.0f && df_side(o.th) <= 0.0f) ||
+                       (df_side(y.th) < 0.0f && df_side(o.th) >= 0.0f)))
+          begin_locate(SURF_EQUATOR, h_step, o);
+        else
+          after_accept(h_step, o);
+      } else {
+        ++n_rej;
+        const float shrink = fmaxf(0.1f, 0.9f * exp2f(-0.25f * log2f(err)));
+        h = hs_f * shrink;
+        if ((int64_t)(n_acc + n_rej) >= I.max_steps) finish(OSIRIS_STATUS_MAXSTEP, y);
+      }
+    } else {  // MODE_LOCATE: Illinois-modified regula falsi on the step length
+      S.root += 1;
+      ++iters;
+      if (df_not_finite(o.r.hi) | df_not_finite(o.th.hi) | df_not_finite(o.ph.hi) |
+          df_not_finite(o.pr.hi) | df_not_finite(o.pth.hi)) {
+        finish(OSIRIS_STATUS_ERROR, y);
+        continue;
+      }
+      const double hs = h_try;
+      const double f = surf(kind, o);
+      const bool to_lo = (f != 0.0) && ((f > 0.0) == (flo > 0.0));
+      if (to_lo) {
+        lo = hs;
+        flo = f;
+        if (side == -1) fhi *= 0.5;
+        side = -1;
+      } else {
+        hi = hs;
+        fhi = f;
+        yF = o;
+        if (side == +1) flo *= 0.5;
+        side = +1;
+      }
+      const double ftol = (kind == SURF_EQUATOR)
+                              ? 1e-15
+                              : 1e-14 * (kind == SURF_CAPTURE ? I.r_cap : I.r_esc);
+      const bool done = (f == 0.0) || (!to_lo && fabs(f) <= ftol) || (hi - lo <= 4e-16 * hi) ||
+                        iters >= 64;
+      if (!done) {
+        h_try = (lo * fhi - hi * flo) / (fhi - flo);
+        if (!(h_try > lo && h_try < hi)) h_try = 0.5 * (lo + hi);
+      } else if (kind == SURF_CAPTURE) {
+        finish(OSIRIS_STATUS_CAPTURED, yF);
+      } else if (kind == SURF_ESCAPE) {
+        finish(OSIRIS_STATUS_ESCAPED, yF);
+      } else {
+        const double rx = df_to_double(yF.r);
+        if (rx >= I.r_in && rx <= I.r_out)
+          finish(OSIRIS_STATUS_DISK, yF);
+        else
+          after_accept(h_step, yE);
+      }
+    }
+  }
+  flush_stats(A, S);
+}
+
+constexpr int kMaxBlock = 256;
+
+__global__ void __launch_bounds__(kMaxBlock) trace_df64_plain(const __grid_constant__ KernelArgs A) {
+  trace_body_df<false>(A);
+}
+
+__global__ void __launch_bounds__(kMaxBlock) trace_df64_persistent(const __grid_constant__ KernelArgs A) {
+  trace_body_df<true>(A);
+}
+
+int launch_trace_df64(const KernelArgs& args, Kernel kind, int grid, int block, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (kind == Kernel::kPersistent)
+    trace_df64_persistent<<<grid, block, 0, s>>>(args);
+  else
+    trace_df64_plain<<<grid, block, 0, s>>>(args);
+  return (int)cudaGetLastError();
+}
+
+int occupancy_df64(Kernel kind, int block, int* blocks_per_sm) {
+  const void* fn = (kind == Kernel::kPersistent) ? (const void*)trace_df64_persistent
+                                                 : (const void*)trace_df64_plain;
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, 0);
+}
+
+}  // namespace osiris_impl

@@ -6,7 +6,10 @@
 namespace osiris_impl {
 
 struct StepperFP64 {
-  static __device__ __forceinline__ bool attempt(const RayK& K, const State& y, double h,
+  struct RayCache {};
+  static __device__ __forceinline__ void prepare(const RayK&, RayCache&) {}
+  static __device__ __forceinline__ bool attempt(const RayK& K, const RayCache&, const State& y,
+                                                 double h,
                                                  State& o, State& d, double& twoH) {
     ck_step64(K, y, h, o, d, twoH);
     return true;

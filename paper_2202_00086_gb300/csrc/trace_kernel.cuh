@@ -2,30 +2,166 @@
 // surfaces located inside the step, per-ray epilogue, and (persistent grids)
 // lane refill from a device ray queue. Instantiated per precision by
 // trace_fp64.cu and trace_mixed.cu through the Stepper policy:
-//   Stepper::attempt(K, y, h, o, d, twoH) -> one Cash-Karp attempt
-//   Stepper::twoH(K, y)                   -> 2H at a state (FP64)
+//   Stepper::RayCache                         per-ray data the stepper derives
+//   Stepper::prepare(K, cache)                once per ray
+//   Stepper::attempt(K, cache, y, h, o, d, twoH) -> one Cash-Karp attempt
+//   Stepper::twoH(K, y)                       -> 2H at a state (FP64)
 #pragma once
 
 #include "trace_device.cuh"
 
 namespace osiris_impl {
 
+// Per-ray identity and constants, common to every lane state machine.
+struct RayInfo {
+  int req;
+  int64_t local;  // index of the ray inside its request
+  RayK K;
+  double r_cap, r_esc, r_in, r_out, tol, h0;
+  int disk;
+  int64_t max_steps;
+};
+
+// Ray g of the launch: its request, constants and initial state (Sec. 2.3,
+// Eq. momentums: pixel centre -> p_theta, L, E, p_r at t = 0, r = r0,
+// theta = theta0, phi = 0; or explicit initial data for the test hook).
+__device__ __forceinline__ void load_ray(const KernelArgs& A, int64_t g, RayInfo& I, State& y) {
+  I.req = find_request(A, g);
+  const ReqDev* R = request_of(A, I.req);
+  I.local = g - R->ray_begin;
+  const double a = R->a;
+  I.K.a = a;
+  I.K.a2 = a * a;
+  if (R->explicit_states) {
+    const double* st = R->states + 6 * I.local;
+    y.r = st[1];
+    y.th = st[2];
+    y.ph = st[3];
+    y.pr = st[4];
+    y.pth = st[5];
+    I.K.E = R->E[I.local];
+    I.K.L = R->L[I.local];
+  } else {
+    const int64_t i = I.local % R->nx, j = I.local / R->nx;
+    const double x = R->x_min + ((double)i + 0.5) * R->x_span / R->nx;
+    const double yy = R->y_min + ((double)j + 0.5) * R->y_span / R->ny;
+    const double Pth = yy / R->r0, Pph = -x / R->r0;
+    I.K.E = R->inv_At + x * R->e_x;
+    I.K.L = x * R->l_x;
+    y.r = R->r0;
+    y.th = R->th0;
+    y.ph = 0.0;
+    y.pth = yy * R->pth_y;
+    y.pr = -sqrt(R->grr * (1.0 - Pth * Pth - Pph * Pph));
+  }
+  I.K.aE = a * I.K.E;
+  I.K.aL = a * I.K.L;
+  I.r_cap = R->r_cap;
+  I.r_esc = R->r_esc;
+  I.r_in = R->r_in;
+  I.r_out = R->r_out;
+  I.disk = R->disk;
+  I.tol = R->tol;
+  I.max_steps = R->max_steps;
+  I.h0 = R->h0;
+}
+
+// Write the outputs of a finished ray (terminal state f, final max |H|) and
+// fold it into the lane's counters.
+__device__ __forceinline__ void write_outputs(const KernelArgs& A, const RayInfo& I, int status,
+                                              const State& f, double max_abs_H, unsigned n_acc,
+                                              unsigned n_rej, LaneStats& S) {
+  const ReqDev* R = request_of(A, I.req);
+  const int64_t local = I.local;
+  const osiris_outputs& O = R->out;
+  if (O.status) O.status[local] = (uint8_t)status;
+  if (O.r) O.r[local] = f.r;
+  if (O.theta) O.theta[local] = f.th;
+  if (O.phi) O.phi[local] = f.ph;
+  if (O.max_abs_H) O.max_abs_H[local] = max_abs_H;
+  if (O.steps) O.steps[local] = n_acc;
+  int ci = -1, cj = -1, par = 0;
+  if (status == OSIRIS_STATUS_ESCAPED) {
+    // celestial checkerboard: fold theta into [0, pi], wrap phi into [0, 2pi)
+    double t = fmod(f.th, TWO_PI);
+    if (t < 0.0) t += TWO_PI;
+    double p = f.ph;
+    if (t > PI_D) {
+      t = TWO_PI - t;
+      p += PI_D;
+    }
+    double q = fmod(p + R->phase_rad, TWO_PI);
+    if (q < 0.0) q += TWO_PI;
+    ci = (int)floor(t / R->cell_rad);
+    cj = (int)floor(q / R->cell_rad);
+    ci = min(max(ci, 0), R->n_th_cells - 1);
+    cj = ((cj % R->n_ph_cells) + R->n_ph_cells) % R->n_ph_cells;
+    par = (ci + cj) & 1;
+  }
+  if (O.cell_i) O.cell_i[local] = (int16_t)ci;
+  if (O.cell_j) O.cell_j[local] = (int16_t)cj;
+  if (O.parity) O.parity[local] = (uint8_t)par;
+  double g = 0.0, Iobs = 0.0, rh = 0.0;
+  if (status == OSIRIS_STATUS_DISK) {
+    // Keplerian disk (Sec. 5): Omega = 1/(r^3/2 + a); u^t from the
+    // normalisation g_ab u^a u^b = -1 in the equatorial plane;
+    // g = 1/(u^t (E - Omega L)); I = g^3 / r^2.
+    const double r = f.r, a = I.K.a;
+    const double Om = 1.0 / fma(r, sqrt(r), a);
+    const double gtt = -(1.0 - 2.0 / r);
+    const double gtp = -2.0 * a / r;
+    const double gpp = r * r + a * a + 2.0 * a * a / r;
+    const double inv_ut = sqrt(-gtt - 2.0 * Om * gtp - Om * Om * gpp);
+    g = inv_ut / (I.K.E - Om * I.K.L);
+    Iobs = g * g * g / (r * r);
+    rh = r;
+  }
+  if (O.g) O.g[local] = g;
+  if (O.intensity) O.intensity[local] = Iobs;
+  if (O.r_hit) O.r_hit[local] = rh;
+  S.rays += 1;
+  S.status[status] += 1;
+  S.acc += n_acc;
+  S.rej += n_rej;
+  S.max_abs_H = fmax(S.max_abs_H, max_abs_H);
+}
+
+// Take the next rays of a persistent grid from the device queue for every
+// lane that needs one (one atomic per warp). Returns the ray index for this
+// lane, or -1 when the queue is drained or the lane needs none.
+__device__ __forceinline__ int64_t refill(const KernelArgs& A, bool need) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(FULL, need);
+  if (!m) return -1;
+  const int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(A.queue, (unsigned long long)__popc(m));
+  base = __shfl_sync(FULL, base, leader);
+  if (!need) return -1;
+  const unsigned long long g = base + __popc(m & ((1u << lane) - 1u));
+  return g < (unsigned long long)A.total_rays ? (int64_t)g : -2;
+}
+
 template <class Stepper, bool PERSISTENT>
 __device__ __forceinline__ void trace_body(const KernelArgs& A) {
   const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
 
   int mode = MODE_IDLE;
   bool drained = !PERSISTENT;
   LaneStats S;
 
   // ray identity and constants
-  int req = 0;
-  int64_t local = 0;
-  RayK K;
-  double r_cap = 0, r_esc = 0, r_in = 0, r_out = 0, tol = 0;
-  int disk = 0;
-  int64_t max_steps = 0;
+  RayInfo I;
+  RayK& K = I.K;
+  typename Stepper::RayCache RC;
+  double& r_cap = I.r_cap;
+  double& r_esc = I.r_esc;
+  double& r_in = I.r_in;
+  double& r_out = I.r_out;
+  double& tol = I.tol;
+  int& disk = I.disk;
+  int64_t& max_steps = I.max_steps;
   // integration state
   State y;
   double h = 0, max_abs_H = 0;
@@ -36,45 +172,9 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
   State yF, yE;  // state at the upper bracket end; end of the accepted step
 
   auto start_ray = [&](int64_t g) {
-    req = find_request(A, g);
-    const ReqDev* R = request_of(A, req);
-    local = g - R->ray_begin;
-    const double a = R->a;
-    K.a = a;
-    K.a2 = a * a;
-    if (R->explicit_states) {
-      const double* st = R->states + 6 * local;
-      y.r = st[1];
-      y.th = st[2];
-      y.ph = st[3];
-      y.pr = st[4];
-      y.pth = st[5];
-      K.E = R->E[local];
-      K.L = R->L[local];
-    } else {
-      // pixel centre, then the initial momenta of Sec. 2.3 (Eq. momentums)
-      const int64_t i = local % R->nx, j = local / R->nx;
-      const double x = R->x_min + ((double)i + 0.5) * R->x_span / R->nx;
-      const double yy = R->y_min + ((double)j + 0.5) * R->y_span / R->ny;
-      const double Pth = yy / R->r0, Pph = -x / R->r0;
-      K.E = R->inv_At + x * R->e_x;
-      K.L = x * R->l_x;
-      y.r = R->r0;
-      y.th = R->th0;
-      y.ph = 0.0;
-      y.pth = yy * R->pth_y;
-      y.pr = -sqrt(R->grr * (1.0 - Pth * Pth - Pph * Pph));
-    }
-    K.aE = a * K.E;
-    K.aL = a * K.L;
-    r_cap = R->r_cap;
-    r_esc = R->r_esc;
-    r_in = R->r_in;
-    r_out = R->r_out;
-    disk = R->disk;
-    tol = R->tol;
-    max_steps = R->max_steps;
-    h = R->h0;
+    load_ray(A, g, I, y);
+    Stepper::prepare(K, RC);
+    h = I.h0;
     max_abs_H = 0.0;
     n_acc = n_rej = 0;
     mode = MODE_INTEGRATE;
@@ -82,62 +182,11 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
 
   // Write the ray's outputs and retire the lane.
   auto finish = [&](int status, const State& f) {
-    const ReqDev* R = request_of(A, req);
     if (status != OSIRIS_STATUS_ERROR) {
       max_abs_H = fmax(max_abs_H, fabs(0.5 * Stepper::twoH(K, f)));
       S.rhs += 1;
     }
-    const osiris_outputs& O = R->out;
-    if (O.status) O.status[local] = (uint8_t)status;
-    if (O.r) O.r[local] = f.r;
-    if (O.theta) O.theta[local] = f.th;
-    if (O.phi) O.phi[local] = f.ph;
-    if (O.max_abs_H) O.max_abs_H[local] = max_abs_H;
-    if (O.steps) O.steps[local] = n_acc;
-    int ci = -1, cj = -1, par = 0;
-    if (status == OSIRIS_STATUS_ESCAPED) {
-      // celestial checkerboard: fold theta into [0, pi], wrap phi into [0, 2pi)
-      double t = fmod(f.th, TWO_PI);
-      if (t < 0.0) t += TWO_PI;
-      double p = f.ph;
-      if (t > PI_D) {
-        t = TWO_PI - t;
-        p += PI_D;
-      }
-      double q = fmod(p + R->phase_rad, TWO_PI);
-      if (q < 0.0) q += TWO_PI;
-      ci = (int)floor(t / R->cell_rad);
-      cj = (int)floor(q / R->cell_rad);
-      ci = min(max(ci, 0), R->n_th_cells - 1);
-      cj = ((cj % R->n_ph_cells) + R->n_ph_cells) % R->n_ph_cells;
-      par = (ci + cj) & 1;
-    }
-    if (O.cell_i) O.cell_i[local] = (int16_t)ci;
-    if (O.cell_j) O.cell_j[local] = (int16_t)cj;
-    if (O.parity) O.parity[local] = (uint8_t)par;
-    double g = 0.0, I = 0.0, rh = 0.0;
-    if (status == OSIRIS_STATUS_DISK) {
-      // Keplerian disk (Sec. 5): Omega = 1/(r^3/2 + a); u^t from the
-      // normalisation g_ab u^a u^b = -1 in the equatorial plane;
-      // g = 1/(u^t (E - Omega L)); I = g^3 / r^2.
-      const double r = f.r, a = K.a;
-      const double Om = 1.0 / fma(r, sqrt(r), a);
-      const double gtt = -(1.0 - 2.0 / r);
-      const double gtp = -2.0 * a / r;
-      const double gpp = r * r + a * a + 2.0 * a * a / r;
-      const double inv_ut = sqrt(-gtt - 2.0 * Om * gtp - Om * Om * gpp);
-      g = inv_ut / (K.E - Om * K.L);
-      I = g * g * g / (r * r);
-      rh = r;
-    }
-    if (O.g) O.g[local] = g;
-    if (O.intensity) O.intensity[local] = I;
-    if (O.r_hit) O.r_hit[local] = rh;
-    S.rays += 1;
-    S.status[status] += 1;
-    S.acc += n_acc;
-    S.rej += n_rej;
-    S.max_abs_H = fmax(S.max_abs_H, max_abs_H);
+    write_outputs(A, I, status, f, max_abs_H, n_acc, n_rej, S);
     mode = MODE_IDLE;
   };
 
@@ -177,21 +226,11 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
 
   for (;;) {
     if (PERSISTENT) {
-      const bool need = (mode == MODE_IDLE) && !drained;
-      const unsigned m = __ballot_sync(FULL, need);
-      if (m) {
-        const int leader = __ffs(m) - 1;
-        unsigned long long base = 0;
-        if (lane == leader) base = atomicAdd(A.queue, (unsigned long long)__popc(m));
-        base = __shfl_sync(FULL, base, leader);
-        if (need) {
-          const unsigned long long g = base + __popc(m & ((1u << lane) - 1u));
-          if (g < (unsigned long long)A.total_rays)
-            start_ray((int64_t)g);
-          else
-            drained = true;
-        }
-      }
+      const int64_t g = refill(A, (mode == MODE_IDLE) && !drained);
+      if (g >= 0)
+        start_ray(g);
+      else if (g == -2)
+        drained = true;
     }
     if (!__any_sync(FULL, mode != MODE_IDLE)) break;
     if (mode == MODE_IDLE) continue;
@@ -199,7 +238,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
     const double hs = (mode == MODE_LOCATE) ? h_try : fmin(h, 0.1 * y.r);
     State o, d;
     double twoH;
-    const bool fp64_step = Stepper::attempt(K, y, hs, o, d, twoH);
+    const bool fp64_step = Stepper::attempt(K, RC, y, hs, o, d, twoH);
     S.rhs += 6;
     S.fp64_steps += fp64_step ? 1 : 0;
 

@@ -63,7 +63,10 @@ __device__ __forceinline__ double twoH_value64(const RayK& K, const State& y) {
 }
 
 struct StepperMixed {
-  static __device__ __forceinline__ bool attempt(const RayK& K, const State& y, double h,
+  struct RayCache {};
+  static __device__ __forceinline__ void prepare(const RayK&, RayCache&) {}
+  static __device__ __forceinline__ bool attempt(const RayK& K, const RayCache&, const State& y,
+                                                 double h,
                                                  State& o, State& d, double& twoH) {
     if (y.r < kMixedFP64Radius || fabs(y.pth) < kMixedFP64Ptheta) {
       ck_step64(K, y, h, o, d, twoH);
