@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--block", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-variants", action="store_true")
     return p.parse_args()
 
 
@@ -294,6 +295,57 @@ def main():
         e2e = {"value": world * n_rays * args.steps / te, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    # ---- double-float variant on the same workload (same rules, own timing) ----
+    variants = {}
+    if precision == osr.FP64 and not args.no_variants:
+        vstats = osr.new_stats()
+        vcommon = dict(common, precision=osr.DF64)
+
+        def vstep(st=None):
+            if args.kernel == "batch":
+                osr.trace_batch([{"camera": c, "out": o} for c, o in zip(cams, outs)], stats=st,
+                                **vcommon)
+            else:
+                for c, o in zip(cams, outs):
+                    osr.trace(c, out=o, persistent=(args.kernel == "persistent"), stats=st,
+                              **vcommon)
+
+        for _ in range(max(1, args.warmup)):
+            vstep()
+        torch.cuda.synchronize()
+        vev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)
+            vev[k][0].record(stream)
+            vstep(vstats)
+            vev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        vms = sum(a.elapsed_time(b) for a, b in vev)
+        tv = torch.tensor([vms], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(tv, op=dist.ReduceOp.MAX)
+        vms = float(tv.item())
+        vs = osr.decode_stats(vstats)
+        vatt = vs["accepted"] + vs["rejected"] + vs["root_steps"]
+        vflops = vs["rhs_evals"] * F_RHS + vatt * F_STEP
+        variants["df64"] = {
+            "value": world * n_rays * args.steps / (vms * 1e-3), "unit": UNIT,
+            "ms_per_step": vms / args.steps,
+            "rhs_evals_per_s": world * vs["rhs_evals"] / (vms * 1e-3),
+            "speedup_vs_fp64": ms_max / vms,
+            "dtype": "f64+df64",
+            "fp64_equivalent_tflops": vflops / (vms * 1e-3) / 1e12,
+            "fp64_equivalent_frac_of_fp64_peak": vflops / (vms * 1e-3) / 1e12 / peaks["fp64"],
+            "max_abs_H": vs["max_abs_H"],
+            "steps_per_ray": {"accepted": vs["accepted"] / (n_rays * args.steps),
+                              "rejected": vs["rejected"] / (n_rays * args.steps),
+                              "locate": vs["root_steps"] / (n_rays * args.steps)},
+        }
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, dt, cores = run_oracle_sample(renders, ORACLE_SAMPLE_STRIDE)
@@ -338,6 +390,7 @@ def main():
                      "flops_per_launch": flops / max(1, kernel_launches),
                      "f_rhs": F_RHS, "f_step": F_STEP},
         "fma_probe_tflops": peaks,
+        "variants": variants,
         "clocks": clk,
         "gpu_launches": kernel_launches,
         "e2e": e2e,

@@ -17,8 +17,8 @@
 // one more factor h/T, so it is summed in FP32.
 //
 // The six stages run as a loop with one copy of the evaluation of Hamilton's
-// equations (the df64 code of six inlined copies overflows the instruction
-// cache); the stage differences live in small per-thread arrays.
+// equations (six inlined df64 copies overflow the instruction cache), and
+// every stage sum is kept in registers.
 #include <cuda_runtime.h>
 
 #include "df64.cuh"
@@ -114,7 +114,7 @@ __device__ __forceinline__ void rhs_df(const RayDF& K, df r, df th, df pr, df pt
 }
 
 // Cash-Karp coefficients for the df64 stepper. Stage s = 0..5 is the
-// tableau's stage s + 1.
+// tableau's stage s + 1; kA[t][s] = a_{t+1, s+1}.
 __constant__ float kA[6][6] = {
     {0, 0, 0, 0, 0, 0},
     {0, 0, 0, 0, 0, 0},
@@ -127,64 +127,93 @@ __constant__ float kCH[6] = {0.0f, 0.20000000298023224f, 0.30000001192092896f,
                              0.6000000238418579f, 1.0f, 0.875f};
 __constant__ float kCL[6] = {0.0f, -2.9802322831784522e-09f, -1.1920929132713809e-08f,
                              -2.3841858265427618e-08f, 0.0f, 0.0f};
-
-namespace dfk {
-// fifth-order weights b_3, b_4, b_6 (b_2 = b_5 = 0) as df
-constexpr float B3H = 0.4025764763355255f, B3L = 1.3197485770888306e-08f;
-constexpr float B4H = 0.21043771505355835f, B4L = -4.615847704059206e-09f;
-constexpr float B6H = 0.2891021966934204f, B6L = 5.452259976834739e-09f;
-// b_i - b*_i for i = 3..6 (i = 2 is zero) as df
-constexpr float D3H = 0.018668586388230324f, D3L = -2.943724985993157e-10f;
-constexpr float D4H = -0.03415502607822418f, D4L = -7.525838841004884e-10f;
-constexpr float D5H = -0.01932198740541935f, D5L = 7.982765004577175e-10f;
-constexpr float D6H = 0.03910220041871071f, D6L = 1.726969678372825e-09f;
-}  // namespace dfk
+// fifth-order weights b_s (zero for s = 0, 1, 4; b_1 multiplies d_1 = 0) and
+// error weights b_s - b*_s (zero for s = 0, 1), as df
+__constant__ float kBH[6] = {0.0f, 0.0f, 0.4025764763355255f, 0.21043771505355835f, 0.0f,
+                             0.2891021966934204f};
+__constant__ float kBL[6] = {0.0f, 0.0f, 1.3197485770888306e-08f, -4.615847704059206e-09f, 0.0f,
+                             5.452259976834739e-09f};
+__constant__ float kDH[6] = {0.0f, 0.0f, 0.018668586388230324f, -0.03415502607822418f,
+                             -0.01932198740541935f, 0.03910220041871071f};
+__constant__ float kDL[6] = {0.0f, 0.0f, -2.943724985993157e-10f, -7.525838841004884e-10f,
+                             7.982765004577175e-10f, 1.726969678372825e-09f};
 
 // One Cash-Karp attempt of length h from y, all in df64: o = fifth-order
 // result, d = fifth minus fourth order (FP32 is enough for the error test).
+// The six stages share one copy of the equations; as soon as stage s gives
+// d_s it is folded into the FP32 sums of the later stage inputs, the df64
+// increment sum and the df64 error sum, so no stage value is kept in memory.
 __device__ __forceinline__ void ck_step_df(const RayDF& K, const StateDF& y, df h, StateDF& o,
                                            float d[5], float& twoH) {
-  using namespace dfk;
-  df k1[5];
-  rhs_df(K, y.r, y.th, y.pr, y.pth, k1[0], k1[1], k1[2], k1[3], k1[4], twoH);
-  df hk1[5];
+  df k1[5], hk1[5], sb[5], sd[5];
+  float acc[4][4];  // FP32 sums sum_j a_tj d_j of stages t = 2..5; (r, theta, p_r, p_theta)
 #pragma unroll
-  for (int c = 0; c < 5; ++c) hk1[c] = df_mul(h, k1[c]);
+  for (int c = 0; c < 5; ++c) {
+    k1[c] = hk1[c] = sb[c] = sd[c] = mk(0.0f, 0.0f);
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[t][c] = 0.0f;
   const df y4[4] = {y.r, y.th, y.pr, y.pth};
   const float hf = h.hi;
-  float dv[6][4];  // d_s in FP32, components (r, theta, p_r, p_theta)
-  df ev[6][5];     // d_s in df64, components (r, theta, phi, p_r, p_theta)
+  twoH = 0.0f;
 #pragma unroll 1
-  for (int s = 1; s < 6; ++s) {
-    const df cs = mk(kCH[s], kCL[s]);
+  for (int s = 0; s < 6; ++s) {
     df in[4];
+    if (s == 0) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int kc = c < 2 ? c : c + 1;  // skip phi in k
-      float fs = 0.0f;
-      for (int t = 1; t < s; ++t) fs = fmaf(kA[s][t], dv[t][c], fs);
-      in[c] = df_add_f(df_add(y4[c], df_mul(hk1[kc], cs)), __fmul_rn(hf, fs));
+      for (int c = 0; c < 4; ++c) in[c] = y4[c];
+    } else {
+      const df cs = mk(kCH[s], kCL[s]);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int kc = c < 2 ? c : c + 1;  // skip phi in k
+        const float fs = s == 2 ? acc[0][c] : s == 3 ? acc[1][c] : s == 4 ? acc[2][c]
+                       : s == 5 ? acc[3][c] : 0.0f;
+        in[c] = df_add_f(df_add(y4[c], df_mul(hk1[kc], cs)), __fmul_rn(hf, fs));
+      }
     }
     df k[5];
-    float unused;
-    rhs_df(K, in[0], in[1], in[2], in[3], k[0], k[1], k[2], k[3], k[4], unused);
+    float h2;
+    rhs_df(K, in[0], in[1], in[2], in[3], k[0], k[1], k[2], k[3], k[4], h2);
+    if (s == 0) {
+      twoH = h2;
 #pragma unroll
-    for (int c = 0; c < 5; ++c) ev[s][c] = df_sub(k[c], k1[c]);
-    dv[s][0] = ev[s][0].hi;
-    dv[s][1] = ev[s][1].hi;
-    dv[s][2] = ev[s][3].hi;
-    dv[s][3] = ev[s][4].hi;
+      for (int c = 0; c < 5; ++c) {
+        k1[c] = k[c];
+        hk1[c] = df_mul(h, k[c]);
+      }
+      continue;
+    }
+    df e[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) e[c] = df_sub(k[c], k1[c]);
+    const float ds[4] = {e[0].hi, e[1].hi, e[3].hi, e[4].hi};
+#pragma unroll
+    for (int t = 2; t < 6; ++t) {
+      if (t > s) {
+        const float a = kA[t][s];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[t - 2][c] = fmaf(a, ds[c], acc[t - 2][c]);
+      }
+    }
+    if (s >= 2) {
+      const df bw = mk(kBH[s], kBL[s]);
+      const df dw = mk(kDH[s], kDL[s]);
+      const bool has_b = (s != 4);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        if (has_b) sb[c] = df_add(sb[c], df_mul(e[c], bw));
+        sd[c] = df_add(sd[c], df_mul(e[c], dw));
+      }
+    }
   }
   df inc[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    const df bs = df_add(df_mul(ev[5][c], mk(B6H, B6L)),
-                         df_add(df_mul(ev[3][c], mk(B4H, B4L)), df_mul(ev[2][c], mk(B3H, B3L))));
-    inc[c] = df_add(hk1[c], df_mul(h, bs));
-    const df ds =
-        df_add(df_add(df_mul(ev[5][c], mk(D6H, D6L)), df_mul(ev[4][c], mk(D5H, D5L))),
-               df_add(df_mul(ev[3][c], mk(D4H, D4L)), df_mul(ev[2][c], mk(D3H, D3L))));
-    d[c] = df_mul(h, ds).hi;
+    inc[c] = df_add(hk1[c], df_mul(h, sb[c]));
+    d[c] = df_mul(h, sd[c]).hi;
   }
   o.r = df_add(y.r, inc[0]);
   o.th = df_add(y.th, inc[1]);
