@@ -42,6 +42,10 @@ F_STEP = 258
 # status 1, r/theta/phi/max|H| 4x8, steps 4, cell_i/cell_j 2x2, parity 1.
 SHADOW_BYTES_PER_RAY = 42
 ORACLE_SAMPLE_STRIDE = 128  # CPU baseline: every 128th pixel of each render
+# DRAM bytes (read + write) of one FP64 trace launch over the 1024^2 set: ncu
+# capture of the same kernel at 512^2 (2.18 MB read + 88.87 MB written), scaled
+# by the 4x rays (profiles/trace_fp64_persistent_kerr12x512_dram.md).
+FP64_TRAFFIC_BYTES_PER_LAUNCH = 364.2e6
 
 
 def parse():
@@ -57,6 +61,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--serve-seconds", type=float, default=2.0)
     return p.parse_args()
 
 
@@ -346,6 +351,28 @@ def main():
                               "locate": vs["root_steps"] / (n_rays * args.steps)},
         }
 
+    # ---- served render stream: continuous batching (DF64) vs one render per
+    # launch (FP64 plain kernel), same Poisson arrivals ----
+    serving = None
+    if args.serve_seconds > 0 and precision == osr.FP64:
+        from paper_2202_00086_gb300 import serve, workloads as wl
+        arrivals = wl.served_stream(duration_s=args.serve_seconds)
+        offered = sum(rd["nx"] * rd["ny"] for _, rd in arrivals) / args.serve_seconds
+        barrier()
+        srv = serve.RenderServer(precision=osr.DF64, round_rays=1 << 21,
+                                 cell_phase_deg=common["cell_phase_deg"])
+        cb = srv.run(arrivals, realtime=True)
+        torch.cuda.synchronize()
+        base = serve.run_one_per_launch(arrivals, precision=osr.FP64, realtime=True,
+                                        cell_phase_deg=common["cell_phase_deg"])
+        serving = {"workload": "Poisson 50 renders/s for %g s (PCG64 seed 5), side log-uniform "
+                               "64..2048, a~U[0,0.998], incl~U[5,85] deg, shadow/disk 50/50, "
+                               "tol 1e-8/1e-10 50/50" % args.serve_seconds,
+                   "offered_rays_per_s": offered,
+                   "continuous_batching_df64": cb, "one_render_per_launch_fp64": base,
+                   "rays_per_s_ratio": (cb["rays_per_s"] / base["rays_per_s"]
+                                        if cb["rays_per_s"] and base["rays_per_s"] else None)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, dt, cores = run_oracle_sample(renders, ORACLE_SAMPLE_STRIDE)
@@ -383,7 +410,10 @@ def main():
                                     "status_error")},
         "max_abs_H": s["max_abs_H"],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (FP64_TRAFFIC_BYTES_PER_LAUNCH
+                                 if precision == osr.FP64 and args.side == 1024
+                                 and args.kernel == "batch" else None),
                      "peak_source": "FMA probe measured in this process (FP64 pipe)"
                                     if precision == osr.FP64 else
                                     "FMA probe measured in this process (FP32 pipe)",
@@ -391,6 +421,7 @@ def main():
                      "f_rhs": F_RHS, "f_step": F_STEP},
         "fma_probe_tflops": peaks,
         "variants": variants,
+        "serving": serving,
         "clocks": clk,
         "gpu_launches": kernel_launches,
         "e2e": e2e,

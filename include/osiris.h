@@ -168,13 +168,18 @@ int osiris_render_disk(const osiris_camera* cam, double r_in, double r_out,
                        const osiris_trace_opts* opts, const osiris_outputs* out,
                        void* cuda_stream);
 
-/* One render of a batch. */
+/* One render (or one contiguous range of its pixels) of a batch. */
 typedef struct {
     const osiris_camera* camera;
     int32_t disk;        /* 0: shadow/lensing, 1: thin disk */
     double r_in, r_out;  /* disk radii (disk = 1) */
     double tol;          /* per-request tolerance; <= 0 takes opts->tol */
-    osiris_outputs out;  /* DEVICE outputs of this request */
+    osiris_outputs out;  /* DEVICE outputs of the whole render (nx * ny entries) */
+    int64_t first_ray;   /* first pixel index traced by this entry */
+    int64_t n_rays;      /* pixels [first_ray, first_ray + n_rays) are traced and their
+                            outputs written; n_rays <= 0 means the whole render
+                            (first_ray must then be 0). A range must lie inside
+                            [0, nx * ny). */
 } osiris_request;
 
 /* Bytes of DEVICE workspace that osiris_trace_batch needs for n requests

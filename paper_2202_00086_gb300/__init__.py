@@ -53,7 +53,8 @@ class Outputs(ctypes.Structure):
 
 class Request(ctypes.Structure):
     _fields_ = [("camera", _vp), ("disk", ctypes.c_int32), ("r_in", _d), ("r_out", _d),
-                ("tol", _d), ("out", Outputs)]
+                ("tol", _d), ("out", Outputs), ("first_ray", ctypes.c_int64),
+                ("n_rays", ctypes.c_int64)]
 
 
 _lib = None
@@ -209,14 +210,12 @@ def render_disk(camera, r_in, r_out, out=None, stream=None, **opts):
     return out
 
 
-def trace_batch(requests, stream=None, **opts):
-    """One persistent launch over many renders (osiris_trace_batch).
-
-    requests: list of dicts with keys camera, disk (bool), r_in, r_out, tol
-    (<= 0: opts tol), out (dict of device tensors). opts must include a
-    workspace tensor of at least workspace_bytes(len(requests)) bytes."""
+def request_array(requests):
+    """ctypes array of osiris_request from dicts with keys camera, disk (bool),
+    r_in, r_out, tol (<= 0: the opts tol), out (dict of device tensors of the
+    whole render) and optionally first_ray / n_rays (a pixel range)."""
     n = len(requests)
-    arr = (Request * n)()
+    arr = (Request * max(1, n))()
     for k, q in enumerate(requests):
         arr[k].camera = q["camera"].handle
         arr[k].disk = 1 if q.get("disk") else 0
@@ -224,6 +223,18 @@ def trace_batch(requests, stream=None, **opts):
         arr[k].r_out = float(q.get("r_out") or 0.0)
         arr[k].tol = float(q.get("tol") or 0.0)
         arr[k].out = outputs_struct(q["out"])
+        arr[k].first_ray = int(q.get("first_ray") or 0)
+        arr[k].n_rays = int(q.get("n_rays") or 0)
+    return arr
+
+
+def trace_batch(requests, stream=None, **opts):
+    """One persistent launch over many renders (osiris_trace_batch).
+
+    requests: see request_array. opts must include a workspace tensor of at
+    least workspace_bytes(len(requests)) bytes."""
+    n = len(requests)
+    arr = request_array(requests)
     o = make_opts(**opts)
     _check(lib().osiris_trace_batch(arr, n, ctypes.byref(o), _stream_handle(stream)),
            "osiris_trace_batch")
@@ -239,14 +250,7 @@ def trace_batch_static(requests, stream=None, **opts):
     fn = L.osiris_trace_batch_static
     fn.argtypes = [_P(Request), ctypes.c_int32, _P(TraceOpts), _vp]
     n = len(requests)
-    arr = (Request * max(1, n))()
-    for k, q in enumerate(requests):
-        arr[k].camera = q["camera"].handle
-        arr[k].disk = 1 if q.get("disk") else 0
-        arr[k].r_in = float(q.get("r_in") or 0.0)
-        arr[k].r_out = float(q.get("r_out") or 0.0)
-        arr[k].tol = float(q.get("tol") or 0.0)
-        arr[k].out = outputs_struct(q["out"])
+    arr = request_array(requests)
     o = make_opts(**opts)
     _check(fn(arr, n, ctypes.byref(o), _stream_handle(stream)), "osiris_trace_batch_static")
     return requests

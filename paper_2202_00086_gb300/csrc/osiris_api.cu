@@ -94,6 +94,17 @@ void fill_camera(ReqDev& R, const osiris_camera* c) {
   R.explicit_states = 0;
   R.states = R.E = R.L = nullptr;
   R.n_rays = static_cast<int64_t>(c->nx) * c->ny;
+  R.pixel_offset = 0;
+}
+
+// Pixel range of a batch entry (the whole render when n_rays <= 0).
+int apply_range(ReqDev& R, const osiris_request& q) {
+  if (q.n_rays <= 0) return q.first_ray == 0 ? OSIRIS_OK : OSIRIS_EINVAL;
+  if (q.first_ray < 0 || q.first_ray > R.n_rays || q.n_rays > R.n_rays - q.first_ray)
+    return OSIRIS_EINVAL;
+  R.pixel_offset = q.first_ray;
+  R.n_rays = q.n_rays;
+  return OSIRIS_OK;
 }
 
 int cuda_rc(int e) { return e == 0 ? OSIRIS_OK : OSIRIS_ECUDA; }
@@ -263,6 +274,7 @@ int osiris_trace_batch(const osiris_request* reqs, int32_t n, const osiris_trace
     std::memset(&R, 0, sizeof(R));
     fill_common(R, q.camera->a, q.camera->r0, o, q.tol, q.disk, q.r_in, q.r_out, &q.out);
     fill_camera(R, q.camera);
+    if (int rc = apply_range(R, q)) return rc;
     R.ray_begin = begin;
     begin += R.n_rays;
   }
@@ -303,6 +315,7 @@ int osiris_trace_states(double a, double r_obs, const double* states, const doub
   R.ny = 1;
   R.n_rays = n;
   R.ray_begin = 0;
+  R.pixel_offset = 0;
   args.n_req = 1;
   args.total_rays = n;
   args.stats = reinterpret_cast<unsigned long long*>(o->stats);
@@ -416,6 +429,7 @@ extern "C" int osiris_trace_batch_static(const osiris_request* reqs, int32_t n,
     std::memset(&R, 0, sizeof(R));
     fill_common(R, q.camera->a, q.camera->r0, &o, q.tol, q.disk, q.r_in, q.r_out, &q.out);
     fill_camera(R, q.camera);
+    if (int rc = apply_range(R, q)) return rc;
     R.ray_begin = begin;
     begin += R.n_rays;
   }

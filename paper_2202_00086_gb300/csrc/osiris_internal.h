@@ -36,8 +36,8 @@ struct alignas(16) ReqDev {
   // celestial checkerboard
   double cell_rad, phase_rad;
   int32_t n_th_cells, n_ph_cells;
-  // position in the launch's global ray queue
-  int64_t ray_begin, n_rays;
+  // position in the launch's global ray queue; pixel index of its first ray
+  int64_t ray_begin, n_rays, pixel_offset;
   osiris_outputs out;
 };
 

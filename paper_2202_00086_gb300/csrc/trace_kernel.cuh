@@ -28,7 +28,7 @@ struct RayInfo {
 __device__ __forceinline__ void load_ray(const KernelArgs& A, int64_t g, RayInfo& I, State& y) {
   I.req = find_request(A, g);
   const ReqDev* R = request_of(A, I.req);
-  I.local = g - R->ray_begin;
+  I.local = g - R->ray_begin + R->pixel_offset;
   const double a = R->a;
   I.K.a = a;
   I.K.a2 = a * a;

@@ -1,0 +1,59 @@
+"""The continuous-batching server on the GPU: each render's outputs are the
+same (bitwise) alone and in the mix, for shadow and disk renders of different
+sizes and tolerances split over several rounds."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2202_00086_gb300 as osr
+from paper_2202_00086_gb300 import serve, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _stream(seed=7, n=10):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        side = int(rng.choice([8, 24, 40, 64]))
+        a = float(rng.uniform(0.0, 0.998))
+        inc = float(rng.uniform(5.0, 85.0))
+        tol = 1e-8 if k % 3 == 0 else 1e-10
+        if k % 2:
+            rd = workloads.render(a, 1000.0, inc, (-25, 25, -25, 25), side, side, mode="disk",
+                                  r_in="isco", r_out=20.0, tol=tol)
+        else:
+            rd = workloads.render(a, 1000.0, inc, (-8, 8, -8, 8), side, side + 2, tol=tol)
+        out.append((0.002 * k, rd))
+    return out
+
+
+def _alone(rd, precision, phase):
+    cam = osr.Camera.from_render(rd)
+    if rd["mode"] == "disk":
+        out = osr.render_disk(cam, osr.resolve_r_in(rd), rd["r_out"], tol=rd["tol"],
+                              precision=precision, cell_phase_deg=phase)
+    else:
+        out = osr.trace(cam, tol=rd["tol"], precision=precision, cell_phase_deg=phase)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+@pytest.mark.parametrize("precision", [osr.DF64, osr.FP64])
+def test_alone_equals_in_the_mix(precision):
+    phase = workloads.checker_phase_deg(2202)
+    arrivals = _stream()
+    srv = serve.RenderServer(precision=precision, round_rays=3000, min_chunk=500,
+                             keep_outputs=True, cell_phase_deg=phase, max_inflight=2)
+    summary = srv.run(arrivals, realtime=True)
+    torch.cuda.synchronize()
+    assert summary["renders"] == len(arrivals)
+    assert srv.rounds > 3
+    assert max(srv.round_entries) > 1  # renders shared launches
+    by_id = {r.rid: r for r in srv.done}
+    for rid, (_, rd) in enumerate(arrivals):
+        got = {k: v.cpu().numpy() for k, v in by_id[rid].out.items()}
+        ref = _alone(rd, precision, phase)
+        for k in ref:
+            assert np.array_equal(got[k], ref[k]), (rid, k)
+    assert summary["p99_latency_s"] >= summary["p50_latency_s"] > 0

@@ -1,0 +1,110 @@
+"""Host logic of the render server, with a fake backend (no GPU): every pixel
+of every admitted render is launched exactly once, rounds respect the ray and
+entry budgets, admission respects the HBM budget, and oversize renders are
+rejected."""
+import numpy as np
+
+from paper_2202_00086_gb300 import serve, workloads
+
+
+class FakeEvent:
+    def __init__(self, ready_after):
+        self.left = ready_after
+
+    def query(self):
+        self.left -= 1
+        return self.left < 0
+
+
+class FakeBackend:
+    def __init__(self, server_ref, delay=2):
+        self.server_ref = server_ref
+        self.delay = delay
+        self.rounds = []
+        self.max_bytes_seen = 0
+
+    def workspace(self, nbytes):
+        return object()
+
+    def camera(self, rd):
+        return ("camera", rd["nx"], rd["ny"])
+
+    def resolve_r_in(self, rd):
+        return 6.0 if rd["r_in"] == "isco" else rd["r_in"]
+
+    def outputs(self, n, disk):
+        return {"hits": np.zeros(n, dtype=np.int64)}
+
+    def launch(self, entries, ws, **opts):
+        self.rounds.append([(e["first_ray"], e["n_rays"]) for e in entries])
+        for e in entries:
+            e["out"]["hits"][e["first_ray"]:e["first_ray"] + e["n_rays"]] += 1
+        srv = self.server_ref[0]
+        self.max_bytes_seen = max(self.max_bytes_seen, srv.bytes_in_use)
+        return FakeEvent(self.delay)
+
+
+def _server(**kw):
+    ref = [None]
+    be = FakeBackend(ref)
+    srv = serve.RenderServer(backend=be, keep_outputs=True, **kw)
+    ref[0] = srv
+    return srv, be
+
+
+def test_every_pixel_once_and_budgets():
+    reqs = workloads.uneven_batch(n=40, seed=4, sides=(16, 32, 64, 128))
+    budget_rays = 20000
+    srv, be = _server(round_rays=budget_rays, min_chunk=1000, max_entries=16,
+                      hbm_budget_bytes=3 * 128 * 128 * 66, max_inflight=2)
+    summary = srv.run([(0.0, rd) for rd in reqs], realtime=False, poll_s=0)
+    assert summary["renders"] == len(reqs) and summary["rejected"] == 0
+    for r in srv.done:
+        assert np.all(r.out["hits"] == 1)
+        # ranges are contiguous and in order
+        pos = 0
+        for first, n in r.chunks:
+            assert first == pos and n > 0
+            pos += n
+        assert pos == r.n_rays
+    for rnd in be.rounds:
+        assert sum(n for _, n in rnd) <= budget_rays
+        assert len(rnd) <= 16
+    assert be.max_bytes_seen <= srv.hbm_budget
+    assert srv.bytes_in_use == 0
+
+
+def test_small_render_finishes_in_its_first_round():
+    big = workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 512, 512)
+    small = workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 16, 16)
+    srv, be = _server(round_rays=50000, min_chunk=4096, max_inflight=1)
+    srv.submit(big, arrival=0.0)
+    srv.step()  # big alone in round 1
+    srv.submit(small, arrival=0.0)
+    while not srv.idle():
+        srv.step()
+    small_r = [r for r in srv.done if r.n_rays == 256][0]
+    assert len(small_r.chunks) == 1
+    # the small render joined the second round, next to the big one
+    assert any(len(rnd) == 2 for rnd in be.rounds[1:3])
+
+
+def test_oversize_render_rejected():
+    rd = workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 256, 256)
+    srv, _ = _server(hbm_budget_bytes=1000)
+    r = srv.submit(rd)
+    assert r in srv.rejected and srv.idle()
+
+
+def test_summary_percentiles():
+    class R:
+        pass
+    done = []
+    for k in range(100):
+        r = R()
+        r.arrival, r.t_done, r.n_rays = 0.0, float(k + 1), 10
+        done.append(r)
+    s = serve.summarize(done, 0.0, 100.0)
+    assert abs(s["p50_latency_s"] - 50.5) < 1e-9
+    assert abs(s["p99_latency_s"] - 99.01) < 1e-9
+    assert s["rays"] == 1000 and abs(s["rays_per_s"] - 10.0) < 1e-12
