@@ -356,15 +356,26 @@ def main():
     serving = None
     if args.serve_seconds > 0 and precision == osr.FP64:
         from paper_2202_00086_gb300 import serve, workloads as wl
-        arrivals = wl.served_stream(duration_s=args.serve_seconds)
-        offered = sum(rd["nx"] * rd["ny"] for _, rd in arrivals) / args.serve_seconds
+        all_arrivals = wl.served_stream(duration_s=args.serve_seconds)
+        offered = sum(rd["nx"] * rd["ny"] for _, rd in all_arrivals) / args.serve_seconds
+        arrivals = serve.shard(all_arrivals, rank, world)  # whole renders per GPU
         barrier()
         srv = serve.RenderServer(precision=osr.DF64, round_rays=1 << 21,
                                  cell_phase_deg=common["cell_phase_deg"])
         cb = srv.run(arrivals, realtime=True)
         torch.cuda.synchronize()
+        cb_rec = serve.local_record(srv.done)
+        barrier()
         base = serve.run_one_per_launch(arrivals, precision=osr.FP64, realtime=True,
                                         cell_phase_deg=common["cell_phase_deg"])
+        if dist is not None:
+            recs = [None] * world
+            dist.all_gather_object(recs, cb_rec)
+            cb = serve.merge_records(recs, launches=cb["launches"])
+            brecs = [None] * world
+            dist.all_gather_object(brecs, base["record"])
+            base = serve.merge_records(brecs, launches=base["launches"])
+        base.pop("record", None)
         serving = {"workload": "Poisson 50 renders/s for %g s (PCG64 seed 5), side log-uniform "
                                "64..2048, a~U[0,0.998], incl~U[5,85] deg, shadow/disk 50/50, "
                                "tol 1e-8/1e-10 50/50" % args.serve_seconds,

@@ -214,6 +214,36 @@ class RenderServer:
                          launches=self.launches)
 
 
+def shard(arrivals, rank, world):
+    """Round-robin share of a render stream (list of (arrival_s, render)) for
+    GPU `rank` of `world`: rays are independent, so renders are dealt out
+    whole and no data moves between GPUs."""
+    ordered = sorted(arrivals, key=lambda x: x[0])
+    return [a for k, a in enumerate(ordered) if k % world == rank]
+
+
+def local_record(done):
+    """Per-GPU part of a multi-GPU summary: latencies, rays and time span."""
+    if not done:
+        return {"latencies": [], "rays": 0, "span": 0.0}
+    return {"latencies": [r.t_done - r.arrival for r in done],
+            "rays": sum(r.n_rays for r in done),
+            "span": max(r.t_done for r in done) - min(r.arrival for r in done)}
+
+
+def merge_records(records, launches=0):
+    """Whole-job summary from the local records of every GPU: percentiles
+    over all renders, rays/s = all rays / the longest span."""
+    lat = np.array([x for rec in records for x in rec["latencies"]])
+    rays = sum(rec["rays"] for rec in records)
+    span = max((rec["span"] for rec in records), default=0.0)
+    return {"renders": int(lat.size), "rays": rays,
+            "p50_latency_s": float(np.percentile(lat, 50)) if lat.size else None,
+            "p99_latency_s": float(np.percentile(lat, 99)) if lat.size else None,
+            "max_latency_s": float(lat.max()) if lat.size else None,
+            "rays_per_s": rays / span if span > 0 else None, "launches": launches}
+
+
 def osr_workspace_bytes(osr, n):
     return osr.workspace_bytes(n)
 
@@ -253,7 +283,9 @@ def run_one_per_launch(arrivals, precision=None, realtime=True, clock=time.perf_
         r.t_done = clock()
         r.out = None
         done.append(r)
-    return summarize(done, t0, clock(), launches=len(done))
+    out = summarize(done, t0, clock(), launches=len(done))
+    out["record"] = local_record(done)
+    return out
 
 
 class _CudaBackend:
