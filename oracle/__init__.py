@@ -17,6 +17,7 @@ import numpy as np
 from . import build as _build
 
 STATUS_NONE, STATUS_CAPTURED, STATUS_ESCAPED, STATUS_DISK, STATUS_MAXSTEP, STATUS_ERROR = range(6)
+RKCK45, RKDP45 = 0, 1
 
 _P = ctypes.POINTER
 _d = ctypes.c_double
@@ -27,7 +28,7 @@ _i32 = ctypes.c_int32
 class OracleOptions(ctypes.Structure):
     _fields_ = [("tol", _d), ("max_steps", _i64), ("r_cap_factor", _d), ("r_esc_factor", _d),
                 ("disk", _i32), ("r_in", _d), ("r_out", _d), ("cell_deg", _d),
-                ("cell_phase_deg", _d)]
+                ("cell_phase_deg", _d), ("integrator", _i32)]
 
 
 _OUT_FIELDS = [
@@ -70,6 +71,9 @@ def lib():
         L.oracle_rhs.argtypes = [_d, _d, _P(_d), _d, _d, _P(_d)]
         L.oracle_ck_step.argtypes = [_d, _d, _P(_d), _d, _d, _d, _P(_d), _P(_d)]
         L.oracle_ck_tableau.argtypes = [_P(_d)] * 4
+        L.oracle_rk_step.argtypes = [_i32, _d, _d, _P(_d), _d, _d, _d, _P(_d), _P(_d)]
+        L.oracle_tableau.argtypes = [_i32] + [_P(_d)] * 4
+        L.oracle_tableau.restype = _i32
         L.oracle_disk_observables.argtypes = [_d, _d, _d, _d, _d, _P(_d), _P(_d)]
         L.oracle_isco.argtypes = [_d, _d]
         L.oracle_isco.restype = _d
@@ -82,9 +86,9 @@ def _ptr(arr, ct):
 
 
 def options(tol=1e-10, max_steps=1_000_000, r_cap_factor=1.01, r_esc_factor=1.1, disk=False,
-            r_in=0.0, r_out=0.0, cell_deg=10.0, cell_phase_deg=0.0):
+            r_in=0.0, r_out=0.0, cell_deg=10.0, cell_phase_deg=0.0, integrator=RKCK45):
     return OracleOptions(tol, max_steps, r_cap_factor, r_esc_factor, 1 if disk else 0, r_in,
-                         r_out, cell_deg, cell_phase_deg)
+                         r_out, cell_deg, cell_phase_deg, int(integrator))
 
 
 def _alloc(n):
@@ -175,6 +179,27 @@ def ck_step(a, y6, E, L_z, h, M=1.0):
     d = np.zeros(6)
     lib().oracle_ck_step(M, a, _ptr(y6, _d), E, L_z, h, _ptr(y5, _d), _ptr(d, _d))
     return y5, d
+
+
+def rk_step(integrator, a, y6, E, L_z, h, M=1.0):
+    """One step of the chosen embedded pair (Sec. 3.1): (y5, y5 - y4)."""
+    y6 = np.ascontiguousarray(y6, dtype=np.float64)
+    y5 = np.zeros(6)
+    d = np.zeros(6)
+    lib().oracle_rk_step(int(integrator), M, a, _ptr(y6, _d), E, L_z, h, _ptr(y5, _d),
+                         _ptr(d, _d))
+    return y5, d
+
+
+def tableau(integrator):
+    """(stages, c, A, b5, b4) of an integrator (7-entry arrays, zero padded)."""
+    c = np.zeros(7)
+    A = np.zeros(49)
+    b5 = np.zeros(7)
+    b4 = np.zeros(7)
+    n = lib().oracle_tableau(int(integrator), _ptr(c, _d), _ptr(A, _d), _ptr(b5, _d),
+                             _ptr(b4, _d))
+    return n, c, A.reshape(7, 7), b5, b4
 
 
 def ck_tableau():

@@ -18,6 +18,7 @@
  *                                                         of t', r', ..., p_theta'
  *      on the Kerr metric in Boyer-Lindquist form      -- Sec. 4.3, Eq. Kerr
  *   3. adaptive Runge-Kutta Cash-Karp 4(5) steps        -- Sec. 3.1 (RKCK45)
+ *      or Dormand-Prince 5(4) steps                      -- Sec. 3.1 (RKDP45)
  *   4. the Hamiltonian-constraint error |H| at every accepted point
  *                                                      -- Sec. 3.1, Error = |H_num|
  *   5. termination on the horizon buffer, the celestial sphere, or the
@@ -223,15 +224,17 @@ void rhs(const Spacetime& S, const Ray& R, const double y[NY], double dy[NY]) {
 // ---------------------------------------------------------------------------
 
 struct Tableau {
-  double c[6];
-  double a[6][6];
-  double b5[6];  // fifth-order weights (the solution that is propagated)
-  double b4[6];  // embedded fourth-order weights
+  int stages;    // 6 (Cash-Karp) or 7 (Dormand-Prince)
+  double c[7];
+  double a[7][7];
+  double b5[7];  // fifth-order weights (the solution that is propagated)
+  double b4[7];  // embedded fourth-order weights
 };
 
 Tableau make_cash_karp() {
   Tableau T;
   std::memset(&T, 0, sizeof(T));
+  T.stages = 6;
   T.c[0] = 0.0;
   T.c[1] = 1.0 / 5.0;
   T.c[2] = 3.0 / 10.0;
@@ -275,27 +278,88 @@ Tableau make_cash_karp() {
   return T;
 }
 
-const Tableau kCK = make_cash_karp();
+// Dormand & Prince (1980) 5(4), the RKDP45 scheme of Sec. 3.1: seven stages,
+// the last evaluated at the fifth-order solution (first same as last), so a
+// step costs six new evaluations.
+Tableau make_dormand_prince() {
+  Tableau T;
+  std::memset(&T, 0, sizeof(T));
+  T.stages = 7;
+  T.c[0] = 0.0;
+  T.c[1] = 1.0 / 5.0;
+  T.c[2] = 3.0 / 10.0;
+  T.c[3] = 4.0 / 5.0;
+  T.c[4] = 8.0 / 9.0;
+  T.c[5] = 1.0;
+  T.c[6] = 1.0;
 
-// One Cash-Karp step of length h from y: y5 is the fifth-order result and
-// delta = y5 - y4 is the embedded error estimate.
-void ck_step(const Spacetime& S, const Ray& R, const double y[NY], double h, double y5[NY],
-             double delta[NY]) {
-  double k[6][NY];
+  T.a[1][0] = 1.0 / 5.0;
+
+  T.a[2][0] = 3.0 / 40.0;
+  T.a[2][1] = 9.0 / 40.0;
+
+  T.a[3][0] = 44.0 / 45.0;
+  T.a[3][1] = -56.0 / 15.0;
+  T.a[3][2] = 32.0 / 9.0;
+
+  T.a[4][0] = 19372.0 / 6561.0;
+  T.a[4][1] = -25360.0 / 2187.0;
+  T.a[4][2] = 64448.0 / 6561.0;
+  T.a[4][3] = -212.0 / 729.0;
+
+  T.a[5][0] = 9017.0 / 3168.0;
+  T.a[5][1] = -355.0 / 33.0;
+  T.a[5][2] = 46732.0 / 5247.0;
+  T.a[5][3] = 49.0 / 176.0;
+  T.a[5][4] = -5103.0 / 18656.0;
+
+  T.a[6][0] = 35.0 / 384.0;
+  T.a[6][1] = 0.0;
+  T.a[6][2] = 500.0 / 1113.0;
+  T.a[6][3] = 125.0 / 192.0;
+  T.a[6][4] = -2187.0 / 6784.0;
+  T.a[6][5] = 11.0 / 84.0;
+
+  for (int j = 0; j < 7; ++j) T.b5[j] = T.a[6][j];  // b5 = last row, b5[6] = 0
+
+  T.b4[0] = 5179.0 / 57600.0;
+  T.b4[1] = 0.0;
+  T.b4[2] = 7571.0 / 16695.0;
+  T.b4[3] = 393.0 / 640.0;
+  T.b4[4] = -92097.0 / 339200.0;
+  T.b4[5] = 187.0 / 2100.0;
+  T.b4[6] = 1.0 / 40.0;
+  return T;
+}
+
+const Tableau kCK = make_cash_karp();
+const Tableau kDP = make_dormand_prince();
+
+enum Integrator { kRKCK45 = 0, kRKDP45 = 1 };
+
+const Tableau& tableau(int integrator) { return integrator == kRKDP45 ? kDP : kCK; }
+
+// One embedded Runge-Kutta step of length h from y with tableau T: y5 is the
+// fifth-order result and delta = y5 - y4 the embedded error estimate. Every
+// stage is evaluated here (the first-same-as-last saving of Dormand-Prince is
+// an optimisation that does not change the result).
+void rk_step(const Tableau& T, const Spacetime& S, const Ray& R, const double y[NY], double h,
+             double y5[NY], double delta[NY]) {
+  double k[7][NY];
   double yi[NY];
-  for (int stage = 0; stage < 6; ++stage) {
+  for (int stage = 0; stage < T.stages; ++stage) {
     for (int n = 0; n < NY; ++n) {
       double acc = 0.0;
-      for (int j = 0; j < stage; ++j) acc += kCK.a[stage][j] * k[j][n];
+      for (int j = 0; j < stage; ++j) acc += T.a[stage][j] * k[j][n];
       yi[n] = y[n] + h * acc;
     }
     rhs(S, R, yi, k[stage]);
   }
   for (int n = 0; n < NY; ++n) {
     double s5 = 0.0, sd = 0.0;
-    for (int j = 0; j < 6; ++j) {
-      s5 += kCK.b5[j] * k[j][n];
-      sd += (kCK.b5[j] - kCK.b4[j]) * k[j][n];
+    for (int j = 0; j < T.stages; ++j) {
+      s5 += T.b5[j] * k[j][n];
+      sd += (T.b5[j] - T.b4[j]) * k[j][n];
     }
     y5[n] = y[n] + h * s5;
     delta[n] = h * sd;
@@ -351,6 +415,7 @@ double pixel_y(const Camera& cam, int64_t j) {
 // ---------------------------------------------------------------------------
 
 struct Options {
+  int integrator;        // kRKCK45 or kRKDP45
   double tol;            // per-step error tolerance
   int64_t max_steps;     // cap on accepted + rejected attempts
   double r_cap_factor;   // captured when r < r_cap_factor * r_H
@@ -390,14 +455,15 @@ double surface_function(Surface kind, const double y[NY], double r_cap, double r
 // Bisection of the last step length (Sec. 4.1 stopping surfaces; the disk of
 // Sec. 5): the root of F(step(y, h')) for h' in [0, h] is bracketed and
 // halved 52 times. Returns the upper end of the bracket and the state there.
-double bisect_step(const Spacetime& S, const Ray& R, const double y[NY], double h, Surface kind,
-                   double r_cap, double r_esc, double y_out[NY], int64_t* n_steps) {
+double bisect_step(const Tableau& T, const Spacetime& S, const Ray& R, const double y[NY],
+                   double h, Surface kind, double r_cap, double r_esc, double y_out[NY],
+                   int64_t* n_steps) {
   double lo = 0.0, hi = h;
   const bool start_positive = surface_function(kind, y, r_cap, r_esc) > 0.0;
   double ytry[NY], dtry[NY];
   for (int it = 0; it < 52; ++it) {
     const double mid = 0.5 * (lo + hi);
-    ck_step(S, R, y, mid, ytry, dtry);
+    rk_step(T, S, R, y, mid, ytry, dtry);
     ++*n_steps;
     const double f = surface_function(kind, ytry, r_cap, r_esc);
     if ((f > 0.0) == start_positive && f != 0.0)
@@ -405,7 +471,7 @@ double bisect_step(const Spacetime& S, const Ray& R, const double y[NY], double 
     else
       hi = mid;
   }
-  ck_step(S, R, y, hi, y_out, dtry);
+  rk_step(T, S, R, y, hi, y_out, dtry);
   ++*n_steps;
   return hi;
 }
@@ -471,6 +537,7 @@ Result integrate(const Spacetime& S, const Ray& R, const double y_init[NY], doub
 
   const double r_cap = o.r_cap_factor * horizon_radius(S);
   const double r_esc = o.r_esc_factor * r0;
+  const Tableau& T = tableau(o.integrator);
 
   double y[NY];
   std::memcpy(y, y_init, sizeof(y));
@@ -491,7 +558,7 @@ Result integrate(const Spacetime& S, const Ray& R, const double y_init[NY], doub
       break;
     }
     const double hs = std::min(h, 0.1 * y[Y_R]);
-    ck_step(S, R, y, hs, y5, delta);
+    rk_step(T, S, R, y, hs, y5, delta);
 
     double err = 0.0;
     for (int m = 0; m < 5; ++m) {
@@ -512,7 +579,7 @@ Result integrate(const Spacetime& S, const Ray& R, const double y_init[NY], doub
 
       if (o.disk && crosses_equator(y, y5)) {
         double yc[NY];
-        bisect_step(S, R, y, hs, kEquator, r_cap, r_esc, yc, &bis);
+        bisect_step(T, S, R, y, hs, kEquator, r_cap, r_esc, yc, &bis);
         if (yc[Y_R] >= o.r_in && yc[Y_R] <= o.r_out) {
           out.status = kDisk;
           std::memcpy(yfin, yc, sizeof(yc));
@@ -520,12 +587,12 @@ Result integrate(const Spacetime& S, const Ray& R, const double y_init[NY], doub
         }
       }
       if (y5[Y_R] < r_cap) {
-        bisect_step(S, R, y, hs, kCapture, r_cap, r_esc, yfin, &bis);
+        bisect_step(T, S, R, y, hs, kCapture, r_cap, r_esc, yfin, &bis);
         out.status = kCaptured;
         break;
       }
       if (y5[Y_R] > r_esc) {
-        bisect_step(S, R, y, hs, kEscape, r_cap, r_esc, yfin, &bis);
+        bisect_step(T, S, R, y, hs, kEscape, r_cap, r_esc, yfin, &bis);
         out.status = kEscaped;
         break;
       }
@@ -604,6 +671,7 @@ struct oracle_options {
   double r_out;
   double cell_deg;
   double cell_phase_deg;
+  int32_t integrator;  // 0 = Cash-Karp 4(5), 1 = Dormand-Prince 5(4)
 };
 
 static void store(const Result& R, oracle_outputs* o, int64_t k) {
@@ -632,6 +700,7 @@ static void store(const Result& R, oracle_outputs* o, int64_t k) {
 
 static Options to_options(const oracle_options* oo) {
   Options o;
+  o.integrator = oo->integrator;
   o.tol = oo->tol;
   o.max_steps = oo->max_steps;
   o.r_cap_factor = oo->r_cap_factor;
@@ -760,7 +829,12 @@ void oracle_rhs(double M, double a, const double* y6, double E, double L, double
 
 void oracle_ck_step(double M, double a, const double* y6, double E, double L, double h,
                     double* y5_out, double* delta_out) {
-  ck_step(Spacetime{M, a}, Ray{E, L}, y6, h, y5_out, delta_out);
+  rk_step(kCK, Spacetime{M, a}, Ray{E, L}, y6, h, y5_out, delta_out);
+}
+
+void oracle_rk_step(int32_t integrator, double M, double a, const double* y6, double E, double L,
+                    double h, double* y5_out, double* delta_out) {
+  rk_step(tableau(integrator), Spacetime{M, a}, Ray{E, L}, y6, h, y5_out, delta_out);
 }
 
 // Cash-Karp tableau: c[6], a[36] (row-major, lower triangular), b5[6], b4[6].
@@ -771,6 +845,19 @@ void oracle_ck_tableau(double* c, double* a, double* b5, double* b4) {
     b4[i] = kCK.b4[i];
     for (int j = 0; j < 6; ++j) a[6 * i + j] = kCK.a[i][j];
   }
+}
+
+// Tableau of an integrator: c[7], a[49] (row-major), b5[7], b4[7]; returns the
+// number of stages (unused entries are zero).
+int32_t oracle_tableau(int32_t integrator, double* c, double* a, double* b5, double* b4) {
+  const Tableau& T = tableau(integrator);
+  for (int i = 0; i < 7; ++i) {
+    c[i] = T.c[i];
+    b5[i] = T.b5[i];
+    b4[i] = T.b4[i];
+    for (int j = 0; j < 7; ++j) a[7 * i + j] = T.a[i][j];
+  }
+  return T.stages;
 }
 
 void oracle_disk_observables(double M, double a, double r, double E, double L, double* g,

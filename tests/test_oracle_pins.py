@@ -510,3 +510,89 @@ def test_cash_karp_convergence_order():
     # pre-asymptotic at the coarse end, ~5.0 once h is small enough
     assert 4.6 < orders[0] < 6.2
     assert 4.7 < orders[1] < 5.3
+
+
+# ---------------------------------------------------------------------------
+# Dormand-Prince 5(4) (Sec. 3.1, the paper's preferred integrator)
+# ---------------------------------------------------------------------------
+
+def test_dormand_prince_tableau():
+    n, c, A, b5, b4 = oracle.tableau(oracle.RKDP45)
+    assert n == 7
+    assert np.allclose(A.sum(axis=1), c, atol=1e-15)
+    # first same as last: the seventh stage is evaluated at the fifth-order solution
+    assert np.array_equal(A[6], b5) and c[6] == 1.0 and b5[6] == 0.0
+    res5 = _order_conditions(A, b5, c, 5)
+    assert max(abs(r) for _, r in res5) < 1e-14
+    res4 = _order_conditions(A, b4, c, 5)
+    assert max(abs(r) for o, r in res4 if o <= 4) < 1e-14
+    assert max(abs(r) for o, r in res4 if o == 5) > 1e-5
+    # the Cash-Karp tableau is unchanged by the generic stepper
+    nc, cc, Ac, b5c, b4c = oracle.tableau(oracle.RKCK45)
+    c0, A0, b50, b40 = oracle.ck_tableau()
+    assert nc == 6 and np.array_equal(Ac[:6, :6], A0) and np.array_equal(b5c[:6], b50)
+
+
+def test_dormand_prince_convergence_order():
+    r0, th0 = 10.0, 1.0
+    x, y = 3.0, -2.0
+    st = oracle.init_ray(0.0, r0, math.degrees(th0), x, y, M=0.0)
+    n0, v = _initial_direction(x, y, r0, th0)
+    lam = 12.0
+    Xf = r0 * n0 + lam * v
+    r_ex = np.linalg.norm(Xf)
+    th_ex, ph_ex = _angles(Xf / r_ex)
+    errs = []
+    for nsteps in (80, 160, 320):
+        yv = st[:6].copy()
+        for _ in range(nsteps):
+            yv, _d = oracle.rk_step(oracle.RKDP45, 0.0, yv, st[6], st[7], lam / nsteps, M=0.0)
+        errs.append(max(abs(yv[1] - r_ex), abs(yv[2] - th_ex),
+                        abs((yv[3] - ph_ex + math.pi) % (2 * math.pi) - math.pi)))
+    orders = [math.log2(e1 / e2) for e1, e2 in zip(errs, errs[1:])]
+    assert 4.6 < orders[1] < 5.6
+
+
+def test_dormand_prince_deflection_and_flags():
+    """The DP45 path reaches the same exact results: Schwarzschild deflection
+    and the finite-r0 critical curve."""
+    r0, inc = 1000.0, 85.0
+    th0 = math.radians(inc)
+    for x, y in [(-6.5, 0.7), (7.0, -3.0)]:
+        st = oracle.init_ray(0.0, r0, inc, x, y)
+        res = oracle.trace_states(0.0, r0, st[None, :6], [st[6]], [st[7]],
+                                  integrator=oracle.RKDP45)
+        b = math.hypot(x, y) / math.sqrt(1 - 2 / r0)
+        Phi = _deflection_sweep(b, r0, 1.1 * r0)
+        n0, v = _initial_direction(x, y, r0, th0)
+        nrm = np.cross(n0, v)
+        nrm /= np.linalg.norm(nrm)
+        uf = n0 * math.cos(Phi) + np.cross(nrm, n0) * math.sin(Phi)
+        th, ph = _angles(uf)
+        _ang_close(res["theta"][0], res["phi"][0] % (2 * math.pi), th, ph, 1e-8)
+    a, inc, n = 0.9, 60.0, 16
+    ext = (-8.0, 8.0, -8.0, 8.0)
+    res = oracle.trace_pixels(a, R0, inc, ext, n, n, integrator=oracle.RKDP45)
+    flags = np.zeros((n, n), bool)
+    for j in range(n):
+        for i in range(n):
+            xx = ext[0] + (i + 0.5) * 16 / n
+            yy = ext[2] + (j + 0.5) * 16 / n
+            flags[j, i] = _captured_by_radial_potential(a, oracle.init_ray(a, R0, inc, xx, yy))
+    got = (res["status"] == oracle.STATUS_CAPTURED).reshape(n, n)
+    keep = ~_band_mask(flags)
+    assert np.array_equal(got[keep], flags[keep])
+
+
+def test_dormand_prince_keeps_H_smaller():
+    """Sec. 3.1-3.2: Dormand-Prince preserves the constraint better than
+    Cash-Karp. At the same tolerance its mean |H| is lower on escaped rays and
+    much lower near the horizon."""
+    out = {}
+    for integ in (oracle.RKCK45, oracle.RKDP45):
+        r = oracle.trace_pixels(0.98, R0, 90.0, (-8, 8, -8, 8), 32, 32, integrator=integ)
+        esc = r["status"] == oracle.STATUS_ESCAPED
+        cap = r["status"] == oracle.STATUS_CAPTURED
+        out[integ] = (r["max_abs_H"][esc].mean(), r["max_abs_H"][cap].mean())
+    assert out[oracle.RKDP45][0] < out[oracle.RKCK45][0]
+    assert out[oracle.RKDP45][1] < out[oracle.RKCK45][1] / 5
