@@ -54,6 +54,11 @@ extern "C" {
                           48-bit significand) on the FP32 pipe; FP64 state
                           and controller */
 
+/* ---- integrator (Sec. 3.1) -------------------------------------------- */
+#define OSIRIS_RKCK45 0 /* Cash-Karp 4(5), six evaluations per attempt */
+#define OSIRIS_RKDP45 1 /* Dormand-Prince 5(4), first same as last: six new
+                           evaluations per attempt (FP64 and DF64 only) */
+
 /* ---- counters written to osiris_trace_opts.stats (uint64 each) --------- */
 #define OSIRIS_STAT_RAYS 0          /* rays finished */
 #define OSIRIS_STAT_ACCEPTED 1      /* accepted Cash-Karp steps */
@@ -92,6 +97,7 @@ typedef struct {
                               for osiris_trace_batch. Not shared between calls
                               that may run at the same time. */
     size_t workspace_bytes;
+    int32_t integrator;    /* OSIRIS_RKCK45 (default) or OSIRIS_RKDP45 */
 } osiris_trace_opts;
 
 /* Per-ray outputs: DEVICE arrays with one entry per ray (NULL = not wanted).
@@ -124,9 +130,9 @@ typedef struct {
     double* r_hit;
 } osiris_outputs;
 
-/* Sets the defaults: tol 1e-10, max_steps 1e6, FP64, non-persistent,
- * r_cap_factor 1.01, r_esc_factor 1.1, 10-degree cells, phase 0, library
- * block size, no stats, no workspace. */
+/* Sets the defaults: tol 1e-10, max_steps 1e6, FP64, Cash-Karp,
+ * non-persistent, r_cap_factor 1.01, r_esc_factor 1.1, 10-degree cells,
+ * phase 0, library block size, no stats, no workspace. */
 void osiris_default_opts(osiris_trace_opts* opts);
 
 /* Create a camera (Sec. 2.3, Eq. momentums; observer at t0 = 0, phi0 = 0):

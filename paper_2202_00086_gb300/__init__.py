@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libosiris.so")
 OK, EINVAL, ECUDA, ENOMEM, ETIMEOUT = 0, -1, -2, -3, -4
 STATUS_NONE, STATUS_CAPTURED, STATUS_ESCAPED, STATUS_DISK, STATUS_MAXSTEP, STATUS_ERROR = range(6)
 FP64, MIXED, DF64 = 0, 1, 2
+RKCK45, RKDP45 = 0, 1
 STATS_LEN = 16
 STAT_NAMES = ["rays", "accepted", "rejected", "root_steps", "rhs_evals", "status_none",
               "status_captured", "status_escaped", "status_disk", "status_maxstep",
@@ -35,7 +36,7 @@ class TraceOpts(ctypes.Structure):
                 ("persistent", ctypes.c_int32), ("r_cap_factor", _d), ("r_esc_factor", _d),
                 ("cell_deg", _d), ("cell_phase_deg", _d), ("block_size", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("stats", _vp), ("workspace", _vp),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("integrator", ctypes.c_int32)]
 
 
 OUTPUT_FIELDS = [("status", torch.uint8), ("r", torch.float64), ("theta", torch.float64),
@@ -151,7 +152,7 @@ def workspace_bytes(n_requests=1):
 
 def make_opts(tol=1e-10, max_steps=1_000_000, precision=FP64, persistent=False,
               r_cap_factor=1.01, r_esc_factor=1.1, cell_deg=10.0, cell_phase_deg=0.0,
-              block_size=0, blocks_per_sm=0, stats=None, workspace=None):
+              block_size=0, blocks_per_sm=0, stats=None, workspace=None, integrator=RKCK45):
     o = TraceOpts()
     lib().osiris_default_opts(ctypes.byref(o))
     o.tol, o.max_steps = float(tol), int(max_steps)
@@ -160,6 +161,7 @@ def make_opts(tol=1e-10, max_steps=1_000_000, precision=FP64, persistent=False,
     o.r_cap_factor, o.r_esc_factor = float(r_cap_factor), float(r_esc_factor)
     o.cell_deg, o.cell_phase_deg = float(cell_deg), float(cell_phase_deg)
     o.block_size, o.blocks_per_sm = int(block_size), int(blocks_per_sm)
+    o.integrator = int(integrator)
     o.stats = stats.data_ptr() if stats is not None else None
     if workspace is not None:
         o.workspace = workspace.data_ptr()

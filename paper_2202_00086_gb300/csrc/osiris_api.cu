@@ -39,6 +39,8 @@ int check_opts(const osiris_trace_opts* o) {
   if (o->max_steps < 1) return OSIRIS_EINVAL;
   if (o->precision != OSIRIS_FP64 && o->precision != OSIRIS_MIXED && o->precision != OSIRIS_DF64)
     return OSIRIS_EINVAL;
+  if (o->integrator != OSIRIS_RKCK45 && o->integrator != OSIRIS_RKDP45) return OSIRIS_EINVAL;
+  if (o->integrator == OSIRIS_RKDP45 && o->precision == OSIRIS_MIXED) return OSIRIS_EINVAL;
   if (!(o->r_cap_factor > 1.0) || !is_fin(o->r_cap_factor)) return OSIRIS_EINVAL;
   if (!(o->r_esc_factor > 1.0) || !is_fin(o->r_esc_factor)) return OSIRIS_EINVAL;
   if (!(o->cell_deg > 0.0 && o->cell_deg <= 180.0)) return OSIRIS_EINVAL;
@@ -129,7 +131,8 @@ int launch(KernelArgs& args, const osiris_trace_opts* o, void* stream) {
     const int64_t grid = (args.total_rays + block - 1) / block;
     if (grid > 0x7fffffff) return OSIRIS_EINVAL;
     args.queue = nullptr;
-    return cuda_rc(launcher(args, Kernel::kPlain, static_cast<int>(grid), block, stream));
+    return cuda_rc(
+        launcher(args, Kernel::kPlain, o->integrator, static_cast<int>(grid), block, stream));
   }
   if (!o->workspace || o->workspace_bytes < osiris_impl::kQueueBytes) return OSIRIS_ENOMEM;
   int sms = 0;
@@ -139,7 +142,8 @@ int launch(KernelArgs& args, const osiris_trace_opts* o, void* stream) {
     auto occ = (o->precision == OSIRIS_MIXED)  ? osiris_impl::occupancy_mixed
                : (o->precision == OSIRIS_DF64) ? osiris_impl::occupancy_df64
                                                : osiris_impl::occupancy_fp64;
-    if (occ(Kernel::kPersistent, block, &per_sm) != 0 || per_sm < 1) return OSIRIS_ECUDA;
+    if (occ(Kernel::kPersistent, o->integrator, block, &per_sm) != 0 || per_sm < 1)
+      return OSIRIS_ECUDA;
   }
   int64_t grid = static_cast<int64_t>(sms) * per_sm;
   const int64_t needed = (args.total_rays + block - 1) / block;
@@ -148,7 +152,8 @@ int launch(KernelArgs& args, const osiris_trace_opts* o, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(args.queue, 0, sizeof(unsigned long long), s) != cudaSuccess)
     return OSIRIS_ECUDA;
-  return cuda_rc(launcher(args, Kernel::kPersistent, static_cast<int>(grid), block, stream));
+  return cuda_rc(
+      launcher(args, Kernel::kPersistent, o->integrator, static_cast<int>(grid), block, stream));
 }
 
 int run_camera(const osiris_camera* cam, int disk, double r_in, double r_out,
@@ -186,6 +191,7 @@ void osiris_default_opts(osiris_trace_opts* o) {
   o->r_esc_factor = 1.1;
   o->cell_deg = 10.0;
   o->cell_phase_deg = 0.0;
+  o->integrator = OSIRIS_RKCK45;
 }
 
 int osiris_init_camera(osiris_camera** out, double a, double r_obs, double incl_deg,

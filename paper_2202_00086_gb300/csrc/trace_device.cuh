@@ -43,6 +43,25 @@ constexpr double D1 = -277.0 / 64512.0, D3 = 6925.0 / 370944.0, D4 = -6925.0 / 2
                  D5 = -277.0 / 14336.0, D6 = 277.0 / 7084.0;
 }  // namespace ck
 
+// Dormand-Prince 5(4) tableau (Dormand & Prince 1980, the RKDP45 scheme of
+// Sec. 3.1). Seven stages; the seventh is evaluated at the fifth-order
+// solution, so it is the first stage of the next step (first same as last).
+namespace dp {
+constexpr double A21 = 1.0 / 5.0;
+constexpr double A31 = 3.0 / 40.0, A32 = 9.0 / 40.0;
+constexpr double A41 = 44.0 / 45.0, A42 = -56.0 / 15.0, A43 = 32.0 / 9.0;
+constexpr double A51 = 19372.0 / 6561.0, A52 = -25360.0 / 2187.0, A53 = 64448.0 / 6561.0,
+                 A54 = -212.0 / 729.0;
+constexpr double A61 = 9017.0 / 3168.0, A62 = -355.0 / 33.0, A63 = 46732.0 / 5247.0,
+                 A64 = 49.0 / 176.0, A65 = -5103.0 / 18656.0;
+// fifth-order weights = the seventh row; b2 = b7 = 0
+constexpr double B1 = 35.0 / 384.0, B3 = 500.0 / 1113.0, B4 = 125.0 / 192.0,
+                 B5 = -2187.0 / 6784.0, B6 = 11.0 / 84.0;
+// fifth minus embedded fourth order, exact rationals
+constexpr double D1 = 71.0 / 57600.0, D3 = -71.0 / 16695.0, D4 = 71.0 / 1920.0,
+                 D5 = -17253.0 / 339200.0, D6 = 22.0 / 525.0, D7 = -1.0 / 40.0;
+}  // namespace dp
+
 // pi/2 split in two doubles: (PIO2_HI - theta) + PIO2_LO has the sign of
 // cos(theta) for theta in (-pi/2, 3pi/2), and equals it to first order near
 // the equator.
@@ -175,6 +194,68 @@ __device__ __forceinline__ void ck_step64(const RayK& K, const State& y, double 
   d.pth = h * OSIRIS_DL(pt);
 #undef OSIRIS_Y5
 #undef OSIRIS_DL
+}
+
+// Derivative vector of the evolved components (r, theta, phi, p_r, p_theta)
+// and 2H at the point where it was evaluated.
+struct Deriv {
+  double r, th, ph, pr, pth, twoH;
+};
+
+__device__ __forceinline__ void rhs64_at(const RayK& K, const State& y, Deriv& k) {
+  rhs64(K, y.r, y.th, y.pr, y.pth, k.r, k.th, k.ph, k.pr, k.pth, k.twoH);
+}
+
+// One Dormand-Prince attempt of length h from y given k1 = f(y): o = fifth-
+// order result, d = fifth minus fourth order, k7 = f(o) (the first stage of
+// the next step if this one is accepted). Six new evaluations.
+__device__ __forceinline__ void dp_step64(const RayK& K, const State& y, double h,
+                                          const Deriv& k1, State& o, State& d, Deriv& k7) {
+  using namespace dp;
+  double hd;
+  double k2r, k2t, k2p, k2pr, k2pt;
+  rhs64(K, fma(h, A21 * k1.r, y.r), fma(h, A21 * k1.th, y.th), fma(h, A21 * k1.pr, y.pr),
+        fma(h, A21 * k1.pth, y.pth), k2r, k2t, k2p, k2pr, k2pt, hd);
+#define DP_S3(a, b, y0) fma(h, fma(A32, b, A31 * a), y0)
+  double k3r, k3t, k3p, k3pr, k3pt;
+  rhs64(K, DP_S3(k1.r, k2r, y.r), DP_S3(k1.th, k2t, y.th), DP_S3(k1.pr, k2pr, y.pr),
+        DP_S3(k1.pth, k2pt, y.pth), k3r, k3t, k3p, k3pr, k3pt, hd);
+#undef DP_S3
+#define DP_S4(a, b, c, y0) fma(h, fma(A43, c, fma(A42, b, A41 * a)), y0)
+  double k4r, k4t, k4p, k4pr, k4pt;
+  rhs64(K, DP_S4(k1.r, k2r, k3r, y.r), DP_S4(k1.th, k2t, k3t, y.th),
+        DP_S4(k1.pr, k2pr, k3pr, y.pr), DP_S4(k1.pth, k2pt, k3pt, y.pth), k4r, k4t, k4p, k4pr,
+        k4pt, hd);
+#undef DP_S4
+#define DP_S5(a, b, c, e, y0) fma(h, fma(A54, e, fma(A53, c, fma(A52, b, A51 * a))), y0)
+  double k5r, k5t, k5p, k5pr, k5pt;
+  rhs64(K, DP_S5(k1.r, k2r, k3r, k4r, y.r), DP_S5(k1.th, k2t, k3t, k4t, y.th),
+        DP_S5(k1.pr, k2pr, k3pr, k4pr, y.pr), DP_S5(k1.pth, k2pt, k3pt, k4pt, y.pth), k5r, k5t,
+        k5p, k5pr, k5pt, hd);
+#undef DP_S5
+#define DP_S6(a, b, c, e, f, y0) \
+  fma(h, fma(A65, f, fma(A64, e, fma(A63, c, fma(A62, b, A61 * a)))), y0)
+  double k6r, k6t, k6p, k6pr, k6pt;
+  rhs64(K, DP_S6(k1.r, k2r, k3r, k4r, k5r, y.r), DP_S6(k1.th, k2t, k3t, k4t, k5t, y.th),
+        DP_S6(k1.pr, k2pr, k3pr, k4pr, k5pr, y.pr),
+        DP_S6(k1.pth, k2pt, k3pt, k4pt, k5pt, y.pth), k6r, k6t, k6p, k6pr, k6pt, hd);
+#undef DP_S6
+#define DP_Y5(a, c, e, f, g) fma(B6, g, fma(B5, f, fma(B4, e, fma(B3, c, B1 * a))))
+  o.r = fma(h, DP_Y5(k1.r, k3r, k4r, k5r, k6r), y.r);
+  o.th = fma(h, DP_Y5(k1.th, k3t, k4t, k5t, k6t), y.th);
+  o.ph = fma(h, DP_Y5(k1.ph, k3p, k4p, k5p, k6p), y.ph);
+  o.pr = fma(h, DP_Y5(k1.pr, k3pr, k4pr, k5pr, k6pr), y.pr);
+  o.pth = fma(h, DP_Y5(k1.pth, k3pt, k4pt, k5pt, k6pt), y.pth);
+#undef DP_Y5
+  rhs64_at(K, o, k7);
+#define DP_DL(a, c, e, f, g, z) \
+  fma(D7, z, fma(D6, g, fma(D5, f, fma(D4, e, fma(D3, c, D1 * a)))))
+  d.r = h * DP_DL(k1.r, k3r, k4r, k5r, k6r, k7.r);
+  d.th = h * DP_DL(k1.th, k3t, k4t, k5t, k6t, k7.th);
+  d.ph = h * DP_DL(k1.ph, k3p, k4p, k5p, k6p, k7.ph);
+  d.pr = h * DP_DL(k1.pr, k3pr, k4pr, k5pr, k6pr, k7.pr);
+  d.pth = h * DP_DL(k1.pth, k3pt, k4pt, k5pt, k6pt, k7.pth);
+#undef DP_DL
 }
 
 // True when x is +-inf or NaN (exponent bits all set); integer test only.

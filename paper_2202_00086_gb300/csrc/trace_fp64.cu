@@ -5,13 +5,50 @@
 
 namespace osiris_impl {
 
-struct StepperFP64 {
+template <int INTEG>
+struct StepperFP64;
+
+// Cash-Karp: every attempt evaluates its six stages.
+template <>
+struct StepperFP64<OSIRIS_RKCK45> {
   struct RayCache {};
+  struct LaneCache {};
   static __device__ __forceinline__ void prepare(const RayK&, RayCache&) {}
-  static __device__ __forceinline__ bool attempt(const RayK& K, const RayCache&, const State& y,
-                                                 double h,
-                                                 State& o, State& d, double& twoH) {
+  static __device__ __forceinline__ void reset(LaneCache&) {}
+  static __device__ __forceinline__ void accepted(LaneCache&) {}
+  static __device__ __forceinline__ bool attempt(const RayK& K, const RayCache&, LaneCache&,
+                                                 const State& y, double h, State& o, State& d,
+                                                 double& twoH) {
     ck_step64(K, y, h, o, d, twoH);
+    return true;
+  }
+  static __device__ __forceinline__ double twoH(const RayK& K, const State& y) {
+    return twoH64(K, y);
+  }
+};
+
+// Dormand-Prince: k1 is carried from the previous accepted attempt's seventh
+// stage; it is evaluated only when a ray starts or resumes (a warp evaluates
+// it when any of its lanes needs it).
+template <>
+struct StepperFP64<OSIRIS_RKDP45> {
+  struct RayCache {};
+  struct LaneCache {
+    Deriv k1, k7;
+    bool valid;
+  };
+  static __device__ __forceinline__ void prepare(const RayK&, RayCache&) {}
+  static __device__ __forceinline__ void reset(LaneCache& c) { c.valid = false; }
+  static __device__ __forceinline__ void accepted(LaneCache& c) { c.k1 = c.k7; }
+  static __device__ __forceinline__ bool attempt(const RayK& K, const RayCache&, LaneCache& c,
+                                                 const State& y, double h, State& o, State& d,
+                                                 double& twoH) {
+    if (!c.valid) {
+      rhs64_at(K, y, c.k1);
+      c.valid = true;
+    }
+    twoH = c.k1.twoH;
+    dp_step64(K, y, h, c.k1, o, d, c.k7);
     return true;
   }
   static __device__ __forceinline__ double twoH(const RayK& K, const State& y) {
@@ -21,26 +58,42 @@ struct StepperFP64 {
 
 constexpr int kMaxBlock = 256;
 
+template <int INTEG>
 __global__ void __launch_bounds__(kMaxBlock) trace_fp64_plain(const __grid_constant__ KernelArgs A) {
-  trace_body<StepperFP64, false>(A);
+  trace_body<StepperFP64<INTEG>, false>(A);
 }
 
+template <int INTEG>
 __global__ void __launch_bounds__(kMaxBlock) trace_fp64_persistent(const __grid_constant__ KernelArgs A) {
-  trace_body<StepperFP64, true>(A);
+  trace_body<StepperFP64<INTEG>, true>(A);
 }
 
-int launch_trace_fp64(const KernelArgs& args, Kernel kind, int grid, int block, void* stream) {
+template <int INTEG>
+static const void* fp64_kernel(Kernel kind) {
+  return kind == Kernel::kPersistent ? (const void*)trace_fp64_persistent<INTEG>
+                                     : (const void*)trace_fp64_plain<INTEG>;
+}
+
+int launch_trace_fp64(const KernelArgs& args, Kernel kind, int integrator, int grid, int block,
+                      void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (kind == Kernel::kPersistent)
-    trace_fp64_persistent<<<grid, block, 0, s>>>(args);
-  else
-    trace_fp64_plain<<<grid, block, 0, s>>>(args);
+  if (integrator == OSIRIS_RKDP45) {
+    if (kind == Kernel::kPersistent)
+      trace_fp64_persistent<OSIRIS_RKDP45><<<grid, block, 0, s>>>(args);
+    else
+      trace_fp64_plain<OSIRIS_RKDP45><<<grid, block, 0, s>>>(args);
+  } else {
+    if (kind == Kernel::kPersistent)
+      trace_fp64_persistent<OSIRIS_RKCK45><<<grid, block, 0, s>>>(args);
+    else
+      trace_fp64_plain<OSIRIS_RKCK45><<<grid, block, 0, s>>>(args);
+  }
   return (int)cudaGetLastError();
 }
 
-int occupancy_fp64(Kernel kind, int block, int* blocks_per_sm) {
-  const void* fn = (kind == Kernel::kPersistent) ? (const void*)trace_fp64_persistent
-                                                 : (const void*)trace_fp64_plain;
+int occupancy_fp64(Kernel kind, int integrator, int block, int* blocks_per_sm) {
+  const void* fn = integrator == OSIRIS_RKDP45 ? fp64_kernel<OSIRIS_RKDP45>(kind)
+                                               : fp64_kernel<OSIRIS_RKCK45>(kind);
   return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, 0);
 }
 

@@ -4,7 +4,11 @@
 // trace_fp64.cu and trace_mixed.cu through the Stepper policy:
 //   Stepper::RayCache                         per-ray data the stepper derives
 //   Stepper::prepare(K, cache)                once per ray
-//   Stepper::attempt(K, cache, y, h, o, d, twoH) -> one Cash-Karp attempt
+//   Stepper::LaneCache                        stage values carried between attempts
+//                                             (first same as last)
+//   Stepper::reset(lane)                      the state changed other than by a step
+//   Stepper::accepted(lane)                   y <- o after an accepted attempt
+//   Stepper::attempt(K, cache, lane, y, h, o, d, twoH) -> one embedded RK attempt
 //   Stepper::twoH(K, y)                       -> 2H at a state (FP64)
 #pragma once
 
@@ -155,6 +159,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
   RayInfo I;
   RayK& K = I.K;
   typename Stepper::RayCache RC;
+  typename Stepper::LaneCache LC;
   double& r_cap = I.r_cap;
   double& r_esc = I.r_esc;
   double& r_in = I.r_in;
@@ -174,6 +179,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
   auto start_ray = [&](int64_t g) {
     load_ray(A, g, I, y);
     Stepper::prepare(K, RC);
+    Stepper::reset(LC);
     h = I.h0;
     max_abs_H = 0.0;
     n_acc = n_rej = 0;
@@ -206,14 +212,19 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
   };
 
   // After an accepted step without a disk hit: capture and escape tests on
-  // the step end o (in this order), else continue from o.
-  auto after_accept = [&](double hs, const State& o) {
+  // the step end o (in this order), else continue from o. `fresh`: the last
+  // attempt was the accepted step itself (its end-stage values are current).
+  auto after_accept = [&](double hs, const State& o, bool fresh) {
     if (o.r < r_cap) {
       begin_locate(SURF_CAPTURE, hs, o);
     } else if (o.r > r_esc) {
       begin_locate(SURF_ESCAPE, hs, o);
     } else {
       y = o;
+      if (fresh)
+        Stepper::accepted(LC);
+      else
+        Stepper::reset(LC);
       mode = MODE_INTEGRATE;
       if ((int64_t)(n_acc + n_rej) >= max_steps) finish(OSIRIS_STATUS_MAXSTEP, y);
     }
@@ -238,7 +249,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
     const double hs = (mode == MODE_LOCATE) ? h_try : fmin(h, 0.1 * y.r);
     State o, d;
     double twoH;
-    const bool fp64_step = Stepper::attempt(K, RC, y, hs, o, d, twoH);
+    const bool fp64_step = Stepper::attempt(K, RC, LC, y, hs, o, d, twoH);
     S.rhs += 6;
     S.fp64_steps += fp64_step ? 1 : 0;
 
@@ -266,7 +277,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
         if (disk && crosses_equator(y, o))
           begin_locate(SURF_EQUATOR, hs, o);
         else
-          after_accept(hs, o);
+          after_accept(hs, o, true);
       } else {
         ++n_rej;
         const float shrink = fmaxf(0.1f, 0.9f * exp2f(-0.25f * log2f(err)));
@@ -309,7 +320,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
       } else {
         // equatorial crossing outside the disk: the accepted step stands;
         // run the capture / escape tests on its end point
-        after_accept(h_step, yE);
+        after_accept(h_step, yE, false);
       }
     }
   }

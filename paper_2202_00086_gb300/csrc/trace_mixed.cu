@@ -64,9 +64,12 @@ __device__ __forceinline__ double twoH_value64(const RayK& K, const State& y) {
 
 struct StepperMixed {
   struct RayCache {};
+  struct LaneCache {};
   static __device__ __forceinline__ void prepare(const RayK&, RayCache&) {}
-  static __device__ __forceinline__ bool attempt(const RayK& K, const RayCache&, const State& y,
-                                                 double h,
+  static __device__ __forceinline__ void reset(LaneCache&) {}
+  static __device__ __forceinline__ void accepted(LaneCache&) {}
+  static __device__ __forceinline__ bool attempt(const RayK& K, const RayCache&, LaneCache&,
+                                                 const State& y, double h,
                                                  State& o, State& d, double& twoH) {
     if (y.r < kMixedFP64Radius || fabs(y.pth) < kMixedFP64Ptheta) {
       ck_step64(K, y, h, o, d, twoH);
@@ -141,7 +144,8 @@ __global__ void __launch_bounds__(kMaxBlock) trace_mixed_persistent(const __grid
   trace_body<StepperMixed, true>(A);
 }
 
-int launch_trace_mixed(const KernelArgs& args, Kernel kind, int grid, int block, void* stream) {
+int launch_trace_mixed(const KernelArgs& args, Kernel kind, int, int grid, int block,
+                       void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (kind == Kernel::kPersistent)
     trace_mixed_persistent<<<grid, block, 0, s>>>(args);
@@ -150,7 +154,7 @@ int launch_trace_mixed(const KernelArgs& args, Kernel kind, int grid, int block,
   return (int)cudaGetLastError();
 }
 
-int occupancy_mixed(Kernel kind, int block, int* blocks_per_sm) {
+int occupancy_mixed(Kernel kind, int, int block, int* blocks_per_sm) {
   const void* fn = (kind == Kernel::kPersistent) ? (const void*)trace_mixed_persistent
                                                  : (const void*)trace_mixed_plain;
   return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, 0);
