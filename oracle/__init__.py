@@ -18,6 +18,7 @@ from . import build as _build
 
 STATUS_NONE, STATUS_CAPTURED, STATUS_ESCAPED, STATUS_DISK, STATUS_MAXSTEP, STATUS_ERROR = range(6)
 RKCK45, RKDP45 = 0, 1
+DISK_KEPLERIAN, DISK_CONSTANT_L = 0, 1
 
 _P = ctypes.POINTER
 _d = ctypes.c_double
@@ -28,7 +29,8 @@ _i32 = ctypes.c_int32
 class OracleOptions(ctypes.Structure):
     _fields_ = [("tol", _d), ("max_steps", _i64), ("r_cap_factor", _d), ("r_esc_factor", _d),
                 ("disk", _i32), ("r_in", _d), ("r_out", _d), ("cell_deg", _d),
-                ("cell_phase_deg", _d), ("integrator", _i32)]
+                ("cell_phase_deg", _d), ("integrator", _i32), ("disk_model", _i32),
+                ("l0", _d)]
 
 
 _OUT_FIELDS = [
@@ -75,6 +77,7 @@ def lib():
         L.oracle_tableau.argtypes = [_i32] + [_P(_d)] * 4
         L.oracle_tableau.restype = _i32
         L.oracle_disk_observables.argtypes = [_d, _d, _d, _d, _d, _P(_d), _P(_d)]
+        L.oracle_disk_observables_l0.argtypes = [_d, _d, _d, _d, _d, _d, _P(_d), _P(_d)]
         L.oracle_isco.argtypes = [_d, _d]
         L.oracle_isco.restype = _d
         _lib = L
@@ -86,9 +89,11 @@ def _ptr(arr, ct):
 
 
 def options(tol=1e-10, max_steps=1_000_000, r_cap_factor=1.01, r_esc_factor=1.1, disk=False,
-            r_in=0.0, r_out=0.0, cell_deg=10.0, cell_phase_deg=0.0, integrator=RKCK45):
+            r_in=0.0, r_out=0.0, cell_deg=10.0, cell_phase_deg=0.0, integrator=RKCK45,
+            disk_model=DISK_KEPLERIAN, l0=0.0):
     return OracleOptions(tol, max_steps, r_cap_factor, r_esc_factor, 1 if disk else 0, r_in,
-                         r_out, cell_deg, cell_phase_deg, int(integrator))
+                         r_out, cell_deg, cell_phase_deg, int(integrator), int(disk_model),
+                         float(l0))
 
 
 def _alloc(n):
@@ -215,6 +220,14 @@ def disk_observables(a, r, E, L_z, M=1.0):
     g = _d()
     I = _d()
     lib().oracle_disk_observables(M, a, r, E, L_z, ctypes.byref(g), ctypes.byref(I))
+    return g.value, I.value
+
+
+def disk_observables_l0(a, r, E, L_z, l0, M=1.0):
+    """(g, I) on a disk of constant specific angular momentum l0 (Sec. 5)."""
+    g = _d()
+    I = _d()
+    lib().oracle_disk_observables_l0(M, a, r, E, L_z, l0, ctypes.byref(g), ctypes.byref(I))
     return g.value, I.value
 
 

@@ -43,8 +43,9 @@
  *     is the terminal state. A disk crossing outside [r_in, r_out] does not
  *     stop the ray; integration continues from the end of the accepted step.
  *   - redshift g = nu_obs / nu_em with nu_obs = P^t = 1 at the observer and
- *     nu_em = u^t (E - Omega L) for a Keplerian disk Omega = M^1/2 /(r^3/2 + a M^1/2);
- *     intensity I = g^3 r^-2.
+ *     nu_em = u^t (E - Omega L) for a Keplerian disk Omega = M^1/2 /(r^3/2 + a M^1/2)
+ *     or a disk of constant l0 = -u_phi/u_t (the printed Omega of Sec. 5 has
+ *     g_phph l0 where l0 = -u_phi/u_t gives g_tt l0); intensity I = g^3 r^-2.
  */
 
 #include <algorithm>
@@ -424,6 +425,8 @@ struct Options {
   double r_in, r_out;
   double cell_deg;       // checkerboard cell size on the celestial sphere
   double cell_phase_deg; // longitude offset of the checkerboard
+  int disk_model;        // kKeplerian or kConstantL
+  double l0;             // specific angular momentum of the constant-l0 disk
 };
 
 struct Result {
@@ -481,16 +484,34 @@ bool crosses_equator(const double y0[NY], const double y1[NY]) {
   return (c0 > 0.0 && c1 <= 0.0) || (c0 < 0.0 && c1 >= 0.0);
 }
 
-// Keplerian redshift and intensity at the disk point r (Sec. 5):
-// Omega = M^1/2 / (r^3/2 + a M^1/2), u^t from g_ab u^a u^b = -1 (Eq. norm) in
-// the equatorial plane, g = 1 / (u^t (E - Omega L)), I = g^3 r^-2.
-void disk_observables(const Spacetime& S, const Ray& R, double r, double* g_out,
-                      double* I_out) {
+enum DiskModel { kKeplerian = 0, kConstantL = 1 };
+
+// Redshift and intensity at the disk point r (Sec. 5). The gas moves on
+// circular orbits with angular velocity Omega:
+//   Keplerian:               Omega = M^1/2 / (r^3/2 + a M^1/2)
+//   constant specific angular momentum l0 = -u_phi / u_t (Sec. 5):
+//                            Omega = -(g_tphi + l0 g_tt) / (g_phph + l0 g_tphi)
+// u^t follows from g_ab u^a u^b = -1 (Eq. norm) in the equatorial plane,
+// g = 1 / (u^t (E - Omega L)) and I = g^3 r^-2. Where no timelike orbit with
+// that Omega exists (the normalisation has no real solution), g = I = 0.
+void disk_observables(const Spacetime& S, const Ray& R, double r, int model, double l0,
+                      double* g_out, double* I_out) {
   double g[4][4];
   metric_cov(S, r, 0.5 * kPi, g);
-  const double sqM = std::sqrt(S.M);
-  const double Omega = sqM / (std::pow(r, 1.5) + S.a * sqM);
-  const double ut = 1.0 / std::sqrt(-g[0][0] - 2.0 * Omega * g[0][3] - Omega * Omega * g[3][3]);
+  double Omega;
+  if (model == kConstantL) {
+    Omega = -(g[0][3] + l0 * g[0][0]) / (g[3][3] + l0 * g[0][3]);
+  } else {
+    const double sqM = std::sqrt(S.M);
+    Omega = sqM / (std::pow(r, 1.5) + S.a * sqM);
+  }
+  const double norm = -g[0][0] - 2.0 * Omega * g[0][3] - Omega * Omega * g[3][3];
+  if (!(norm > 0.0)) {
+    *g_out = 0.0;
+    *I_out = 0.0;
+    return;
+  }
+  const double ut = 1.0 / std::sqrt(norm);
   const double redshift = 1.0 / (ut * (R.E - Omega * R.L));
   *g_out = redshift;
   *I_out = redshift * redshift * redshift / (r * r);
@@ -622,7 +643,7 @@ Result integrate(const Spacetime& S, const Ray& R, const double y_init[NY], doub
     sky_cell(o, yfin[Y_TH], yfin[Y_PH], &out.cell_i, &out.cell_j, &out.parity);
   } else if (out.status == kDisk) {
     out.r_hit = yfin[Y_R];
-    disk_observables(S, R, yfin[Y_R], &out.g, &out.intensity);
+    disk_observables(S, R, yfin[Y_R], o.disk_model, o.l0, &out.g, &out.intensity);
   }
   return out;
 }
@@ -672,6 +693,8 @@ struct oracle_options {
   double cell_deg;
   double cell_phase_deg;
   int32_t integrator;  // 0 = Cash-Karp 4(5), 1 = Dormand-Prince 5(4)
+  int32_t disk_model;  // 0 = Keplerian, 1 = constant specific angular momentum l0
+  double l0;
 };
 
 static void store(const Result& R, oracle_outputs* o, int64_t k) {
@@ -710,6 +733,8 @@ static Options to_options(const oracle_options* oo) {
   o.r_out = oo->r_out;
   o.cell_deg = oo->cell_deg;
   o.cell_phase_deg = oo->cell_phase_deg;
+  o.disk_model = oo->disk_model;
+  o.l0 = oo->l0;
   return o;
 }
 
@@ -862,7 +887,12 @@ int32_t oracle_tableau(int32_t integrator, double* c, double* a, double* b5, dou
 
 void oracle_disk_observables(double M, double a, double r, double E, double L, double* g,
                              double* I) {
-  disk_observables(Spacetime{M, a}, Ray{E, L}, r, g, I);
+  disk_observables(Spacetime{M, a}, Ray{E, L}, r, kKeplerian, 0.0, g, I);
+}
+
+void oracle_disk_observables_l0(double M, double a, double r, double E, double L, double l0,
+                                double* g, double* I) {
+  disk_observables(Spacetime{M, a}, Ray{E, L}, r, kConstantL, l0, g, I);
 }
 
 // Radius of the innermost stable circular prograde orbit (Bardeen, Press &

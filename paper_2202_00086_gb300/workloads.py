@@ -32,11 +32,14 @@ def checker_phase_deg(seed: int, cell_deg: float = 10.0) -> float:
 
 
 def render(a, r_obs, incl_deg, extent, nx, ny, mode="shadow", r_in=None, r_out=None,
-           tol=1e-10, cell_deg=10.0, seed=2202):
+           tol=1e-10, cell_deg=10.0, seed=2202, l0=None):
+    """mode "disk" with l0=None: Keplerian disk; with l0: disk of constant
+    specific angular momentum l0."""
     return dict(a=float(a), r_obs=float(r_obs), incl_deg=float(incl_deg),
                 extent=tuple(float(v) for v in extent), nx=int(nx), ny=int(ny), mode=mode,
                 r_in=r_in, r_out=r_out, tol=float(tol), cell_deg=float(cell_deg),
-                cell_phase_deg=checker_phase_deg(seed, cell_deg))
+                cell_phase_deg=checker_phase_deg(seed, cell_deg),
+                l0=None if l0 is None else float(l0))
 
 
 def schwarzschild_shadow_64():
@@ -60,6 +63,17 @@ def schwarzschild_disk(side=2048):
     r_obs=1000, side x side on [-25,25]^2, tol 1e-10."""
     return render(0.0, 1000.0, 80.0, (-25.0, 25.0, -25.0, 25.0), side, side, mode="disk",
                   r_in=6.0, r_out=20.0)
+
+
+PAPER_DISK_CASES = ((0.0, 2.8), (0.5, 2.8), (0.998, 1.8))
+
+
+def paper_disk_figure(nx=2048, ny=1024):
+    """The thin-disk figure set-up of Sec. 5: a in {0, 0.5, 0.998} with
+    l0 = 2.8, 2.8, 1.8, r_obs = 1000, 85 deg, r_in = ISCO(a), r_out = 20,
+    x in [-24, 24], y in [-12, 12], 2048 x 1024 pixels."""
+    return [render(a, 1000.0, 85.0, (-24.0, 24.0, -12.0, 12.0), nx, ny, mode="disk",
+                   r_in="isco", r_out=20.0, l0=l0) for a, l0 in PAPER_DISK_CASES]
 
 
 def uneven_batch(n=256, seed=4, sides=(128, 256, 512, 1024)):

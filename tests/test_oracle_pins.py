@@ -596,3 +596,41 @@ def test_dormand_prince_keeps_H_smaller():
         out[integ] = (r["max_abs_H"][esc].mean(), r["max_abs_H"][cap].mean())
     assert out[oracle.RKDP45][0] < out[oracle.RKCK45][0]
     assert out[oracle.RKDP45][1] < out[oracle.RKCK45][1] / 5
+
+
+# ---------------------------------------------------------------------------
+# Disk of constant specific angular momentum l0 (Sec. 5)
+# ---------------------------------------------------------------------------
+
+def test_constant_l0_disk_closed_forms():
+    # Schwarzschild: Omega = l0 (1 - 2/r) / r^2, u^t = 1/sqrt((1 - 2/r) - Omega^2 r^2)
+    for r, l0, E, L in ((6.0, 2.8, 0.97, 1.3), (11.0, 3.5, 1.0, -2.0)):
+        g, I = oracle.disk_observables_l0(0.0, r, E, L, l0)
+        Om = l0 * (1 - 2 / r) / r ** 2
+        g_expect = math.sqrt((1 - 2 / r) - Om ** 2 * r ** 2) / (E - Om * L)
+        assert g == pytest.approx(g_expect, rel=1e-13)
+        assert I == pytest.approx(g_expect ** 3 / r ** 2, rel=1e-13)
+    # l0 equal to the Keplerian l(r) = (r^2 - 2 a sqrt r + a^2) / (r^3/2 - 2 sqrt r + a)
+    # at radius r reproduces the Keplerian redshift there (Schwarzschild and Kerr)
+    for a, r in ((0.0, 7.5), (0.9, 3.1), (0.998, 1.6)):
+        lk = (r * r - 2 * a * math.sqrt(r) + a * a) / (r ** 1.5 - 2 * math.sqrt(r) + a)
+        gk, _ = oracle.disk_observables(a, r, 0.93, 2.2)
+        gl, _ = oracle.disk_observables_l0(a, r, 0.93, 2.2, lk)
+        assert gl == pytest.approx(gk, rel=1e-12)
+
+
+def test_constant_l0_disk_render():
+    rd = workloads.paper_disk_figure(nx=48, ny=24)[2]  # a = 0.998, l0 = 1.8
+    res = oracle.trace_pixels(rd["a"], rd["r_obs"], rd["incl_deg"], rd["extent"], rd["nx"],
+                              rd["ny"], disk=True, r_in=oracle.isco(rd["a"]), r_out=20.0,
+                              disk_model=oracle.DISK_CONSTANT_L, l0=rd["l0"])
+    disk = res["status"] == oracle.STATUS_DISK
+    assert disk.sum() > 100
+    # the l0 model changes only the observables: every other output equals the
+    # Keplerian render's
+    kep = oracle.trace_pixels(rd["a"], rd["r_obs"], rd["incl_deg"], rd["extent"], rd["nx"],
+                              rd["ny"], disk=True, r_in=oracle.isco(rd["a"]), r_out=20.0)
+    for key in ("status", "r", "theta", "phi", "accepted"):
+        assert np.array_equal(res[key], kep[key]), key
+    assert not np.allclose(res["g"][disk], kep["g"][disk])
+    assert np.all(res["g"][disk] > 0)
