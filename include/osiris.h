@@ -174,10 +174,26 @@ int osiris_render_disk(const osiris_camera* cam, double r_in, double r_out,
                        const osiris_trace_opts* opts, const osiris_outputs* out,
                        void* cuda_stream);
 
+/* Disk models (Sec. 5): how the gas on circular equatorial orbits moves. */
+#define OSIRIS_DISK_NONE 0      /* shadow / lensing render */
+#define OSIRIS_DISK_KEPLERIAN 1 /* Omega = 1 / (r^3/2 + a) */
+#define OSIRIS_DISK_CONSTANT_L 2 /* constant specific angular momentum
+                                    l0 = -u_phi / u_t:
+                                    Omega = -(g_tphi + l0 g_tt) / (g_phph + l0 g_tphi) */
+
+/* Thin-disk render with a disk of constant specific angular momentum l0
+ * (Sec. 5): as osiris_render_disk, with Omega = -(g_tphi + l0 g_tt) /
+ * (g_phph + l0 g_tphi) at the hit radius. Where that motion is not timelike
+ * (g_ab u^a u^b = -1 has no solution) the hit still stops the ray and g and
+ * the intensity are 0. l0 must be finite. */
+int osiris_render_disk_l0(const osiris_camera* cam, double r_in, double r_out, double l0,
+                          const osiris_trace_opts* opts, const osiris_outputs* out,
+                          void* cuda_stream);
+
 /* One render (or one contiguous range of its pixels) of a batch. */
 typedef struct {
     const osiris_camera* camera;
-    int32_t disk;        /* 0: shadow/lensing, 1: thin disk */
+    int32_t disk;        /* OSIRIS_DISK_NONE, _KEPLERIAN or _CONSTANT_L */
     double r_in, r_out;  /* disk radii (disk = 1) */
     double tol;          /* per-request tolerance; <= 0 takes opts->tol */
     osiris_outputs out;  /* DEVICE outputs of the whole render (nx * ny entries) */
@@ -186,6 +202,7 @@ typedef struct {
                             outputs written; n_rays <= 0 means the whole render
                             (first_ray must then be 0). A range must lie inside
                             [0, nx * ny). */
+    double l0;           /* specific angular momentum (disk = OSIRIS_DISK_CONSTANT_L) */
 } osiris_request;
 
 /* Bytes of DEVICE workspace that osiris_trace_batch needs for n requests

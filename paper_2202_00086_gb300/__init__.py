@@ -21,6 +21,7 @@ OK, EINVAL, ECUDA, ENOMEM, ETIMEOUT = 0, -1, -2, -3, -4
 STATUS_NONE, STATUS_CAPTURED, STATUS_ESCAPED, STATUS_DISK, STATUS_MAXSTEP, STATUS_ERROR = range(6)
 FP64, MIXED, DF64 = 0, 1, 2
 RKCK45, RKDP45 = 0, 1
+DISK_NONE, DISK_KEPLERIAN, DISK_CONSTANT_L = 0, 1, 2
 STATS_LEN = 16
 STAT_NAMES = ["rays", "accepted", "rejected", "root_steps", "rhs_evals", "status_none",
               "status_captured", "status_escaped", "status_disk", "status_maxstep",
@@ -55,7 +56,7 @@ class Outputs(ctypes.Structure):
 class Request(ctypes.Structure):
     _fields_ = [("camera", _vp), ("disk", ctypes.c_int32), ("r_in", _d), ("r_out", _d),
                 ("tol", _d), ("out", Outputs), ("first_ray", ctypes.c_int64),
-                ("n_rays", ctypes.c_int64)]
+                ("n_rays", ctypes.c_int64), ("l0", _d)]
 
 
 _lib = None
@@ -77,6 +78,7 @@ def lib():
         L.osiris_camera_rays.restype = ctypes.c_int64
         L.osiris_trace.argtypes = [_vp, _P(TraceOpts), _P(Outputs), _vp]
         L.osiris_render_disk.argtypes = [_vp, _d, _d, _P(TraceOpts), _P(Outputs), _vp]
+        L.osiris_render_disk_l0.argtypes = [_vp, _d, _d, _d, _P(TraceOpts), _P(Outputs), _vp]
         L.osiris_workspace_bytes.argtypes = [ctypes.c_int32]
         L.osiris_workspace_bytes.restype = ctypes.c_size_t
         L.osiris_trace_batch.argtypes = [_P(Request), ctypes.c_int32, _P(TraceOpts), _vp]
@@ -200,15 +202,21 @@ def trace(camera, out=None, stream=None, **opts):
     return out
 
 
-def render_disk(camera, r_in, r_out, out=None, stream=None, **opts):
-    """Thin Keplerian disk render (osiris_render_disk)."""
+def render_disk(camera, r_in, r_out, out=None, stream=None, l0=None, **opts):
+    """Thin-disk render: Keplerian (osiris_render_disk) or, with l0, a disk of
+    constant specific angular momentum (osiris_render_disk_l0)."""
     if out is None:
         out = alloc_outputs(camera.n_rays, fields=DISK_FIELDS)
     o = make_opts(**opts)
     os_ = outputs_struct(out)
-    _check(lib().osiris_render_disk(camera.handle, float(r_in), float(r_out), ctypes.byref(o),
-                                    ctypes.byref(os_), _stream_handle(stream)),
-           "osiris_render_disk")
+    if l0 is None:
+        _check(lib().osiris_render_disk(camera.handle, float(r_in), float(r_out),
+                                        ctypes.byref(o), ctypes.byref(os_),
+                                        _stream_handle(stream)), "osiris_render_disk")
+    else:
+        _check(lib().osiris_render_disk_l0(camera.handle, float(r_in), float(r_out), float(l0),
+                                           ctypes.byref(o), ctypes.byref(os_),
+                                           _stream_handle(stream)), "osiris_render_disk_l0")
     return out
 
 
@@ -220,7 +228,10 @@ def request_array(requests):
     arr = (Request * max(1, n))()
     for k, q in enumerate(requests):
         arr[k].camera = q["camera"].handle
-        arr[k].disk = 1 if q.get("disk") else 0
+        dk = q.get("disk")
+        arr[k].disk = (DISK_NONE if not dk else
+                       DISK_CONSTANT_L if q.get("l0") is not None else DISK_KEPLERIAN)
+        arr[k].l0 = float(q.get("l0") or 0.0)
         arr[k].r_in = float(q.get("r_in") or 0.0)
         arr[k].r_out = float(q.get("r_out") or 0.0)
         arr[k].tol = float(q.get("tol") or 0.0)

@@ -62,14 +62,16 @@ int check_disk(double a, double r_cap_factor, double r_esc, double r_in, double 
 
 // Fields common to pixel and explicit-state requests.
 void fill_common(ReqDev& R, double a, double r0, const osiris_trace_opts* o, double tol,
-                 int disk, double r_in, double r_out, const osiris_outputs* out) {
+                 int disk, double r_in, double r_out, const osiris_outputs* out,
+                 double l0 = 0.0) {
   R.a = a;
   R.r0 = r0;
   R.r_cap = o->r_cap_factor * horizon(a);
   R.r_esc = o->r_esc_factor * r0;
-  R.disk = disk ? 1 : 0;
+  R.disk = disk;
   R.r_in = disk ? r_in : 0.0;
   R.r_out = disk ? r_out : 0.0;
+  R.l0 = disk == OSIRIS_DISK_CONSTANT_L ? l0 : 0.0;
   R.tol = tol > 0.0 ? tol : o->tol;
   R.h0 = 0.01 * r0;
   R.max_steps = o->max_steps;
@@ -156,17 +158,18 @@ int launch(KernelArgs& args, const osiris_trace_opts* o, void* stream) {
       launcher(args, Kernel::kPersistent, o->integrator, static_cast<int>(grid), block, stream));
 }
 
-int run_camera(const osiris_camera* cam, int disk, double r_in, double r_out,
+int run_camera(const osiris_camera* cam, int disk, double r_in, double r_out, double l0,
                const osiris_trace_opts* o, const osiris_outputs* out, void* stream) {
   if (!cam || !out) return OSIRIS_EINVAL;
   if (int rc = check_opts(o)) return rc;
   const double r_esc = o->r_esc_factor * cam->r0;
   if (disk)
     if (int rc = check_disk(cam->a, o->r_cap_factor, r_esc, r_in, r_out)) return rc;
+  if (!is_fin(l0)) return OSIRIS_EINVAL;
   KernelArgs args;
   std::memset(&args, 0, sizeof(args));
   ReqDev& R = args.single;
-  fill_common(R, cam->a, cam->r0, o, o->tol, disk, r_in, r_out, out);
+  fill_common(R, cam->a, cam->r0, o, o->tol, disk, r_in, r_out, out, l0);
   fill_camera(R, cam);
   R.ray_begin = 0;
   args.reqs = nullptr;
@@ -248,13 +251,19 @@ int64_t osiris_camera_rays(const osiris_camera* cam) {
 
 int osiris_trace(const osiris_camera* cam, const osiris_trace_opts* opts,
                  const osiris_outputs* out, void* cuda_stream) {
-  return run_camera(cam, 0, 0.0, 0.0, opts, out, cuda_stream);
+  return run_camera(cam, OSIRIS_DISK_NONE, 0.0, 0.0, 0.0, opts, out, cuda_stream);
 }
 
 int osiris_render_disk(const osiris_camera* cam, double r_in, double r_out,
                        const osiris_trace_opts* opts, const osiris_outputs* out,
                        void* cuda_stream) {
-  return run_camera(cam, 1, r_in, r_out, opts, out, cuda_stream);
+  return run_camera(cam, OSIRIS_DISK_KEPLERIAN, r_in, r_out, 0.0, opts, out, cuda_stream);
+}
+
+int osiris_render_disk_l0(const osiris_camera* cam, double r_in, double r_out, double l0,
+                          const osiris_trace_opts* opts, const osiris_outputs* out,
+                          void* cuda_stream) {
+  return run_camera(cam, OSIRIS_DISK_CONSTANT_L, r_in, r_out, l0, opts, out, cuda_stream);
 }
 
 size_t osiris_workspace_bytes(int32_t n_requests) {
@@ -273,12 +282,14 @@ int osiris_trace_batch(const osiris_request* reqs, int32_t n, const osiris_trace
     const osiris_request& q = reqs[k];
     if (!q.camera) return OSIRIS_EINVAL;
     if (q.tol < 0.0 || !is_fin(q.tol)) return OSIRIS_EINVAL;
+    if (q.disk < OSIRIS_DISK_NONE || q.disk > OSIRIS_DISK_CONSTANT_L || !is_fin(q.l0))
+      return OSIRIS_EINVAL;
     const double r_esc = o->r_esc_factor * q.camera->r0;
     if (q.disk)
       if (int rc = check_disk(q.camera->a, o->r_cap_factor, r_esc, q.r_in, q.r_out)) return rc;
     ReqDev& R = table[k];
     std::memset(&R, 0, sizeof(R));
-    fill_common(R, q.camera->a, q.camera->r0, o, q.tol, q.disk, q.r_in, q.r_out, &q.out);
+    fill_common(R, q.camera->a, q.camera->r0, o, q.tol, q.disk, q.r_in, q.r_out, &q.out, q.l0);
     fill_camera(R, q.camera);
     if (int rc = apply_range(R, q)) return rc;
     R.ray_begin = begin;
@@ -427,13 +438,16 @@ extern "C" int osiris_trace_batch_static(const osiris_request* reqs, int32_t n,
     const osiris_request& q = reqs[k];
     if (!q.camera) return OSIRIS_EINVAL;
     if (q.tol < 0.0 || !is_fin(q.tol)) return OSIRIS_EINVAL;
+    if (q.disk < OSIRIS_DISK_NONE || q.disk > OSIRIS_DISK_CONSTANT_L || !is_fin(q.l0))
+      return OSIRIS_EINVAL;
     if (q.disk)
       if (int rc = check_disk(q.camera->a, o.r_cap_factor, o.r_esc_factor * q.camera->r0, q.r_in,
                               q.r_out))
         return rc;
     ReqDev& R = g_static_table[k];
     std::memset(&R, 0, sizeof(R));
-    fill_common(R, q.camera->a, q.camera->r0, &o, q.tol, q.disk, q.r_in, q.r_out, &q.out);
+    fill_common(R, q.camera->a, q.camera->r0, &o, q.tol, q.disk, q.r_in, q.r_out, &q.out,
+                q.l0);
     fill_camera(R, q.camera);
     if (int rc = apply_range(R, q)) return rc;
     R.ray_begin = begin;

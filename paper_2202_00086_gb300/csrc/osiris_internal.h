@@ -25,7 +25,8 @@ struct alignas(16) ReqDev {
   double inv_At, e_x, l_x, pth_y, grr;
   // stopping surfaces (Sec. 4.1, Sec. 5)
   double r_cap, r_esc, r_in, r_out;
-  int32_t disk;
+  int32_t disk;             // OSIRIS_DISK_* (0: no disk)
+  double l0;                // constant-l0 disk
   int32_t explicit_states;  // 1: rays start from states / E / L (test hook)
   const double* states;     // n x 6 rows (t, r, theta, phi, p_r, p_theta)
   const double* E;

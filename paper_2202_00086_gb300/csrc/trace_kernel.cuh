@@ -107,17 +107,22 @@ __device__ __forceinline__ void write_outputs(const KernelArgs& A, const RayInfo
   if (O.parity) O.parity[local] = (uint8_t)par;
   double g = 0.0, Iobs = 0.0, rh = 0.0;
   if (status == OSIRIS_STATUS_DISK) {
-    // Keplerian disk (Sec. 5): Omega = 1/(r^3/2 + a); u^t from the
-    // normalisation g_ab u^a u^b = -1 in the equatorial plane;
-    // g = 1/(u^t (E - Omega L)); I = g^3 / r^2.
+    // Disk gas on circular orbits (Sec. 5): Keplerian Omega = 1/(r^3/2 + a),
+    // or constant l0 = -u_phi/u_t: Omega = -(g_tphi + l0 g_tt)/(g_phph + l0 g_tphi).
+    // u^t from the normalisation g_ab u^a u^b = -1 in the equatorial plane;
+    // g = 1/(u^t (E - Omega L)); I = g^3 / r^2 (0 where no timelike orbit exists).
     const double r = f.r, a = I.K.a;
-    const double Om = 1.0 / fma(r, sqrt(r), a);
     const double gtt = -(1.0 - 2.0 / r);
     const double gtp = -2.0 * a / r;
     const double gpp = r * r + a * a + 2.0 * a * a / r;
-    const double inv_ut = sqrt(-gtt - 2.0 * Om * gtp - Om * Om * gpp);
-    g = inv_ut / (I.K.E - Om * I.K.L);
-    Iobs = g * g * g / (r * r);
+    const double Om = (R->disk == OSIRIS_DISK_CONSTANT_L)
+                          ? -(gtp + R->l0 * gtt) / (gpp + R->l0 * gtp)
+                          : 1.0 / fma(r, sqrt(r), a);
+    const double norm = -gtt - 2.0 * Om * gtp - Om * Om * gpp;
+    if (norm > 0.0) {
+      g = sqrt(norm) / (I.K.E - Om * I.K.L);
+      Iobs = g * g * g / (r * r);
+    }
     rh = r;
   }
   if (O.g) O.g[local] = g;

@@ -154,7 +154,8 @@ class RenderServer:
         entries = []
         for r, first, n in parts:
             entries.append({"camera": r.camera, "disk": r.disk, "r_in": r.r_in, "r_out": r.r_out,
-                            "tol": r.tol, "out": r.out, "first_ray": first, "n_rays": n})
+                            "tol": r.tol, "out": r.out, "first_ray": first, "n_rays": n,
+                            "l0": r.render.get("l0") if r.disk else None})
             r.chunks.append((first, n))
         event = self.backend.launch(entries, self._ws[k], precision=self.precision,
                                     cell_deg=self.cell_deg, cell_phase_deg=self.cell_phase_deg)
@@ -317,7 +318,8 @@ class _CudaBackend:
 
     def single(self, r, **opts):
         if r.disk:
-            self.osr.render_disk(r.camera, r.r_in, r.r_out, out=r.out, tol=r.tol, **opts)
+            self.osr.render_disk(r.camera, r.r_in, r.r_out, out=r.out, tol=r.tol,
+                                 l0=r.render.get("l0"), **opts)
         else:
             self.osr.trace(r.camera, out=r.out, tol=r.tol, **opts)
         self.torch.cuda.synchronize()

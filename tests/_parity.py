@@ -53,7 +53,7 @@ def gpu_render(rd, precision=osr.FP64, persistent=False, stats=None, fields=None
         fields = osr.DISK_FIELDS if disk else osr.SHADOW_FIELDS
     out = osr.alloc_outputs(cam.n_rays, fields=fields)
     if disk:
-        osr.render_disk(cam, osr.resolve_r_in(rd), rd["r_out"], out=out, **opts)
+        osr.render_disk(cam, osr.resolve_r_in(rd), rd["r_out"], out=out, l0=rd.get("l0"), **opts)
     else:
         osr.trace(cam, out=out, **opts)
     torch.cuda.synchronize()
@@ -65,6 +65,8 @@ def oracle_render(rd, pixels=None, **extra):
     r_in = oracle.isco(rd["a"]) if rd.get("r_in") == "isco" else (rd.get("r_in") or 0.0)
     opts = dict(tol=rd["tol"], cell_deg=rd["cell_deg"], cell_phase_deg=rd["cell_phase_deg"],
                 disk=disk, r_in=r_in, r_out=rd.get("r_out") or 0.0)
+    if rd.get("l0") is not None:
+        opts.update(disk_model=oracle.DISK_CONSTANT_L, l0=rd["l0"])
     opts.update(extra)
     return oracle.trace_pixels(rd["a"], rd["r_obs"], rd["incl_deg"], rd["extent"], rd["nx"],
                                rd["ny"], pixels=pixels, **opts)
