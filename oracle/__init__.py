@@ -19,6 +19,7 @@ from . import build as _build
 STATUS_NONE, STATUS_CAPTURED, STATUS_ESCAPED, STATUS_DISK, STATUS_MAXSTEP, STATUS_ERROR = range(6)
 RKCK45, RKDP45 = 0, 1
 DISK_KEPLERIAN, DISK_CONSTANT_L = 0, 1
+KERR, QMETRIC = 0, 1
 
 _P = ctypes.POINTER
 _d = ctypes.c_double
@@ -30,7 +31,7 @@ class OracleOptions(ctypes.Structure):
     _fields_ = [("tol", _d), ("max_steps", _i64), ("r_cap_factor", _d), ("r_esc_factor", _d),
                 ("disk", _i32), ("r_in", _d), ("r_out", _d), ("cell_deg", _d),
                 ("cell_phase_deg", _d), ("integrator", _i32), ("disk_model", _i32),
-                ("l0", _d)]
+                ("l0", _d), ("spacetime", _i32), ("q", _d), ("mass2", _d)]
 
 
 _OUT_FIELDS = [
@@ -78,6 +79,11 @@ def lib():
         L.oracle_tableau.restype = _i32
         L.oracle_disk_observables.argtypes = [_d, _d, _d, _d, _d, _P(_d), _P(_d)]
         L.oracle_disk_observables_l0.argtypes = [_d, _d, _d, _d, _d, _d, _P(_d), _P(_d)]
+        L.oracle_metric_sp.argtypes = [_i32, _d, _d, _d, _d, _d] + [_P(_d)] * 4
+        L.oracle_hamiltonian_sp.argtypes = [_i32, _d, _d, _d, _P(_d), _d, _d]
+        L.oracle_hamiltonian_sp.restype = _d
+        L.oracle_rhs_sp.argtypes = [_i32, _d, _d, _d, _P(_d), _d, _d, _P(_d)]
+        L.oracle_init_ray_sp.argtypes = [_i32, _d, _d, _d, _d, _d, _d, _d, _P(_d)]
         L.oracle_isco.argtypes = [_d, _d]
         L.oracle_isco.restype = _d
         _lib = L
@@ -90,10 +96,12 @@ def _ptr(arr, ct):
 
 def options(tol=1e-10, max_steps=1_000_000, r_cap_factor=1.01, r_esc_factor=1.1, disk=False,
             r_in=0.0, r_out=0.0, cell_deg=10.0, cell_phase_deg=0.0, integrator=RKCK45,
-            disk_model=DISK_KEPLERIAN, l0=0.0):
+            disk_model=DISK_KEPLERIAN, l0=0.0, spacetime=KERR, q=0.0, mass2=0.0):
+    """spacetime KERR (the `a` argument of the trace calls is the spin) or
+    QMETRIC (quadrupole q, Appendix A); mass2 = 0 null, 1 time-like."""
     return OracleOptions(tol, max_steps, r_cap_factor, r_esc_factor, 1 if disk else 0, r_in,
                          r_out, cell_deg, cell_phase_deg, int(integrator), int(disk_model),
-                         float(l0))
+                         float(l0), int(spacetime), float(q), float(mass2))
 
 
 def _alloc(n):
@@ -229,6 +237,31 @@ def disk_observables_l0(a, r, E, L_z, l0, M=1.0):
     I = _d()
     lib().oracle_disk_observables_l0(M, a, r, E, L_z, l0, ctypes.byref(g), ctypes.byref(I))
     return g.value, I.value
+
+
+def metric_sp(kind, r, th, a=0.0, q=0.0, M=1.0):
+    """(g_cov, g_con, d_r g_con, d_theta g_con) for Kerr (kind 0) or the q-metric (1)."""
+    out = [np.zeros(16) for _ in range(4)]
+    lib().oracle_metric_sp(kind, M, a, q, r, th, *[_ptr(o, _d) for o in out])
+    return tuple(o.reshape(4, 4) for o in out)
+
+
+def hamiltonian_sp(kind, y6, E, L_z, a=0.0, q=0.0, M=1.0):
+    y6 = np.ascontiguousarray(y6, dtype=np.float64)
+    return lib().oracle_hamiltonian_sp(kind, M, a, q, _ptr(y6, _d), E, L_z)
+
+
+def rhs_sp(kind, y6, E, L_z, a=0.0, q=0.0, M=1.0):
+    y6 = np.ascontiguousarray(y6, dtype=np.float64)
+    dy = np.zeros(6)
+    lib().oracle_rhs_sp(kind, M, a, q, _ptr(y6, _d), E, L_z, _ptr(dy, _d))
+    return dy
+
+
+def init_ray_sp(kind, r_obs, incl_deg, x, y, a=0.0, q=0.0, M=1.0):
+    out = np.zeros(8)
+    lib().oracle_init_ray_sp(kind, M, a, q, r_obs, incl_deg, x, y, _ptr(out, _d))
+    return out
 
 
 def isco(a, M=1.0):

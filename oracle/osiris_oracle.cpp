@@ -17,6 +17,8 @@
  *                                                         and the explicit list
  *                                                         of t', r', ..., p_theta'
  *      on the Kerr metric in Boyer-Lindquist form      -- Sec. 4.3, Eq. Kerr
+ *      or on the q-metric                                -- Appendix A, Eq. q-metric
+ *      for null (H = 0) or time-like (H = -1/2) geodesics
  *   3. adaptive Runge-Kutta Cash-Karp 4(5) steps        -- Sec. 3.1 (RKCK45)
  *      or Dormand-Prince 5(4) steps                      -- Sec. 3.1 (RKDP45)
  *   4. the Hamiltonian-constraint error |H| at every accepted point
@@ -70,17 +72,109 @@ enum Status : int {
   kError = 5,
 };
 
+enum SpacetimeKind { kKerr = 0, kQMetric = 1 };
+
 struct Spacetime {
-  double M;  // mass (the paper sets M = 1; M = 0 gives flat space)
-  double a;  // spin parameter a = J / M
+  double M;          // mass (the paper sets M = 1; M = 0 gives flat space)
+  double a;          // Kerr spin parameter a = J / M
+  int kind = kKerr;  // kKerr or kQMetric (Appendix A)
+  double q = 0.0;    // quadrupole parameter of the q-metric
 };
 
 // ---------------------------------------------------------------------------
 // Metric (Sec. 4.3, Eq. Kerr). Index order 0 = t, 1 = r, 2 = theta, 3 = phi.
 // ---------------------------------------------------------------------------
 
-// Covariant components g_{mu nu} of the Kerr line element.
+// ---------------------------------------------------------------------------
+// q-metric (Appendix A, Eq. q-metric): static, axisymmetric, diagonal. The
+// paper prints it with signature (+,-,-,-); with the (-,+,+,+) signature of
+// Sec. 1 and f = 1 - 2m/r, X = 1 + m^2 sin^2 / (r^2 - 2 m r), k = q (2 + q):
+//   g_tt = -f^(1+q),  g_rr = f^(-1-q) X^-k,  g_thth = f^-q r^2 X^-k,
+//   g_phph = f^-q r^2 sin^2.   q = 0 is Schwarzschild.
+// ---------------------------------------------------------------------------
+void qmetric_cov(const Spacetime& S, double r, double th, double g[4][4]) {
+  const double m = S.M, q = S.q, k = q * (2.0 + q);
+  const double s = std::sin(th);
+  const double f = 1.0 - 2.0 * m / r;
+  const double X = 1.0 + m * m * s * s / (r * r - 2.0 * m * r);
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) g[i][j] = 0.0;
+  g[0][0] = -std::pow(f, 1.0 + q);
+  g[1][1] = std::pow(f, -1.0 - q) * std::pow(X, -k);
+  g[2][2] = std::pow(f, -q) * r * r * std::pow(X, -k);
+  g[3][3] = std::pow(f, -q) * r * r * s * s;
+}
+
+void qmetric_con(const Spacetime& S, double r, double th, double gi[4][4]) {
+  double g[4][4];
+  qmetric_cov(S, r, th, g);
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) gi[i][j] = 0.0;
+  for (int i = 0; i < 4; ++i) gi[i][i] = 1.0 / g[i][i];
+}
+
+// r- and theta-derivatives of the diagonal g^{mu mu} of the q-metric, by the
+// product and power rules:
+//   g^tt = -f^(-1-q), g^rr = f^(1+q) X^k, g^thth = f^q X^k / r^2,
+//   g^phph = f^q / (r^2 sin^2), with f_r = 2m/r^2, X_r = -m^2 sin^2 (2r - 2m)/(r^2 - 2mr)^2,
+//   X_th = 2 m^2 sin cos / (r^2 - 2mr).
+void qmetric_con_derivs(const Spacetime& S, double r, double th, double dr[4][4],
+                        double dth[4][4]) {
+  const double m = S.M, q = S.q, k = q * (2.0 + q);
+  const double s = std::sin(th), c = std::cos(th);
+  const double f = 1.0 - 2.0 * m / r;
+  const double f_r = 2.0 * m / (r * r);
+  const double D = r * r - 2.0 * m * r;
+  const double X = 1.0 + m * m * s * s / D;
+  const double X_r = -m * m * s * s * (2.0 * r - 2.0 * m) / (D * D);
+  const double X_th = 2.0 * m * m * s * c / D;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      dr[i][j] = 0.0;
+      dth[i][j] = 0.0;
+    }
+  const double fq = std::pow(f, q), Xk = std::pow(X, k);
+  const double dfq = q * std::pow(f, q - 1.0) * f_r;  // d(f^q)/dr
+  const double dXk_r = k * std::pow(X, k - 1.0) * X_r;
+  const double dXk_th = k * std::pow(X, k - 1.0) * X_th;
+  dr[0][0] = (1.0 + q) * std::pow(f, -2.0 - q) * f_r;
+  dr[1][1] = (1.0 + q) * fq * f_r * Xk + std::pow(f, 1.0 + q) * dXk_r;
+  dr[2][2] = (dfq * Xk + fq * dXk_r) / (r * r) - 2.0 * fq * Xk / (r * r * r);
+  dr[3][3] = dfq / (r * r * s * s) - 2.0 * fq / (r * r * r * s * s);
+  dth[1][1] = std::pow(f, 1.0 + q) * dXk_th;
+  dth[2][2] = fq * dXk_th / (r * r);
+  dth[3][3] = fq / (r * r) * (-2.0 * c / (s * s * s));
+}
+
+void metric_cov_kerr(const Spacetime& S, double r, double th, double g[4][4]);
+void metric_con_kerr(const Spacetime& S, double r, double th, double gi[4][4]);
+void metric_con_derivs_kerr(const Spacetime& S, double r, double th, double dr[4][4],
+                            double dth[4][4]);
+
 void metric_cov(const Spacetime& S, double r, double th, double g[4][4]) {
+  if (S.kind == kQMetric)
+    qmetric_cov(S, r, th, g);
+  else
+    metric_cov_kerr(S, r, th, g);
+}
+
+void metric_con(const Spacetime& S, double r, double th, double gi[4][4]) {
+  if (S.kind == kQMetric)
+    qmetric_con(S, r, th, gi);
+  else
+    metric_con_kerr(S, r, th, gi);
+}
+
+void metric_con_derivs(const Spacetime& S, double r, double th, double dr[4][4],
+                       double dth[4][4]) {
+  if (S.kind == kQMetric)
+    qmetric_con_derivs(S, r, th, dr, dth);
+  else
+    metric_con_derivs_kerr(S, r, th, dr, dth);
+}
+
+// Covariant components g_{mu nu} of the Kerr line element.
+void metric_cov_kerr(const Spacetime& S, double r, double th, double g[4][4]) {
   const double M = S.M, a = S.a;
   const double s = std::sin(th), c = std::cos(th);
   const double Sigma = r * r + a * a * c * c;
@@ -102,7 +196,7 @@ void metric_cov(const Spacetime& S, double r, double th, double g[4][4]) {
 //   g^tphi = -2 M a r / (Sigma Delta)
 //   g^phph = (Delta - a^2 sin^2) / (Sigma Delta sin^2)
 //   g^rr = Delta / Sigma,  g^thth = 1 / Sigma
-void metric_con(const Spacetime& S, double r, double th, double gi[4][4]) {
+void metric_con_kerr(const Spacetime& S, double r, double th, double gi[4][4]) {
   const double M = S.M, a = S.a;
   const double s = std::sin(th), c = std::cos(th);
   const double s2 = s * s;
@@ -123,8 +217,8 @@ void metric_con(const Spacetime& S, double r, double th, double gi[4][4]) {
 // Partial derivatives of g^{mu nu} with respect to r (dr) and theta (dth),
 // obtained by differentiating the closed forms above by hand with the
 // quotient rule.
-void metric_con_derivs(const Spacetime& S, double r, double th, double dr[4][4],
-                       double dth[4][4]) {
+void metric_con_derivs_kerr(const Spacetime& S, double r, double th, double dr[4][4],
+                            double dth[4][4]) {
   const double M = S.M, a = S.a;
   const double s = std::sin(th), c = std::cos(th);
   const double s2 = s * s;
@@ -427,6 +521,7 @@ struct Options {
   double cell_phase_deg; // longitude offset of the checkerboard
   int disk_model;        // kKeplerian or kConstantL
   double l0;             // specific angular momentum of the constant-l0 disk
+  double mass2;          // 0: null geodesics (H = 0); 1: time-like (H = -1/2), Sec. 2.1
 };
 
 struct Result {
@@ -440,7 +535,10 @@ struct Result {
   double carter0, max_carter_drift;
 };
 
+// Inner stopping surface scale: the Kerr event horizon r_H = M + sqrt(M^2 - a^2)
+// (Sec. 4.3), or the singular surface r = 2m of the q-metric (Appendix A).
 double horizon_radius(const Spacetime& S) {
+  if (S.kind == kQMetric) return 2.0 * S.M;
   return S.M + std::sqrt(S.M * S.M - S.a * S.a);
 }
 
@@ -563,7 +661,9 @@ Result integrate(const Spacetime& S, const Ray& R, const double y_init[NY], doub
   double y[NY];
   std::memcpy(y, y_init, sizeof(y));
   double h = 0.01 * r0;
-  double max_H = std::fabs(hamiltonian(S, R, y));
+  // Error = |H_num - H| (Sec. 3.1) with H = -mass2 / 2 on the mass shell
+  const double H_shell = -0.5 * o.mass2;
+  double max_H = std::fabs(hamiltonian(S, R, y) - H_shell);
   const double Q0 = carter(S, R, y);
   double max_dQ = 0.0;
   double y5[NY], delta[NY], yfin[NY];
@@ -618,7 +718,7 @@ Result integrate(const Spacetime& S, const Ray& R, const double y_init[NY], doub
         break;
       }
       std::memcpy(y, y5, sizeof(y));
-      max_H = std::max(max_H, std::fabs(hamiltonian(S, R, y)));
+      max_H = std::max(max_H, std::fabs(hamiltonian(S, R, y) - H_shell));
       max_dQ = std::max(max_dQ, std::fabs(carter(S, R, y) - Q0));
     } else {
       ++rej;
@@ -628,7 +728,7 @@ Result integrate(const Spacetime& S, const Ray& R, const double y_init[NY], doub
   }
 
   if (out.status != kError) {
-    max_H = std::max(max_H, std::fabs(hamiltonian(S, R, yfin)));
+    max_H = std::max(max_H, std::fabs(hamiltonian(S, R, yfin) - H_shell));
     max_dQ = std::max(max_dQ, std::fabs(carter(S, R, yfin) - Q0));
   }
   std::memcpy(out.y, yfin, sizeof(yfin));
@@ -695,6 +795,9 @@ struct oracle_options {
   int32_t integrator;  // 0 = Cash-Karp 4(5), 1 = Dormand-Prince 5(4)
   int32_t disk_model;  // 0 = Keplerian, 1 = constant specific angular momentum l0
   double l0;
+  int32_t spacetime;   // 0 = Kerr (parameter a), 1 = q-metric (parameter q)
+  double q;
+  double mass2;        // 0 = null, 1 = time-like
 };
 
 static void store(const Result& R, oracle_outputs* o, int64_t k) {
@@ -735,6 +838,7 @@ static Options to_options(const oracle_options* oo) {
   o.cell_phase_deg = oo->cell_phase_deg;
   o.disk_model = oo->disk_model;
   o.l0 = oo->l0;
+  o.mass2 = oo->mass2;
   return o;
 }
 
@@ -748,6 +852,8 @@ int oracle_trace_pixels(double M, double a, double r0, double incl_deg, double x
   Camera cam;
   cam.S.M = M;
   cam.S.a = a;
+  cam.S.kind = opts->spacetime;
+  cam.S.q = opts->q;
   cam.r0 = r0;
   cam.th0 = incl_deg * kPi / 180.0;
   cam.x_min = x_min;
@@ -791,7 +897,7 @@ int oracle_trace_pixels(double M, double a, double r0, double incl_deg, double x
 int oracle_trace_states(double M, double a, double r0, const oracle_options* opts,
                         const double* states, const double* E, const double* L, int64_t count,
                         oracle_outputs* out) {
-  Spacetime S{M, a};
+  Spacetime S{M, a, opts->spacetime, opts->q};
   const Options o = to_options(opts);
   for (int64_t k = 0; k < count; ++k) {
     Ray R{E[k], L[k]};
@@ -809,6 +915,48 @@ void oracle_init_ray(double M, double a, double r0, double incl_deg, double x, d
   std::memset(&cam, 0, sizeof(cam));
   cam.S.M = M;
   cam.S.a = a;
+  cam.r0 = r0;
+  cam.th0 = incl_deg * kPi / 180.0;
+  Ray R;
+  double st[NY];
+  init_ray(cam, x, y, &R, st);
+  for (int n = 0; n < NY; ++n) out8[n] = st[n];
+  out8[6] = R.E;
+  out8[7] = R.L;
+}
+
+// Metric functions for either space-time: kind 0 = Kerr (a), 1 = q-metric (q).
+void oracle_metric_sp(int32_t kind, double M, double a, double q, double r, double th,
+                      double* cov16, double* con16, double* dr16, double* dth16) {
+  const Spacetime S{M, a, kind, q};
+  double g[4][4], gi[4][4], dr[4][4], dth[4][4];
+  metric_cov(S, r, th, g);
+  metric_con(S, r, th, gi);
+  metric_con_derivs(S, r, th, dr, dth);
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      cov16[4 * i + j] = g[i][j];
+      con16[4 * i + j] = gi[i][j];
+      dr16[4 * i + j] = dr[i][j];
+      dth16[4 * i + j] = dth[i][j];
+    }
+}
+
+double oracle_hamiltonian_sp(int32_t kind, double M, double a, double q, const double* y6,
+                             double E, double L) {
+  return hamiltonian(Spacetime{M, a, kind, q}, Ray{E, L}, y6);
+}
+
+void oracle_rhs_sp(int32_t kind, double M, double a, double q, const double* y6, double E,
+                   double L, double* dy6) {
+  rhs(Spacetime{M, a, kind, q}, Ray{E, L}, y6, dy6);
+}
+
+void oracle_init_ray_sp(int32_t kind, double M, double a, double q, double r0, double incl_deg,
+                        double x, double y, double* out8) {
+  Camera cam;
+  std::memset(&cam, 0, sizeof(cam));
+  cam.S = Spacetime{M, a, kind, q};
   cam.r0 = r0;
   cam.th0 = incl_deg * kPi / 180.0;
   Ray R;

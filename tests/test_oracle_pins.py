@@ -634,3 +634,97 @@ def test_constant_l0_disk_render():
         assert np.array_equal(res[key], kep[key]), key
     assert not np.allclose(res["g"][disk], kep["g"][disk])
     assert np.all(res["g"][disk] > 0)
+
+
+# ---------------------------------------------------------------------------
+# q-metric (Appendix A) and time-like geodesics
+# ---------------------------------------------------------------------------
+
+def _qmetric_line_element(q, r, th):
+    """The q-metric of Appendix A, converted to signature (-,+,+,+)."""
+    f = 1 - 2 / r
+    X = 1 + math.sin(th) ** 2 / (r * r - 2 * r)
+    k = q * (2 + q)
+    return np.diag([-f ** (1 + q), f ** (-1 - q) * X ** -k, f ** -q * r * r * X ** -k,
+                    f ** -q * (r * math.sin(th)) ** 2])
+
+
+@pytest.mark.parametrize("q", [0.5, -0.5, 0.2])
+def test_qmetric_components_and_derivatives(q):
+    for r, th in ((3.5, 1.0), (9.0, 0.4), (25.0, 2.0), (4.2, math.pi / 2)):
+        g, gi, dr, dth = oracle.metric_sp(oracle.QMETRIC, r, th, q=q)
+        assert np.allclose(g, _qmetric_line_element(q, r, th), rtol=1e-14, atol=0)
+        assert np.allclose(gi @ g, np.eye(4), atol=1e-13)
+        fr = _fd(lambda rr: oracle.metric_sp(oracle.QMETRIC, rr, th, q=q)[1], r, 1e-3 * r)
+        ft = _fd(lambda tt: oracle.metric_sp(oracle.QMETRIC, r, tt, q=q)[1], th, 1e-3)
+        scale = np.abs(fr).max()
+        assert np.abs(dr - fr).max() <= 1e-8 * scale
+        # theta-derivatives vanish on the equator: compare on the r-derivative scale
+        assert np.abs(dth - ft).max() <= 1e-8 * max(np.abs(ft).max(), scale)
+
+
+def test_qmetric_q0_is_schwarzschild():
+    for r, th in ((3.0, 0.7), (50.0, 2.2)):
+        gq = oracle.metric_sp(oracle.QMETRIC, r, th, q=0.0)
+        gk = oracle.metric_sp(oracle.KERR, r, th, a=0.0)
+        for A, B in zip(gq, gk):
+            assert np.allclose(A, B, rtol=1e-13, atol=1e-300)
+    n = 16
+    rq = oracle.trace_pixels(0.0, R0, 60.0, (-8, 8, -8, 8), n, n, spacetime=oracle.QMETRIC,
+                             q=0.0)
+    rk = oracle.trace_pixels(0.0, R0, 60.0, (-8, 8, -8, 8), n, n)
+    assert np.array_equal(rq["status"], rk["status"])
+    for key in ("r", "theta", "phi"):
+        assert np.allclose(rq[key], rk[key], rtol=1e-9, atol=1e-9), key
+
+
+def _circular_orbit(q, r):
+    """Equatorial circular time-like orbit of the static metric from the line
+    element alone: Omega^2 = -d_r g_tt / d_r g_phph, u^t from g_ab u^a u^b = -1,
+    E = -g_tt u^t, L = g_phph Omega u^t."""
+    h = 1e-5 * r
+    g = _qmetric_line_element(q, r, math.pi / 2)
+    gp = _qmetric_line_element(q, r + h, math.pi / 2)
+    gm = _qmetric_line_element(q, r - h, math.pi / 2)
+    dgtt = (gp[0, 0] - gm[0, 0]) / (2 * h)
+    dgpp = (gp[3, 3] - gm[3, 3]) / (2 * h)
+    Om = math.sqrt(-dgtt / dgpp)
+    ut = 1 / math.sqrt(-g[0, 0] - g[3, 3] * Om * Om)
+    return Om, -g[0, 0] * ut, g[3, 3] * Om * ut
+
+
+@pytest.mark.parametrize("q", [0.0, 0.5, -0.5])
+def test_timelike_circular_orbits(q):
+    r = 12.0
+    Om, E, L = _circular_orbit(q, r)
+    if q == 0.0:  # Schwarzschild closed form
+        assert E == pytest.approx((1 - 2 / r) / math.sqrt(1 - 3 / r), rel=1e-9)
+        assert L == pytest.approx(math.sqrt(r) / math.sqrt(1 - 3 / r), rel=1e-9)
+    st = np.array([[0.0, r, math.pi / 2, 0.0, 0.0, 0.0]])
+    # the initial data lie on the mass shell H = -1/2
+    assert oracle.hamiltonian_sp(oracle.QMETRIC, st[0], E, L, q=q) == pytest.approx(-0.5,
+                                                                                   abs=1e-9)
+    res = oracle.trace_states(0.0, 1000.0, st, [E], [L], spacetime=oracle.QMETRIC, q=q,
+                              mass2=1.0, max_steps=150)
+    assert res["status"][0] == oracle.STATUS_MAXSTEP
+    assert res["r"][0] == pytest.approx(r, rel=1e-7)
+    assert res["phi"][0] / res["t"][0] == pytest.approx(Om, rel=1e-7)
+    assert res["max_abs_H"][0] < 1e-8
+
+
+def test_timelike_radial_escape_and_H_shell():
+    """An unbound time-like particle (E > 1) in the q-metric escapes, keeping
+    |H + 1/2| near the tolerance; the same ray traced as null data fails the
+    null constraint, which is what max_abs_H reports."""
+    q = -0.5
+    r = 30.0
+    g = _qmetric_line_element(q, r, math.pi / 2)
+    E, L, pth = 1.2, 4.0, 0.0
+    # p_r from the mass shell g^tt E^2 + g^rr p_r^2 + g^phph L^2 = -1
+    pr = math.sqrt((-1 + E * E / -g[0, 0] - L * L / g[3, 3]) * g[1, 1])
+    st = np.array([[0.0, r, math.pi / 2, 0.0, pr, pth]])
+    res = oracle.trace_states(0.0, 100.0, st, [E], [L], spacetime=oracle.QMETRIC, q=q, mass2=1.0)
+    assert res["status"][0] == oracle.STATUS_ESCAPED
+    assert res["max_abs_H"][0] < 1e-8
+    res0 = oracle.trace_states(0.0, 100.0, st, [E], [L], spacetime=oracle.QMETRIC, q=q)
+    assert abs(res0["max_abs_H"][0] - 0.5) < 1e-8
