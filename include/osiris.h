@@ -59,6 +59,10 @@ extern "C" {
 #define OSIRIS_RKDP45 1 /* Dormand-Prince 5(4), first same as last: six new
                            evaluations per attempt (FP64 and DF64 only) */
 
+/* ---- space-times ------------------------------------------------------- */
+#define OSIRIS_SPACETIME_KERR 0    /* Kerr, Boyer-Lindquist (Sec. 4.3), spin a */
+#define OSIRIS_SPACETIME_QMETRIC 1 /* q-metric (Appendix A), quadrupole q, m = 1 */
+
 /* ---- counters written to osiris_trace_opts.stats (uint64 each) --------- */
 #define OSIRIS_STAT_RAYS 0          /* rays finished */
 #define OSIRIS_STAT_ACCEPTED 1      /* accepted Cash-Karp steps */
@@ -152,6 +156,19 @@ void osiris_default_opts(osiris_trace_opts* opts);
 int osiris_init_camera(osiris_camera** out, double a, double r_obs, double incl_deg,
                        double x_min, double x_max, double y_min, double y_max, int32_t nx,
                        int32_t ny);
+
+/* Camera in the q-metric (Appendix A, Eq. q-metric with m = 1, written in
+ * signature (-,+,+,+)): g_tt = -f^(1+q), g_rr = f^(-1-q) X^-k,
+ * g_thth = f^-q r^2 X^-k, g_phph = f^-q r^2 sin^2, f = 1 - 2/r,
+ * X = 1 + sin^2/(r^2 - 2r), k = q (2 + q). q = 0 is Schwarzschild; q in
+ * (-1, -1 + sqrt(3/2)) \ {0} describes naked singularities. The initial data
+ * are those of osiris_init_camera for this static metric; rays end at
+ * r < r_cap_factor * 2 (the singular surface r = 2) or at the celestial
+ * sphere. q-metric renders run in FP64 (OSIRIS_FP64) without a disk.
+ *   q          > -1; r_obs > 20; the other arguments as osiris_init_camera. */
+int osiris_init_camera_q(osiris_camera** out, double q, double r_obs, double incl_deg,
+                         double x_min, double x_max, double y_min, double y_max, int32_t nx,
+                         int32_t ny);
 
 void osiris_destroy_camera(osiris_camera* cam);
 
@@ -258,6 +275,17 @@ int osiris_trace_states(double a, double r_obs, const double* states, const doub
                         const double* L, int64_t n, int32_t disk, double r_in, double r_out,
                         const osiris_trace_opts* opts, const osiris_outputs* out,
                         void* cuda_stream);
+
+/* Test hook for either space-time and for massive particles: as
+ * osiris_trace_states, with spacetime = OSIRIS_SPACETIME_KERR (param = a) or
+ * OSIRIS_SPACETIME_QMETRIC (param = q), and mass2 = 0 for light (H = 0) or
+ * 1 for a unit-mass particle on the shell H = -1/2 (time-like geodesics,
+ * Sec. 2.1 and Appendix A). max_abs_H then reports max |H - H_shell|. The
+ * q-metric needs OSIRIS_FP64 and disk = 0. */
+int osiris_trace_states_ex(int32_t spacetime, double param, double r_obs, double mass2,
+                           const double* states, const double* E, const double* L, int64_t n,
+                           int32_t disk, double r_in, double r_out, const osiris_trace_opts* opts,
+                           const osiris_outputs* out, void* cuda_stream);
 
 /* Copy n entries of every non-NULL field of dev (DEVICE) to the same field of
  * host (HOST, preferably pinned), asynchronously on the stream. Fields that

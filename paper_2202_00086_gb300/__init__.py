@@ -22,6 +22,7 @@ STATUS_NONE, STATUS_CAPTURED, STATUS_ESCAPED, STATUS_DISK, STATUS_MAXSTEP, STATU
 FP64, MIXED, DF64 = 0, 1, 2
 RKCK45, RKDP45 = 0, 1
 DISK_NONE, DISK_KEPLERIAN, DISK_CONSTANT_L = 0, 1, 2
+SPACETIME_KERR, SPACETIME_QMETRIC = 0, 1
 STATS_LEN = 16
 STAT_NAMES = ["rays", "accepted", "rejected", "root_steps", "rhs_evals", "status_none",
               "status_captured", "status_escaped", "status_disk", "status_maxstep",
@@ -73,6 +74,11 @@ def lib():
         L.osiris_default_opts.argtypes = [_P(TraceOpts)]
         L.osiris_init_camera.argtypes = [_P(_vp), _d, _d, _d, _d, _d, _d, _d, ctypes.c_int32,
                                          ctypes.c_int32]
+        L.osiris_init_camera_q.argtypes = [_P(_vp), _d, _d, _d, _d, _d, _d, _d, ctypes.c_int32,
+                                           ctypes.c_int32]
+        L.osiris_trace_states_ex.argtypes = [ctypes.c_int32, _d, _d, _d, _vp, _vp, _vp,
+                                             ctypes.c_int64, ctypes.c_int32, _d, _d,
+                                             _P(TraceOpts), _P(Outputs), _vp]
         L.osiris_destroy_camera.argtypes = [_vp]
         L.osiris_camera_rays.argtypes = [_vp]
         L.osiris_camera_rays.restype = ctypes.c_int64
@@ -119,12 +125,20 @@ class Camera:
     """Observer at (r_obs, incl_deg), image plane extent (x_min, x_max, y_min,
     y_max) with nx x ny pixels (osiris_init_camera)."""
 
-    def __init__(self, a, r_obs, incl_deg, extent, nx, ny):
+    def __init__(self, a, r_obs, incl_deg, extent, nx, ny, q=None):
+        """Kerr camera with spin a; with q given, a q-metric camera
+        (osiris_init_camera_q, a is ignored)."""
         h = _vp()
         x0, x1, y0, y1 = (float(v) for v in extent)
-        _check(lib().osiris_init_camera(ctypes.byref(h), float(a), float(r_obs),
-                                        float(incl_deg), x0, x1, y0, y1, int(nx), int(ny)),
-               "osiris_init_camera")
+        if q is None:
+            _check(lib().osiris_init_camera(ctypes.byref(h), float(a), float(r_obs),
+                                            float(incl_deg), x0, x1, y0, y1, int(nx), int(ny)),
+                   "osiris_init_camera")
+        else:
+            _check(lib().osiris_init_camera_q(ctypes.byref(h), float(q), float(r_obs),
+                                              float(incl_deg), x0, x1, y0, y1, int(nx),
+                                              int(ny)), "osiris_init_camera_q")
+        self.q = q
         self._h = h
         self.a, self.r_obs, self.incl_deg = float(a), float(r_obs), float(incl_deg)
         self.extent, self.nx, self.ny = (x0, x1, y0, y1), int(nx), int(ny)
@@ -145,7 +159,8 @@ class Camera:
 
     @classmethod
     def from_render(cls, rd):
-        return cls(rd["a"], rd["r_obs"], rd["incl_deg"], rd["extent"], rd["nx"], rd["ny"])
+        return cls(rd["a"], rd["r_obs"], rd["incl_deg"], rd["extent"], rd["nx"], rd["ny"],
+                   q=rd.get("q"))
 
 
 def workspace_bytes(n_requests=1):
@@ -270,8 +285,10 @@ def trace_batch_static(requests, stream=None, **opts):
 
 
 def trace_states(a, r_obs, states, E, L, out=None, disk=False, r_in=0.0, r_out=0.0,
-                 stream=None, **opts):
-    """Trace rays from explicit device initial data (osiris_trace_states)."""
+                 stream=None, q=None, mass2=0.0, **opts):
+    """Trace rays from explicit device initial data (osiris_trace_states_ex):
+    Kerr with spin a, or the q-metric when q is given; mass2 = 0 for light,
+    1 for unit-mass particles (H = -1/2)."""
     n = int(E.numel())
     assert states.is_cuda and states.dtype == torch.float64 and states.is_contiguous()
     assert E.is_cuda and L.is_cuda and E.dtype == torch.float64 and L.dtype == torch.float64
@@ -279,10 +296,12 @@ def trace_states(a, r_obs, states, E, L, out=None, disk=False, r_in=0.0, r_out=0
         out = alloc_outputs(n, fields=DISK_FIELDS if disk else SHADOW_FIELDS)
     o = make_opts(**opts)
     os_ = outputs_struct(out)
-    _check(lib().osiris_trace_states(float(a), float(r_obs), states.data_ptr(), E.data_ptr(),
-                                     L.data_ptr(), n, 1 if disk else 0, float(r_in),
-                                     float(r_out), ctypes.byref(o), ctypes.byref(os_),
-                                     _stream_handle(stream)), "osiris_trace_states")
+    sp, param = (SPACETIME_QMETRIC, float(q)) if q is not None else (SPACETIME_KERR, float(a))
+    _check(lib().osiris_trace_states_ex(sp, param, float(r_obs), float(mass2),
+                                        states.data_ptr(), E.data_ptr(), L.data_ptr(), n,
+                                        1 if disk else 0, float(r_in), float(r_out),
+                                        ctypes.byref(o), ctypes.byref(os_),
+                                        _stream_handle(stream)), "osiris_trace_states_ex")
     return out
 
 

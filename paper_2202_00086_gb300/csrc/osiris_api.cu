@@ -17,6 +17,8 @@ using osiris_impl::KernelArgs;
 using osiris_impl::ReqDev;
 
 struct osiris_camera {
+  int32_t spacetime;  // OSIRIS_SPACETIME_*
+  double q;           // q-metric quadrupole
   double a, r0, incl_deg, th0;
   double x_min, x_max, y_min, y_max;
   int32_t nx, ny;
@@ -32,6 +34,11 @@ constexpr int kDefaultBlock = 128;
 bool is_fin(double v) { return std::isfinite(v); }
 
 double horizon(double a) { return 1.0 + std::sqrt(1.0 - a * a); }
+
+// Inner stopping surface scale: Kerr horizon, or the q-metric's r = 2.
+double inner_radius(int spacetime, double a) {
+  return spacetime == OSIRIS_SPACETIME_QMETRIC ? 2.0 : horizon(a);
+}
 
 int check_opts(const osiris_trace_opts* o) {
   if (!o) return OSIRIS_EINVAL;
@@ -63,10 +70,14 @@ int check_disk(double a, double r_cap_factor, double r_esc, double r_in, double 
 // Fields common to pixel and explicit-state requests.
 void fill_common(ReqDev& R, double a, double r0, const osiris_trace_opts* o, double tol,
                  int disk, double r_in, double r_out, const osiris_outputs* out,
-                 double l0 = 0.0) {
+                 double l0 = 0.0, int spacetime = OSIRIS_SPACETIME_KERR, double q = 0.0,
+                 double mass2 = 0.0) {
+  R.spacetime = spacetime;
   R.a = a;
+  R.q = q;
+  R.H0 = -0.5 * mass2;
   R.r0 = r0;
-  R.r_cap = o->r_cap_factor * horizon(a);
+  R.r_cap = o->r_cap_factor * inner_radius(spacetime, a);
   R.r_esc = o->r_esc_factor * r0;
   R.disk = disk;
   R.r_in = disk ? r_in : 0.0;
@@ -112,6 +123,14 @@ int apply_range(ReqDev& R, const osiris_request& q) {
 }
 
 int cuda_rc(int e) { return e == 0 ? OSIRIS_OK : OSIRIS_ECUDA; }
+
+// The q-metric runs in FP64 without a disk.
+int check_spacetime(int spacetime, int disk, const osiris_trace_opts* o) {
+  if (spacetime == OSIRIS_SPACETIME_KERR) return OSIRIS_OK;
+  if (spacetime != OSIRIS_SPACETIME_QMETRIC) return OSIRIS_EINVAL;
+  if (o->precision != OSIRIS_FP64 || disk) return OSIRIS_EINVAL;
+  return OSIRIS_OK;
+}
 
 int sm_count(int* n) {
   int dev = 0;
@@ -166,10 +185,13 @@ int run_camera(const osiris_camera* cam, int disk, double r_in, double r_out, do
   if (disk)
     if (int rc = check_disk(cam->a, o->r_cap_factor, r_esc, r_in, r_out)) return rc;
   if (!is_fin(l0)) return OSIRIS_EINVAL;
+  if (int rc = check_spacetime(cam->spacetime, disk, o)) return rc;
   KernelArgs args;
   std::memset(&args, 0, sizeof(args));
   ReqDev& R = args.single;
-  fill_common(R, cam->a, cam->r0, o, o->tol, disk, r_in, r_out, out, l0);
+  fill_common(R, cam->a, cam->r0, o, o->tol, disk, r_in, r_out, out, l0, cam->spacetime,
+              cam->q);
+  args.spacetime = cam->spacetime;
   fill_camera(R, cam);
   R.ray_begin = 0;
   args.reqs = nullptr;
@@ -214,6 +236,8 @@ int osiris_init_camera(osiris_camera** out, double a, double r_obs, double incl_
 
   osiris_camera* c = new (std::nothrow) osiris_camera;
   if (!c) return OSIRIS_ENOMEM;
+  c->spacetime = OSIRIS_SPACETIME_KERR;
+  c->q = 0.0;
   c->a = a;
   c->r0 = r_obs;
   c->incl_deg = incl_deg;
@@ -240,6 +264,38 @@ int osiris_init_camera(osiris_camera** out, double a, double r_obs, double incl_
   c->pth_y = std::sqrt(Sigma) / r;
   c->grr = Sigma / Delta;
   *out = c;
+  return OSIRIS_OK;
+}
+
+int osiris_init_camera_q(osiris_camera** out, double q, double r_obs, double incl_deg,
+                         double x_min, double x_max, double y_min, double y_max, int32_t nx,
+                         int32_t ny) {
+  if (!out) return OSIRIS_EINVAL;
+  *out = nullptr;
+  if (!is_fin(q) || !(q > -1.0)) return OSIRIS_EINVAL;
+  // validate the image plane with the Kerr a = 0 checks (same r_obs > 20 bound)
+  osiris_camera* tmp = nullptr;
+  if (int rc = osiris_init_camera(&tmp, 0.0, r_obs, incl_deg, x_min, x_max, y_min, y_max, nx,
+                                  ny))
+    return rc;
+  tmp->spacetime = OSIRIS_SPACETIME_QMETRIC;
+  tmp->q = q;
+  // observer terms of the initial momenta on the static q-metric (g_tphi = 0,
+  // so A_t = 1/sqrt(-g_tt)) at (r_obs, theta0)
+  const double r = r_obs, s = std::sin(tmp->th0);
+  const double k = q * (2.0 + q);
+  const double f = 1.0 - 2.0 / r;
+  const double X = 1.0 + s * s / (r * r - 2.0 * r);
+  const double g_tt = -std::pow(f, 1.0 + q);
+  const double g_rr = std::pow(f, -1.0 - q) * std::pow(X, -k);
+  const double g_thth = std::pow(f, -q) * r * r * std::pow(X, -k);
+  const double g_phph = std::pow(f, -q) * r * r * s * s;
+  tmp->inv_At = std::sqrt(-g_tt);
+  tmp->e_x = 0.0;
+  tmp->l_x = -std::sqrt(g_phph) / r;
+  tmp->pth_y = std::sqrt(g_thth) / r;
+  tmp->grr = g_rr;
+  *out = tmp;
   return OSIRIS_OK;
 }
 
@@ -284,12 +340,15 @@ int osiris_trace_batch(const osiris_request* reqs, int32_t n, const osiris_trace
     if (q.tol < 0.0 || !is_fin(q.tol)) return OSIRIS_EINVAL;
     if (q.disk < OSIRIS_DISK_NONE || q.disk > OSIRIS_DISK_CONSTANT_L || !is_fin(q.l0))
       return OSIRIS_EINVAL;
+    if (q.camera->spacetime != reqs[0].camera->spacetime) return OSIRIS_EINVAL;
+    if (int rc = check_spacetime(q.camera->spacetime, q.disk, o)) return rc;
     const double r_esc = o->r_esc_factor * q.camera->r0;
     if (q.disk)
       if (int rc = check_disk(q.camera->a, o->r_cap_factor, r_esc, q.r_in, q.r_out)) return rc;
     ReqDev& R = table[k];
     std::memset(&R, 0, sizeof(R));
-    fill_common(R, q.camera->a, q.camera->r0, o, q.tol, q.disk, q.r_in, q.r_out, &q.out, q.l0);
+    fill_common(R, q.camera->a, q.camera->r0, o, q.tol, q.disk, q.r_in, q.r_out, &q.out, q.l0,
+                q.camera->spacetime, q.camera->q);
     fill_camera(R, q.camera);
     if (int rc = apply_range(R, q)) return rc;
     R.ray_begin = begin;
@@ -310,20 +369,32 @@ int osiris_trace_batch(const osiris_request* reqs, int32_t n, const osiris_trace
   return launch(args, o, cuda_stream);
 }
 
-int osiris_trace_states(double a, double r_obs, const double* states, const double* E,
-                        const double* L, int64_t n, int32_t disk, double r_in, double r_out,
-                        const osiris_trace_opts* o, const osiris_outputs* out,
-                        void* cuda_stream) {
+int osiris_trace_states_ex(int32_t spacetime, double param, double r_obs, double mass2,
+                           const double* states, const double* E, const double* L, int64_t n,
+                           int32_t disk, double r_in, double r_out, const osiris_trace_opts* o,
+                           const osiris_outputs* out, void* cuda_stream) {
   if (!out || n < 0) return OSIRIS_EINVAL;
   if (n > 0 && (!states || !E || !L)) return OSIRIS_EINVAL;
-  if (!(a >= 0.0 && a < 1.0) || !is_fin(r_obs) || !(r_obs > 0.0)) return OSIRIS_EINVAL;
+  if (!is_fin(r_obs) || !(r_obs > 0.0) || !is_fin(mass2) || mass2 < 0.0) return OSIRIS_EINVAL;
+  double a = 0.0, q = 0.0;
+  if (spacetime == OSIRIS_SPACETIME_KERR) {
+    if (!(param >= 0.0 && param < 1.0)) return OSIRIS_EINVAL;
+    a = param;
+  } else if (spacetime == OSIRIS_SPACETIME_QMETRIC) {
+    if (!is_fin(param) || !(param > -1.0)) return OSIRIS_EINVAL;
+    q = param;
+  } else {
+    return OSIRIS_EINVAL;
+  }
   if (int rc = check_opts(o)) return rc;
+  if (int rc = check_spacetime(spacetime, disk, o)) return rc;
   if (disk)
     if (int rc = check_disk(a, o->r_cap_factor, o->r_esc_factor * r_obs, r_in, r_out)) return rc;
   KernelArgs args;
   std::memset(&args, 0, sizeof(args));
   ReqDev& R = args.single;
-  fill_common(R, a, r_obs, o, o->tol, disk, r_in, r_out, out);
+  fill_common(R, a, r_obs, o, o->tol, disk ? OSIRIS_DISK_KEPLERIAN : OSIRIS_DISK_NONE, r_in,
+              r_out, out, 0.0, spacetime, q, mass2);
   R.explicit_states = 1;
   R.states = states;
   R.E = E;
@@ -334,9 +405,18 @@ int osiris_trace_states(double a, double r_obs, const double* states, const doub
   R.ray_begin = 0;
   R.pixel_offset = 0;
   args.n_req = 1;
+  args.spacetime = spacetime;
   args.total_rays = n;
   args.stats = reinterpret_cast<unsigned long long*>(o->stats);
   return launch(args, o, cuda_stream);
+}
+
+int osiris_trace_states(double a, double r_obs, const double* states, const double* E,
+                        const double* L, int64_t n, int32_t disk, double r_in, double r_out,
+                        const osiris_trace_opts* o, const osiris_outputs* out,
+                        void* cuda_stream) {
+  return osiris_trace_states_ex(OSIRIS_SPACETIME_KERR, a, r_obs, 0.0, states, E, L, n, disk,
+                                r_in, r_out, o, out, cuda_stream);
 }
 
 int osiris_copy_outputs_to_host(const osiris_outputs* dev, const osiris_outputs* host, int64_t n,
@@ -440,6 +520,8 @@ extern "C" int osiris_trace_batch_static(const osiris_request* reqs, int32_t n,
     if (q.tol < 0.0 || !is_fin(q.tol)) return OSIRIS_EINVAL;
     if (q.disk < OSIRIS_DISK_NONE || q.disk > OSIRIS_DISK_CONSTANT_L || !is_fin(q.l0))
       return OSIRIS_EINVAL;
+    if (q.camera->spacetime != reqs[0].camera->spacetime) return OSIRIS_EINVAL;
+    if (int rc = check_spacetime(q.camera->spacetime, q.disk, &o)) return rc;
     if (q.disk)
       if (int rc = check_disk(q.camera->a, o.r_cap_factor, o.r_esc_factor * q.camera->r0, q.r_in,
                               q.r_out))
@@ -447,7 +529,7 @@ extern "C" int osiris_trace_batch_static(const osiris_request* reqs, int32_t n,
     ReqDev& R = g_static_table[k];
     std::memset(&R, 0, sizeof(R));
     fill_common(R, q.camera->a, q.camera->r0, &o, q.tol, q.disk, q.r_in, q.r_out, &q.out,
-                q.l0);
+                q.l0, q.camera->spacetime, q.camera->q);
     fill_camera(R, q.camera);
     if (int rc = apply_range(R, q)) return rc;
     R.ray_begin = begin;
@@ -467,6 +549,7 @@ extern "C" int osiris_trace_batch_static(const osiris_request* reqs, int32_t n,
   std::memset(&args, 0, sizeof(args));
   args.reqs = dev_table;
   args.n_req = n;
+  args.spacetime = reqs[0].camera->spacetime;
   args.total_rays = begin;
   args.stats = reinterpret_cast<unsigned long long*>(o.stats);
   o.workspace = base;  // launch() clears the queue counter at its head

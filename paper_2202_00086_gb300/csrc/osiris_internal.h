@@ -13,8 +13,12 @@ namespace osiris_impl {
 // kernel parameter space for single renders and in the workspace for
 // batches. Every quantity the kernels need per ray is precomputed on the host.
 struct alignas(16) ReqDev {
-  // space-time (M = 1)
+  // space-time (M = 1): Kerr with spin a, or the q-metric with quadrupole q
+  int32_t spacetime;  // OSIRIS_SPACETIME_*
   double a;
+  double q;
+  // mass shell: H = H0 (0 for light, -1/2 for massive particles)
+  double H0;
   // observer and image plane (Sec. 2.3)
   double r0, th0;
   double x_min, x_span, y_min, y_span;  // centre of pixel i: x_min + (i + 1/2) x_span / nx
@@ -46,6 +50,7 @@ struct alignas(16) ReqDev {
 struct KernelArgs {
   const ReqDev* reqs;              // device table (batch); nullptr -> use `single`
   int32_t n_req;
+  int32_t spacetime;               // of every request in the launch
   int64_t total_rays;
   unsigned long long* queue;       // persistent grids: next ray index (device)
   unsigned long long* stats;       // optional OSIRIS_STATS_LEN counters (device)

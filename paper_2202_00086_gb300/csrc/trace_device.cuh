@@ -77,9 +77,11 @@ struct State {  // evolved coordinates and momenta (t does not feed back; not in
   double r, th, ph, pr, pth;
 };
 
-// Per-ray constants of the Hamiltonian.
+// Per-ray constants of the Hamiltonian (Kerr: a and its products; q-metric:
+// q and kap = q (2 + q)).
 struct RayK {
   double a, a2, aE, aL, E, L;
+  double q, kap;
 };
 
 // ---------------------------------------------------------------------------
@@ -128,29 +130,91 @@ __device__ __forceinline__ void rhs64(const RayK& K, double r, double th, double
   twoH = NiS;
 }
 
+// ---------------------------------------------------------------------------
+// Hamilton's equations on the q-metric (Appendix A, Eq. q-metric, signature
+// -+++, m = 1). The metric is diagonal, so with f = 1 - 2/r, D = r^2 - 2r,
+// X = 1 + sin^2 / D, k = q (2 + q):
+//   g^tt = -f^-(1+q), g^rr = f^(1+q) X^k, g^thth = f^q X^k / r^2,
+//   g^phph = f^q / (r^2 sin^2),
+// and each derivative is g^{mu mu} times its logarithmic derivative
+// (d ln f / dr = 2/D, d ln X / dr = -sin^2 (2r - 2) / (D^2 X),
+//  d ln X / dtheta = 2 sin cos / (D X)).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void rhs_q64(const RayK& K, double r, double th, double pr,
+                                        double pth, double& dr, double& dth, double& dph,
+                                        double& dpr, double& dpth, double& twoH) {
+  double s, c;
+  sincos(th, &s, &c);
+  const double ir = 1.0 / r;
+  const double f = 1.0 - 2.0 * ir;
+  const double iD = 1.0 / (r * r - 2.0 * r);
+  const double s2 = s * s;
+  const double X = fma(s2, iD, 1.0);
+  const double iX = 1.0 / X;
+  const double fq = exp(K.q * log(f));
+  const double Xk = exp(K.kap * log(X));
+  const double ir2 = ir * ir;
+  const double gtt = -1.0 / (f * fq);
+  const double grr = f * fq * Xk;
+  const double gthth = fq * Xk * ir2;
+  const double gpp = fq * ir2 / s2;
+  const double Lf = 2.0 * iD;
+  const double LXr = -s2 * (2.0 * r - 2.0) * iD * iD * iX;
+  const double LXth = 2.0 * s * c * iD * iX;
+  const double E2 = K.E * K.E, L2 = K.L * K.L, pr2 = pr * pr, pth2 = pth * pth;
+  twoH = gtt * E2 + grr * pr2 + gthth * pth2 + gpp * L2;
+  dr = grr * pr;
+  dth = gthth * pth;
+  dph = gpp * K.L;
+  const double dgtt = -gtt * (1.0 + K.q) * Lf;
+  const double dgrr = grr * fma(1.0 + K.q, Lf, K.kap * LXr);
+  const double dgthth = gthth * (fma(K.q, Lf, K.kap * LXr) - 2.0 * ir);
+  const double dgpp = gpp * fma(K.q, Lf, -2.0 * ir);
+  dpr = -0.5 * (dgtt * E2 + dgrr * pr2 + dgthth * pth2 + dgpp * L2);
+  dpth = -0.5 * (K.kap * LXth * (grr * pr2 + gthth * pth2) - 2.0 * (c / s) * gpp * L2);
+}
+
+// Metric policies for the FP64 steppers.
+struct KerrMetric {
+  static __device__ __forceinline__ void rhs(const RayK& K, double r, double th, double pr,
+                                             double pth, double& dr, double& dth, double& dph,
+                                             double& dpr, double& dpth, double& twoH) {
+    rhs64(K, r, th, pr, pth, dr, dth, dph, dpr, dpth, twoH);
+  }
+};
+struct QMetric {
+  static __device__ __forceinline__ void rhs(const RayK& K, double r, double th, double pr,
+                                             double pth, double& dr, double& dth, double& dph,
+                                             double& dpr, double& dpth, double& twoH) {
+    rhs_q64(K, r, th, pr, pth, dr, dth, dph, dpr, dpth, twoH);
+  }
+};
+
 // 2H at a state (used once per ray for the terminal point).
+template <class Met = KerrMetric>
 __device__ __forceinline__ double twoH64(const RayK& K, const State& y) {
   double a0, a1, a2, a3, a4, h2;
-  rhs64(K, y.r, y.th, y.pr, y.pth, a0, a1, a2, a3, a4, h2);
+  Met::rhs(K, y.r, y.th, y.pr, y.pth, a0, a1, a2, a3, a4, h2);
   return h2;
 }
 
 // One Cash-Karp attempt of length h from y (FP64 everywhere): o = fifth-order
 // result, d = fifth minus fourth order. phi is cyclic, so its stage values
 // are never needed; only its increment is accumulated.
+template <class Met = KerrMetric>
 __device__ __forceinline__ void ck_step64(const RayK& K, const State& y, double h, State& o,
                                           State& d, double& twoH) {
   using namespace ck;
   double k1r, k1t, k1p, k1pr, k1pt;
-  rhs64(K, y.r, y.th, y.pr, y.pth, k1r, k1t, k1p, k1pr, k1pt, twoH);
+  Met::rhs(K, y.r, y.th, y.pr, y.pth, k1r, k1t, k1p, k1pr, k1pt, twoH);
   double k2r, k2t, k2p, k2pr, k2pt, hd;
-  rhs64(K, fma(h, A21 * k1r, y.r), fma(h, A21 * k1t, y.th), fma(h, A21 * k1pr, y.pr),
+  Met::rhs(K, fma(h, A21 * k1r, y.r), fma(h, A21 * k1t, y.th), fma(h, A21 * k1pr, y.pr),
         fma(h, A21 * k1pt, y.pth), k2r, k2t, k2p, k2pr, k2pt, hd);
 #define OSIRIS_S3(c) fma(h, fma(A32, k2##c, A31 * k1##c), y_##c)
   double k3r, k3t, k3p, k3pr, k3pt;
   {
     const double y_r = y.r, y_t = y.th, y_pr = y.pr, y_pt = y.pth;
-    rhs64(K, OSIRIS_S3(r), OSIRIS_S3(t), OSIRIS_S3(pr), OSIRIS_S3(pt), k3r, k3t, k3p, k3pr, k3pt,
+    Met::rhs(K, OSIRIS_S3(r), OSIRIS_S3(t), OSIRIS_S3(pr), OSIRIS_S3(pt), k3r, k3t, k3p, k3pr, k3pt,
           hd);
   }
 #undef OSIRIS_S3
@@ -158,7 +222,7 @@ __device__ __forceinline__ void ck_step64(const RayK& K, const State& y, double 
   double k4r, k4t, k4p, k4pr, k4pt;
   {
     const double y_r = y.r, y_t = y.th, y_pr = y.pr, y_pt = y.pth;
-    rhs64(K, OSIRIS_S4(r), OSIRIS_S4(t), OSIRIS_S4(pr), OSIRIS_S4(pt), k4r, k4t, k4p, k4pr, k4pt,
+    Met::rhs(K, OSIRIS_S4(r), OSIRIS_S4(t), OSIRIS_S4(pr), OSIRIS_S4(pt), k4r, k4t, k4p, k4pr, k4pt,
           hd);
   }
 #undef OSIRIS_S4
@@ -167,7 +231,7 @@ __device__ __forceinline__ void ck_step64(const RayK& K, const State& y, double 
   double k5r, k5t, k5p, k5pr, k5pt;
   {
     const double y_r = y.r, y_t = y.th, y_pr = y.pr, y_pt = y.pth;
-    rhs64(K, OSIRIS_S5(r), OSIRIS_S5(t), OSIRIS_S5(pr), OSIRIS_S5(pt), k5r, k5t, k5p, k5pr, k5pt,
+    Met::rhs(K, OSIRIS_S5(r), OSIRIS_S5(t), OSIRIS_S5(pr), OSIRIS_S5(pt), k5r, k5t, k5p, k5pr, k5pt,
           hd);
   }
 #undef OSIRIS_S5
@@ -176,7 +240,7 @@ __device__ __forceinline__ void ck_step64(const RayK& K, const State& y, double 
   double k6r, k6t, k6p, k6pr, k6pt;
   {
     const double y_r = y.r, y_t = y.th, y_pr = y.pr, y_pt = y.pth;
-    rhs64(K, OSIRIS_S6(r), OSIRIS_S6(t), OSIRIS_S6(pr), OSIRIS_S6(pt), k6r, k6t, k6p, k6pr, k6pt,
+    Met::rhs(K, OSIRIS_S6(r), OSIRIS_S6(t), OSIRIS_S6(pr), OSIRIS_S6(pt), k6r, k6t, k6p, k6pr, k6pt,
           hd);
   }
 #undef OSIRIS_S6
@@ -202,41 +266,43 @@ struct Deriv {
   double r, th, ph, pr, pth, twoH;
 };
 
+template <class Met = KerrMetric>
 __device__ __forceinline__ void rhs64_at(const RayK& K, const State& y, Deriv& k) {
-  rhs64(K, y.r, y.th, y.pr, y.pth, k.r, k.th, k.ph, k.pr, k.pth, k.twoH);
+  Met::rhs(K, y.r, y.th, y.pr, y.pth, k.r, k.th, k.ph, k.pr, k.pth, k.twoH);
 }
 
 // One Dormand-Prince attempt of length h from y given k1 = f(y): o = fifth-
 // order result, d = fifth minus fourth order, k7 = f(o) (the first stage of
 // the next step if this one is accepted). Six new evaluations.
+template <class Met = KerrMetric>
 __device__ __forceinline__ void dp_step64(const RayK& K, const State& y, double h,
                                           const Deriv& k1, State& o, State& d, Deriv& k7) {
   using namespace dp;
   double hd;
   double k2r, k2t, k2p, k2pr, k2pt;
-  rhs64(K, fma(h, A21 * k1.r, y.r), fma(h, A21 * k1.th, y.th), fma(h, A21 * k1.pr, y.pr),
+  Met::rhs(K, fma(h, A21 * k1.r, y.r), fma(h, A21 * k1.th, y.th), fma(h, A21 * k1.pr, y.pr),
         fma(h, A21 * k1.pth, y.pth), k2r, k2t, k2p, k2pr, k2pt, hd);
 #define DP_S3(a, b, y0) fma(h, fma(A32, b, A31 * a), y0)
   double k3r, k3t, k3p, k3pr, k3pt;
-  rhs64(K, DP_S3(k1.r, k2r, y.r), DP_S3(k1.th, k2t, y.th), DP_S3(k1.pr, k2pr, y.pr),
+  Met::rhs(K, DP_S3(k1.r, k2r, y.r), DP_S3(k1.th, k2t, y.th), DP_S3(k1.pr, k2pr, y.pr),
         DP_S3(k1.pth, k2pt, y.pth), k3r, k3t, k3p, k3pr, k3pt, hd);
 #undef DP_S3
 #define DP_S4(a, b, c, y0) fma(h, fma(A43, c, fma(A42, b, A41 * a)), y0)
   double k4r, k4t, k4p, k4pr, k4pt;
-  rhs64(K, DP_S4(k1.r, k2r, k3r, y.r), DP_S4(k1.th, k2t, k3t, y.th),
+  Met::rhs(K, DP_S4(k1.r, k2r, k3r, y.r), DP_S4(k1.th, k2t, k3t, y.th),
         DP_S4(k1.pr, k2pr, k3pr, y.pr), DP_S4(k1.pth, k2pt, k3pt, y.pth), k4r, k4t, k4p, k4pr,
         k4pt, hd);
 #undef DP_S4
 #define DP_S5(a, b, c, e, y0) fma(h, fma(A54, e, fma(A53, c, fma(A52, b, A51 * a))), y0)
   double k5r, k5t, k5p, k5pr, k5pt;
-  rhs64(K, DP_S5(k1.r, k2r, k3r, k4r, y.r), DP_S5(k1.th, k2t, k3t, k4t, y.th),
+  Met::rhs(K, DP_S5(k1.r, k2r, k3r, k4r, y.r), DP_S5(k1.th, k2t, k3t, k4t, y.th),
         DP_S5(k1.pr, k2pr, k3pr, k4pr, y.pr), DP_S5(k1.pth, k2pt, k3pt, k4pt, y.pth), k5r, k5t,
         k5p, k5pr, k5pt, hd);
 #undef DP_S5
 #define DP_S6(a, b, c, e, f, y0) \
   fma(h, fma(A65, f, fma(A64, e, fma(A63, c, fma(A62, b, A61 * a)))), y0)
   double k6r, k6t, k6p, k6pr, k6pt;
-  rhs64(K, DP_S6(k1.r, k2r, k3r, k4r, k5r, y.r), DP_S6(k1.th, k2t, k3t, k4t, k5t, y.th),
+  Met::rhs(K, DP_S6(k1.r, k2r, k3r, k4r, k5r, y.r), DP_S6(k1.th, k2t, k3t, k4t, k5t, y.th),
         DP_S6(k1.pr, k2pr, k3pr, k4pr, k5pr, y.pr),
         DP_S6(k1.pth, k2pt, k3pt, k4pt, k5pt, y.pth), k6r, k6t, k6p, k6pr, k6pt, hd);
 #undef DP_S6
@@ -247,7 +313,7 @@ __device__ __forceinline__ void dp_step64(const RayK& K, const State& y, double 
   o.pr = fma(h, DP_Y5(k1.pr, k3pr, k4pr, k5pr, k6pr), y.pr);
   o.pth = fma(h, DP_Y5(k1.pth, k3pt, k4pt, k5pt, k6pt), y.pth);
 #undef DP_Y5
-  rhs64_at(K, o, k7);
+  rhs64_at<Met>(K, o, k7);
 #define DP_DL(a, c, e, f, g, z) \
   fma(D7, z, fma(D6, g, fma(D5, f, fma(D4, e, fma(D3, c, D1 * a)))))
   d.r = h * DP_DL(k1.r, k3r, k4r, k5r, k6r, k7.r);

@@ -354,7 +354,7 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
     const State f = to_double(fd);
     double mh = (double)max_abs_H;
     if (status != OSIRIS_STATUS_ERROR) {
-      mh = fmax(mh, fabs(0.5 * twoH64(I.K, f)));
+      mh = fmax(mh, fabs(0.5 * twoH64(I.K, f) - I.H0));
       S.rhs += 1;
     }
     write_outputs(A, I, status, f, mh, n_acc, n_rej, S);
@@ -424,7 +424,7 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
     S.rhs += 6;
 
     if (mode == MODE_INTEGRATE) {
-      max_abs_H = fmaxf(max_abs_H, fabsf(0.5f * twoH));
+      max_abs_H = fmaxf(max_abs_H, fabsf(0.5f * twoH - (float)I.H0));
       const float ys[5] = {y.r.hi, y.th.hi, y.ph.hi, y.pr.hi, y.pth.hi};
       const float os[5] = {o.r.hi, o.th.hi, o.ph.hi, o.pr.hi, o.pth.hi};
       bool bad = false, ok = true;

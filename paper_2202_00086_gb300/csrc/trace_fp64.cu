@@ -5,12 +5,12 @@
 
 namespace osiris_impl {
 
-template <int INTEG>
+template <int INTEG, class Met>
 struct StepperFP64;
 
 // Cash-Karp: every attempt evaluates its six stages.
-template <>
-struct StepperFP64<OSIRIS_RKCK45> {
+template <class Met>
+struct StepperFP64<OSIRIS_RKCK45, Met> {
   struct RayCache {};
   struct LaneCache {};
   static __device__ __forceinline__ void prepare(const RayK&, RayCache&) {}
@@ -19,19 +19,19 @@ struct StepperFP64<OSIRIS_RKCK45> {
   static __device__ __forceinline__ bool attempt(const RayK& K, const RayCache&, LaneCache&,
                                                  const State& y, double h, State& o, State& d,
                                                  double& twoH) {
-    ck_step64(K, y, h, o, d, twoH);
+    ck_step64<Met>(K, y, h, o, d, twoH);
     return true;
   }
   static __device__ __forceinline__ double twoH(const RayK& K, const State& y) {
-    return twoH64(K, y);
+    return twoH64<Met>(K, y);
   }
 };
 
 // Dormand-Prince: k1 is carried from the previous accepted attempt's seventh
 // stage; it is evaluated only when a ray starts or resumes (a warp evaluates
 // it when any of its lanes needs it).
-template <>
-struct StepperFP64<OSIRIS_RKDP45> {
+template <class Met>
+struct StepperFP64<OSIRIS_RKDP45, Met> {
   struct RayCache {};
   struct LaneCache {
     Deriv k1, k7;
@@ -44,57 +44,57 @@ struct StepperFP64<OSIRIS_RKDP45> {
                                                  const State& y, double h, State& o, State& d,
                                                  double& twoH) {
     if (!c.valid) {
-      rhs64_at(K, y, c.k1);
+      rhs64_at<Met>(K, y, c.k1);
       c.valid = true;
     }
     twoH = c.k1.twoH;
-    dp_step64(K, y, h, c.k1, o, d, c.k7);
+    dp_step64<Met>(K, y, h, c.k1, o, d, c.k7);
     return true;
   }
   static __device__ __forceinline__ double twoH(const RayK& K, const State& y) {
-    return twoH64(K, y);
+    return twoH64<Met>(K, y);
   }
 };
 
 constexpr int kMaxBlock = 256;
 
-template <int INTEG>
+template <int INTEG, class Met>
 __global__ void __launch_bounds__(kMaxBlock) trace_fp64_plain(const __grid_constant__ KernelArgs A) {
-  trace_body<StepperFP64<INTEG>, false>(A);
+  trace_body<StepperFP64<INTEG, Met>, false>(A);
 }
 
-template <int INTEG>
+template <int INTEG, class Met>
 __global__ void __launch_bounds__(kMaxBlock) trace_fp64_persistent(const __grid_constant__ KernelArgs A) {
-  trace_body<StepperFP64<INTEG>, true>(A);
+  trace_body<StepperFP64<INTEG, Met>, true>(A);
 }
 
-template <int INTEG>
+template <int INTEG, class Met>
 static const void* fp64_kernel(Kernel kind) {
-  return kind == Kernel::kPersistent ? (const void*)trace_fp64_persistent<INTEG>
-                                     : (const void*)trace_fp64_plain<INTEG>;
+  return kind == Kernel::kPersistent ? (const void*)trace_fp64_persistent<INTEG, Met>
+                                     : (const void*)trace_fp64_plain<INTEG, Met>;
+}
+
+static const void* select_fp64(Kernel kind, int integrator, int spacetime) {
+  if (spacetime == OSIRIS_SPACETIME_QMETRIC)
+    return integrator == OSIRIS_RKDP45 ? fp64_kernel<OSIRIS_RKDP45, QMetric>(kind)
+                                       : fp64_kernel<OSIRIS_RKCK45, QMetric>(kind);
+  return integrator == OSIRIS_RKDP45 ? fp64_kernel<OSIRIS_RKDP45, KerrMetric>(kind)
+                                     : fp64_kernel<OSIRIS_RKCK45, KerrMetric>(kind);
 }
 
 int launch_trace_fp64(const KernelArgs& args, Kernel kind, int integrator, int grid, int block,
                       void* stream) {
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (integrator == OSIRIS_RKDP45) {
-    if (kind == Kernel::kPersistent)
-      trace_fp64_persistent<OSIRIS_RKDP45><<<grid, block, 0, s>>>(args);
-    else
-      trace_fp64_plain<OSIRIS_RKDP45><<<grid, block, 0, s>>>(args);
-  } else {
-    if (kind == Kernel::kPersistent)
-      trace_fp64_persistent<OSIRIS_RKCK45><<<grid, block, 0, s>>>(args);
-    else
-      trace_fp64_plain<OSIRIS_RKCK45><<<grid, block, 0, s>>>(args);
-  }
-  return (int)cudaGetLastError();
+  const int spacetime = args.reqs ? args.spacetime : args.single.spacetime;
+  const void* fn = select_fp64(kind, integrator, spacetime);
+  void* params[] = {const_cast<KernelArgs*>(&args)};
+  return (int)cudaLaunchKernel(fn, dim3(grid), dim3(block), params, 0,
+                               static_cast<cudaStream_t>(stream));
 }
 
 int occupancy_fp64(Kernel kind, int integrator, int block, int* blocks_per_sm) {
-  const void* fn = integrator == OSIRIS_RKDP45 ? fp64_kernel<OSIRIS_RKDP45>(kind)
-                                               : fp64_kernel<OSIRIS_RKCK45>(kind);
-  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, 0);
+  // same resources for both space-times within an integrator
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      blocks_per_sm, select_fp64(kind, integrator, OSIRIS_SPACETIME_QMETRIC), block, 0);
 }
 
 // Roofline probe: 8 independent FMA chains per thread.

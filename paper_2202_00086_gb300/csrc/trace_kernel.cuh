@@ -21,6 +21,7 @@ struct RayInfo {
   int req;
   int64_t local;  // index of the ray inside its request
   RayK K;
+  double H0;      // mass shell: the error tracked is |H - H0| (Sec. 3.1)
   double r_cap, r_esc, r_in, r_out, tol, h0;
   int disk;
   int64_t max_steps;
@@ -36,6 +37,9 @@ __device__ __forceinline__ void load_ray(const KernelArgs& A, int64_t g, RayInfo
   const double a = R->a;
   I.K.a = a;
   I.K.a2 = a * a;
+  I.K.q = R->q;
+  I.K.kap = R->q * (2.0 + R->q);
+  I.H0 = R->H0;
   if (R->explicit_states) {
     const double* st = R->states + 6 * I.local;
     y.r = st[1];
@@ -194,7 +198,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
   // Write the ray's outputs and retire the lane.
   auto finish = [&](int status, const State& f) {
     if (status != OSIRIS_STATUS_ERROR) {
-      max_abs_H = fmax(max_abs_H, fabs(0.5 * Stepper::twoH(K, f)));
+      max_abs_H = fmax(max_abs_H, fabs(0.5 * Stepper::twoH(K, f) - I.H0));
       S.rhs += 1;
     }
     write_outputs(A, I, status, f, max_abs_H, n_acc, n_rej, S);
@@ -259,7 +263,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
     S.fp64_steps += fp64_step ? 1 : 0;
 
     if (mode == MODE_INTEGRATE) {
-      max_abs_H = fmax(max_abs_H, fabs(0.5 * twoH));
+      max_abs_H = fmax(max_abs_H, fabs(0.5 * twoH - I.H0));
       if (state_not_finite(o) || state_not_finite(d)) {
         finish(OSIRIS_STATUS_ERROR, y);
         continue;

@@ -32,14 +32,14 @@ def checker_phase_deg(seed: int, cell_deg: float = 10.0) -> float:
 
 
 def render(a, r_obs, incl_deg, extent, nx, ny, mode="shadow", r_in=None, r_out=None,
-           tol=1e-10, cell_deg=10.0, seed=2202, l0=None):
+           tol=1e-10, cell_deg=10.0, seed=2202, l0=None, q=None):
     """mode "disk" with l0=None: Keplerian disk; with l0: disk of constant
-    specific angular momentum l0."""
+    specific angular momentum l0. q given: the q-metric (a is ignored)."""
     return dict(a=float(a), r_obs=float(r_obs), incl_deg=float(incl_deg),
                 extent=tuple(float(v) for v in extent), nx=int(nx), ny=int(ny), mode=mode,
                 r_in=r_in, r_out=r_out, tol=float(tol), cell_deg=float(cell_deg),
                 cell_phase_deg=checker_phase_deg(seed, cell_deg),
-                l0=None if l0 is None else float(l0))
+                l0=None if l0 is None else float(l0), q=None if q is None else float(q))
 
 
 def schwarzschild_shadow_64():

@@ -67,6 +67,8 @@ def oracle_render(rd, pixels=None, **extra):
                 disk=disk, r_in=r_in, r_out=rd.get("r_out") or 0.0)
     if rd.get("l0") is not None:
         opts.update(disk_model=oracle.DISK_CONSTANT_L, l0=rd["l0"])
+    if rd.get("q") is not None:
+        opts.update(spacetime=oracle.QMETRIC, q=rd["q"])
     opts.update(extra)
     return oracle.trace_pixels(rd["a"], rd["r_obs"], rd["incl_deg"], rd["extent"], rd["nx"],
                                rd["ny"], pixels=pixels, **opts)

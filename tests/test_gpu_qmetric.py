@@ -1,0 +1,84 @@
+"""The q-metric (Appendix A) and time-like geodesics on the GPU, against the
+oracle: q-metric shadow renders (q = 0 equal to the Kerr a = 0 render),
+circular and escaping massive particles, and the mass-shell error."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2202_00086_gb300 as osr
+from paper_2202_00086_gb300 import workloads
+
+from _parity import assert_parity, compare, gpu_render, oracle_render
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("q", [-0.5, 0.1, 0.5])
+@pytest.mark.parametrize("inc", [30.0, 90.0])
+def test_qmetric_render_parity(q, inc):
+    rd = workloads.render(0.0, 1000.0, inc, (-8, 8, -8, 8), 32, 32, q=q)
+    rep = compare(rd, gpu_render(rd), oracle_render(rd))
+    print(rep)
+    assert_parity(rep)
+
+
+def test_qmetric_q0_equals_schwarzschild_on_gpu():
+    rq = workloads.render(0.0, 1000.0, 60.0, (-8, 8, -8, 8), 24, 24, q=0.0)
+    rk = workloads.render(0.0, 1000.0, 60.0, (-8, 8, -8, 8), 24, 24)
+    gq, gk = gpu_render(rq), gpu_render(rk)
+    assert np.array_equal(gq["status"], gk["status"])
+    for key in ("r", "theta", "phi"):
+        assert np.allclose(gq[key], gk[key], rtol=1e-9, atol=1e-9)
+
+
+def _line_element(q, r):
+    """g_tt, g_rr, g_phph of the q-metric on the equator (sin = 1)."""
+    f = 1 - 2 / r
+    X = 1 + 1 / (r * r - 2 * r)
+    k = q * (2 + q)
+    return -f ** (1 + q), f ** (-1 - q) * X ** -k, f ** -q * r * r
+
+
+@pytest.mark.parametrize("q", [0.0, 0.5, -0.5])
+def test_timelike_orbits_parity(q):
+    r = 12.0
+    # circular orbit from the covariant metric: Omega^2 = -d g_tt / d g_phph
+    h = 1e-5 * r
+    gp, gm = _line_element(q, r + h), _line_element(q, r - h)
+    Om = math.sqrt(-(gp[0] - gm[0]) / (gp[2] - gm[2]))
+    g = _line_element(q, r)
+    ut = 1 / math.sqrt(-g[0] - g[2] * Om * Om)
+    Ec, Lc = -g[0] * ut, g[2] * Om * ut
+    # an unbound particle launched outwards from r = 30
+    g30 = _line_element(q, 30.0)
+    Eu, Lu = 1.2, 4.0
+    pru = math.sqrt((-1 + Eu * Eu / -g30[0] - Lu * Lu / g30[2]) * g30[1])
+    st = np.array([[0.0, r, math.pi / 2, 0.0, 0.0, 0.0], [0.0, 30.0, math.pi / 2, 0.0, pru, 0.0]])
+    E = np.array([Ec, Eu])
+    L = np.array([Lc, Lu])
+    out = osr.trace_states(0.0, 100.0, torch.tensor(st, device="cuda"),
+                           torch.tensor(E, device="cuda"), torch.tensor(L, device="cuda"),
+                           q=q, mass2=1.0, max_steps=150)
+    torch.cuda.synchronize()
+    ref = oracle.trace_states(0.0, 100.0, st, E, L, spacetime=oracle.QMETRIC, q=q, mass2=1.0,
+                              max_steps=150)
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    assert got["status"].tolist() == ref["status"].tolist() == [osr.STATUS_MAXSTEP,
+                                                               osr.STATUS_ESCAPED]
+    assert abs(got["r"][0] - r) < 1e-6 * r  # stays on the circular orbit
+    for key in ("r", "theta", "phi"):  # the escape point is located exactly
+        assert abs(got[key][1] - ref[key][1]) <= 1e-8 * max(1.0, abs(ref[key][1])), key
+    assert got["max_abs_H"].max() < 1e-8
+    assert np.allclose(got["max_abs_H"], ref["max_abs_H"], rtol=0.05, atol=1e-13)
+
+
+def test_qmetric_rejects_unsupported_modes():
+    cam = osr.Camera(0.0, 1000.0, 60.0, (-8, 8, -8, 8), 8, 8, q=0.5)
+    for kw in (dict(precision=osr.DF64), dict(precision=osr.MIXED)):
+        with pytest.raises(osr.OsirisError):
+            osr.trace(cam, **kw)
+    with pytest.raises(osr.OsirisError):
+        osr.render_disk(cam, 6.0, 20.0)
