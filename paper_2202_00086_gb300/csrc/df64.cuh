@@ -65,6 +65,20 @@ __device__ __forceinline__ df df_add(df a, df b) {
 
 __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
 
+// Sum without the final renormalisation: the TwoSum of the leading words is
+// exact for any inputs, so hi + lo stays an exact-enough pair (|lo| a few
+// ulp(hi)) for further sums and products. Used for intermediate terms whose
+// leading word is not itself inspected.
+__device__ __forceinline__ df df_add_u(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return s;
+}
+
+__device__ __forceinline__ df df_sub_u(df a, df b) { return df_add_u(a, df_neg(b)); }
+
+__device__ __forceinline__ df df_norm(df a) { return fast_two_sum(a.hi, a.lo); }
+
 __device__ __forceinline__ df df_add_f(df a, float b) {
   df s = two_sum(a.hi, b);
   s.lo = __fadd_rn(s.lo, a.lo);

@@ -85,32 +85,35 @@ __device__ __forceinline__ bool df_not_finite(float x) {
 // every operation in df64.
 __device__ __forceinline__ void rhs_df(const RayDF& K, df r, df th, df pr, df pth, df& dr,
                                        df& dth, df& dph, df& dpr, df& dpth, float& twoH) {
+  // Intermediate sums are left unrenormalised (df_add_u); the five outputs
+  // are renormalised at the end.
   df s, c;
   df_sincos(th, s, c);
   const df r2 = df_sqr(r);
-  const df Delta = df_add(df_mul(r, df_add_f(r, -2.0f)), K.a2);
-  const df Sigma = df_add(r2, df_mul(K.a2, df_sqr(c)));
-  const df P = df_sub(df_mul(df_add(r2, K.a2), K.E), K.aL);
+  const df Delta = df_add_u(df_mul(r, df_add_f(r, -2.0f)), K.a2);
+  const df Sigma = df_add_u(r2, df_mul(K.a2, df_sqr(c)));
+  const df P = df_sub_u(df_mul(df_add_u(r2, K.a2), K.E), K.aL);
   const df DS = df_mul(Delta, Sigma);
   const df inv = df_rcp(df_mul(DS, s));
   const df iSig = df_mul(df_mul(Delta, s), inv);
   const df iDel = df_mul(df_mul(Sigma, s), inv);
   const df is = df_mul(DS, inv);
-  const df W = df_sub(df_mul(K.L, is), df_mul(K.aE, s));
+  const df W = df_sub_u(df_mul(K.L, is), df_mul(K.aE, s));
   const df u = df_mul(P, iDel);
   const df Dpr = df_mul(Delta, pr);
-  const df N = df_add(df_add(df_mul(Dpr, pr), df_sqr(pth)), df_sub(df_sqr(W), df_mul(P, u)));
+  const df N =
+      df_add_u(df_add_u(df_mul(Dpr, pr), df_sqr(pth)), df_sub_u(df_sqr(W), df_mul(P, u)));
   const df NiS = df_mul(N, iSig);
-  dr = df_mul(Dpr, iSig);
-  dth = df_mul(pth, iSig);
-  dph = df_mul(df_add(df_mul(W, is), df_mul(K.a, u)), iSig);
-  const df t1 = df_add(df_mul(r, NiS), df_mul(df_mul(r, K.twoE), u));
-  const df t2 = df_mul(df_add_f(r, -1.0f), df_add(df_sqr(u), df_sqr(pr)));
-  dpr = df_mul(iSig, df_sub(t1, t2));
-  const df t3 = df_mul(W, df_add(df_mul(K.L, df_sqr(is)), K.aE));
+  dr = df_norm(df_mul(Dpr, iSig));
+  dth = df_norm(df_mul(pth, iSig));
+  dph = df_norm(df_mul(df_add_u(df_mul(W, is), df_mul(K.a, u)), iSig));
+  const df t1 = df_add_u(df_mul(r, NiS), df_mul(df_mul(r, K.twoE), u));
+  const df t2 = df_mul(df_add_f(r, -1.0f), df_add_u(df_sqr(u), df_sqr(pr)));
+  dpr = df_norm(df_mul(iSig, df_sub_u(t1, t2)));
+  const df t3 = df_mul(W, df_add_u(df_mul(K.L, df_sqr(is)), K.aE));
   const df t4 = df_mul(df_mul(K.a2, s), NiS);
-  dpth = df_mul(df_mul(c, iSig), df_sub(t3, t4));
-  twoH = NiS.hi;
+  dpth = df_norm(df_mul(df_mul(c, iSig), df_sub_u(t3, t4)));
+  twoH = NiS.hi + NiS.lo;
 }
 
 // Tableaus for the df64 stepper, [integrator][stage]; stage s = 0..6 is the
@@ -289,8 +292,8 @@ __device__ __forceinline__ void rk_step_df(const RayDF& K, LaneCacheDF<INTEG>& L
       const bool has_b = (bw.hi != 0.0f);
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
-        if (has_b) sb[c] = df_add(sb[c], df_mul(e[c], bw));
-        sd[c] = df_add(sd[c], df_mul(e[c], dw));
+        if (has_b) sb[c] = df_add_u(sb[c], df_mul(e[c], bw));
+        sd[c] = df_add_u(sd[c], df_mul(e[c], dw));
       }
     }
   }
