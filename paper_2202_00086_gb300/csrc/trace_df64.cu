@@ -249,7 +249,7 @@ __device__ __forceinline__ void rk_step_df(const RayDF& K, LaneCacheDF<INTEG>& L
         const int kc = c < 2 ? c : c + 1;  // skip phi in k
         const float fs = s == 2 ? acc[0][c] : s == 3 ? acc[1][c] : s == 4 ? acc[2][c]
                        : s == 5 ? acc[3][c] : 0.0f;
-        in[c] = df_add_f(df_add(y4[c], df_mul(hk1[kc], cs)), __fmul_rn(hf, fs));
+        in[c] = df_add_f(df_add_u(y4[c], df_mul(hk1[kc], cs)), __fmul_rn(hf, fs));
       }
     }
     df k[5];
@@ -276,7 +276,7 @@ __device__ __forceinline__ void rk_step_df(const RayDF& K, LaneCacheDF<INTEG>& L
     }
     df e[5];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) e[c] = df_sub(k[c], k1[c]);
+    for (int c = 0; c < 5; ++c) e[c] = df_sub(k[c], k1[c]);  // renormalised: the error sum cancels to O(h^5)
     const float ds[4] = {e[0].hi, e[1].hi, e[3].hi, e[4].hi};
 #pragma unroll
     for (int t = 2; t < 6; ++t) {
