@@ -11,6 +11,7 @@ struct StepperFP64;
 // Cash-Karp: every attempt evaluates its six stages.
 template <class Met>
 struct StepperFP64<OSIRIS_RKCK45, Met> {
+  static constexpr double kLocateRel = 0.0;
   struct RayCache {};
   struct LaneCache {};
   static __device__ __forceinline__ void prepare(const RayK&, RayCache&) {}
@@ -32,6 +33,7 @@ struct StepperFP64<OSIRIS_RKCK45, Met> {
 // it when any of its lanes needs it).
 template <class Met>
 struct StepperFP64<OSIRIS_RKDP45, Met> {
+  static constexpr double kLocateRel = 0.0;
   struct RayCache {};
   struct LaneCache {
     Deriv k1, k7;

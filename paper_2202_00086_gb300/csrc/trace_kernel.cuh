@@ -315,8 +315,10 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
         side = +1;
       }
       const double ftol = (kind == SURF_EQUATOR) ? 1e-15 : 1e-14 * (kind == SURF_CAPTURE ? r_cap : r_esc);
-      const bool done = (f == 0.0) || (!to_lo && fabs(f) <= ftol) || (hi - lo <= 4e-16 * hi) ||
-                        iters >= 64;
+      // Stepper::kLocateRel: the relative bracket width below which the
+      // stepper's own rounding noise decides the sign of f (0 for FP64)
+      const bool done = (f == 0.0) || (!to_lo && fabs(f) <= ftol) ||
+                        (hi - lo <= (4e-16 + Stepper::kLocateRel) * hi) || iters >= 64;
       if (!done) {
         h_try = (lo * fhi - hi * flo) / (fhi - flo);
         if (!(h_try > lo && h_try < hi)) h_try = 0.5 * (lo + hi);

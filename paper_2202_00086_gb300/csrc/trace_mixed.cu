@@ -63,6 +63,9 @@ __device__ __forceinline__ double twoH_value64(const RayK& K, const State& y) {
 }
 
 struct StepperMixed {
+  // FP32 stage values put ~1e-7 relative noise on a trial step's end point;
+  // a bracket narrower than that cannot be resolved further
+  static constexpr double kLocateRel = 2e-7;
   struct RayCache {};
   struct LaneCache {};
   static __device__ __forceinline__ void prepare(const RayK&, RayCache&) {}
