@@ -344,6 +344,38 @@ __device__ __forceinline__ void err_component(double y, double o, double d, doub
   err = fmaxf(err, __fdividef((float)ad, (float)scale));
 }
 
+// |x| as FP32 by truncating the significand with integer operations only
+// (relative error < 2^-23; values below the FP32 normal range become 0,
+// above it +inf). Keeps these conversions off the FP64 pipe.
+__device__ __forceinline__ float abs_to_float_rz(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  const int e = (int)(b >> 52) - 1023 + 127;
+  if (e <= 0) return 0.0f;
+  if (e >= 255) return __int_as_float(0x7f800000);
+  return __int_as_float((e << 23) | (int)((b >> 29) & 0x7fffffull));
+}
+
+// The error norm of a step (max over the five components of
+// |d| / (tol (1 + max(|y|, |o|)))) in FP32 from truncated copies; the ratio is
+// within a relative 1e-6 of the FP64 one. The caller decides accept/reject
+// from it and falls back to the exact FP64 test (err_component) only when it
+// lies within 1e-5 of 1, so the decision is always the FP64 one.
+__device__ __forceinline__ float err_norm32(const State& y, const State& o, const State& d,
+                                            float tol32) {
+  float err = 0.0f;
+#define OSIRIS_ERR32(c)                                                                  \
+  err = fmaxf(err, __fdividef(abs_to_float_rz(d.c),                                     \
+                              tol32 * (1.0f + fmaxf(abs_to_float_rz(y.c),               \
+                                                    abs_to_float_rz(o.c)))))
+  OSIRIS_ERR32(r);
+  OSIRIS_ERR32(th);
+  OSIRIS_ERR32(ph);
+  OSIRIS_ERR32(pr);
+  OSIRIS_ERR32(pth);
+#undef OSIRIS_ERR32
+  return err;
+}
+
 // Value whose sign tells which side of a stopping surface a state is on;
 // the crossing is where it changes sign.
 __device__ __forceinline__ double surface_value(int kind, const State& s, double r_cap,

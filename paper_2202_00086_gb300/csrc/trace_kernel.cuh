@@ -178,6 +178,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
   int64_t& max_steps = I.max_steps;
   // integration state
   State y;
+  float tol32 = 0.0f;
   double h = 0, max_abs_H = 0;
   unsigned n_acc = 0, n_rej = 0;
   // surface location (LOCATE)
@@ -187,6 +188,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
 
   auto start_ray = [&](int64_t g) {
     load_ray(A, g, I, y);
+    tol32 = (float)I.tol;
     Stepper::prepare(K, RC);
     Stepper::reset(LC);
     h = I.h0;
@@ -268,13 +270,17 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
         finish(OSIRIS_STATUS_ERROR, y);
         continue;
       }
-      bool ok = true;
-      float err = 0.0f;
-      err_component(y.r, o.r, d.r, tol, ok, err);
-      err_component(y.th, o.th, d.th, tol, ok, err);
-      err_component(y.ph, o.ph, d.ph, tol, ok, err);
-      err_component(y.pr, o.pr, d.pr, tol, ok, err);
-      err_component(y.pth, o.pth, d.pth, tol, ok, err);
+      float err = err_norm32(y, o, d, tol32);
+      bool ok = err < 1.0f;
+      if (fabsf(err - 1.0f) < 1e-5f) {  // too close to call in FP32: exact FP64 test
+        ok = true;
+        err = 0.0f;
+        err_component(y.r, o.r, d.r, tol, ok, err);
+        err_component(y.th, o.th, d.th, tol, ok, err);
+        err_component(y.ph, o.ph, d.ph, tol, ok, err);
+        err_component(y.pr, o.pr, d.pr, tol, ok, err);
+        err_component(y.pth, o.pth, d.pth, tol, ok, err);
+      }
       if (ok) {
         ++n_acc;
         // step-size controller (FP32 is enough to size the next step):
