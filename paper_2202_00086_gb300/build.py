@@ -19,6 +19,11 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
 
+# The FP64 and mixed units write every fused multiply-add explicitly; with
+# contraction off the compiler cannot fuse a product into a sum differently in
+# different kernels, so every kernel computes bit-identical results.
+TU_FLAGS = {"trace_fp64.cu": ["-fmad=false"], "trace_mixed.cu": ["-fmad=false"]}
+
 
 def _nvcc():
     for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
@@ -43,7 +48,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT, src.replace(".cu", ".o"))
-        cmd = [nvcc] + ARCH + FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc] + ARCH + FLAGS + TU_FLAGS.get(src, []) + ["-c", os.path.join(CSRC, src),
+                                                              "-o", obj]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, p.stdout, p.stderr))

@@ -85,6 +85,109 @@ struct RayK {
 };
 
 // ---------------------------------------------------------------------------
+// FP64 sine/cosine and reciprocal with few FP64-pipe instructions.
+//
+// GB300 issues about one FP64 warp instruction per 19 SM cycles, while its
+// FP32, integer and shared-memory pipes are nearly idle in this kernel; the
+// two helpers below move the argument reduction, table look-up and seeds onto
+// those pipes and keep only the accuracy-critical FP64 arithmetic.
+//
+// sincos_tab: theta = theta_k + x with theta_k = k pi/256 (the nearest node,
+// found in FP32) and |x| <= pi/512 (+ FP32 rounding). sin/cos of the node come
+// from a per-block shared-memory table; sin x and cos x - 1 from their Taylor
+// series (truncation below 0.1 ulp at |x| = 0.0062):
+//   sin x = x + x^3 (-1/6 + x^2/120)
+//   cos x - 1 = x^2 (-1/2 + x^2 (1/24 - x^2/720))
+//   sin theta = S_k + (S_k (cos x - 1) + C_k sin x), cos similarly,
+// 12 FP64 instructions. The reduction x = (theta - N_k) - T_k uses the node
+// as a double-double (N_k + T_k = k pi/256 to ~1e-32), so sin theta keeps
+// its relative accuracy next to theta = 0 and pi (k = 0, 256: S_k = 0).
+// The table covers theta in [-pi/2, 5pi/2]; outside it (never reached by a
+// ray in the Boyer-Lindquist chart) the library sincos is used.
+// ---------------------------------------------------------------------------
+constexpr int kTrigPerPi = 256;                 // nodes per pi
+constexpr int kTrigFirst = -kTrigPerPi / 2;     // node index of the first entry
+constexpr int kTrigNodes = 3 * kTrigPerPi + 1;  // k in [-128, 640]
+
+struct TrigNode {
+  double2 sc;  // sin(k pi/256), cos(k pi/256)
+  double2 nt;  // k pi/256 = n + t (double-double)
+};
+
+__device__ __forceinline__ TrigNode* trig_table() {
+  __shared__ TrigNode table[kTrigNodes];
+  return table;
+}
+
+// Fill the block's table (all threads of the block, before any divergence).
+__device__ __forceinline__ void trig_table_init() {
+  constexpr double PI_HI = 3.141592653589793116;          // pi rounded to double
+  constexpr double PI_LO = 1.2246467991473532072e-16;     // pi - PI_HI
+  TrigNode* t = trig_table();
+  for (int i = threadIdx.x; i < kTrigNodes; i += blockDim.x) {
+    const double u = (double)(i + kTrigFirst) / kTrigPerPi;  // exact
+    double s, c;
+    sincospi(u, &s, &c);
+    const double n = u * PI_HI;
+    const double tail = fma(u, PI_HI, -n) + u * PI_LO;
+    t[i].sc = make_double2(s, c);
+    t[i].nt = make_double2(n, tail);
+  }
+  __syncthreads();
+}
+
+// x as FP32, significand truncated with integer operations only (relative
+// error < 2^-23); zero below the FP32 normal range, +-inf above it.
+__device__ __forceinline__ float to_float_rz(double x) {
+  const long long b = __double_as_longlong(x);
+  const int hi = (int)(b >> 32);
+  const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;
+  const int sign = hi & (int)0x80000000;
+  if (e <= 0) return __int_as_float(sign);
+  if (e >= 255) return __int_as_float(sign | 0x7f800000);
+  return __int_as_float(sign | (e << 23) | (int)((b >> 29) & 0x7fffff));
+}
+
+__device__ __forceinline__ void sincos_tab(double th, double& s, double& c) {
+  // nearest node in FP32: 1.5 * 2^23 added to round to an integer
+  const float tk = fmaf(to_float_rz(th), (float)(kTrigPerPi / 3.14159265358979323846),
+                        12582912.0f);
+  const int idx = (__float_as_int(tk) - 0x4B400000) - kTrigFirst;
+  if ((unsigned)idx >= (unsigned)kTrigNodes) {  // also NaN / inf
+    sincos(th, &s, &c);
+    return;
+  }
+  const TrigNode* t = trig_table() + idx;
+  const double2 nt = t->nt;
+  const double2 sc = t->sc;
+  const double x = (th - nt.x) - nt.y;
+  const double x2 = x * x;
+  const double sx = fma(x * x2, fma(x2, 1.0 / 120.0, -1.0 / 6.0), x);
+  const double cm = x2 * fma(x2, fma(x2, -1.0 / 720.0, 1.0 / 24.0), -0.5);
+  s = fma(sc.y, sx, fma(sc.x, cm, sc.x));
+  c = fma(-sc.x, sx, fma(sc.y, cm, sc.y));
+}
+
+// 1/d: FP32 seed x0 (|x0 d - 1| < 2^-21), then one Newton step with the
+// cubic term, x0 (1 + e + e^2) with e = 1 - d x0, relative error e^3 plus
+// the final rounding (3 FP64 instructions). Outside the FP32 range: 1/d.
+__device__ __forceinline__ double rcp64(double d) {
+  const long long b = __double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  if (e < 2 || e > 252) return 1.0 / d;
+  const float f = __int_as_float((int)((b >> 32) & 0x80000000) | (e << 23) |
+                                 (int)((b >> 29) & 0x7fffff));
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f));
+  const unsigned rb = __float_as_uint(rf);
+  const long long er = (long long)((rb >> 23) & 0xff) - 127 + 1023;
+  const double x0 = __longlong_as_double((long long)(rb & 0x80000000u) << 32 | er << 52 |
+                                         (long long)(rb & 0x7fffffu) << 29);
+  const double eps = fma(-d, x0, 1.0);
+  return fma(x0, fma(eps, eps, eps), x0);
+}
+
+// ---------------------------------------------------------------------------
 // Hamilton's equations in separated form.
 //
 // With p_t = -E, p_phi = L, the Kerr Hamiltonian H = 1/2 g^{mu nu} p_mu p_nu
@@ -107,13 +210,13 @@ __device__ __forceinline__ void rhs64(const RayK& K, double r, double th, double
                                       double& dr, double& dth, double& dph, double& dpr,
                                       double& dpth, double& twoH) {
   double s, c;
-  sincos(th, &s, &c);
+  sincos_tab(th, s, c);
   const double r2 = r * r;
   const double Delta = fma(r, r - 2.0, K.a2);
   const double Sigma = fma(K.a2 * c, c, r2);
-  const double P = fma(r2 + K.a2, K.E, -K.aL);
+  const double P = fma(fma(r, r, K.a2), K.E, -K.aL);
   const double DS = Delta * Sigma;
-  const double inv = __drcp_rn(DS * s);
+  const double inv = rcp64(DS * s);
   const double iSig = (Delta * s) * inv;
   const double iDel = (Sigma * s) * inv;
   const double is = DS * inv;
@@ -125,7 +228,7 @@ __device__ __forceinline__ void rhs64(const RayK& K, double r, double th, double
   dr = Dpr * iSig;
   dth = pth * iSig;
   dph = fma(W, is, K.a * u) * iSig;
-  dpr = iSig * (fma(r, NiS, 2.0 * r * K.E * u) - (r - 1.0) * fma(u, u, pr * pr));
+  dpr = iSig * fma(1.0 - r, fma(u, u, pr * pr), fma(r, NiS, (r + r) * K.E * u));
   dpth = (c * iSig) * fma(W, fma(K.L, is * is, K.aE), -(K.a2 * s) * NiS);
   twoH = NiS;
 }
@@ -146,8 +249,8 @@ __device__ __forceinline__ void rhs_q64(const RayK& K, double r, double th, doub
   double s, c;
   sincos(th, &s, &c);
   const double ir = 1.0 / r;
-  const double f = 1.0 - 2.0 * ir;
-  const double iD = 1.0 / (r * r - 2.0 * r);
+  const double f = fma(-2.0, ir, 1.0);
+  const double iD = 1.0 / (r * (r - 2.0));
   const double s2 = s * s;
   const double X = fma(s2, iD, 1.0);
   const double iX = 1.0 / X;
@@ -162,20 +265,21 @@ __device__ __forceinline__ void rhs_q64(const RayK& K, double r, double th, doub
   const double LXr = -s2 * (2.0 * r - 2.0) * iD * iD * iX;
   const double LXth = 2.0 * s * c * iD * iX;
   const double E2 = K.E * K.E, L2 = K.L * K.L, pr2 = pr * pr, pth2 = pth * pth;
-  twoH = gtt * E2 + grr * pr2 + gthth * pth2 + gpp * L2;
+  twoH = fma(gtt, E2, fma(grr, pr2, fma(gthth, pth2, gpp * L2)));
   dr = grr * pr;
   dth = gthth * pth;
   dph = gpp * K.L;
   const double dgtt = -gtt * (1.0 + K.q) * Lf;
   const double dgrr = grr * fma(1.0 + K.q, Lf, K.kap * LXr);
-  const double dgthth = gthth * (fma(K.q, Lf, K.kap * LXr) - 2.0 * ir);
+  const double dgthth = gthth * fma(K.kap, LXr, fma(K.q, Lf, -2.0 * ir));
   const double dgpp = gpp * fma(K.q, Lf, -2.0 * ir);
-  dpr = -0.5 * (dgtt * E2 + dgrr * pr2 + dgthth * pth2 + dgpp * L2);
-  dpth = -0.5 * (K.kap * LXth * (grr * pr2 + gthth * pth2) - 2.0 * (c / s) * gpp * L2);
+  dpr = -0.5 * fma(dgtt, E2, fma(dgrr, pr2, fma(dgthth, pth2, dgpp * L2)));
+  dpth = -0.5 * fma(K.kap * LXth, fma(grr, pr2, gthth * pth2), -2.0 * (c / s) * gpp * L2);
 }
 
 // Metric policies for the FP64 steppers.
 struct KerrMetric {
+  static constexpr bool kTrigTable = true;  // rhs64 reads the block's sincos table
   static __device__ __forceinline__ void rhs(const RayK& K, double r, double th, double pr,
                                              double pth, double& dr, double& dth, double& dph,
                                              double& dpr, double& dpth, double& twoH) {
@@ -183,6 +287,7 @@ struct KerrMetric {
   }
 };
 struct QMetric {
+  static constexpr bool kTrigTable = false;
   static __device__ __forceinline__ void rhs(const RayK& K, double r, double th, double pr,
                                              double pth, double& dr, double& dth, double& dph,
                                              double& dpr, double& dpth, double& twoH) {

@@ -12,6 +12,7 @@ struct StepperFP64;
 template <class Met>
 struct StepperFP64<OSIRIS_RKCK45, Met> {
   static constexpr double kLocateRel = 0.0;
+  static constexpr bool kTrigTable = Met::kTrigTable;
   struct RayCache {};
   struct LaneCache {};
   static __device__ __forceinline__ void prepare(const RayK&, RayCache&) {}
@@ -34,6 +35,7 @@ struct StepperFP64<OSIRIS_RKCK45, Met> {
 template <class Met>
 struct StepperFP64<OSIRIS_RKDP45, Met> {
   static constexpr double kLocateRel = 0.0;
+  static constexpr bool kTrigTable = Met::kTrigTable;
   struct RayCache {};
   struct LaneCache {
     Deriv k1, k7;

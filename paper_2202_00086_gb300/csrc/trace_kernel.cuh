@@ -159,6 +159,7 @@ __device__ __forceinline__ int64_t refill(const KernelArgs& A, bool need) {
 template <class Stepper, bool PERSISTENT>
 __device__ __forceinline__ void trace_body(const KernelArgs& A) {
   const unsigned FULL = 0xffffffffu;
+  if (Stepper::kTrigTable) trig_table_init();
 
   int mode = MODE_IDLE;
   bool drained = !PERSISTENT;

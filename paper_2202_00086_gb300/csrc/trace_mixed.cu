@@ -27,7 +27,7 @@ __device__ __forceinline__ void rhs32(const RayK32& K, float r, float th, float 
   const float r2 = r * r;
   const float Delta = fmaf(r, r - 2.0f, K.a2);
   const float Sigma = fmaf(K.a2 * c, c, r2);
-  const float P = fmaf(r2 + K.a2, K.E, -K.aL);
+  const float P = fmaf(fmaf(r, r, K.a2), K.E, -K.aL);
   const float DS = Delta * Sigma;
   const float inv = __frcp_rn(DS * s);
   const float iSig = (Delta * s) * inv;
@@ -41,7 +41,7 @@ __device__ __forceinline__ void rhs32(const RayK32& K, float r, float th, float 
   dr = Dpr * iSig;
   dth = pth * iSig;
   dph = fmaf(W, is, K.a * u) * iSig;
-  dpr = iSig * (fmaf(r, NiS, 2.0f * r * K.E * u) - (r - 1.0f) * fmaf(u, u, pr * pr));
+  dpr = iSig * fmaf(1.0f - r, fmaf(u, u, pr * pr), fmaf(r, NiS, (r + r) * K.E * u));
   dpth = (c * iSig) * fmaf(W, fmaf(K.L, is * is, K.aE), -(K.a2 * s) * NiS);
 }
 
@@ -52,7 +52,7 @@ __device__ __forceinline__ double twoH_value64(const RayK& K, const State& y) {
   const double r2 = y.r * y.r;
   const double Delta = fma(y.r, y.r - 2.0, K.a2);
   const double Sigma = fma(K.a2 * c, c, r2);
-  const double P = fma(r2 + K.a2, K.E, -K.aL);
+  const double P = fma(fma(y.r, y.r, K.a2), K.E, -K.aL);
   const double DS = Delta * Sigma;
   const double inv = __drcp_rn(DS * s);
   const double iSig = (Delta * s) * inv;
@@ -66,6 +66,7 @@ struct StepperMixed {
   // FP32 stage values put ~1e-7 relative noise on a trial step's end point;
   // a bracket narrower than that cannot be resolved further
   static constexpr double kLocateRel = 2e-7;
+  static constexpr bool kTrigTable = true;  // its FP64 steps use rhs64
   struct RayCache {};
   struct LaneCache {};
   static __device__ __forceinline__ void prepare(const RayK&, RayCache&) {}
