@@ -81,6 +81,7 @@ struct State {  // evolved coordinates and momenta (t does not feed back; not in
 // q and kap = q (2 + q)).
 struct RayK {
   double a, a2, aE, aL, E, L;
+  double E2;  // 2E
   double q, kap;
 };
 
@@ -92,46 +93,42 @@ struct RayK {
 // two helpers below move the argument reduction, table look-up and seeds onto
 // those pipes and keep only the accuracy-critical FP64 arithmetic.
 //
-// sincos_tab: theta = theta_k + x with theta_k = k pi/256 (the nearest node,
-// found in FP32) and |x| <= pi/512 (+ FP32 rounding). sin/cos of the node come
-// from a per-block shared-memory table; sin x and cos x - 1 from their Taylor
-// series (truncation below 0.1 ulp at |x| = 0.0062):
-//   sin x = x + x^3 (-1/6 + x^2/120)
-//   cos x - 1 = x^2 (-1/2 + x^2 (1/24 - x^2/720))
-//   sin theta = S_k + (S_k (cos x - 1) + C_k sin x), cos similarly,
-// 12 FP64 instructions. The reduction x = (theta - N_k) - T_k uses the node
-// as a double-double (N_k + T_k = k pi/256 to ~1e-32), so sin theta keeps
-// its relative accuracy next to theta = 0 and pi (k = 0, 256: S_k = 0).
-// The table covers theta in [-pi/2, 5pi/2]; outside it (never reached by a
-// ray in the Boyer-Lindquist chart) the library sincos is used.
+// sincos_tab: theta = N_k + x, where the node N_k is the double nearest to
+// k pi/512 (the node index found in FP32), so that x = theta - N_k is exact
+// (Sterbenz) and |x| <= pi/1024 (+ FP32 rounding). sin and cos of the node
+// itself (not of k pi/512) come from a per-block shared-memory table filled
+// with the library sincos; sin x and cos x - 1 from their Taylor series
+// (truncation below 0.01 ulp at |x| = 0.0031):
+//   sin x = x + x^3 (-1/6 + x^2/120),   cos x - 1 = x^2 (-1/2 + x^2/24),
+//   sin theta = S_k + (S_k (cos x - 1) + C_k sin x), cos similarly:
+// 11 FP64 instructions. The table covers theta in [-pi/16, 17 pi/16], which
+// holds every ray except one passing almost exactly over a pole; outside it
+// the library sincos is used.
 // ---------------------------------------------------------------------------
-constexpr int kTrigPerPi = 256;                 // nodes per pi
-constexpr int kTrigFirst = -kTrigPerPi / 2;     // node index of the first entry
-constexpr int kTrigNodes = 3 * kTrigPerPi + 1;  // k in [-128, 640]
+constexpr int kTrigPerPi = 512;                      // nodes per pi
+constexpr int kTrigFirst = -kTrigPerPi / 16;         // node index of the first entry
+constexpr int kTrigNodes = kTrigPerPi + 2 * (kTrigPerPi / 16) + 1;
 
-struct TrigNode {
-  double2 sc;  // sin(k pi/256), cos(k pi/256)
-  double2 nt;  // k pi/256 = n + t (double-double)
+struct TrigTable {
+  double2 sc[kTrigNodes];  // sin N_k, cos N_k
+  double n[kTrigNodes];    // N_k
 };
 
-__device__ __forceinline__ TrigNode* trig_table() {
-  __shared__ TrigNode table[kTrigNodes];
+__device__ __forceinline__ TrigTable& trig_table() {
+  __shared__ TrigTable table;
   return table;
 }
 
 // Fill the block's table (all threads of the block, before any divergence).
 __device__ __forceinline__ void trig_table_init() {
-  constexpr double PI_HI = 3.141592653589793116;          // pi rounded to double
-  constexpr double PI_LO = 1.2246467991473532072e-16;     // pi - PI_HI
-  TrigNode* t = trig_table();
+  constexpr double STEP = 3.141592653589793116 / kTrigPerPi;  // exact: pi rounded / 2^9
+  TrigTable& t = trig_table();
   for (int i = threadIdx.x; i < kTrigNodes; i += blockDim.x) {
-    const double u = (double)(i + kTrigFirst) / kTrigPerPi;  // exact
+    const double n = (double)(i + kTrigFirst) * STEP;
     double s, c;
-    sincospi(u, &s, &c);
-    const double n = u * PI_HI;
-    const double tail = fma(u, PI_HI, -n) + u * PI_LO;
-    t[i].sc = make_double2(s, c);
-    t[i].nt = make_double2(n, tail);
+    sincos(n, &s, &c);
+    t.sc[i] = make_double2(s, c);
+    t.n[i] = n;
   }
   __syncthreads();
 }
@@ -157,15 +154,29 @@ __device__ __forceinline__ void sincos_tab(double th, double& s, double& c) {
     sincos(th, &s, &c);
     return;
   }
-  const TrigNode* t = trig_table() + idx;
-  const double2 nt = t->nt;
-  const double2 sc = t->sc;
-  const double x = (th - nt.x) - nt.y;
+  const TrigTable& t = trig_table();
+  const double2 sc = t.sc[idx];
+  const double x = th - t.n[idx];
   const double x2 = x * x;
   const double sx = fma(x * x2, fma(x2, 1.0 / 120.0, -1.0 / 6.0), x);
-  const double cm = x2 * fma(x2, fma(x2, -1.0 / 720.0, 1.0 / 24.0), -0.5);
+  const double cm = x2 * fma(x2, 1.0 / 24.0, -0.5);
   s = fma(sc.y, sx, fma(sc.x, cm, sc.x));
   c = fma(-sc.x, sx, fma(sc.y, cm, sc.y));
+}
+
+// A normal FP32 value as a double, by integer operations only.
+__device__ __forceinline__ double float_to_double(float f) {
+  const unsigned b = __float_as_uint(f);
+  const long long e = (long long)((b >> 23) & 0xff) - 127 + 1023;
+  return __longlong_as_double((long long)(b & 0x80000000u) << 32 | e << 52 |
+                              (long long)(b & 0x7fffffu) << 29);
+}
+
+// max |H - H0| kept as the bit pattern of a non-negative double: |v| and the
+// maximum are integer operations; NaN is ignored like fmax does.
+__device__ __forceinline__ void track_abs_H(long long& max_bits, double twoH, double H0) {
+  const long long b = __double_as_longlong(fma(0.5, twoH, -H0)) & 0x7fffffffffffffffLL;
+  if (b <= 0x7ff0000000000000LL && b > max_bits) max_bits = b;
 }
 
 // 1/d: FP32 seed x0 (|x0 d - 1| < 2^-21), then one Newton step with the
@@ -179,10 +190,7 @@ __device__ __forceinline__ double rcp64(double d) {
                                  (int)((b >> 29) & 0x7fffff));
   float rf;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f));
-  const unsigned rb = __float_as_uint(rf);
-  const long long er = (long long)((rb >> 23) & 0xff) - 127 + 1023;
-  const double x0 = __longlong_as_double((long long)(rb & 0x80000000u) << 32 | er << 52 |
-                                         (long long)(rb & 0x7fffffu) << 29);
+  const double x0 = float_to_double(rf);
   const double eps = fma(-d, x0, 1.0);
   return fma(x0, fma(eps, eps, eps), x0);
 }
@@ -217,8 +225,9 @@ __device__ __forceinline__ void rhs64(const RayK& K, double r, double th, double
   const double P = fma(fma(r, r, K.a2), K.E, -K.aL);
   const double DS = Delta * Sigma;
   const double inv = rcp64(DS * s);
-  const double iSig = (Delta * s) * inv;
-  const double iDel = (Sigma * s) * inv;
+  const double sinv = s * inv;  // 1 / (Delta Sigma)
+  const double iSig = Delta * sinv;
+  const double iDel = Sigma * sinv;
   const double is = DS * inv;
   const double W = fma(K.L, is, -K.aE * s);
   const double u = P * iDel;
@@ -228,7 +237,7 @@ __device__ __forceinline__ void rhs64(const RayK& K, double r, double th, double
   dr = Dpr * iSig;
   dth = pth * iSig;
   dph = fma(W, is, K.a * u) * iSig;
-  dpr = iSig * fma(1.0 - r, fma(u, u, pr * pr), fma(r, NiS, (r + r) * K.E * u));
+  dpr = iSig * fma(1.0 - r, fma(u, u, pr * pr), fma(r, NiS, (r * K.E2) * u));
   dpth = (c * iSig) * fma(W, fma(K.L, is * is, K.aE), -(K.a2 * s) * NiS);
   twoH = NiS;
 }

@@ -64,6 +64,7 @@ __device__ __forceinline__ void load_ray(const KernelArgs& A, int64_t g, RayInfo
   }
   I.K.aE = a * I.K.E;
   I.K.aL = a * I.K.L;
+  I.K.E2 = I.K.E + I.K.E;
   I.r_cap = R->r_cap;
   I.r_esc = R->r_esc;
   I.r_in = R->r_in;
@@ -180,7 +181,8 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
   // integration state
   State y;
   float tol32 = 0.0f;
-  double h = 0, max_abs_H = 0;
+  double h = 0;
+  long long max_abs_H = 0;  // bit pattern of max |H - H0| (non-negative doubles order as integers)
   unsigned n_acc = 0, n_rej = 0;
   // surface location (LOCATE)
   int kind = 0, side = 0, iters = 0;
@@ -193,7 +195,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
     Stepper::prepare(K, RC);
     Stepper::reset(LC);
     h = I.h0;
-    max_abs_H = 0.0;
+    max_abs_H = 0;
     n_acc = n_rej = 0;
     mode = MODE_INTEGRATE;
   };
@@ -201,10 +203,10 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
   // Write the ray's outputs and retire the lane.
   auto finish = [&](int status, const State& f) {
     if (status != OSIRIS_STATUS_ERROR) {
-      max_abs_H = fmax(max_abs_H, fabs(0.5 * Stepper::twoH(K, f) - I.H0));
+      track_abs_H(max_abs_H, Stepper::twoH(K, f), I.H0);
       S.rhs += 1;
     }
-    write_outputs(A, I, status, f, max_abs_H, n_acc, n_rej, S);
+    write_outputs(A, I, status, f, __longlong_as_double(max_abs_H), n_acc, n_rej, S);
     mode = MODE_IDLE;
   };
 
@@ -266,7 +268,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
     S.fp64_steps += fp64_step ? 1 : 0;
 
     if (mode == MODE_INTEGRATE) {
-      max_abs_H = fmax(max_abs_H, fabs(0.5 * twoH - I.H0));
+      track_abs_H(max_abs_H, twoH, I.H0);
       if (state_not_finite(o) || state_not_finite(d)) {
         finish(OSIRIS_STATUS_ERROR, y);
         continue;
@@ -287,7 +289,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
         // step-size controller (FP32 is enough to size the next step):
         // min(5, max(0.2, 0.9 err^-1/5))
         const float grow = fminf(5.0f, fmaxf(0.2f, 0.9f * exp2f(-0.2f * log2f(err))));
-        h = hs * (double)grow;
+        h = hs * float_to_double(grow);
         h_step = hs;
         yE = o;
         if (disk && crosses_equator(y, o))
@@ -297,7 +299,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
       } else {
         ++n_rej;
         const float shrink = fmaxf(0.1f, 0.9f * exp2f(-0.25f * log2f(err)));
-        h = hs * (double)shrink;
+        h = hs * float_to_double(shrink);
         if ((int64_t)(n_acc + n_rej) >= max_steps) finish(OSIRIS_STATUS_MAXSTEP, y);
       }
     } else {  // MODE_LOCATE: Illinois-modified regula falsi on the step length
