@@ -88,7 +88,7 @@ __device__ __forceinline__ void rhs_df(const RayDF& K, df r, df th, df pr, df pt
   // Intermediate sums are left unrenormalised (df_add_u); the five outputs
   // are renormalised at the end.
   df s, c;
-  df_sincos(th, s, c);
+  df_sincos_tab(th, s, c);
   const df r2 = df_sqr(r);
   const df Delta = df_add_u(df_mul(r, df_add_f(r, -2.0f)), K.a2);
   const df Sigma = df_add_u(r2, df_mul(K.a2, df_sqr(c)));
@@ -322,6 +322,7 @@ __device__ __forceinline__ void rk_step_df(const RayDF& K, LaneCacheDF<INTEG>& L
 template <bool PERSISTENT, int INTEG>
 __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
   const unsigned FULL = 0xffffffffu;
+  df_trig_table_init();
   int mode = MODE_IDLE;
   bool drained = !PERSISTENT;
   LaneStats S;
