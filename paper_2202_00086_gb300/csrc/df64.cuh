@@ -196,92 +196,4 @@ __device__ __forceinline__ void df_sincos(df x, df& s, df& c) {
   }
 }
 
-// ---------------------------------------------------------------------------
-// Table-driven df64 sine and cosine.
-//
-// theta is first reduced by the nearest multiple q of pi/2 (three-float pi/2,
-// as in df_sincos), so t = theta - q pi/2 keeps full relative accuracy next
-// to 0, pi/2 and pi. Then t = N_k + x with the node N_k = k STEP: STEP has 12
-// significant bits, so k STEP (|k| <= 1401) is an exact float and
-// x = t - N_k is one exact fmaf; |x| <= STEP/2 = 2.8e-4. sin and cos of each
-// node (of N_k itself) are df64 pairs in a per-block shared-memory table
-// filled from the FP64 library sincos. With u = x^2 (df64):
-//   sin x = x + x u (-1/6 + u/120)      (correction 1.3e-8 |x|: FP32)
-//   cos x - 1 = -u/2 + u^2/24           (df64)
-//   sin t = S_k + (S_k (cos x - 1) + C_k sin x), cos t similarly,
-// about 75 FP32 instructions against ~150 for the series of df_sincos, with a
-// relative error below 1e-14 (an FP32 emulation against 130-bit references
-// over [-pi/16, 17 pi/16]).
-// ---------------------------------------------------------------------------
-namespace dftab {
-constexpr float STEP = 2353.0f / 4194304.0f;         // 2353 * 2^-22 ~ pi / 5600
-constexpr float INV_STEP = (float)(4194304.0 / 2353.0);
-constexpr int FIRST = -1401;                         // 1400 STEP > pi/4
-constexpr int NODES = 2803;
-}  // namespace dftab
-
-struct DfTrigTable {
-  float4 v[dftab::NODES];  // sin N_k (hi, lo), cos N_k (hi, lo)
-};
-
-__device__ __forceinline__ DfTrigTable& df_trig_table() {
-  __shared__ DfTrigTable table;
-  return table;
-}
-
-// Fill the block's table (all threads of the block, before any divergence).
-__device__ __forceinline__ void df_trig_table_init() {
-  DfTrigTable& t = df_trig_table();
-  for (int i = threadIdx.x; i < dftab::NODES; i += blockDim.x) {
-    const double n = (double)(i + dftab::FIRST) * (double)dftab::STEP;  // exact
-    double sd, cd;
-    sincos(n, &sd, &cd);
-    const df S = df_from_double(sd), C = df_from_double(cd);
-    t.v[i] = make_float4(S.hi, S.lo, C.hi, C.lo);
-  }
-  __syncthreads();
-}
-
-__device__ __forceinline__ void df_sincos_tab(df x, df& s, df& c) {
-  using namespace dfc;
-  const float q = rintf(x.hi * 0.636619772367581343f);
-  const float a = fmaf(-q, P1, x.hi);
-  const df b = two_sum(x.lo, __fmul_rn(-q, P2));
-  df t = two_sum(a, b.hi);
-  t.lo = __fadd_rn(t.lo, fmaf(-q, P3, b.lo));
-  t = fast_two_sum(t.hi, t.lo);
-  // nearest node: 1.5 * 2^23 added to round to an integer
-  const int k = __float_as_int(fmaf(t.hi, dftab::INV_STEP, 12582912.0f)) - 0x4B400000;
-  const int idx = k - dftab::FIRST;
-  if ((unsigned)idx >= (unsigned)dftab::NODES) {  // NaN / inf only
-    df_sincos(x, s, c);
-    return;
-  }
-  const float4 e = df_trig_table().v[idx];
-  const df xr = two_sum(fmaf(-(float)k, dftab::STEP, t.hi), t.lo);
-  df u = two_prod(xr.hi, xr.hi);
-  u.lo = fmaf(__fadd_rn(xr.hi, xr.hi), xr.lo, u.lo);
-  const df cm = mk(__fmul_rn(-0.5f, u.hi),
-                   fmaf(__fmul_rn(u.hi, 1.0f / 24.0f), u.hi, __fmul_rn(-0.5f, u.lo)));
-  const df sx = mk(xr.hi, fmaf(__fmul_rn(xr.hi, u.hi), fmaf(u.hi, 1.0f / 120.0f, -1.0f / 6.0f),
-                               xr.lo));
-  const df S = mk(e.x, e.y), C = mk(e.z, e.w);
-  const df st = df_add(S, df_add_u(df_mul(S, cm), df_mul(C, sx)));
-  const df ct = df_add(C, df_add_u(df_mul(C, cm), df_mul(df_neg(S), sx)));
-  const int quad = ((int)q) & 3;
-  if (quad == 0) {
-    s = st;
-    c = ct;
-  } else if (quad == 1) {
-    s = ct;
-    c = df_neg(st);
-  } else if (quad == 2) {
-    s = df_neg(st);
-    c = df_neg(ct);
-  } else {
-    s = df_neg(ct);
-    c = st;
-  }
-}
-
 }  // namespace osiris_impl

@@ -88,7 +88,7 @@ __device__ __forceinline__ void rhs_df(const RayDF& K, df r, df th, df pr, df pt
   // Intermediate sums are left unrenormalised (df_add_u); the five outputs
   // are renormalised at the end.
   df s, c;
-  df_sincos_tab(th, s, c);
+  df_sincos(th, s, c);
   const df r2 = df_sqr(r);
   const df Delta = df_add_u(df_mul(r, df_add_f(r, -2.0f)), K.a2);
   const df Sigma = df_add_u(r2, df_mul(K.a2, df_sqr(c)));
@@ -322,7 +322,6 @@ __device__ __forceinline__ void rk_step_df(const RayDF& K, LaneCacheDF<INTEG>& L
 template <bool PERSISTENT, int INTEG>
 __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
   const unsigned FULL = 0xffffffffu;
-  df_trig_table_init();
   int mode = MODE_IDLE;
   bool drained = !PERSISTENT;
   LaneStats S;
@@ -509,10 +508,13 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
   flush_stats(A, S);
 }
 
-// Registers capped at 168 so that three blocks of 128 threads are resident
-// per SM: the double-float dependency chains need the extra warps more than
-// they lose to the few spilled values (measured +5 % over two blocks).
-constexpr int kMaxRegs = 168;
+// Registers capped at 128 so that four blocks of 128 threads (16 warps) are
+// resident per SM: the double-float dependency chains need the extra warps
+// more than they lose to the spilled values, which stay in L1 as long as no
+// shared memory is reserved. Measured on the 12 x 1024^2 Kerr set (Mrays/s,
+// Cash-Karp): 168 registers (three blocks) 14.4, 128: 15.5, 112: 15.4,
+// 96: 15.3, 80: 14.7.
+constexpr int kMaxRegs = 128;
 
 template <int INTEG>
 __global__ void __maxnreg__(kMaxRegs) trace_df64_plain(const __grid_constant__ KernelArgs A) {
