@@ -289,6 +289,9 @@ __device__ __forceinline__ void rhs_q64(const RayK& K, double r, double th, doub
 // Metric policies for the FP64 steppers.
 struct KerrMetric {
   static constexpr bool kTrigTable = true;  // rhs64 reads the block's sincos table
+  // 168 registers: three blocks of 128 threads per SM (+1.7 % over the 190
+  // the compiler picks, which leaves two; 152 and 128 gain nothing).
+  static constexpr int kMaxRegs = 168;
   static __device__ __forceinline__ void rhs(const RayK& K, double r, double th, double pr,
                                              double pth, double& dr, double& dth, double& dph,
                                              double& dpr, double& dpth, double& twoH) {
@@ -297,6 +300,7 @@ struct KerrMetric {
 };
 struct QMetric {
   static constexpr bool kTrigTable = false;
+  static constexpr int kMaxRegs = 255;  // two logarithms and exponentials: no cap
   static __device__ __forceinline__ void rhs(const RayK& K, double r, double th, double pr,
                                              double pth, double& dr, double& dth, double& dph,
                                              double& dpr, double& dpth, double& twoH) {

@@ -60,15 +60,14 @@ struct StepperFP64<OSIRIS_RKDP45, Met> {
   }
 };
 
-constexpr int kMaxBlock = 256;
 
 template <int INTEG, class Met>
-__global__ void __launch_bounds__(kMaxBlock) trace_fp64_plain(const __grid_constant__ KernelArgs A) {
+__global__ void __maxnreg__(Met::kMaxRegs) trace_fp64_plain(const __grid_constant__ KernelArgs A) {
   trace_body<StepperFP64<INTEG, Met>, false>(A);
 }
 
 template <int INTEG, class Met>
-__global__ void __launch_bounds__(kMaxBlock) trace_fp64_persistent(const __grid_constant__ KernelArgs A) {
+__global__ void __maxnreg__(Met::kMaxRegs) trace_fp64_persistent(const __grid_constant__ KernelArgs A) {
   trace_body<StepperFP64<INTEG, Met>, true>(A);
 }
 
