@@ -236,6 +236,43 @@ size_t osiris_workspace_bytes(int32_t n_requests);
 int osiris_trace_batch(const osiris_request* reqs, int32_t n_requests,
                        const osiris_trace_opts* opts, void* cuda_stream);
 
+/* Batch plan: a batched persistent launch (osiris_trace_batch) recorded once
+ * as a CUDA graph and replayed per batch, for request loops that launch many
+ * rounds (the continuous-batching server). The graph holds the upload of the
+ * request table from a pinned host staging table (all max_requests entries),
+ * the reset of the device ray queue and the trace kernel; each launch
+ * rewrites the staging table and patches the kernel arguments and the grid
+ * into the instantiated graph, then launches it: one API launch per round.
+ * Results are those of osiris_trace_batch with the same requests and opts. */
+typedef struct osiris_batch_plan osiris_batch_plan;
+
+/* Create a plan for batches of up to max_requests (1..65536) requests in the
+ * given space-time (OSIRIS_SPACETIME_*), with opts fixed for the plan's life:
+ * precision, integrator, launch shape, stats and per-request defaults
+ * (tol <= 0 in a request takes opts->tol). opts->workspace (DEVICE, >=
+ * osiris_workspace_bytes(max_requests) bytes) belongs to the plan until it is
+ * destroyed and must not be used by other calls meanwhile. The plan allocates
+ * max_requests table entries of pinned host memory. Returns OSIRIS_EINVAL
+ * (bad arguments, q-metric without FP64), OSIRIS_ENOMEM (workspace too small
+ * or no pinned memory) or OSIRIS_ECUDA; *plan is NULL on error. */
+int osiris_batch_plan_create(osiris_batch_plan** plan, int32_t max_requests, int32_t spacetime,
+                             const osiris_trace_opts* opts);
+
+/* Launch one batch (1 <= n_requests <= max_requests, all in the plan's
+ * space-time) on cuda_stream, asynchronously. Requests are validated as in
+ * osiris_trace_batch; the host array may be reused when the call returns.
+ * Before rewriting the staging table the call waits (host) until the
+ * previous launch of this plan has uploaded it. Launches of one plan must be
+ * ordered (one stream, or streams the caller orders), since they share the
+ * device table and queue; use one plan per batch in flight. Not thread-safe
+ * per plan. */
+int osiris_batch_plan_launch(osiris_batch_plan* plan, const osiris_request* reqs,
+                             int32_t n_requests, void* cuda_stream);
+
+/* Free a plan (NULL is ignored). Waits for the last upload; launches already
+ * queued still complete. */
+void osiris_batch_plan_destroy(osiris_batch_plan* plan);
+
 /* Most requests osiris_trace_batch_static takes in one call. */
 #define OSIRIS_STATIC_MAX_REQUESTS 256
 

@@ -88,6 +88,10 @@ def lib():
         L.osiris_workspace_bytes.argtypes = [ctypes.c_int32]
         L.osiris_workspace_bytes.restype = ctypes.c_size_t
         L.osiris_trace_batch.argtypes = [_P(Request), ctypes.c_int32, _P(TraceOpts), _vp]
+        L.osiris_batch_plan_create.argtypes = [_P(_vp), ctypes.c_int32, ctypes.c_int32,
+                                               _P(TraceOpts)]
+        L.osiris_batch_plan_launch.argtypes = [_vp, _P(Request), ctypes.c_int32, _vp]
+        L.osiris_batch_plan_destroy.argtypes = [_vp]
         L.osiris_trace_states.argtypes = [_d, _d, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32,
                                           _d, _d, _P(TraceOpts), _P(Outputs), _vp]
         L.osiris_copy_outputs_to_host.argtypes = [_P(Outputs), _P(Outputs), ctypes.c_int64, _vp]
@@ -267,6 +271,43 @@ def trace_batch(requests, stream=None, **opts):
     _check(lib().osiris_trace_batch(arr, n, ctypes.byref(o), _stream_handle(stream)),
            "osiris_trace_batch")
     return requests
+
+
+class BatchPlan:
+    """A batched persistent launch recorded as a CUDA graph and replayed per
+    batch (osiris_batch_plan_*): create once with the plan's fixed options
+    (workspace of workspace_bytes(max_requests) bytes, precision, integrator,
+    launch shape, ...), then launch(requests) for each round. The plan keeps
+    the workspace tensor alive; launches of one plan must go to one stream."""
+
+    def __init__(self, max_requests, spacetime=None, **opts):
+        if spacetime is None:
+            spacetime = SPACETIME_KERR
+        self._opts = make_opts(**opts)
+        self._keep = opts.get("workspace"), opts.get("stats")
+        self.max_requests = int(max_requests)
+        h = _vp()
+        _check(lib().osiris_batch_plan_create(ctypes.byref(h), self.max_requests, int(spacetime),
+                                              ctypes.byref(self._opts)),
+               "osiris_batch_plan_create")
+        self._h = h
+
+    def launch(self, requests, stream=None):
+        """Trace the requests (see request_array) in one graph launch."""
+        arr = request_array(requests)
+        _check(lib().osiris_batch_plan_launch(self._h, arr, len(requests),
+                                              _stream_handle(stream)),
+               "osiris_batch_plan_launch")
+        return requests
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.osiris_batch_plan_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 def trace_batch_static(requests, stream=None, **opts):

@@ -140,22 +140,19 @@ int sm_count(int* n) {
   return OSIRIS_OK;
 }
 
-// Launch the trace kernel for the requests in args (args.reqs / single).
-int launch(KernelArgs& args, const osiris_trace_opts* o, void* stream) {
-  if (args.total_rays == 0) return OSIRIS_OK;
-  const int block = o->block_size ? o->block_size : kDefaultBlock;
-  const bool persistent = o->persistent != 0 || args.reqs != nullptr;
-  auto launcher = (o->precision == OSIRIS_MIXED)  ? osiris_impl::launch_trace_mixed
-                  : (o->precision == OSIRIS_DF64) ? osiris_impl::launch_trace_df64
-                                                  : osiris_impl::launch_trace_fp64;
-  if (!persistent) {
-    const int64_t grid = (args.total_rays + block - 1) / block;
-    if (grid > 0x7fffffff) return OSIRIS_EINVAL;
-    args.queue = nullptr;
-    return cuda_rc(
-        launcher(args, Kernel::kPlain, o->integrator, static_cast<int>(grid), block, stream));
-  }
-  if (!o->workspace || o->workspace_bytes < osiris_impl::kQueueBytes) return OSIRIS_ENOMEM;
+using Launcher = int (*)(const KernelArgs&, Kernel, int, int, int, void*);
+
+Launcher launcher_of(const osiris_trace_opts* o) {
+  return (o->precision == OSIRIS_MIXED)  ? osiris_impl::launch_trace_mixed
+         : (o->precision == OSIRIS_DF64) ? osiris_impl::launch_trace_df64
+                                         : osiris_impl::launch_trace_fp64;
+}
+
+// Launch shape of a persistent grid: threads per block and the full grid
+// (SMs x resident blocks per SM of the kernel that will run).
+int persistent_shape(const osiris_trace_opts* o, int spacetime, int* block,
+                     int64_t* full_grid) {
+  *block = o->block_size ? o->block_size : kDefaultBlock;
   int sms = 0;
   if (int rc = sm_count(&sms)) return rc;
   int per_sm = o->blocks_per_sm;
@@ -163,10 +160,31 @@ int launch(KernelArgs& args, const osiris_trace_opts* o, void* stream) {
     auto occ = (o->precision == OSIRIS_MIXED)  ? osiris_impl::occupancy_mixed
                : (o->precision == OSIRIS_DF64) ? osiris_impl::occupancy_df64
                                                : osiris_impl::occupancy_fp64;
-    if (occ(Kernel::kPersistent, o->integrator, block, &per_sm) != 0 || per_sm < 1)
+    if (occ(Kernel::kPersistent, o->integrator, spacetime, *block, &per_sm) != 0 || per_sm < 1)
       return OSIRIS_ECUDA;
   }
-  int64_t grid = static_cast<int64_t>(sms) * per_sm;
+  *full_grid = static_cast<int64_t>(sms) * per_sm;
+  return OSIRIS_OK;
+}
+
+// Launch the trace kernel for the requests in args (args.reqs / single).
+int launch(KernelArgs& args, const osiris_trace_opts* o, void* stream) {
+  if (args.total_rays == 0) return OSIRIS_OK;
+  const bool persistent = o->persistent != 0 || args.reqs != nullptr;
+  const Launcher launcher = launcher_of(o);
+  if (!persistent) {
+    const int block = o->block_size ? o->block_size : kDefaultBlock;
+    const int64_t grid = (args.total_rays + block - 1) / block;
+    if (grid > 0x7fffffff) return OSIRIS_EINVAL;
+    args.queue = nullptr;
+    return cuda_rc(
+        launcher(args, Kernel::kPlain, o->integrator, static_cast<int>(grid), block, stream));
+  }
+  if (!o->workspace || o->workspace_bytes < osiris_impl::kQueueBytes) return OSIRIS_ENOMEM;
+  int block = 0;
+  int64_t grid = 0;
+  const int spacetime = args.reqs ? args.spacetime : args.single.spacetime;
+  if (int rc = persistent_shape(o, spacetime, &block, &grid)) return rc;
   const int64_t needed = (args.total_rays + block - 1) / block;
   if (grid > needed) grid = needed;
   args.queue = static_cast<unsigned long long*>(o->workspace);
@@ -175,6 +193,35 @@ int launch(KernelArgs& args, const osiris_trace_opts* o, void* stream) {
     return OSIRIS_ECUDA;
   return cuda_rc(
       launcher(args, Kernel::kPersistent, o->integrator, static_cast<int>(grid), block, stream));
+}
+
+// Validate a batch and fill its request table (host memory, n entries);
+// *total receives the number of rays. All requests share one space-time.
+int build_table(const osiris_request* reqs, int32_t n, const osiris_trace_opts* o,
+                ReqDev* table, int64_t* total) {
+  int64_t begin = 0;
+  for (int32_t k = 0; k < n; ++k) {
+    const osiris_request& q = reqs[k];
+    if (!q.camera) return OSIRIS_EINVAL;
+    if (q.tol < 0.0 || !is_fin(q.tol)) return OSIRIS_EINVAL;
+    if (q.disk < OSIRIS_DISK_NONE || q.disk > OSIRIS_DISK_CONSTANT_L || !is_fin(q.l0))
+      return OSIRIS_EINVAL;
+    if (q.camera->spacetime != reqs[0].camera->spacetime) return OSIRIS_EINVAL;
+    if (int rc = check_spacetime(q.camera->spacetime, q.disk, o)) return rc;
+    const double r_esc = o->r_esc_factor * q.camera->r0;
+    if (q.disk)
+      if (int rc = check_disk(q.camera->a, o->r_cap_factor, r_esc, q.r_in, q.r_out)) return rc;
+    ReqDev& R = table[k];
+    std::memset(&R, 0, sizeof(R));
+    fill_common(R, q.camera->a, q.camera->r0, o, q.tol, q.disk, q.r_in, q.r_out, &q.out, q.l0,
+                q.camera->spacetime, q.camera->q);
+    fill_camera(R, q.camera);
+    if (int rc = apply_range(R, q)) return rc;
+    R.ray_begin = begin;
+    begin += R.n_rays;
+  }
+  *total = begin;
+  return OSIRIS_OK;
 }
 
 int run_camera(const osiris_camera* cam, int disk, double r_in, double r_out, double l0,
@@ -334,26 +381,7 @@ int osiris_trace_batch(const osiris_request* reqs, int32_t n, const osiris_trace
   if (!o->workspace || o->workspace_bytes < osiris_workspace_bytes(n)) return OSIRIS_ENOMEM;
   std::vector<ReqDev> table(static_cast<size_t>(n));
   int64_t begin = 0;
-  for (int32_t k = 0; k < n; ++k) {
-    const osiris_request& q = reqs[k];
-    if (!q.camera) return OSIRIS_EINVAL;
-    if (q.tol < 0.0 || !is_fin(q.tol)) return OSIRIS_EINVAL;
-    if (q.disk < OSIRIS_DISK_NONE || q.disk > OSIRIS_DISK_CONSTANT_L || !is_fin(q.l0))
-      return OSIRIS_EINVAL;
-    if (q.camera->spacetime != reqs[0].camera->spacetime) return OSIRIS_EINVAL;
-    if (int rc = check_spacetime(q.camera->spacetime, q.disk, o)) return rc;
-    const double r_esc = o->r_esc_factor * q.camera->r0;
-    if (q.disk)
-      if (int rc = check_disk(q.camera->a, o->r_cap_factor, r_esc, q.r_in, q.r_out)) return rc;
-    ReqDev& R = table[k];
-    std::memset(&R, 0, sizeof(R));
-    fill_common(R, q.camera->a, q.camera->r0, o, q.tol, q.disk, q.r_in, q.r_out, &q.out, q.l0,
-                q.camera->spacetime, q.camera->q);
-    fill_camera(R, q.camera);
-    if (int rc = apply_range(R, q)) return rc;
-    R.ray_begin = begin;
-    begin += R.n_rays;
-  }
+  if (int rc = build_table(reqs, n, o, table.data(), &begin)) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   char* ws = static_cast<char*>(o->workspace);
   ReqDev* dev_table = reinterpret_cast<ReqDev*>(ws + osiris_impl::kQueueBytes);
@@ -364,6 +392,7 @@ int osiris_trace_batch(const osiris_request* reqs, int32_t n, const osiris_trace
   std::memset(&args, 0, sizeof(args));
   args.reqs = dev_table;
   args.n_req = n;
+  args.spacetime = reqs[0].camera->spacetime;
   args.total_rays = begin;
   args.stats = reinterpret_cast<unsigned long long*>(o->stats);
   return launch(args, o, cuda_stream);
@@ -514,27 +543,7 @@ extern "C" int osiris_trace_batch_static(const osiris_request* reqs, int32_t n,
 
   std::lock_guard<std::mutex> lock(g_static_mutex);
   int64_t begin = 0;
-  for (int32_t k = 0; k < n; ++k) {
-    const osiris_request& q = reqs[k];
-    if (!q.camera) return OSIRIS_EINVAL;
-    if (q.tol < 0.0 || !is_fin(q.tol)) return OSIRIS_EINVAL;
-    if (q.disk < OSIRIS_DISK_NONE || q.disk > OSIRIS_DISK_CONSTANT_L || !is_fin(q.l0))
-      return OSIRIS_EINVAL;
-    if (q.camera->spacetime != reqs[0].camera->spacetime) return OSIRIS_EINVAL;
-    if (int rc = check_spacetime(q.camera->spacetime, q.disk, &o)) return rc;
-    if (q.disk)
-      if (int rc = check_disk(q.camera->a, o.r_cap_factor, o.r_esc_factor * q.camera->r0, q.r_in,
-                              q.r_out))
-        return rc;
-    ReqDev& R = g_static_table[k];
-    std::memset(&R, 0, sizeof(R));
-    fill_common(R, q.camera->a, q.camera->r0, &o, q.tol, q.disk, q.r_in, q.r_out, &q.out,
-                q.l0, q.camera->spacetime, q.camera->q);
-    fill_camera(R, q.camera);
-    if (int rc = apply_range(R, q)) return rc;
-    R.ray_begin = begin;
-    begin += R.n_rays;
-  }
+  if (int rc = build_table(reqs, n, &o, g_static_table, &begin)) return rc;
   void* base = nullptr;
   if (int rc = static_workspace_address(&base)) return rc;
   char* ws = static_cast<char*>(base);
@@ -556,3 +565,166 @@ extern "C" int osiris_trace_batch_static(const osiris_request* reqs, int32_t n,
   o.workspace_bytes = kStaticBytes;
   return launch(args, &o, cuda_stream);
 }
+
+// ---------------------------------------------------------------------------
+// Batch plans: the three operations of a batched persistent launch (request
+// table upload, queue reset, trace kernel) recorded once as a CUDA graph and
+// replayed per batch. The upload always copies the plan's whole staging table
+// (max_requests entries of a few hundred bytes), so only the kernel arguments
+// and the grid change between batches; they are patched into the
+// instantiated graph.
+// ---------------------------------------------------------------------------
+struct osiris_batch_plan {
+  osiris_trace_opts opts;  // fixed per plan (workspace, stats, launch shape, defaults)
+  int32_t max_requests = 0;
+  int32_t spacetime = OSIRIS_SPACETIME_KERR;
+  int block = 0;
+  int64_t full_grid = 0;
+  ReqDev* staging = nullptr;    // pinned host copy of the request table
+  ReqDev* dev_table = nullptr;  // inside opts.workspace
+  cudaEvent_t copied = nullptr;  // recorded by the graph once the table is uploaded
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t kernel_node = nullptr;
+  cudaKernelNodeParams kernel{};  // function, block and shared memory of the launch
+};
+
+namespace {
+
+void release(osiris_batch_plan* p) {
+  if (!p) return;
+  if (p->copied) cudaEventSynchronize(p->copied);  // the last upload reads staging
+  if (p->exec) cudaGraphExecDestroy(p->exec);    // in-flight launches still complete
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->copied) cudaEventDestroy(p->copied);
+  if (p->staging) cudaFreeHost(p->staging);
+  delete p;
+}
+
+// Record upload -> event -> queue reset -> kernel on a private stream.
+int record_plan(osiris_batch_plan* p) {
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return OSIRIS_ECUDA;
+  int rc = OSIRIS_OK;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return OSIRIS_ECUDA;
+  }
+  KernelArgs args;
+  std::memset(&args, 0, sizeof(args));
+  args.reqs = p->dev_table;
+  args.n_req = 1;
+  args.spacetime = p->spacetime;
+  args.total_rays = 1;
+  args.stats = reinterpret_cast<unsigned long long*>(p->opts.stats);
+  args.queue = static_cast<unsigned long long*>(p->opts.workspace);
+  // An external event record node: the host waits on it before rewriting the
+  // staging table.
+  if (cudaMemcpyAsync(p->dev_table, p->staging,
+                      sizeof(ReqDev) * static_cast<size_t>(p->max_requests),
+                      cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+      cudaEventRecordWithFlags(p->copied, cs, cudaEventRecordExternal) != cudaSuccess ||
+      cudaMemsetAsync(args.queue, 0, sizeof(unsigned long long), cs) != cudaSuccess ||
+      launcher_of(&p->opts)(args, Kernel::kPersistent, p->opts.integrator, 1, p->block, cs) != 0)
+    rc = OSIRIS_ECUDA;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamEndCapture(cs, &g) != cudaSuccess) rc = OSIRIS_ECUDA;
+  cudaStreamDestroy(cs);
+  p->graph = g;
+  if (rc != OSIRIS_OK) return rc;
+
+  size_t count = 0;
+  if (cudaGraphGetNodes(g, nullptr, &count) != cudaSuccess) return OSIRIS_ECUDA;
+  std::vector<cudaGraphNode_t> nodes(count);
+  if (count == 0 || cudaGraphGetNodes(g, nodes.data(), &count) != cudaSuccess)
+    return OSIRIS_ECUDA;
+  for (cudaGraphNode_t n : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(n, &t) != cudaSuccess) return OSIRIS_ECUDA;
+    if (t == cudaGraphNodeTypeKernel) {
+      p->kernel_node = n;
+      if (cudaGraphKernelNodeGetParams(n, &p->kernel) != cudaSuccess) return OSIRIS_ECUDA;
+    }
+  }
+  if (!p->kernel_node) return OSIRIS_ECUDA;
+  if (cudaGraphInstantiate(&p->exec, g, 0) != cudaSuccess) return OSIRIS_ECUDA;
+  return OSIRIS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int osiris_batch_plan_create(osiris_batch_plan** out, int32_t max_requests, int32_t spacetime,
+                             const osiris_trace_opts* opts) {
+  if (!out || !opts || max_requests < 1 || max_requests > 65536) return OSIRIS_EINVAL;
+  *out = nullptr;
+  if (int rc = check_opts(opts)) return rc;
+  if (int rc = check_spacetime(spacetime, OSIRIS_DISK_NONE, opts)) return rc;
+  if (!opts->workspace || opts->workspace_bytes < osiris_workspace_bytes(max_requests))
+    return OSIRIS_ENOMEM;
+  osiris_batch_plan* p = new (std::nothrow) osiris_batch_plan;
+  if (!p) return OSIRIS_ENOMEM;
+  p->opts = *opts;
+  p->opts.persistent = 1;
+  p->max_requests = max_requests;
+  p->spacetime = spacetime;
+  p->dev_table = reinterpret_cast<ReqDev*>(static_cast<char*>(opts->workspace) +
+                                           osiris_impl::kQueueBytes);
+  int rc = persistent_shape(&p->opts, spacetime, &p->block, &p->full_grid);
+  if (rc == OSIRIS_OK &&
+      cudaMallocHost(&p->staging, sizeof(ReqDev) * static_cast<size_t>(max_requests)) !=
+          cudaSuccess) {
+    p->staging = nullptr;
+    rc = OSIRIS_ENOMEM;
+  }
+  if (rc == OSIRIS_OK &&
+      cudaEventCreateWithFlags(&p->copied, cudaEventDisableTiming) != cudaSuccess) {
+    p->copied = nullptr;
+    rc = OSIRIS_ECUDA;
+  }
+  if (rc == OSIRIS_OK) {
+    std::memset(p->staging, 0, sizeof(ReqDev) * static_cast<size_t>(max_requests));
+    rc = record_plan(p);
+  }
+  if (rc != OSIRIS_OK) {
+    release(p);
+    return rc;
+  }
+  *out = p;
+  return OSIRIS_OK;
+}
+
+int osiris_batch_plan_launch(osiris_batch_plan* p, const osiris_request* reqs, int32_t n,
+                             void* cuda_stream) {
+  if (!p || !reqs || n < 1 || n > p->max_requests) return OSIRIS_EINVAL;
+  if (!reqs[0].camera || reqs[0].camera->spacetime != p->spacetime) return OSIRIS_EINVAL;
+  // The previous batch's upload must have read the staging table.
+  if (cudaEventSynchronize(p->copied) != cudaSuccess) return OSIRIS_ECUDA;
+  int64_t total = 0;
+  if (int rc = build_table(reqs, n, &p->opts, p->staging, &total)) return rc;
+  if (total == 0) return OSIRIS_OK;
+  KernelArgs args;
+  std::memset(&args, 0, sizeof(args));
+  args.reqs = p->dev_table;
+  args.n_req = n;
+  args.spacetime = p->spacetime;
+  args.total_rays = total;
+  args.stats = reinterpret_cast<unsigned long long*>(p->opts.stats);
+  args.queue = static_cast<unsigned long long*>(p->opts.workspace);
+  int64_t grid = (total + p->block - 1) / p->block;
+  if (grid > p->full_grid) grid = p->full_grid;
+  cudaKernelNodeParams k = p->kernel;
+  void* argv[] = {&args};
+  k.gridDim = dim3(static_cast<unsigned>(grid), 1, 1);
+  k.kernelParams = argv;
+  k.extra = nullptr;
+  if (cudaGraphExecKernelNodeSetParams(p->exec, p->kernel_node, &k) != cudaSuccess ||
+      cudaGraphLaunch(p->exec, static_cast<cudaStream_t>(cuda_stream)) != cudaSuccess)
+    return OSIRIS_ECUDA;
+  return OSIRIS_OK;
+}
+
+void osiris_batch_plan_destroy(osiris_batch_plan* p) { release(p); }
+
+}  // extern "C"

@@ -69,9 +69,9 @@ int launch_trace_mixed(const KernelArgs& args, Kernel kind, int integrator, int 
                        void* stream);
 int launch_trace_df64(const KernelArgs& args, Kernel kind, int integrator, int grid, int block,
                       void* stream);
-int occupancy_fp64(Kernel kind, int integrator, int block, int* blocks_per_sm);
-int occupancy_mixed(Kernel kind, int integrator, int block, int* blocks_per_sm);
-int occupancy_df64(Kernel kind, int integrator, int block, int* blocks_per_sm);
+int occupancy_fp64(Kernel kind, int integrator, int spacetime, int block, int* blocks_per_sm);
+int occupancy_mixed(Kernel kind, int integrator, int spacetime, int block, int* blocks_per_sm);
+int occupancy_df64(Kernel kind, int integrator, int spacetime, int block, int* blocks_per_sm);
 int launch_fma_probe(int precision, int64_t n_threads, int iters, double* out, void* stream);
 
 }  // namespace osiris_impl

@@ -289,9 +289,11 @@ __device__ __forceinline__ void rhs_q64(const RayK& K, double r, double th, doub
 // Metric policies for the FP64 steppers.
 struct KerrMetric {
   static constexpr bool kTrigTable = true;  // rhs64 reads the block's sincos table
-  // 168 registers: three blocks of 128 threads per SM (+1.7 % over the 190
-  // the compiler picks, which leaves two; 152 and 128 gain nothing).
-  static constexpr int kMaxRegs = 168;
+  // No register cap (the compiler takes ~200, two blocks of 128 threads per
+  // SM): measured on the 12 x 1024^2 Kerr set, 3.09 Mrays/s uncapped against
+  // 2.95 at 168 registers (three blocks) and 2.90 at 152 or 128 (three or
+  // four blocks). The FP64 pipe needs the scheduling freedom more than warps.
+  static constexpr int kMaxRegs = 255;
   static __device__ __forceinline__ void rhs(const RayK& K, double r, double th, double pr,
                                              double pth, double& dr, double& dth, double& dph,
                                              double& dpr, double& dpth, double& twoH) {
@@ -300,7 +302,7 @@ struct KerrMetric {
 };
 struct QMetric {
   static constexpr bool kTrigTable = false;
-  static constexpr int kMaxRegs = 255;  // two logarithms and exponentials: no cap
+  static constexpr int kMaxRegs = 255;
   static __device__ __forceinline__ void rhs(const RayK& K, double r, double th, double pr,
                                              double pth, double& dr, double& dth, double& dph,
                                              double& dpr, double& dpth, double& twoH) {

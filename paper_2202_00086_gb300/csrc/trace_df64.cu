@@ -549,7 +549,7 @@ int launch_trace_df64(const KernelArgs& args, Kernel kind, int integrator, int g
   return (int)cudaGetLastError();
 }
 
-int occupancy_df64(Kernel kind, int integrator, int block, int* blocks_per_sm) {
+int occupancy_df64(Kernel kind, int integrator, int, int block, int* blocks_per_sm) {
   const void* fn = integrator == OSIRIS_RKDP45 ? df64_kernel<OSIRIS_RKDP45>(kind)
                                                : df64_kernel<OSIRIS_RKCK45>(kind);
   return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, 0);

@@ -94,10 +94,9 @@ int launch_trace_fp64(const KernelArgs& args, Kernel kind, int integrator, int g
                                static_cast<cudaStream_t>(stream));
 }
 
-int occupancy_fp64(Kernel kind, int integrator, int block, int* blocks_per_sm) {
-  // same resources for both space-times within an integrator
+int occupancy_fp64(Kernel kind, int integrator, int spacetime, int block, int* blocks_per_sm) {
   return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      blocks_per_sm, select_fp64(kind, integrator, OSIRIS_SPACETIME_QMETRIC), block, 0);
+      blocks_per_sm, select_fp64(kind, integrator, spacetime), block, 0);
 }
 
 // Roofline probe: 8 independent FMA chains per thread.

@@ -158,7 +158,7 @@ int launch_trace_mixed(const KernelArgs& args, Kernel kind, int, int grid, int b
   return (int)cudaGetLastError();
 }
 
-int occupancy_mixed(Kernel kind, int, int block, int* blocks_per_sm) {
+int occupancy_mixed(Kernel kind, int, int, int block, int* blocks_per_sm) {
   const void* fn = (kind == Kernel::kPersistent) ? (const void*)trace_mixed_persistent
                                                  : (const void*)trace_mixed_plain;
   return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, 0);

@@ -3,10 +3,13 @@
 Renders (camera set-ups) arrive over time. The server:
   - admits a waiting render when its output buffers fit in an HBM budget
     (outputs stay on the device until the render completes);
-  - runs rounds: each round is ONE persistent batched launch
-    (osiris_trace_batch) over pixel ranges of every active render, so renders
-    that arrive while others are on the GPU join the next round and their
-    rays share launches with the older renders';
+  - runs rounds: each round is ONE persistent batched launch over pixel
+    ranges of every active render, so renders that arrive while others are on
+    the GPU join the next round and their rays share launches with the older
+    renders'. With graphs (the default) each in-flight slot owns a batch plan
+    (osiris_batch_plan_*): table upload, queue reset and kernel recorded once
+    as a CUDA graph, so a round is one graph launch with patched arguments;
+    without, a round is one osiris_trace_batch call;
   - keeps up to `max_inflight` rounds queued on the stream, so the GPU never
     waits for the host between rounds;
   - detects round completion with CUDA events and timestamps each render at
@@ -67,7 +70,7 @@ class RenderServer:
     def __init__(self, precision=None, round_rays=1 << 21, min_chunk=1 << 14,
                  hbm_budget_bytes=8 << 30, max_inflight=2, max_entries=4096,
                  keep_outputs=False, cell_deg=10.0, cell_phase_deg=0.0, backend=None,
-                 clock=time.perf_counter):
+                 clock=time.perf_counter, graphs=True):
         import paper_2202_00086_gb300 as osr
         self.osr = osr
         self.precision = osr.DF64 if precision is None else precision
@@ -94,6 +97,12 @@ class RenderServer:
         self._ws = [self.backend.workspace(osr_workspace_bytes(osr, self.max_entries))
                     for _ in range(self.max_inflight)]
         self._ws_free = list(range(self.max_inflight))
+        self._plans = None
+        if graphs and hasattr(self.backend, "plan"):
+            self._plans = [self.backend.plan(ws, self.max_entries, precision=self.precision,
+                                             cell_deg=self.cell_deg,
+                                             cell_phase_deg=self.cell_phase_deg)
+                           for ws in self._ws]
 
     # ---- submission and admission ----
     def submit(self, render, arrival=None):
@@ -157,8 +166,12 @@ class RenderServer:
                             "tol": r.tol, "out": r.out, "first_ray": first, "n_rays": n,
                             "l0": r.render.get("l0") if r.disk else None})
             r.chunks.append((first, n))
-        event = self.backend.launch(entries, self._ws[k], precision=self.precision,
-                                    cell_deg=self.cell_deg, cell_phase_deg=self.cell_phase_deg)
+        if self._plans is not None:
+            event = self.backend.launch_plan(self._plans[k], entries)
+        else:
+            event = self.backend.launch(entries, self._ws[k], precision=self.precision,
+                                        cell_deg=self.cell_deg,
+                                        cell_phase_deg=self.cell_phase_deg)
         self.inflight.append(_Round(event, parts, k, self.clock()))
         self.round_entries.append(len(parts))
         self.rounds += 1
@@ -312,6 +325,15 @@ class _CudaBackend:
 
     def launch(self, entries, ws, **opts):
         self.osr.trace_batch(entries, workspace=ws, **opts)
+        ev = self.torch.cuda.Event()
+        ev.record()
+        return ev
+
+    def plan(self, ws, max_entries, **opts):
+        return self.osr.BatchPlan(max_entries, workspace=ws, **opts)
+
+    def launch_plan(self, plan, entries):
+        plan.launch(entries)
         ev = self.torch.cuda.Event()
         ev.record()
         return ev

@@ -74,6 +74,30 @@ def test_trace_validation_before_launch(osr):
     assert osr.workspace_bytes(10) > osr.workspace_bytes(1) >= 256
 
 
+def test_batch_plan_validation_before_any_cuda_call(osr):
+    """Argument errors of the batch-plan entry points are reported before the
+    plan touches the device (no workspace, no pinned memory, no graph)."""
+    L = osr.lib()
+    h = ctypes.c_void_p()
+    o = osr.make_opts()
+    assert L.osiris_batch_plan_create(ctypes.byref(h), 0, osr.SPACETIME_KERR,
+                                      ctypes.byref(o)) == osr.EINVAL
+    assert L.osiris_batch_plan_create(ctypes.byref(h), 70000, osr.SPACETIME_KERR,
+                                      ctypes.byref(o)) == osr.EINVAL
+    assert L.osiris_batch_plan_create(ctypes.byref(h), 4, 7, ctypes.byref(o)) == osr.EINVAL
+    o_df = osr.make_opts(precision=osr.DF64)
+    assert L.osiris_batch_plan_create(ctypes.byref(h), 4, osr.SPACETIME_QMETRIC,
+                                      ctypes.byref(o_df)) == osr.EINVAL  # q-metric: FP64 only
+    assert L.osiris_batch_plan_create(ctypes.byref(h), 4, osr.SPACETIME_KERR,
+                                      ctypes.byref(osr.make_opts(tol=0.0))) == osr.EINVAL
+    assert L.osiris_batch_plan_create(ctypes.byref(h), 4, osr.SPACETIME_KERR,
+                                      ctypes.byref(o)) == osr.ENOMEM  # no workspace
+    assert not h.value
+    arr = (osr.Request * 1)()
+    assert L.osiris_batch_plan_launch(None, arr, 1, None) == osr.EINVAL
+    L.osiris_batch_plan_destroy(None)
+
+
 def test_oracle_library_loads():
     import oracle
     lib = oracle.lib()

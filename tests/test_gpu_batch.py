@@ -55,3 +55,86 @@ def test_uneven_batch_256():
         alone = gpu_render(rds[k], precision=osr.DF64)
         for f in alone:
             assert np.array_equal(outs[k][f].cpu().numpy(), alone[f]), (k, f)
+
+
+def _requests(rds, outs, ranges=None):
+    reqs = []
+    for k, (rd, o) in enumerate(zip(rds, outs)):
+        disk = rd["mode"] == "disk"
+        q = {"camera": osr.Camera.from_render(rd), "disk": disk,
+             "r_in": osr.resolve_r_in(rd) if disk else 0.0,
+             "r_out": rd["r_out"] if disk else 0.0, "tol": rd["tol"], "out": o}
+        if ranges is not None:
+            q["first_ray"], q["n_rays"] = ranges[k]
+        reqs.append(q)
+    return reqs
+
+
+def _alloc(rds):
+    return [osr.alloc_outputs(rd["nx"] * rd["ny"], fields=osr.DISK_FIELDS if rd["mode"] == "disk"
+                              else osr.SHADOW_FIELDS) for rd in rds]
+
+
+@pytest.mark.parametrize("precision", [osr.FP64, osr.DF64])
+def test_batch_plan_graph_matches_trace_batch(precision):
+    """Rounds of different sizes and pixel ranges through two CUDA-graph batch
+    plans (two rounds in flight on one stream) give bit-identical outputs to
+    osiris_trace_batch, and the plan's stats counters add up."""
+    rds = workloads.uneven_batch(n=10, seed=9, sides=(16, 32, 48))
+    phase = rds[0]["cell_phase_deg"]
+    ref = _alloc(rds)
+    ws_ref = torch.empty(osr.workspace_bytes(len(rds)), dtype=torch.uint8, device="cuda")
+    osr.trace_batch(_requests(rds, ref), workspace=ws_ref, precision=precision,
+                    cell_phase_deg=phase)
+    got = _alloc(rds)
+    stats = osr.new_stats()
+    plans = [osr.BatchPlan(8, workspace=torch.empty(osr.workspace_bytes(8), dtype=torch.uint8,
+                                                     device="cuda"),
+                           precision=precision, cell_phase_deg=phase, stats=stats)
+             for _ in range(2)]
+    # round k: a pixel range of each render in a sliding window of renders
+    n_pix = [rd["nx"] * rd["ny"] for rd in rds]
+    done = [0] * len(rds)
+    k = 0
+    while min(done[i] - n_pix[i] for i in range(len(rds))) < 0:
+        idx = [i for i in range(len(rds)) if done[i] < n_pix[i]][: 3 + k % 6]
+        ranges = []
+        for i in idx:
+            n = min(n_pix[i] - done[i], 97 + 211 * (k % 4))
+            ranges.append((done[i], n))
+            done[i] += n
+        reqs = _requests([rds[i] for i in idx], [got[i] for i in idx], ranges)
+        plans[k % 2].launch(reqs)
+        k += 1
+    torch.cuda.synchronize()
+    assert k >= 4
+    for i, (a, b) in enumerate(zip(ref, got)):
+        for f in a:
+            assert torch.equal(a[f], b[f]), (i, f)
+    s = osr.decode_stats(stats)
+    assert s["rays"] == sum(n_pix) and s["status_error"] == 0
+    for p in plans:
+        p.close()
+
+
+def test_batch_plan_qmetric_and_errors():
+    rds = [workloads.render(0.0, 1000.0, inc, (-8, 8, -8, 8), 12, 10, q=0.3)
+           for inc in (40.0, 80.0)]
+    ws = torch.empty(osr.workspace_bytes(4), dtype=torch.uint8, device="cuda")
+    plan = osr.BatchPlan(4, spacetime=osr.SPACETIME_QMETRIC, workspace=ws,
+                         cell_phase_deg=rds[0]["cell_phase_deg"])
+    outs = _alloc(rds)
+    plan.launch(_requests(rds, outs))
+    torch.cuda.synchronize()
+    for rd, o in zip(rds, outs):
+        alone = gpu_render(rd)
+        for f in alone:
+            assert np.array_equal(o[f].cpu().numpy(), alone[f]), f
+    kerr = workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 4, 4)
+    with pytest.raises(osr.OsirisError) as e:  # another space-time than the plan's
+        plan.launch(_requests([kerr], _alloc([kerr])))
+    assert e.value.code == osr.EINVAL
+    with pytest.raises(osr.OsirisError) as e:  # more requests than the plan holds
+        plan.launch(_requests(rds * 3, _alloc(rds * 3)))
+    assert e.value.code == osr.EINVAL
+    plan.close()

@@ -171,3 +171,22 @@ def test_full_size_kerr_sampled():
     rep = compare(rd, gpu, ref, pixels=pix, band=band)
     print(rep)
     assert_parity(rep)
+
+
+@pytest.mark.parametrize("precision", [osr.FP64, osr.DF64])
+def test_full_size_schwarzschild_disk_sampled(precision):
+    """The 2048^2 Schwarzschild thin disk (r_in = 6, r_out = 20, 80 deg) in
+    one persistent launch; 2000 sampled pixels checked against the oracle one
+    by one, over 200 of them disk hits (g, intensity, r_hit)."""
+    rd = workloads.schwarzschild_disk()
+    assert rd["nx"] == rd["ny"] == 2048
+    gpu = gpu_render(rd, precision=precision, persistent=True)
+    assert int((gpu["status"] == 0).sum()) == 0
+    rng = np.random.default_rng(13)
+    pix = np.sort(rng.choice(2048 * 2048, 2000, replace=False))
+    ref = oracle_render(rd, pixels=pix)
+    band = band_mask(gpu["status"].reshape(2048, 2048)).reshape(-1)
+    rep = compare(rd, gpu, ref, pixels=pix, band=band)
+    print(rep)
+    assert_parity(rep)
+    assert rep["n_disk"] > 200

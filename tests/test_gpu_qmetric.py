@@ -82,3 +82,26 @@ def test_qmetric_rejects_unsupported_modes():
             osr.trace(cam, **kw)
     with pytest.raises(osr.OsirisError):
         osr.render_disk(cam, 6.0, 20.0)
+
+
+def test_qmetric_batch_equals_single_calls():
+    """q-metric renders in one batched persistent launch give the outputs of
+    the same renders traced one by one, and a batch may not mix space-times."""
+    rds = [workloads.render(0.0, 1000.0, inc, (-8, 8, -8, 8), 20, 16, q=q)
+           for q, inc in ((0.5, 30.0), (-0.5, 60.0), (0.1, 90.0))]
+    cams = [osr.Camera.from_render(rd) for rd in rds]
+    outs = [osr.alloc_outputs(c.n_rays) for c in cams]
+    reqs = [{"camera": c, "out": o, "tol": rd["tol"]} for c, o, rd in zip(cams, outs, rds)]
+    ws = torch.empty(osr.workspace_bytes(len(reqs)), dtype=torch.uint8, device="cuda")
+    osr.trace_batch(reqs, workspace=ws, cell_deg=rds[0]["cell_deg"],
+                    cell_phase_deg=rds[0]["cell_phase_deg"])
+    torch.cuda.synchronize()
+    for rd, o in zip(rds, outs):
+        alone = gpu_render(rd)
+        for f in alone:
+            assert np.array_equal(o[f].cpu().numpy(), alone[f]), f
+    kerr = osr.Camera.from_render(workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 4, 4))
+    mixed = reqs[:1] + [{"camera": kerr, "out": osr.alloc_outputs(16), "tol": 1e-10}]
+    with pytest.raises(osr.OsirisError) as e:
+        osr.trace_batch(mixed, workspace=ws)
+    assert e.value.code == osr.EINVAL
