@@ -1,0 +1,74 @@
+"""Error of every output of every precision mode against the FP64 oracle.
+
+Three render kinds (a Kerr shadow with its checkerboard, the Schwarzschild
+thin disk and a Kerr disk from the ISCO) are traced in FP64, DF64 and MIXED
+precision. The reference is the oracle at tol 1e-10 in every case, so the
+MIXED rows (which run at tol 1e-8 and 1e-7, where FP32 stage evaluations
+are usable) include their tolerance error as well as their precision error.
+Per output the test records:
+  flags: status mismatches outside the one-pixel band; checkerboard cell and
+         parity mismatches outside the 1e-6 rad margin;
+  positions: max relative error of the final r, theta, phi;
+  disk: max relative error of g, intensity and r_hit;
+and asserts the bounds stated for the mode (MODES). Run with -s to print the
+table.
+"""
+import pytest
+
+import paper_2202_00086_gb300 as osr
+from paper_2202_00086_gb300 import workloads
+
+from _parity import compare, gpu_render, oracle_render
+
+pytestmark = pytest.mark.gpu
+
+RENDERS = {
+    "kerr a=0.998 60deg shadow": workloads.render(0.998, 1000.0, 60.0, (-8, 8, -8, 8), 48, 48),
+    "schwarzschild disk 80deg": workloads.schwarzschild_disk(side=48),
+    "kerr a=0.9 disk from ISCO": workloads.render(0.9, 1000.0, 60.0, (-25, 25, -25, 25), 48, 48,
+                                                  mode="disk", r_in="isco", r_out=20.0),
+}
+# mode -> (precision, tol, strict). Strict modes must meet the FP64 parity bar
+# (no flag mismatch, positions and g / I / r_hit within 1e-8). The MIXED modes
+# must keep every status outside the band and g (r_hit) within 1e-5, the
+# intensity g^3 r^-2 within 3e-5; their positions and checkerboard cells are
+# reported, not bounded (their tolerance alone moves near-critical rays).
+MODES = {
+    "FP64 tol 1e-10": (osr.FP64, 1e-10, True),
+    "DF64 tol 1e-10": (osr.DF64, 1e-10, True),
+    "MIXED tol 1e-8": (osr.MIXED, 1e-8, False),
+    "MIXED tol 1e-7": (osr.MIXED, 1e-7, False),
+}
+
+_ref_cache = {}
+
+
+def _reference(name):
+    if name not in _ref_cache:
+        _ref_cache[name] = oracle_render(RENDERS[name])
+    return _ref_cache[name]
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+def test_error_of_every_output(mode):
+    precision, tol, strict = MODES[mode]
+    rows = []
+    for name, rd in RENDERS.items():
+        ref = _reference(name)
+        rep = compare(rd, gpu_render(dict(rd, tol=tol), precision=precision), ref)
+        cells = rep.get("cell_mismatch", 0) + rep.get("parity_mismatch", 0)
+        pos = max(rep["r_max_rel"], rep["theta_max_rel"], rep["phi_max_rel"])
+        g, inten, rh = (rep.get(k + "_max_rel", 0.0) for k in ("g", "intensity", "r_hit"))
+        rows.append("| %s | %s | %d | %d | %.1e | %.1e | %.1e | %.1e | %.1e | %.1e |" % (
+            mode, name, rep["status_mismatch"], cells, rep["r_max_rel"], rep["theta_max_rel"],
+            rep["phi_max_rel"], g, inten, rh))
+        assert rep["status_mismatch"] == 0, (mode, name, rep)
+        if strict:
+            assert cells == 0 and pos <= 1e-8 and max(g, inten, rh) <= 1e-8, (mode, name, rep)
+        else:
+            assert g <= 1e-5 and rh <= 1e-5 and inten <= 3e-5, (mode, name, rep)
+    print()
+    print("| mode | render | status mismatches | cell/parity mismatches | r | theta | phi | g |"
+          " intensity | r_hit |")
+    print("|---|---|---|---|---|---|---|---|---|---|")
+    print("\n".join(rows))
