@@ -71,6 +71,9 @@ def test_trace_validation_before_launch(osr):
     assert rc == osr.EINVAL
     rc = osr.lib().osiris_trace_batch(None, 0, ctypes.byref(o), None)
     assert rc == osr.EINVAL
+    reqs = (osr.Request * 1)()
+    rc = osr.lib().osiris_trace_batch(reqs, 65537, ctypes.byref(o), None)  # above the maximum
+    assert rc == osr.EINVAL
     assert osr.workspace_bytes(10) > osr.workspace_bytes(1) >= 256
 
 

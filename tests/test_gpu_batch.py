@@ -138,3 +138,39 @@ def test_batch_plan_qmetric_and_errors():
         plan.launch(_requests(rds * 3, _alloc(rds * 3)))
     assert e.value.code == osr.EINVAL
     plan.close()
+
+
+def test_batch_of_the_maximum_request_count():
+    """65536 requests (the most one batch takes), each a one-pixel range of
+    one 256^2 render, in one launch: bit-identical to the render traced whole."""
+    rd = workloads.render(0.9, 1000.0, 60.0, (-8, 8, -8, 8), 256, 256)
+    cam = osr.Camera.from_render(rd)
+    out = osr.alloc_outputs(cam.n_rays)
+    reqs = [{"camera": cam, "out": out, "tol": rd["tol"], "first_ray": k, "n_rays": 1}
+            for k in range(cam.n_rays)]
+    assert len(reqs) == 65536
+    ws = torch.empty(osr.workspace_bytes(len(reqs)), dtype=torch.uint8, device="cuda")
+    stats = osr.new_stats()
+    osr.trace_batch(reqs, workspace=ws, stats=stats, cell_deg=rd["cell_deg"],
+                    cell_phase_deg=rd["cell_phase_deg"])
+    torch.cuda.synchronize()
+    assert osr.decode_stats(stats)["rays"] == 65536
+    alone = gpu_render(rd)
+    for f in alone:
+        assert np.array_equal(out[f].cpu().numpy(), alone[f]), f
+
+
+def test_empty_explicit_states_launch_nothing():
+    """Zero explicit rays: the call succeeds, launches nothing and leaves the
+    outputs and counters untouched."""
+    z = torch.empty(0, dtype=torch.float64, device="cuda")
+    st = torch.empty((0, 6), dtype=torch.float64, device="cuda")
+    out = osr.alloc_outputs(1)
+    before = {f: v.clone() for f, v in out.items()}
+    stats = osr.new_stats()
+    osr.trace_states(0.5, 1000.0, st, z, z, out=out, stats=stats)
+    osr.trace_states(0.5, 1000.0, st, z, z, out=out, stats=stats, precision=osr.DF64)
+    torch.cuda.synchronize()
+    assert osr.decode_stats(stats)["rays"] == 0
+    for f in out:
+        assert torch.equal(out[f], before[f]), f
