@@ -7,7 +7,7 @@ choice as keyword arguments for the trace calls.
 
 Two launch parameters are fixed by the kernel design rather than tuned:
   - rays per thread = 1: a lane's whole ray state lives in registers, and the
-    register budget (FP64: ~190, DF64: 168 per thread) leaves no room for a
+    register budget (FP64: ~200, DF64: 128 per thread) leaves no room for a
     second ray;
   - refill granularity = 1 warp-wide atomic as soon as any lane is idle: a
     ray start costs about one evaluation of the equations against ~350
