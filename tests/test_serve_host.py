@@ -79,7 +79,7 @@ def test_small_render_finishes_in_its_first_round():
     small = workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 16, 16)
     srv, be = _server(round_rays=50000, min_chunk=4096, max_inflight=1)
     srv.submit(big, arrival=0.0)
-    srv.step()  # big alone in round 1
+    srv.step()  # the first serving round holds only the big render
     srv.submit(small, arrival=0.0)
     while not srv.idle():
         srv.step()
