@@ -133,6 +133,34 @@ def test_explicit_states_hook():
     assert abs(float(o["r"][0]) - 3.0) < 1e-8
 
 
+@pytest.mark.parametrize("precision", [osr.FP64, osr.DF64])
+def test_kerr_spherical_photon_orbits(precision):
+    """Kerr spherical photon orbits (closed-form constants, see the oracle pin
+    of the same name) traced on the GPU: r stays fixed to 1e-8 over 800 steps,
+    theta stays inside its turning points, |H| stays small, and the final r
+    agrees with the oracle's."""
+    from test_oracle_pins import spherical_photon_orbit
+    rows, E, L, cases = [], [], [], []
+    for a in (0.5, 0.9, 0.998):
+        for f in (0.25, 0.5, 0.75):
+            r, xi, eta, u_plus = spherical_photon_orbit(a, f)
+            cases.append((a, r, xi, eta, u_plus))
+    for a, r, xi, eta, u_plus in cases:
+        st = np.array([[0.0, r, math.pi / 2, 0.0, 0.0, math.sqrt(eta)]])
+        o = osr.trace_states(a, 1000.0, torch.tensor(st, device="cuda"),
+                             torch.ones(1, device="cuda", dtype=torch.float64),
+                             torch.full((1,), xi, device="cuda", dtype=torch.float64),
+                             max_steps=800, tol=1e-12, precision=precision)
+        torch.cuda.synchronize()
+        ref = oracle.trace_states(a, 1000.0, st, [1.0], [xi], max_steps=800, tol=1e-12)
+        assert int(o["status"][0]) == osr.STATUS_MAXSTEP
+        rg = float(o["r"][0])
+        assert abs(rg - r) < 1e-8 * r, (a, r, rg)
+        assert abs(rg - ref["r"][0]) < 1e-8 * r
+        assert math.cos(float(o["theta"][0])) ** 2 <= u_plus * (1 + 1e-7)
+        assert float(o["max_abs_H"][0]) < 1e-9
+
+
 def test_stats_counters():
     rd = workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 32, 32)
     stats = osr.new_stats()

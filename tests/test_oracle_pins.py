@@ -277,6 +277,43 @@ def test_photon_sphere_orbit():
     assert res["t"][0] > 20.0
 
 
+def spherical_photon_orbit(a, f):
+    """A Kerr spherical photon orbit (Teo 2003): radius r a fraction f of the
+    way from the prograde to the retrograde equatorial photon orbit
+    r_ph = 2 (1 + cos(2/3 arccos(-+a))); with E = 1 its constants are
+    xi = L/E = -(r^3 - 3 r^2 + a^2 r + a^2) / (a (r - 1)),
+    eta = Q/E^2 = -r^3 (r^3 - 6 r^2 + 9 r - 4 a^2) / (a^2 (r - 1)^2),
+    for which the radial potential and its derivative vanish at r. Returns
+    (r, xi, eta, u_plus) with u_plus = cos^2 of the theta turning points."""
+    r_pro = 2 * (1 + math.cos(2 / 3 * math.acos(-a)))
+    r_retro = 2 * (1 + math.cos(2 / 3 * math.acos(a)))
+    r = r_pro + f * (r_retro - r_pro)
+    xi = -(r ** 3 - 3 * r ** 2 + a * a * r + a * a) / (a * (r - 1))
+    eta = -r ** 3 * (r ** 3 - 6 * r ** 2 + 9 * r - 4 * a * a) / (a * a * (r - 1) ** 2)
+    b = eta + xi * xi - a * a
+    u_plus = (-b + math.sqrt(b * b + 4 * a * a * eta)) / (2 * a * a)
+    return r, xi, eta, u_plus
+
+
+@pytest.mark.parametrize("a", [0.5, 0.9, 0.998])
+@pytest.mark.parametrize("f", [0.25, 0.5, 0.75])
+def test_kerr_spherical_photon_orbits(a, f):
+    """Started on the equator with p_r = 0 and p_theta = sqrt(eta), a photon
+    with the spherical-orbit constants keeps r fixed (the frame-dragging terms
+    of dp_r/dlambda must cancel exactly) while theta oscillates between the
+    turning points cos^2(theta) = u_plus, and the Carter constant stays eta."""
+    r, xi, eta, u_plus = spherical_photon_orbit(a, f)
+    st = np.array([[0.0, r, math.pi / 2, 0.0, 0.0, math.sqrt(eta)]])
+    res = oracle.trace_states(a, R0, st, [1.0], [xi], max_steps=800, tol=1e-12)
+    assert res["status"][0] == oracle.STATUS_MAXSTEP
+    assert res["t"][0] > 20.0
+    assert abs(res["r"][0] - r) < 1e-8 * r
+    assert math.cos(res["theta"][0]) ** 2 <= u_plus * (1 + 1e-9)
+    assert res["carter0"][0] == pytest.approx(eta, rel=1e-12)
+    assert res["max_carter_drift"][0] < 1e-9
+    assert res["max_abs_H"][0] < 1e-10
+
+
 def _cartesian_frame(th, ph):
     er = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
     et = np.array([math.cos(th) * math.cos(ph), math.cos(th) * math.sin(ph), -math.sin(th)])
