@@ -361,6 +361,39 @@ def test_flat_space_straight_lines():
         assert res["max_abs_H"][0] < 1e-9  # truncation error at tol 1e-10
 
 
+def test_checkerboard_cells_from_exact_directions():
+    """Celestial cells and parity (Sec. 4.1 set-up, 10-degree cells with a
+    longitude phase) of flat-space rays, whose final directions are known
+    exactly: straight lines to the escape sphere. The x = 0 rays (L = 0) cross
+    the polar axis, so their coordinate theta leaves [0, pi] (above pi and
+    below 0) and the fold theta -> -theta or 2 pi - theta, phi -> phi + pi must
+    bring them back to the geometric direction."""
+    r0, inc, cell_deg, phase_deg = 1000.0, 70.0, 10.0, 3.7
+    th0, cell, phase = math.radians(inc), math.radians(cell_deg), math.radians(phase_deg)
+    rng = np.random.default_rng(6)
+    pts = [tuple(p) for p in rng.uniform(-400, 400, size=(24, 2))]
+    pts += [(0.0, 150.0), (0.0, -150.0), (0.0, 420.0), (0.0, -600.0)]
+    checked, folded = 0, 0
+    for x, y in pts:
+        st = oracle.init_ray(0.0, r0, inc, x, y, M=0.0)
+        res = oracle.trace_states(0.0, r0, st[None, :6], [st[6]], [st[7]], M=0.0,
+                                  cell_deg=cell_deg, cell_phase_deg=phase_deg)
+        assert res["status"][0] == oracle.STATUS_ESCAPED
+        n0, v = _initial_direction(x, y, r0, th0)
+        X0 = r0 * n0
+        bdot = X0 @ v
+        Xf = X0 + (-bdot + math.sqrt(bdot * bdot - r0 * r0 + (1.1 * r0) ** 2)) * v
+        th, ph = _angles(Xf / np.linalg.norm(Xf))
+        q = (ph + phase) % (2 * math.pi)
+        if min(abs(th / cell - round(th / cell)), abs(q / cell - round(q / cell))) * cell < 1e-6:
+            continue  # too close to a cell edge to be decided by the direction alone
+        i, j = int(th // cell), int(q // cell)
+        assert (res["cell_i"][0], res["cell_j"][0], res["parity"][0]) == (i, j, (i + j) % 2), (x, y)
+        checked += 1
+        folded += not (0.0 <= res["theta"][0] <= math.pi)
+    assert checked >= 24 and folded == 4
+
+
 def _deflection_sweep(b, r0, r_esc):
     """Swept orbital angle from r0 in to the turning point and out to r_esc
     (Schwarzschild, M = 1): with u = 1/r the orbit equation reads
