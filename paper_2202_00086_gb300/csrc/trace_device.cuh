@@ -216,7 +216,7 @@ __device__ __forceinline__ double rcp64(double d) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void rhs64(const RayK& K, double r, double th, double pr, double pth,
                                       double& dr, double& dth, double& dph, double& dpr,
-                                      double& dpth, double& twoH) {
+                                      double& dpth, double& twoH, double& scale) {
   double s, c;
   sincos_tab(th, s, c);
   const double r2 = r * r;
@@ -234,11 +234,14 @@ __device__ __forceinline__ void rhs64(const RayK& K, double r, double th, double
   const double Dpr = Delta * pr;
   const double N = fma(Dpr, pr, fma(pth, pth, fma(W, W, -P * u)));
   const double NiS = N * iSig;
-  dr = Dpr * iSig;
-  dth = pth * iSig;
-  dph = fma(W, is, K.a * u) * iSig;
-  dpr = iSig * fma(1.0 - r, fma(u, u, pr * pr), fma(r, NiS, (r * K.E2) * u));
-  dpth = (c * iSig) * fma(W, fma(K.L, is * is, K.aE), -(K.a2 * s) * NiS);
+  // Every derivative carries the factor 1/Sigma; it is returned separately
+  // (scale) and folded into the stepper's tableau coefficients.
+  dr = Dpr;
+  dth = pth;
+  dph = fma(W, is, K.a * u);
+  dpr = fma(1.0 - r, fma(u, u, pr * pr), fma(r, NiS, (r * K.E2) * u));
+  dpth = c * fma(W, fma(K.L, is * is, K.aE), -(K.a2 * s) * NiS);
+  scale = iSig;
   twoH = NiS;
 }
 
@@ -254,7 +257,8 @@ __device__ __forceinline__ void rhs64(const RayK& K, double r, double th, double
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void rhs_q64(const RayK& K, double r, double th, double pr,
                                         double pth, double& dr, double& dth, double& dph,
-                                        double& dpr, double& dpth, double& twoH) {
+                                        double& dpr, double& dpth, double& twoH, double& scale) {
+  scale = 1.0;
   double s, c;
   sincos(th, &s, &c);
   const double ir = 1.0 / r;
@@ -296,8 +300,9 @@ struct KerrMetric {
   static constexpr int kMaxRegs = 255;
   static __device__ __forceinline__ void rhs(const RayK& K, double r, double th, double pr,
                                              double pth, double& dr, double& dth, double& dph,
-                                             double& dpr, double& dpth, double& twoH) {
-    rhs64(K, r, th, pr, pth, dr, dth, dph, dpr, dpth, twoH);
+                                             double& dpr, double& dpth, double& twoH,
+                                             double& scale) {
+    rhs64(K, r, th, pr, pth, dr, dth, dph, dpr, dpth, twoH, scale);
   }
 };
 struct QMetric {
@@ -305,143 +310,154 @@ struct QMetric {
   static constexpr int kMaxRegs = 255;
   static __device__ __forceinline__ void rhs(const RayK& K, double r, double th, double pr,
                                              double pth, double& dr, double& dth, double& dph,
-                                             double& dpr, double& dpth, double& twoH) {
-    rhs_q64(K, r, th, pr, pth, dr, dth, dph, dpr, dpth, twoH);
+                                             double& dpr, double& dpth, double& twoH,
+                                             double& scale) {
+    rhs_q64(K, r, th, pr, pth, dr, dth, dph, dpr, dpth, twoH, scale);
   }
 };
+
+// One evaluation of Hamilton's equations in scaled form: the derivative of
+// the evolved components (r, theta, phi, p_r, p_theta) is scale * (r, th, ph,
+// pr, pth); twoH = 2H at the evaluation point.
+struct Deriv {
+  double r, th, ph, pr, pth;
+  double scale, twoH;
+};
+
+template <class Met = KerrMetric>
+__device__ __forceinline__ void rhs64_at(const RayK& K, double r, double th, double pr,
+                                         double pth, Deriv& k) {
+  Met::rhs(K, r, th, pr, pth, k.r, k.th, k.ph, k.pr, k.pth, k.twoH, k.scale);
+}
+
+template <class Met = KerrMetric>
+__device__ __forceinline__ void rhs64_at(const RayK& K, const State& y, Deriv& k) {
+  rhs64_at<Met>(K, y.r, y.th, y.pr, y.pth, k);
+}
 
 // 2H at a state (used once per ray for the terminal point).
 template <class Met = KerrMetric>
 __device__ __forceinline__ double twoH64(const RayK& K, const State& y) {
-  double a0, a1, a2, a3, a4, h2;
-  Met::rhs(K, y.r, y.th, y.pr, y.pth, a0, a1, a2, a3, a4, h2);
-  return h2;
+  Deriv k;
+  rhs64_at<Met>(K, y, k);
+  return k.twoH;
 }
 
-// One Cash-Karp attempt of length h from y (FP64 everywhere): o = fifth-order
-// result, d = fifth minus fourth order. phi is cyclic, so its stage values
-// are never needed; only its increment is accumulated.
+// Embedded Runge-Kutta attempt of length h from y with the tableau T (FP64
+// everywhere): o = fifth-order result, d = fifth minus fourth order. The
+// stage derivative k_j = scale_j * k~_j enters every sum through the
+// coefficient T.a[s][j] * (h scale_j), so the evaluations never multiply their
+// outputs by 1/Sigma; the stage inputs and o are accumulated directly onto y
+// (a few ulp of |y| per step, far below the truncation error at any usable
+// tolerance). phi is cyclic: its stage values are never needed, only its
+// increment. With FSAL the last stage is evaluated at o itself and k[NS - 1]
+// is the first stage of the next step.
+template <int NS>
+struct Tableau64 {
+  double a[NS][NS];  // a[s][j], j < s
+  double b[NS];      // fifth-order weights
+  double e[NS];      // fifth minus embedded fourth order
+};
+
+// Stages 1 .. NS-1 (stage 0, k[0], is given), o and d. FSAL: the last
+// stage is evaluated at o.
+template <class Met, int NS, bool FSAL>
+__device__ __forceinline__ void rk_attempt64(const Tableau64<NS>& T, const RayK& K,
+                                             const State& y, double h, Deriv (&k)[NS],
+                                             State& o, State& d) {
+  double w[NS];
+  w[0] = h * k[0].scale;
+  constexpr int NI = FSAL ? NS - 1 : NS;  // stages whose input is a stage sum
+#pragma unroll
+  for (int s = 1; s < NI; ++s) {
+    double ir = y.r, it = y.th, ip = y.pr, iq = y.pth;
+#pragma unroll
+    for (int j = 0; j < s; ++j) {
+      if (T.a[s][j] != 0.0) {
+        const double c = T.a[s][j] * w[j];
+        ir = fma(c, k[j].r, ir);
+        it = fma(c, k[j].th, it);
+        ip = fma(c, k[j].pr, ip);
+        iq = fma(c, k[j].pth, iq);
+      }
+    }
+    rhs64_at<Met>(K, ir, it, ip, iq, k[s]);
+    w[s] = h * k[s].scale;
+  }
+  o = y;
+#pragma unroll
+  for (int j = 0; j < NI; ++j) {
+    if (T.b[j] != 0.0) {
+      const double c = T.b[j] * w[j];
+      o.r = fma(c, k[j].r, o.r);
+      o.th = fma(c, k[j].th, o.th);
+      o.ph = fma(c, k[j].ph, o.ph);
+      o.pr = fma(c, k[j].pr, o.pr);
+      o.pth = fma(c, k[j].pth, o.pth);
+    }
+  }
+  if (FSAL) {
+    rhs64_at<Met>(K, o, k[NS - 1]);
+    w[NS - 1] = h * k[NS - 1].scale;
+  }
+  const double c0 = T.e[0] * w[0];
+  d.r = c0 * k[0].r;
+  d.th = c0 * k[0].th;
+  d.ph = c0 * k[0].ph;
+  d.pr = c0 * k[0].pr;
+  d.pth = c0 * k[0].pth;
+#pragma unroll
+  for (int j = 1; j < NS; ++j) {
+    if (T.e[j] != 0.0) {
+      const double c = T.e[j] * w[j];
+      d.r = fma(c, k[j].r, d.r);
+      d.th = fma(c, k[j].th, d.th);
+      d.ph = fma(c, k[j].ph, d.ph);
+      d.pr = fma(c, k[j].pr, d.pr);
+      d.pth = fma(c, k[j].pth, d.pth);
+    }
+  }
+}
+
+// One Cash-Karp attempt of length h from y (Sec. 3.1, RKCK45).
 template <class Met = KerrMetric>
 __device__ __forceinline__ void ck_step64(const RayK& K, const State& y, double h, State& o,
                                           State& d, double& twoH) {
-  using namespace ck;
-  double k1r, k1t, k1p, k1pr, k1pt;
-  Met::rhs(K, y.r, y.th, y.pr, y.pth, k1r, k1t, k1p, k1pr, k1pt, twoH);
-  double k2r, k2t, k2p, k2pr, k2pt, hd;
-  Met::rhs(K, fma(h, A21 * k1r, y.r), fma(h, A21 * k1t, y.th), fma(h, A21 * k1pr, y.pr),
-        fma(h, A21 * k1pt, y.pth), k2r, k2t, k2p, k2pr, k2pt, hd);
-#define OSIRIS_S3(c) fma(h, fma(A32, k2##c, A31 * k1##c), y_##c)
-  double k3r, k3t, k3p, k3pr, k3pt;
-  {
-    const double y_r = y.r, y_t = y.th, y_pr = y.pr, y_pt = y.pth;
-    Met::rhs(K, OSIRIS_S3(r), OSIRIS_S3(t), OSIRIS_S3(pr), OSIRIS_S3(pt), k3r, k3t, k3p, k3pr, k3pt,
-          hd);
-  }
-#undef OSIRIS_S3
-#define OSIRIS_S4(c) fma(h, fma(A43, k3##c, fma(A42, k2##c, A41 * k1##c)), y_##c)
-  double k4r, k4t, k4p, k4pr, k4pt;
-  {
-    const double y_r = y.r, y_t = y.th, y_pr = y.pr, y_pt = y.pth;
-    Met::rhs(K, OSIRIS_S4(r), OSIRIS_S4(t), OSIRIS_S4(pr), OSIRIS_S4(pt), k4r, k4t, k4p, k4pr, k4pt,
-          hd);
-  }
-#undef OSIRIS_S4
-#define OSIRIS_S5(c) \
-  fma(h, fma(A54, k4##c, fma(A53, k3##c, fma(A52, k2##c, A51 * k1##c))), y_##c)
-  double k5r, k5t, k5p, k5pr, k5pt;
-  {
-    const double y_r = y.r, y_t = y.th, y_pr = y.pr, y_pt = y.pth;
-    Met::rhs(K, OSIRIS_S5(r), OSIRIS_S5(t), OSIRIS_S5(pr), OSIRIS_S5(pt), k5r, k5t, k5p, k5pr, k5pt,
-          hd);
-  }
-#undef OSIRIS_S5
-#define OSIRIS_S6(c) \
-  fma(h, fma(A65, k5##c, fma(A64, k4##c, fma(A63, k3##c, fma(A62, k2##c, A61 * k1##c)))), y_##c)
-  double k6r, k6t, k6p, k6pr, k6pt;
-  {
-    const double y_r = y.r, y_t = y.th, y_pr = y.pr, y_pt = y.pth;
-    Met::rhs(K, OSIRIS_S6(r), OSIRIS_S6(t), OSIRIS_S6(pr), OSIRIS_S6(pt), k6r, k6t, k6p, k6pr, k6pt,
-          hd);
-  }
-#undef OSIRIS_S6
-#define OSIRIS_Y5(c) fma(B6, k6##c, fma(B4, k4##c, fma(B3, k3##c, B1 * k1##c)))
-#define OSIRIS_DL(c) fma(D6, k6##c, fma(D5, k5##c, fma(D4, k4##c, fma(D3, k3##c, D1 * k1##c))))
-  o.r = fma(h, OSIRIS_Y5(r), y.r);
-  o.th = fma(h, OSIRIS_Y5(t), y.th);
-  o.ph = fma(h, OSIRIS_Y5(p), y.ph);
-  o.pr = fma(h, OSIRIS_Y5(pr), y.pr);
-  o.pth = fma(h, OSIRIS_Y5(pt), y.pth);
-  d.r = h * OSIRIS_DL(r);
-  d.th = h * OSIRIS_DL(t);
-  d.ph = h * OSIRIS_DL(p);
-  d.pr = h * OSIRIS_DL(pr);
-  d.pth = h * OSIRIS_DL(pt);
-#undef OSIRIS_Y5
-#undef OSIRIS_DL
+  constexpr Tableau64<6> T = {
+      {{0, 0, 0, 0, 0, 0},
+       {ck::A21, 0, 0, 0, 0, 0},
+       {ck::A31, ck::A32, 0, 0, 0, 0},
+       {ck::A41, ck::A42, ck::A43, 0, 0, 0},
+       {ck::A51, ck::A52, ck::A53, ck::A54, 0, 0},
+       {ck::A61, ck::A62, ck::A63, ck::A64, ck::A65, 0}},
+      {ck::B1, 0, ck::B3, ck::B4, 0, ck::B6},
+      {ck::D1, 0, ck::D3, ck::D4, ck::D5, ck::D6}};
+  Deriv k[6];
+  rhs64_at<Met>(K, y, k[0]);
+  twoH = k[0].twoH;
+  rk_attempt64<Met, 6, false>(T, K, y, h, k, o, d);
 }
 
-// Derivative vector of the evolved components (r, theta, phi, p_r, p_theta)
-// and 2H at the point where it was evaluated.
-struct Deriv {
-  double r, th, ph, pr, pth, twoH;
-};
-
-template <class Met = KerrMetric>
-__device__ __forceinline__ void rhs64_at(const RayK& K, const State& y, Deriv& k) {
-  Met::rhs(K, y.r, y.th, y.pr, y.pth, k.r, k.th, k.ph, k.pr, k.pth, k.twoH);
-}
-
-// One Dormand-Prince attempt of length h from y given k1 = f(y): o = fifth-
-// order result, d = fifth minus fourth order, k7 = f(o) (the first stage of
-// the next step if this one is accepted). Six new evaluations.
+// One Dormand-Prince attempt of length h from y given k1 = f(y) (Sec. 3.1,
+// RKDP45): six new evaluations; k7 = f(o) is the first stage of the next
+// step if this one is accepted.
 template <class Met = KerrMetric>
 __device__ __forceinline__ void dp_step64(const RayK& K, const State& y, double h,
                                           const Deriv& k1, State& o, State& d, Deriv& k7) {
-  using namespace dp;
-  double hd;
-  double k2r, k2t, k2p, k2pr, k2pt;
-  Met::rhs(K, fma(h, A21 * k1.r, y.r), fma(h, A21 * k1.th, y.th), fma(h, A21 * k1.pr, y.pr),
-        fma(h, A21 * k1.pth, y.pth), k2r, k2t, k2p, k2pr, k2pt, hd);
-#define DP_S3(a, b, y0) fma(h, fma(A32, b, A31 * a), y0)
-  double k3r, k3t, k3p, k3pr, k3pt;
-  Met::rhs(K, DP_S3(k1.r, k2r, y.r), DP_S3(k1.th, k2t, y.th), DP_S3(k1.pr, k2pr, y.pr),
-        DP_S3(k1.pth, k2pt, y.pth), k3r, k3t, k3p, k3pr, k3pt, hd);
-#undef DP_S3
-#define DP_S4(a, b, c, y0) fma(h, fma(A43, c, fma(A42, b, A41 * a)), y0)
-  double k4r, k4t, k4p, k4pr, k4pt;
-  Met::rhs(K, DP_S4(k1.r, k2r, k3r, y.r), DP_S4(k1.th, k2t, k3t, y.th),
-        DP_S4(k1.pr, k2pr, k3pr, y.pr), DP_S4(k1.pth, k2pt, k3pt, y.pth), k4r, k4t, k4p, k4pr,
-        k4pt, hd);
-#undef DP_S4
-#define DP_S5(a, b, c, e, y0) fma(h, fma(A54, e, fma(A53, c, fma(A52, b, A51 * a))), y0)
-  double k5r, k5t, k5p, k5pr, k5pt;
-  Met::rhs(K, DP_S5(k1.r, k2r, k3r, k4r, y.r), DP_S5(k1.th, k2t, k3t, k4t, y.th),
-        DP_S5(k1.pr, k2pr, k3pr, k4pr, y.pr), DP_S5(k1.pth, k2pt, k3pt, k4pt, y.pth), k5r, k5t,
-        k5p, k5pr, k5pt, hd);
-#undef DP_S5
-#define DP_S6(a, b, c, e, f, y0) \
-  fma(h, fma(A65, f, fma(A64, e, fma(A63, c, fma(A62, b, A61 * a)))), y0)
-  double k6r, k6t, k6p, k6pr, k6pt;
-  Met::rhs(K, DP_S6(k1.r, k2r, k3r, k4r, k5r, y.r), DP_S6(k1.th, k2t, k3t, k4t, k5t, y.th),
-        DP_S6(k1.pr, k2pr, k3pr, k4pr, k5pr, y.pr),
-        DP_S6(k1.pth, k2pt, k3pt, k4pt, k5pt, y.pth), k6r, k6t, k6p, k6pr, k6pt, hd);
-#undef DP_S6
-#define DP_Y5(a, c, e, f, g) fma(B6, g, fma(B5, f, fma(B4, e, fma(B3, c, B1 * a))))
-  o.r = fma(h, DP_Y5(k1.r, k3r, k4r, k5r, k6r), y.r);
-  o.th = fma(h, DP_Y5(k1.th, k3t, k4t, k5t, k6t), y.th);
-  o.ph = fma(h, DP_Y5(k1.ph, k3p, k4p, k5p, k6p), y.ph);
-  o.pr = fma(h, DP_Y5(k1.pr, k3pr, k4pr, k5pr, k6pr), y.pr);
-  o.pth = fma(h, DP_Y5(k1.pth, k3pt, k4pt, k5pt, k6pt), y.pth);
-#undef DP_Y5
-  rhs64_at<Met>(K, o, k7);
-#define DP_DL(a, c, e, f, g, z) \
-  fma(D7, z, fma(D6, g, fma(D5, f, fma(D4, e, fma(D3, c, D1 * a)))))
-  d.r = h * DP_DL(k1.r, k3r, k4r, k5r, k6r, k7.r);
-  d.th = h * DP_DL(k1.th, k3t, k4t, k5t, k6t, k7.th);
-  d.ph = h * DP_DL(k1.ph, k3p, k4p, k5p, k6p, k7.ph);
-  d.pr = h * DP_DL(k1.pr, k3pr, k4pr, k5pr, k6pr, k7.pr);
-  d.pth = h * DP_DL(k1.pth, k3pt, k4pt, k5pt, k6pt, k7.pth);
-#undef DP_DL
+  constexpr Tableau64<7> T = {
+      {{0, 0, 0, 0, 0, 0, 0},
+       {dp::A21, 0, 0, 0, 0, 0, 0},
+       {dp::A31, dp::A32, 0, 0, 0, 0, 0},
+       {dp::A41, dp::A42, dp::A43, 0, 0, 0, 0},
+       {dp::A51, dp::A52, dp::A53, dp::A54, 0, 0, 0},
+       {dp::A61, dp::A62, dp::A63, dp::A64, dp::A65, 0, 0},
+       {0, 0, 0, 0, 0, 0, 0}},  // the seventh stage is evaluated at o
+      {dp::B1, 0, dp::B3, dp::B4, dp::B5, dp::B6, 0},
+      {dp::D1, 0, dp::D3, dp::D4, dp::D5, dp::D6, dp::D7}};
+  Deriv k[7];
+  k[0] = k1;
+  rk_attempt64<Met, 7, true>(T, K, y, h, k, o, d);
+  k7 = k[6];
 }
 
 // True when x is +-inf or NaN (exponent bits all set); integer test only.
