@@ -219,17 +219,20 @@ __device__ __forceinline__ void rhs64(const RayK& K, double r, double th, double
                                       double& dpth, double& twoH, double& scale) {
   double s, c;
   sincos_tab(th, s, c);
-  const double r2 = r * r;
+  const double ra2 = fma(r, r, K.a2);  // r^2 + a^2
+  const double a2s = K.a2 * s;
   const double Delta = fma(r, r - 2.0, K.a2);
-  const double Sigma = fma(K.a2 * c, c, r2);
-  const double P = fma(fma(r, r, K.a2), K.E, -K.aL);
+  // Sigma = r^2 + a^2 cos^2 = (r^2 + a^2) - a^2 sin^2 (no cancellation: r > a)
+  const double Sigma = fma(-a2s, s, ra2);
+  const double P = fma(ra2, K.E, -K.aL);
   const double DS = Delta * Sigma;
   const double inv = rcp64(DS * s);
   const double sinv = s * inv;  // 1 / (Delta Sigma)
   const double iSig = Delta * sinv;
   const double iDel = Sigma * sinv;
   const double is = DS * inv;
-  const double W = fma(K.L, is, -K.aE * s);
+  const double Lis = K.L * is;  // L / sin
+  const double W = fma(-K.aE, s, Lis);
   const double u = P * iDel;
   const double Dpr = Delta * pr;
   const double N = fma(Dpr, pr, fma(pth, pth, fma(W, W, -P * u)));
@@ -239,8 +242,10 @@ __device__ __forceinline__ void rhs64(const RayK& K, double r, double th, double
   dr = Dpr;
   dth = pth;
   dph = fma(W, is, K.a * u);
-  dpr = fma(1.0 - r, fma(u, u, pr * pr), fma(r, NiS, (r * K.E2) * u));
-  dpth = c * fma(W, fma(K.L, is * is, K.aE), -(K.a2 * s) * NiS);
+  // -dH/dr: (1 - r)(u^2 + p_r^2) + r (2H + 2E u)
+  dpr = fma(r, fma(K.E2, u, NiS), (1.0 - r) * fma(u, u, pr * pr));
+  // -dH/dtheta: cos (W (L / sin^2 + a E) - a^2 sin 2H)
+  dpth = c * fma(W, fma(Lis, is, K.aE), -a2s * NiS);
   scale = iSig;
   twoH = NiS;
 }
