@@ -242,8 +242,9 @@ __device__ __forceinline__ void rhs64(const RayK& K, double r, double th, double
   dr = Dpr;
   dth = pth;
   dph = fma(W, is, K.a * u);
-  // -dH/dr: (1 - r)(u^2 + p_r^2) + r (2H + 2E u)
-  dpr = fma(r, fma(K.E2, u, NiS), (1.0 - r) * fma(u, u, pr * pr));
+  // -dH/dr: (1 - r) Y + r X = Y + r (X - Y), Y = u^2 + p_r^2, X = 2H + 2E u
+  const double Y = fma(u, u, pr * pr);
+  dpr = fma(r, fma(K.E2, u, NiS) - Y, Y);
   // -dH/dtheta: cos (W (L / sin^2 + a E) - a^2 sin 2H)
   dpth = c * fma(W, fma(Lis, is, K.aE), -a2s * NiS);
   scale = iSig;
