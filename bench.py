@@ -43,9 +43,9 @@ F_STEP = 258
 SHADOW_BYTES_PER_RAY = 42
 ORACLE_SAMPLE_STRIDE = 128  # CPU baseline: every 128th pixel of each render
 # DRAM bytes (read + write) of one FP64 trace launch over the 1024^2 set: ncu
-# capture of the same kernel at 512^2 (2.51 MB read + 89.00 MB written), scaled
+# capture of the same kernel at 512^2 (2.62 MB read + 90.56 MB written), scaled
 # by the 4x rays (profiles/trace_fp64_persistent_kerr12x512_dram.md).
-FP64_TRAFFIC_BYTES_PER_LAUNCH = 366.0e6
+FP64_TRAFFIC_BYTES_PER_LAUNCH = 372.7e6
 
 
 def parse():
