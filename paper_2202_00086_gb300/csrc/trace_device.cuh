@@ -212,7 +212,12 @@ __device__ __forceinline__ double rcp64(double d) {
 //   p_theta' =  cos [ W (L / sin^2 + a E) - a^2 sin N / Sigma ] / Sigma
 // which are the component equations of Sec. 2.1 after the common factors
 // are collected. One reciprocal of Delta Sigma sin(theta) yields all three
-// reciprocals. twoH receives 2H = N / Sigma at the evaluation point.
+// reciprocals. The outputs are the bracketed terms (the derivatives times
+// Sigma) and scale = 1 / Sigma, which the stepper folds into its tableau
+// coefficients; products are shared where the algebra allows (Sigma from
+// r^2 + a^2 - a^2 sin^2, p_r' as Y + r (X - Y) with X = 2H + 2 E u and
+// Y = p_r^2 + u^2, L / sin reused). twoH receives 2H = N / Sigma at the
+// evaluation point.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void rhs64(const RayK& K, double r, double th, double pr, double pth,
                                       double& dr, double& dth, double& dph, double& dpr,
