@@ -89,16 +89,18 @@ __device__ __forceinline__ void rhs_df(const RayDF& K, df r, df th, df pr, df pt
   // are renormalised at the end.
   df s, c;
   df_sincos(th, s, c);
-  const df r2 = df_sqr(r);
+  const df ra2 = df_add_u(df_sqr(r), K.a2);  // r^2 + a^2
+  const df a2s = df_mul(K.a2, s);
   const df Delta = df_add_u(df_mul(r, df_add_f(r, -2.0f)), K.a2);
-  const df Sigma = df_add_u(r2, df_mul(K.a2, df_sqr(c)));
-  const df P = df_sub_u(df_mul(df_add_u(r2, K.a2), K.E), K.aL);
+  const df Sigma = df_sub_u(ra2, df_mul(a2s, s));  // r^2 + a^2 cos^2 (r > a: no cancellation)
+  const df P = df_sub_u(df_mul(ra2, K.E), K.aL);
   const df DS = df_mul(Delta, Sigma);
   const df inv = df_rcp(df_mul(DS, s));
   const df iSig = df_mul(df_mul(Delta, s), inv);
   const df iDel = df_mul(df_mul(Sigma, s), inv);
   const df is = df_mul(DS, inv);
-  const df W = df_sub_u(df_mul(K.L, is), df_mul(K.aE, s));
+  const df Lis = df_mul(K.L, is);  // L / sin
+  const df W = df_sub_u(Lis, df_mul(K.aE, s));
   const df u = df_mul(P, iDel);
   const df Dpr = df_mul(Delta, pr);
   const df N =
@@ -107,11 +109,12 @@ __device__ __forceinline__ void rhs_df(const RayDF& K, df r, df th, df pr, df pt
   dr = df_norm(df_mul(Dpr, iSig));
   dth = df_norm(df_mul(pth, iSig));
   dph = df_norm(df_mul(df_add_u(df_mul(W, is), df_mul(K.a, u)), iSig));
-  const df t1 = df_add_u(df_mul(r, NiS), df_mul(df_mul(r, K.twoE), u));
-  const df t2 = df_mul(df_add_f(r, -1.0f), df_add_u(df_sqr(u), df_sqr(pr)));
-  dpr = df_norm(df_mul(iSig, df_sub_u(t1, t2)));
-  const df t3 = df_mul(W, df_add_u(df_mul(K.L, df_sqr(is)), K.aE));
-  const df t4 = df_mul(df_mul(K.a2, s), NiS);
+  // p_r' Sigma = (1 - r) Y + r X = Y + r (X - Y), Y = u^2 + p_r^2, X = 2H + 2 E u
+  const df Y = df_add_u(df_sqr(u), df_sqr(pr));
+  const df X = df_add_u(NiS, df_mul(K.twoE, u));
+  dpr = df_norm(df_mul(iSig, df_add_u(Y, df_mul(r, df_sub_u(X, Y)))));
+  const df t3 = df_mul(W, df_add_u(df_mul(Lis, is), K.aE));
+  const df t4 = df_mul(a2s, NiS);
   dpth = df_norm(df_mul(df_mul(c, iSig), df_sub_u(t3, t4)));
   twoH = NiS.hi + NiS.lo;
 }
