@@ -96,8 +96,9 @@ __device__ __forceinline__ void rhs_df(const RayDF& K, df r, df th, df pr, df pt
   const df P = df_sub_u(df_mul(ra2, K.E), K.aL);
   const df DS = df_mul(Delta, Sigma);
   const df inv = df_rcp(df_mul(DS, s));
-  const df iSig = df_mul(df_mul(Delta, s), inv);
-  const df iDel = df_mul(df_mul(Sigma, s), inv);
+  const df sinv = df_mul(s, inv);  // 1 / (Delta Sigma)
+  const df iSig = df_mul(Delta, sinv);
+  const df iDel = df_mul(Sigma, sinv);
   const df is = df_mul(DS, inv);
   const df Lis = df_mul(K.L, is);  // L / sin
   const df W = df_sub_u(Lis, df_mul(K.aE, s));
