@@ -1,0 +1,64 @@
+"""The JSON line bench.py prints: every key the benchmark contract asks for,
+with the right types, for the reference arm (the CPU oracle, runs anywhere)
+and for the GPU arm (a small render set, marked gpu)."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+COMMON = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+          "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "e2e",
+          "cpu_baseline")
+
+
+def _run(*args):
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], cwd=ROOT,
+                       capture_output=True, text=True, timeout=900)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, p.stdout
+    return json.loads(lines[0])
+
+
+def _check_common(d, steps, warmup):
+    for k in COMMON:
+        assert k in d, k
+    assert d["value"] > 0 and d["unit"] == "rays/s" and d["higher_is_better"] is True
+    assert d["n_gpus"] == 1 and d["steps"] == steps and d["warmup"] == warmup
+    assert d["scaling"] == "weak" and d["data"] == "synthetic" and d["dtype"] == "f64"
+    assert d["vs_baseline"] is None  # the paper publishes no number for this workload
+    assert isinstance(d["config"]["workload"], str) and d["config"]["workload"]
+    e = d["e2e"]
+    assert e["value"] > 0 and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] >= 0 and e["d2h_bytes_per_step"] >= 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] > 0 and cb["sample"]
+
+
+def test_reference_arm_line():
+    d = _run("--impl", "reference", "--side", "128", "--steps", "1", "--warmup", "1")
+    _check_common(d, 1, 1)
+    assert d["impl"] == "reference"
+    assert d["cpu_baseline"]["value"] == d["value"] == d["e2e"]["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+@pytest.mark.gpu
+def test_gpu_arm_line():
+    d = _run("--side", "64", "--steps", "1", "--warmup", "3", "--serve-seconds", "0.5")
+    _check_common(d, 1, 3)
+    assert "impl" not in d or d["impl"] != "reference"
+    r = d["roofline"]
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["peak"] > 0
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], rel=1e-9)
+    assert "traffic" in r
+    c = d["clocks"]
+    assert c["sm_max_mhz"] > 0 and isinstance(c["reasons"], list)
+    assert d["gpu_launches"] == 1  # one batched launch per timed step
+    assert d["e2e"]["api"] == "osiris_batch_plan_launch"
+    assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
+    assert d["variants"]["df64"]["value"] > 0
+    assert d["serving"]["continuous_batching_df64"]["p99_latency_s"] > 0
