@@ -379,7 +379,12 @@ int osiris_trace_batch(const osiris_request* reqs, int32_t n, const osiris_trace
   if (!reqs || n < 1 || n > 65536) return OSIRIS_EINVAL;
   if (int rc = check_opts(o)) return rc;
   if (!o->workspace || o->workspace_bytes < osiris_workspace_bytes(n)) return OSIRIS_ENOMEM;
-  std::vector<ReqDev> table(static_cast<size_t>(n));
+  std::vector<ReqDev> table;
+  try {
+    table.resize(static_cast<size_t>(n));
+  } catch (...) {  // no exception crosses the C interface
+    return OSIRIS_ENOMEM;
+  }
   int64_t begin = 0;
   if (int rc = build_table(reqs, n, o, table.data(), &begin)) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -635,7 +640,12 @@ int record_plan(osiris_batch_plan* p) {
 
   size_t count = 0;
   if (cudaGraphGetNodes(g, nullptr, &count) != cudaSuccess) return OSIRIS_ECUDA;
-  std::vector<cudaGraphNode_t> nodes(count);
+  std::vector<cudaGraphNode_t> nodes;
+  try {
+    nodes.resize(count);
+  } catch (...) {
+    return OSIRIS_ENOMEM;
+  }
   if (count == 0 || cudaGraphGetNodes(g, nodes.data(), &count) != cudaSuccess)
     return OSIRIS_ECUDA;
   for (cudaGraphNode_t n : nodes) {
