@@ -301,6 +301,25 @@ __device__ __forceinline__ void rhs_q64(const RayK& K, double r, double th, doub
   dpth = -0.5 * fma(K.kap * LXth, fma(grr, pr2, gthth * pth2), -2.0 * (c / s) * gpp * L2);
 }
 
+// 2H = N / Sigma in Kerr, in FP64, without the derivatives and without the
+// block's sine table (library sincos, correctly rounded reciprocal): usable
+// from kernels that do not fill the table (the double-float and mixed
+// kernels check |H| at a ray's end point with it).
+__device__ __forceinline__ double twoH_kerr_direct(const RayK& K, const State& y) {
+  double s, c;
+  sincos(y.th, &s, &c);
+  const double Delta = fma(y.r, y.r - 2.0, K.a2);
+  const double Sigma = fma(K.a2 * c, c, y.r * y.r);
+  const double P = fma(fma(y.r, y.r, K.a2), K.E, -K.aL);
+  const double DS = Delta * Sigma;
+  const double inv = __drcp_rn(DS * s);
+  const double iSig = (Delta * s) * inv;
+  const double iDel = (Sigma * s) * inv;
+  const double W = fma(K.L, DS * inv, -K.aE * s);
+  const double N = fma(Delta * y.pr, y.pr, fma(y.pth, y.pth, fma(W, W, -P * (P * iDel))));
+  return N * iSig;
+}
+
 // Metric policies for the FP64 steppers.
 struct KerrMetric {
   static constexpr bool kTrigTable = true;  // rhs64 reads the block's sincos table

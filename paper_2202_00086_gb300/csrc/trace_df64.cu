@@ -28,6 +28,7 @@ namespace osiris_impl {
 
 struct RayDF {
   df a, a2, aE, aL, E, L, twoE;
+  float twoH0;  // 2 H0 on the mass shell: 0 for light, -1 for unit-mass particles
 };
 
 __device__ __forceinline__ RayDF to_df(const RayK& K) {
@@ -39,6 +40,7 @@ __device__ __forceinline__ RayDF to_df(const RayK& K) {
   k.E = df_from_double(K.E);
   k.L = df_from_double(K.L);
   k.twoE = df_scale(k.E, 2.0f);
+  k.twoH0 = 0.0f;
   return k;
 }
 
@@ -117,7 +119,9 @@ __device__ __forceinline__ void rhs_df(const RayDF& K, df r, df th, df pr, df pt
   const df t3 = df_mul(W, df_add_u(df_mul(Lis, is), K.aE));
   const df t4 = df_mul(a2s, NiS);
   dpth = df_norm(df_mul(df_mul(c, iSig), df_sub_u(t3, t4)));
-  twoH = NiS.hi + NiS.lo;
+  // 2 (H - H0): the leading word minus 2 H0 is exact (both are close or 2 H0
+  // is 0), so the deviation keeps double-float precision on the mass shell.
+  twoH = __fadd_rn(__fsub_rn(NiS.hi, K.twoH0), NiS.lo);
 }
 
 // Tableaus for the df64 stepper, [integrator][stage]; stage s = 0..6 is the
@@ -348,6 +352,7 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
     LC.reset();
     y = to_df(y0);
     KD = to_df(I.K);
+    KD.twoH0 = (float)(2.0 * I.H0);
     r_cap = df_from_double(I.r_cap);
     r_esc = df_from_double(I.r_esc);
     tol = (float)I.tol;
@@ -361,7 +366,7 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
     const State f = to_double(fd);
     double mh = (double)max_abs_H;
     if (status != OSIRIS_STATUS_ERROR) {
-      mh = fmax(mh, fabs(0.5 * twoH64(I.K, f) - I.H0));
+      mh = fmax(mh, fabs(0.5 * twoH_kerr_direct(I.K, f) - I.H0));
       S.rhs += 1;
     }
     write_outputs(A, I, status, f, mh, n_acc, n_rej, S);
@@ -431,7 +436,7 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
     S.rhs += 6;
 
     if (mode == MODE_INTEGRATE) {
-      max_abs_H = fmaxf(max_abs_H, fabsf(0.5f * twoH - (float)I.H0));
+      max_abs_H = fmaxf(max_abs_H, fabsf(0.5f * twoH));  // twoH is 2 (H - H0) here
       const float ys[5] = {y.r.hi, y.th.hi, y.ph.hi, y.pr.hi, y.pth.hi};
       const float os[5] = {o.r.hi, o.th.hi, o.ph.hi, o.pr.hi, o.pth.hi};
       bool bad = false, ok = true;

@@ -45,23 +45,6 @@ __device__ __forceinline__ void rhs32(const RayK32& K, float r, float th, float 
   dpth = (c * iSig) * fmaf(W, fmaf(K.L, is * is, K.aE), -(K.a2 * s) * NiS);
 }
 
-// 2H = N / Sigma in FP64 without the derivatives.
-__device__ __forceinline__ double twoH_value64(const RayK& K, const State& y) {
-  double s, c;
-  sincos(y.th, &s, &c);
-  const double r2 = y.r * y.r;
-  const double Delta = fma(y.r, y.r - 2.0, K.a2);
-  const double Sigma = fma(K.a2 * c, c, r2);
-  const double P = fma(fma(y.r, y.r, K.a2), K.E, -K.aL);
-  const double DS = Delta * Sigma;
-  const double inv = __drcp_rn(DS * s);
-  const double iSig = (Delta * s) * inv;
-  const double iDel = (Sigma * s) * inv;
-  const double W = fma(K.L, DS * inv, -K.aE * s);
-  const double N = fma(Delta * y.pr, y.pr, fma(y.pth, y.pth, fma(W, W, -P * (P * iDel))));
-  return N * iSig;
-}
-
 struct StepperMixed {
   // FP32 stage values put ~1e-7 relative noise on a trial step's end point;
   // a bracket narrower than that cannot be resolved further
@@ -130,11 +113,11 @@ struct StepperMixed {
     d.pth = (double)DLT(pt);
 #undef INC
 #undef DLT
-    twoH = twoH_value64(K, y);
+    twoH = twoH_kerr_direct(K, y);
     return false;
   }
   static __device__ __forceinline__ double twoH(const RayK& K, const State& y) {
-    return twoH_value64(K, y);
+    return twoH_kerr_direct(K, y);
   }
 };
 

@@ -83,3 +83,37 @@ def test_mixed_error_bound(tol):
     print(rep)
     assert_parity(rep)
     assert rep["n_disk"] > 150
+
+
+def test_df64_tracks_H_like_fp64():
+    """The double-float kernel reports the same constraint error as the FP64
+    kernel: per-ray max |H| of a Kerr render (light, H0 = 0), and of unit-mass
+    particles (H0 = -1/2, where |H - H0| ~ 1e-10 sits far below FP32's
+    resolution of H0 itself)."""
+    import math
+    rd = workloads.render(0.998, 1000.0, 60.0, (-8, 8, -8, 8), 40, 40)
+    h64 = gpu_render(rd)["max_abs_H"]
+    hdf = gpu_render(rd, precision=osr.DF64)["max_abs_H"]
+    assert np.all(np.isfinite(hdf)) and np.all(hdf > 0)
+    assert hdf.max() == pytest.approx(h64.max(), rel=0.2)
+    assert 0.9 < np.median(hdf / h64) < 1.1
+    # unit-mass particles launched outwards from r = 30 in Kerr a = 0.9
+    a, r = 0.9, 30.0
+    rng = np.random.default_rng(8)
+    th = rng.uniform(0.4, math.pi - 0.4, 64)
+    E = np.full(64, 1.2)
+    L = rng.uniform(-4.0, 4.0, 64)
+    s2 = np.sin(th) ** 2
+    Sig, Del = r * r + a * a * (1 - s2), r * r - 2 * r + a * a
+    A = (r * r + a * a) ** 2 - a * a * Del * s2
+    gtt, gtp = -A / (Sig * Del), -2 * a * r / (Sig * Del)
+    gpp, grr = (Del - a * a * s2) / (Sig * Del * s2), Del / Sig
+    pr = np.sqrt((-1.0 - (gtt * E * E - 2 * gtp * E * L + gpp * L * L)) / grr)
+    st = np.zeros((64, 6))
+    st[:, 1], st[:, 2], st[:, 4] = r, th, pr
+    args = (torch.tensor(st, device="cuda"), torch.tensor(E, device="cuda"),
+            torch.tensor(L, device="cuda"))
+    res = {p: osr.trace_states(a, 1000.0, *args, mass2=1.0, precision=p)["max_abs_H"]
+           .cpu().numpy() for p in (osr.FP64, osr.DF64)}
+    assert np.all(res[osr.DF64] > 0) and np.all(res[osr.FP64] > 0)
+    assert res[osr.DF64].max() == pytest.approx(res[osr.FP64].max(), rel=0.5)
