@@ -106,7 +106,12 @@ class RenderServer:
 
     # ---- submission and admission ----
     def submit(self, render, arrival=None):
-        """Queue a render (a workloads.render dict). Returns its ServedRender."""
+        """Queue a render (a workloads.render dict). Returns its ServedRender.
+        The server serves Kerr renders (a batched launch holds one space-time);
+        a q-metric render raises ValueError here, not in a later round."""
+        if render.get("q") is not None:
+            raise ValueError("the render server serves Kerr renders; trace q-metric renders "
+                             "with trace() or trace_batch()")
         now = self.clock()
         r = ServedRender(self._next_id, render, now if arrival is None else arrival)
         self._next_id += 1

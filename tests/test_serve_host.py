@@ -108,3 +108,12 @@ def test_summary_percentiles():
     assert abs(s["p50_latency_s"] - 50.5) < 1e-9
     assert abs(s["p99_latency_s"] - 99.01) < 1e-9
     assert s["rays"] == 1000 and abs(s["rays_per_s"] - 10.0) < 1e-12
+
+
+def test_qmetric_render_is_refused_at_submission():
+    import pytest
+    srv, be = _server()
+    rd = workloads.render(0.0, 1000.0, 60.0, (-8, 8, -8, 8), 16, 16, q=0.3)
+    with pytest.raises(ValueError):
+        srv.submit(rd)
+    assert srv.idle() and not be.rounds
