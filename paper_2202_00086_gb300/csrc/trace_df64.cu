@@ -84,7 +84,8 @@ __device__ __forceinline__ bool df_not_finite(float x) {
 }
 
 // Hamilton's equations in the separated form of rhs64 (trace_device.cuh),
-// every operation in df64.
+// every operation in df64. twoH receives 2 (H - H0), the distance from the
+// mass shell, at the evaluation point.
 __device__ __forceinline__ void rhs_df(const RayDF& K, df r, df th, df pr, df pth, df& dr,
                                        df& dth, df& dph, df& dpr, df& dpth, float& twoH) {
   // Intermediate sums are left unrenormalised (df_add_u); the five outputs
@@ -200,7 +201,8 @@ struct LaneCacheDF<OSIRIS_RKDP45> {
 // inputs, the df64 increment sum and the df64 error sum, so no stage value is
 // kept in memory. Dormand-Prince: the seventh stage input is the fifth-order
 // solution itself (formed in df64 exactly as o), its derivative is cached as
-// the next k1, and k1 is evaluated here only when the cache is empty.
+// the next k1, and k1 is evaluated here only when the cache is empty. twoH
+// is 2 (H - H0) at y.
 template <int INTEG>
 __device__ __forceinline__ void rk_step_df(const RayDF& K, LaneCacheDF<INTEG>& LC,
                                            const StateDF& y, df h, StateDF& o, float d[5],
