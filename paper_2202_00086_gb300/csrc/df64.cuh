@@ -85,6 +85,13 @@ __device__ __forceinline__ df df_add_f(df a, float b) {
   return fast_two_sum(s.hi, s.lo);
 }
 
+// df_add_f without the final renormalisation (see df_add_u).
+__device__ __forceinline__ df df_add_f_u(df a, float b) {
+  df s = two_sum(a.hi, b);
+  s.lo = __fadd_rn(s.lo, a.lo);
+  return s;
+}
+
 // Products are left unrenormalised: TwoProd gives |lo| <= ulp(hi)/2 and the
 // cross terms add at most ~2 ulp(hi), so hi + lo is a valid (slightly
 // redundant) df; every df_add renormalises. This keeps a product at 4 FP32

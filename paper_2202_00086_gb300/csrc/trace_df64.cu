@@ -88,8 +88,9 @@ __device__ __forceinline__ bool df_not_finite(float x) {
 // mass shell, at the evaluation point.
 __device__ __forceinline__ void rhs_df(const RayDF& K, df r, df th, df pr, df pth, df& dr,
                                        df& dth, df& dph, df& dpr, df& dpth, float& twoH) {
-  // Intermediate sums are left unrenormalised (df_add_u); the five outputs
-  // are renormalised at the end.
+  // Intermediate sums and the five outputs are left unrenormalised: every
+  // consumer of an output is a product or the renormalising difference
+  // k - k1.
   df s, c;
   df_sincos(th, s, c);
   const df ra2 = df_add_u(df_sqr(r), K.a2);  // r^2 + a^2
@@ -110,16 +111,16 @@ __device__ __forceinline__ void rhs_df(const RayDF& K, df r, df th, df pr, df pt
   const df N =
       df_add_u(df_add_u(df_mul(Dpr, pr), df_sqr(pth)), df_sub_u(df_sqr(W), df_mul(P, u)));
   const df NiS = df_mul(N, iSig);
-  dr = df_norm(df_mul(Dpr, iSig));
-  dth = df_norm(df_mul(pth, iSig));
-  dph = df_norm(df_mul(df_add_u(df_mul(W, is), df_mul(K.a, u)), iSig));
+  dr = df_mul(Dpr, iSig);
+  dth = df_mul(pth, iSig);
+  dph = df_mul(df_add_u(df_mul(W, is), df_mul(K.a, u)), iSig);
   // p_r' Sigma = (1 - r) Y + r X = Y + r (X - Y), Y = u^2 + p_r^2, X = 2H + 2 E u
   const df Y = df_add_u(df_sqr(u), df_sqr(pr));
   const df X = df_add_u(NiS, df_mul(K.twoE, u));
-  dpr = df_norm(df_mul(iSig, df_add_u(Y, df_mul(r, df_sub_u(X, Y)))));
+  dpr = df_mul(iSig, df_add_u(Y, df_mul(r, df_sub_u(X, Y))));
   const df t3 = df_mul(W, df_add_u(df_mul(Lis, is), K.aE));
   const df t4 = df_mul(a2s, NiS);
-  dpth = df_norm(df_mul(df_mul(c, iSig), df_sub_u(t3, t4)));
+  dpth = df_mul(df_mul(c, iSig), df_sub_u(t3, t4));
   // 2 (H - H0): the leading word minus 2 H0 is exact (both are close or 2 H0
   // is 0), so the deviation keeps double-float precision on the mass shell.
   twoH = __fadd_rn(__fsub_rn(NiS.hi, K.twoH0), NiS.lo);
@@ -259,7 +260,7 @@ __device__ __forceinline__ void rk_step_df(const RayDF& K, LaneCacheDF<INTEG>& L
         const int kc = c < 2 ? c : c + 1;  // skip phi in k
         const float fs = s == 2 ? acc[0][c] : s == 3 ? acc[1][c] : s == 4 ? acc[2][c]
                        : s == 5 ? acc[3][c] : 0.0f;
-        in[c] = df_add_f(df_add_u(y4[c], df_mul(hk1[kc], cs)), __fmul_rn(hf, fs));
+        in[c] = df_add_f_u(df_add_u(y4[c], df_mul(hk1[kc], cs)), __fmul_rn(hf, fs));
       }
     }
     df k[5];
