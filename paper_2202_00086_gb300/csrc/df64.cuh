@@ -170,22 +170,24 @@ __device__ __forceinline__ void df_sincos(df x, df& s, df& c) {
   df t = two_sum(a, b.hi);
   t.lo = __fadd_rn(t.lo, fmaf(-k, P3, b.lo));
   t = fast_two_sum(t.hi, t.lo);
+  // The series steps and the results are left unrenormalised: their only
+  // consumers are products and further sums.
   const df u = df_sqr(t);
   const float uf = u.hi;
   // sin t = t (1 - u/3! + u^2/5! - ... ): inner terms in FP32
   float ps = fmaf(uf, fmaf(uf, -I15, I13), -I11);  // -1/11! + u/13! - u^2/15!
-  df qs = df_add_f(mk(I9H, I9L), __fmul_rn(uf, ps));          // 1/9! - u/11! + ...
-  qs = df_add(mk(-I7H, -I7L), df_mul(u, qs));
-  qs = df_add(mk(I5H, I5L), df_mul(u, qs));
-  qs = df_add(mk(-I3H, -I3L), df_mul(u, qs));
-  const df st = df_add(t, df_mul(df_mul(t, u), qs));
+  df qs = df_add_f_u(mk(I9H, I9L), __fmul_rn(uf, ps));          // 1/9! - u/11! + ...
+  qs = df_add_u(mk(-I7H, -I7L), df_mul(u, qs));
+  qs = df_add_u(mk(I5H, I5L), df_mul(u, qs));
+  qs = df_add_u(mk(-I3H, -I3L), df_mul(u, qs));
+  const df st = df_add_u(t, df_mul(df_mul(t, u), qs));
   // cos t = 1 - u/2 + u^2/4! - ...
   float pc = fmaf(uf, fmaf(uf, fmaf(uf, I16, -I14), I12), -I10);  // -1/10! + ...
-  df qc = df_add_f(mk(I8H, I8L), __fmul_rn(uf, pc));
-  qc = df_add(mk(-I6H, -I6L), df_mul(u, qc));
-  qc = df_add(mk(I4H, I4L), df_mul(u, qc));
-  qc = df_add_f(df_mul(u, qc), -0.5f);
-  const df ct = df_add_f(df_mul(u, qc), 1.0f);
+  df qc = df_add_f_u(mk(I8H, I8L), __fmul_rn(uf, pc));
+  qc = df_add_u(mk(-I6H, -I6L), df_mul(u, qc));
+  qc = df_add_u(mk(I4H, I4L), df_mul(u, qc));
+  qc = df_add_f_u(df_mul(u, qc), -0.5f);
+  const df ct = df_add_f_u(df_mul(u, qc), 1.0f);
   // quadrant
   const int q = ((int)k) & 3;
   if (q == 0) {
