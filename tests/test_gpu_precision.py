@@ -54,15 +54,18 @@ def test_df64_max_steps_and_states():
     assert (ref["status"] == osr.STATUS_MAXSTEP).sum() > 0
 
 
-def test_df64_full_size_batch_sampled():
-    """The 12-render 1024^2 Kerr set in one batched launch (the benchmark's
-    configuration), 50 sampled pixels per render checked against the oracle."""
+@pytest.mark.parametrize("precision", [osr.FP64, osr.DF64])
+def test_full_size_batch_sampled(precision):
+    """The 12-render 1024^2 Kerr set in one batched launch, exactly as the
+    benchmark times it (FP64 headline and DF64 variant), 50 sampled pixels per
+    render checked against the oracle."""
     rds = workloads.kerr_shadow_ring_set(1024)
     cams = [osr.Camera.from_render(rd) for rd in rds]
     outs = [osr.alloc_outputs(c.n_rays) for c in cams]
     ws = torch.empty(osr.workspace_bytes(len(cams)), dtype=torch.uint8, device="cuda")
     osr.trace_batch([{"camera": c, "out": o} for c, o in zip(cams, outs)], workspace=ws,
-                    precision=osr.DF64, cell_phase_deg=rds[0]["cell_phase_deg"])
+                    precision=precision, tol=1e-10, cell_deg=rds[0]["cell_deg"],
+                    cell_phase_deg=rds[0]["cell_phase_deg"])
     torch.cuda.synchronize()
     rng = np.random.default_rng(12)
     for rd, o in zip(rds, outs):
