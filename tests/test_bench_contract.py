@@ -38,6 +38,23 @@ def _check_common(d, steps, warmup):
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] > 0 and cb["sample"]
 
 
+def test_clock_summary_flags_throttling():
+    """The clocks object: median SM clock under load, and every throttle
+    reason that was Active in any sample (the contract rejects runs with
+    hw_slowdown, hw_thermal_slowdown or sw_thermal_slowdown)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    idle = "0, 2070, 2070, 245.50, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active"
+    capped = "0, 1905, 2070, 1398.20, 0x0000000000000004, Not Active, Not Active, Not Active, Active"
+    hot = "0, 1500, 2070, 900.00, 0x0000000000000048, Active, Active, Not Active, Not Active"
+    c = bench.summarize_clock_lines([idle, idle, capped, "garbage line", idle])
+    assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0 and c["samples"] == 4
+    assert c["reasons"] == ["sw_power_cap"] and c["power_w_max"] == 1398.2
+    c = bench.summarize_clock_lines([hot, idle, hot])
+    assert c["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"] and c["sm_mhz"] == 1500.0
+    assert bench.summarize_clock_lines([])["reasons"] == ["no samples"]
+
+
 def test_reference_arm_line():
     d = _run("--impl", "reference", "--side", "128", "--steps", "1", "--warmup", "1")
     _check_common(d, 1, 1)
