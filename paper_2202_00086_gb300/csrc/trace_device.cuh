@@ -271,20 +271,25 @@ __device__ __forceinline__ void rhs_q64(const RayK& K, double r, double th, doub
                                         double& dpr, double& dpth, double& twoH, double& scale) {
   scale = 1.0;
   double s, c;
-  sincos(th, &s, &c);
-  const double ir = 1.0 / r;
-  const double f = fma(-2.0, ir, 1.0);
-  const double iD = 1.0 / (r * (r - 2.0));
+  sincos_tab(th, s, c);
+  // four reciprocals (1/D, 1/X, 1/sin^2, 1/(f f^q)) serve every quotient:
+  // 1/r = (r - 2)/D, and f = (r - 2)/r keeps its relative accuracy at r -> 2
+  const double rm2 = r - 2.0;
+  const double iD = rcp64(r * rm2);
+  const double ir = rm2 * iD;
+  const double f = rm2 * ir;
   const double s2 = s * s;
+  const double is2 = rcp64(s2);
   const double X = fma(s2, iD, 1.0);
-  const double iX = 1.0 / X;
+  const double iX = rcp64(X);
   const double fq = exp(K.q * log(f));
   const double Xk = exp(K.kap * log(X));
   const double ir2 = ir * ir;
-  const double gtt = -1.0 / (f * fq);
-  const double grr = f * fq * Xk;
+  const double ffq = f * fq;
+  const double gtt = -rcp64(ffq);
+  const double grr = ffq * Xk;
   const double gthth = fq * Xk * ir2;
-  const double gpp = fq * ir2 / s2;
+  const double gpp = fq * ir2 * is2;
   const double Lf = 2.0 * iD;
   const double LXr = -s2 * (2.0 * r - 2.0) * iD * iD * iX;
   const double LXth = 2.0 * s * c * iD * iX;
@@ -298,7 +303,8 @@ __device__ __forceinline__ void rhs_q64(const RayK& K, double r, double th, doub
   const double dgthth = gthth * fma(K.kap, LXr, fma(K.q, Lf, -2.0 * ir));
   const double dgpp = gpp * fma(K.q, Lf, -2.0 * ir);
   dpr = -0.5 * fma(dgtt, E2, fma(dgrr, pr2, fma(dgthth, pth2, dgpp * L2)));
-  dpth = -0.5 * fma(K.kap * LXth, fma(grr, pr2, gthth * pth2), -2.0 * (c / s) * gpp * L2);
+  // cos / sin = sin cos / sin^2
+  dpth = -0.5 * fma(K.kap * LXth, fma(grr, pr2, gthth * pth2), -2.0 * (c * s * is2) * gpp * L2);
 }
 
 // 2H = N / Sigma in Kerr, in FP64, without the derivatives and without the
@@ -336,7 +342,7 @@ struct KerrMetric {
   }
 };
 struct QMetric {
-  static constexpr bool kTrigTable = false;
+  static constexpr bool kTrigTable = true;  // rhs_q64 reads the block's sincos table
   static constexpr int kMaxRegs = 255;
   static __device__ __forceinline__ void rhs(const RayK& K, double r, double th, double pr,
                                              double pth, double& dr, double& dth, double& dph,
