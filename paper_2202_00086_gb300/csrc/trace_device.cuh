@@ -21,6 +21,7 @@
 
 #include <cstdint>
 
+#include "explog.cuh"
 #include "osiris_internal.h"
 
 namespace osiris_impl {
@@ -129,6 +130,22 @@ __device__ __forceinline__ void trig_table_init() {
     sincos(n, &s, &c);
     t.sc[i] = make_double2(s, c);
     t.n[i] = n;
+  }
+  __syncthreads();
+}
+
+// The block's copy of the exp/log breakpoint tables (explog.cuh), filled by
+// all threads of the block before any divergence.
+__device__ __forceinline__ osiris_explog::Tables& explog_table() {
+  __shared__ osiris_explog::Tables table;
+  return table;
+}
+
+__device__ __forceinline__ void explog_table_init() {
+  osiris_explog::Tables& t = explog_table();
+  for (int i = threadIdx.x; i < osiris_explog::kLogN; i += blockDim.x) {
+    if (i < osiris_explog::kExpN) t.t2[i] = osiris_explog::kT2[i];
+    t.lg[i] = osiris_explog::kLg[i];
   }
   __syncthreads();
 }
@@ -265,6 +282,8 @@ __device__ __forceinline__ void rhs64(const RayK& K, double r, double th, double
 // and each derivative is g^{mu mu} times its logarithmic derivative
 // (d ln f / dr = 2/D, d ln X / dr = -sin^2 (2r - 2) / (D^2 X),
 //  d ln X / dtheta = 2 sin cos / (D X)).
+// The powers f^q and X^k come from the table-driven exp and log of
+// explog.cuh (about a third of the library's FP64 instructions).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void rhs_q64(const RayK& K, double r, double th, double pr,
                                         double pth, double& dr, double& dth, double& dph,
@@ -282,8 +301,9 @@ __device__ __forceinline__ void rhs_q64(const RayK& K, double r, double th, doub
   const double is2 = rcp64(s2);
   const double X = fma(s2, iD, 1.0);
   const double iX = rcp64(X);
-  const double fq = exp(K.q * log(f));
-  const double Xk = exp(K.kap * log(X));
+  const osiris_explog::Tables& T = explog_table();
+  const double fq = osiris_explog::exp_tab(K.q * osiris_explog::log_tab(f, T.lg), T.t2);
+  const double Xk = osiris_explog::exp_tab(K.kap * osiris_explog::log_tab(X, T.lg), T.t2);
   const double ir2 = ir * ir;
   const double ffq = f * fq;
   const double gtt = -rcp64(ffq);
@@ -329,6 +349,7 @@ __device__ __forceinline__ double twoH_kerr_direct(const RayK& K, const State& y
 // Metric policies for the FP64 steppers.
 struct KerrMetric {
   static constexpr bool kTrigTable = true;  // rhs64 reads the block's sincos table
+  static constexpr bool kExpLogTable = false;
   // No register cap (the compiler takes ~200, two blocks of 128 threads per
   // SM): measured on the 12 x 1024^2 Kerr set, 3.09 Mrays/s uncapped against
   // 2.95 at 168 registers (three blocks) and 2.90 at 152 or 128 (three or
@@ -343,6 +364,7 @@ struct KerrMetric {
 };
 struct QMetric {
   static constexpr bool kTrigTable = true;  // rhs_q64 reads the block's sincos table
+  static constexpr bool kExpLogTable = true;  // and the exp/log tables
   static constexpr int kMaxRegs = 255;
   static __device__ __forceinline__ void rhs(const RayK& K, double r, double th, double pr,
                                              double pth, double& dr, double& dth, double& dph,

@@ -13,6 +13,7 @@ template <class Met>
 struct StepperFP64<OSIRIS_RKCK45, Met> {
   static constexpr double kLocateRel = 0.0;
   static constexpr bool kTrigTable = Met::kTrigTable;
+  static constexpr bool kExpLogTable = Met::kExpLogTable;
   struct RayCache {};
   struct LaneCache {};
   static __device__ __forceinline__ void prepare(const RayK&, RayCache&) {}
@@ -36,6 +37,7 @@ template <class Met>
 struct StepperFP64<OSIRIS_RKDP45, Met> {
   static constexpr double kLocateRel = 0.0;
   static constexpr bool kTrigTable = Met::kTrigTable;
+  static constexpr bool kExpLogTable = Met::kExpLogTable;
   struct RayCache {};
   struct LaneCache {
     Deriv k1, k7;

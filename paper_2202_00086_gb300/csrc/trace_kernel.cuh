@@ -161,6 +161,7 @@ template <class Stepper, bool PERSISTENT>
 __device__ __forceinline__ void trace_body(const KernelArgs& A) {
   const unsigned FULL = 0xffffffffu;
   if (Stepper::kTrigTable) trig_table_init();
+  if (Stepper::kExpLogTable) explog_table_init();
 
   int mode = MODE_IDLE;
   bool drained = !PERSISTENT;

@@ -50,6 +50,7 @@ struct StepperMixed {
   // a bracket narrower than that cannot be resolved further
   static constexpr double kLocateRel = 2e-7;
   static constexpr bool kTrigTable = true;  // its FP64 steps use rhs64
+  static constexpr bool kExpLogTable = false;
   struct RayCache {};
   struct LaneCache {};
   static __device__ __forceinline__ void prepare(const RayK&, RayCache&) {}
