@@ -306,25 +306,28 @@ __device__ __forceinline__ void rhs_q64(const RayK& K, double r, double th, doub
   const double Xk = osiris_explog::exp_tab(K.kap * osiris_explog::log_tab(X, T.lg), T.t2);
   const double ir2 = ir * ir;
   const double ffq = f * fq;
+  const double fXk = fq * Xk;
   const double gtt = -rcp64(ffq);
-  const double grr = ffq * Xk;
-  const double gthth = fq * Xk * ir2;
+  const double grr = f * fXk;
+  const double gthth = fXk * ir2;
   const double gpp = fq * ir2 * is2;
-  const double Lf = 2.0 * iD;
-  const double LXr = -s2 * (2.0 * r - 2.0) * iD * iD * iX;
-  const double LXth = 2.0 * s * c * iD * iX;
-  const double E2 = K.E * K.E, L2 = K.L * K.L, pr2 = pr * pr, pth2 = pth * pth;
-  twoH = fma(gtt, E2, fma(grr, pr2, fma(gthth, pth2, gpp * L2)));
   dr = grr * pr;
   dth = gthth * pth;
   dph = gpp * K.L;
-  const double dgtt = -gtt * (1.0 + K.q) * Lf;
-  const double dgrr = grr * fma(1.0 + K.q, Lf, K.kap * LXr);
-  const double dgthth = gthth * fma(K.kap, LXr, fma(K.q, Lf, -2.0 * ir));
-  const double dgpp = gpp * fma(K.q, Lf, -2.0 * ir);
-  dpr = -0.5 * fma(dgtt, E2, fma(dgrr, pr2, fma(dgthth, pth2, dgpp * L2)));
-  // cos / sin = sin cos / sin^2
-  dpth = -0.5 * fma(K.kap * LXth, fma(grr, pr2, gthth * pth2), -2.0 * (c * s * is2) * gpp * L2);
+  // the four terms of 2H
+  const double Ht = gtt * (K.E * K.E), Hr = dr * pr, Hth = dth * pth, Hph = dph * K.L;
+  twoH = (Ht + Hr) + (Hth + Hph);
+  // -dH/dr = -1/2 sum_mu (d ln g^mumu / dr) H_mu, collected by logarithmic
+  // derivative: -1/2 [(1+q) d ln f (Hr - Ht) + k d ln X (Hr + Hth)
+  //                   + (q d ln f - 2/r) (Hth + Hph)]
+  const double iDX = iD * iX;
+  const double a1 = fma(-K.q, iD, -iD);                 // -(1+q)/D
+  const double a2 = K.kap * s2 * (r - 1.0) * iD * iDX;  // k sin^2 (r-1) / (D^2 X)
+  const double a3 = fma(-K.q, iD, ir);                  // 1/r - q/D
+  dpr = fma(a1, Hr - Ht, fma(a2, Hr + Hth, a3 * (Hth + Hph)));
+  // -dH/dtheta = -1/2 (k d ln X/dtheta (Hr + Hth) - 2 (cos/sin) Hph)
+  //            = sin cos (Hph / sin^2 - k (Hr + Hth) / (D X))
+  dpth = (c * s) * fma(-K.kap * iDX, Hr + Hth, Hph * is2);
 }
 
 // 2H = N / Sigma in Kerr, in FP64, without the derivatives and without the
