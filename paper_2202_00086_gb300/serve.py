@@ -15,9 +15,14 @@ Renders (camera set-ups) arrive over time. The server:
   - detects round completion with CUDA events and timestamps each render at
     the completion of its last pixel range.
 
-Round composition: every active render first receives up to `min_chunk`
-rays in arrival order (small renders finish in one round), then the rest of
-the round budget goes to the oldest renders. Rays are independent, so a
+Round composition: a batched launch holds one space-time and one precision,
+so each render has a kind: Kerr renders run at the server's precision,
+q-metric renders (shadow and lensing; Appendix A) in FP64. A round serves one
+kind: that of the oldest render with rays left, or the next kind in that
+order when the previous round served it, so kinds alternate while several
+have work. Within the round every active render of the kind first receives up
+to `min_chunk` rays in arrival order (small renders finish in one round),
+then the rest of the round budget goes to the oldest of them. Rays are independent, so a
 render's outputs are the same whether it runs alone or in a mix (the GPU
 tests check this bitwise).
 
@@ -37,7 +42,7 @@ DISK_BYTES_PER_RAY = 66    # + g, intensity, r_hit
 class ServedRender:
     __slots__ = ("rid", "render", "arrival", "camera", "disk", "r_in", "r_out", "tol",
                  "n_rays", "next_ray", "rays_done", "out", "bytes", "t_submit", "t_admit",
-                 "t_done", "chunks")
+                 "t_done", "chunks", "kind")
 
     def __init__(self, rid, render, arrival):
         self.rid = rid
@@ -54,6 +59,7 @@ class ServedRender:
         self.tol = render["tol"]
         self.t_submit = self.t_admit = self.t_done = None
         self.chunks = []  # (first_ray, n_rays) in launch order
+        self.kind = None  # (space-time, precision) of the launches that trace it
 
 
 class _Round:
@@ -97,23 +103,30 @@ class RenderServer:
         self._ws = [self.backend.workspace(osr_workspace_bytes(osr, self.max_entries))
                     for _ in range(self.max_inflight)]
         self._ws_free = list(range(self.max_inflight))
-        self._plans = None
+        self._last_kind = None
+        self._plans = None  # per in-flight slot: {kind: plan}, made on first use
         if graphs and hasattr(self.backend, "plan"):
-            self._plans = [self.backend.plan(ws, self.max_entries, precision=self.precision,
-                                             cell_deg=self.cell_deg,
-                                             cell_phase_deg=self.cell_phase_deg)
-                           for ws in self._ws]
+            self._plans = [{} for _ in self._ws]
+            for k in range(len(self._ws)):  # Kerr plans up front, off the serving path
+                self._plan(k, (osr.SPACETIME_KERR, self.precision))
 
     # ---- submission and admission ----
     def submit(self, render, arrival=None):
         """Queue a render (a workloads.render dict). Returns its ServedRender.
-        The server serves Kerr renders (a batched launch holds one space-time);
-        a q-metric render raises ValueError here, not in a later round."""
+        Kerr renders run at the server's precision, q-metric renders in FP64;
+        a q-metric disk render (the q-metric has no disk model) raises
+        ValueError here, not in a later round."""
+        osr = self.osr
         if render.get("q") is not None:
-            raise ValueError("the render server serves Kerr renders; trace q-metric renders "
-                             "with trace() or trace_batch()")
+            if render["mode"] == "disk":
+                raise ValueError("q-metric renders are shadow/lensing renders: the q-metric "
+                                 "has no disk model")
+            kind = (osr.SPACETIME_QMETRIC, osr.FP64)
+        else:
+            kind = (osr.SPACETIME_KERR, self.precision)
         now = self.clock()
         r = ServedRender(self._next_id, render, now if arrival is None else arrival)
+        r.kind = kind
         self._next_id += 1
         r.t_submit = now
         if r.bytes > self.hbm_budget:
@@ -136,12 +149,26 @@ class RenderServer:
             self.active.append(r)
 
     # ---- rounds ----
+    def _next_kind(self):
+        kinds = []  # kinds with rays left, in order of their oldest such render
+        for r in self.active:
+            if r.next_ray < r.n_rays and r.kind not in kinds:
+                kinds.append(r.kind)
+        if not kinds:
+            return None
+        if len(kinds) > 1 and kinds[0] == self._last_kind:
+            return kinds[1]
+        return kinds[0]
+
     def _compose(self):
+        kind = self._next_kind()
         budget = self.round_rays
         parts = []
         for r in self.active:  # first pass: a small chunk for every active render
             if budget <= 0 or len(parts) >= self.max_entries:
                 break
+            if r.kind != kind:
+                continue
             left = r.n_rays - r.next_ray
             if left <= 0:
                 continue
@@ -158,10 +185,19 @@ class RenderServer:
                 p[2] += extra
                 r.next_ray += extra
                 budget -= extra
-        return [tuple(p) for p in parts]
+        return kind, [tuple(p) for p in parts]
+
+    def _plan(self, k, kind):
+        plan = self._plans[k].get(kind)
+        if plan is None:
+            plan = self.backend.plan(self._ws[k], self.max_entries, spacetime=kind[0],
+                                     precision=kind[1], cell_deg=self.cell_deg,
+                                     cell_phase_deg=self.cell_phase_deg)
+            self._plans[k][kind] = plan
+        return plan
 
     def _launch(self):
-        parts = self._compose()
+        kind, parts = self._compose()
         if not parts:
             return False
         k = self._ws_free.pop()
@@ -172,11 +208,12 @@ class RenderServer:
                             "l0": r.render.get("l0") if r.disk else None})
             r.chunks.append((first, n))
         if self._plans is not None:
-            event = self.backend.launch_plan(self._plans[k], entries)
+            event = self.backend.launch_plan(self._plan(k, kind), entries)
         else:
-            event = self.backend.launch(entries, self._ws[k], precision=self.precision,
+            event = self.backend.launch(entries, self._ws[k], precision=kind[1],
                                         cell_deg=self.cell_deg,
                                         cell_phase_deg=self.cell_phase_deg)
+        self._last_kind = kind
         self.inflight.append(_Round(event, parts, k, self.clock()))
         self.round_entries.append(len(parts))
         self.rounds += 1

@@ -57,3 +57,33 @@ def test_alone_equals_in_the_mix(precision):
         for k in ref:
             assert np.array_equal(got[k], ref[k]), (rid, k)
     assert summary["p99_latency_s"] >= summary["p50_latency_s"] > 0
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_kerr_and_qmetric_in_one_stream(graphs):
+    """q-metric renders (FP64) served next to Kerr renders (DF64), in rounds of
+    one kind each: every render equals the same render traced alone."""
+    phase = workloads.checker_phase_deg(2202)
+    rng = np.random.default_rng(3)
+    arrivals = []
+    for k in range(8):
+        side = int(rng.choice([16, 40]))
+        if k % 2:
+            rd = workloads.render(0.0, 1000.0, float(rng.uniform(20, 85)), (-8, 8, -8, 8), side,
+                                  side, q=float(rng.choice([-0.5, 0.1, 0.5])))
+        else:
+            rd = workloads.render(float(rng.uniform(0, 0.99)), 1000.0, 60.0, (-8, 8, -8, 8),
+                                  side, side)
+        arrivals.append((0.001 * k, rd))
+    srv = serve.RenderServer(round_rays=1500, min_chunk=400, keep_outputs=True,
+                             cell_phase_deg=phase, max_inflight=2, graphs=graphs)
+    summary = srv.run(arrivals, realtime=True)
+    torch.cuda.synchronize()
+    assert summary["renders"] == len(arrivals)
+    by_id = {r.rid: r for r in srv.done}
+    for rid, (_, rd) in enumerate(arrivals):
+        got = {k: v.cpu().numpy() for k, v in by_id[rid].out.items()}
+        prec = osr.FP64 if rd.get("q") is not None else osr.DF64
+        ref = _alone(rd, prec, phase)
+        for k in ref:
+            assert np.array_equal(got[k], ref[k]), (rid, k)

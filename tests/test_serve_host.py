@@ -1,7 +1,8 @@
 """Host logic of the render server, with a fake backend (no GPU): every pixel
 of every admitted render is launched exactly once, rounds respect the ray and
 entry budgets, admission respects the HBM budget, and oversize renders are
-rejected."""
+rejected; Kerr and q-metric renders share the server in rounds of one kind
+each."""
 import numpy as np
 
 from paper_2202_00086_gb300 import serve, workloads
@@ -21,13 +22,14 @@ class FakeBackend:
         self.server_ref = server_ref
         self.delay = delay
         self.rounds = []
+        self.round_kinds = []  # (set of camera q values, precision) per round
         self.max_bytes_seen = 0
 
     def workspace(self, nbytes):
         return object()
 
     def camera(self, rd):
-        return ("camera", rd["nx"], rd["ny"])
+        return ("camera", rd["nx"], rd["ny"], rd.get("q"))
 
     def resolve_r_in(self, rd):
         return 6.0 if rd["r_in"] == "isco" else rd["r_in"]
@@ -37,6 +39,7 @@ class FakeBackend:
 
     def launch(self, entries, ws, **opts):
         self.rounds.append([(e["first_ray"], e["n_rays"]) for e in entries])
+        self.round_kinds.append(({e["camera"][3] for e in entries}, opts.get("precision")))
         for e in entries:
             e["out"]["hits"][e["first_ray"]:e["first_ray"] + e["n_rays"]] += 1
         srv = self.server_ref[0]
@@ -110,10 +113,46 @@ def test_summary_percentiles():
     assert s["rays"] == 1000 and abs(s["rays_per_s"] - 10.0) < 1e-12
 
 
-def test_qmetric_render_is_refused_at_submission():
+def test_qmetric_disk_render_is_refused_at_submission():
     import pytest
     srv, be = _server()
-    rd = workloads.render(0.0, 1000.0, 60.0, (-8, 8, -8, 8), 16, 16, q=0.3)
+    rd = workloads.render(0.0, 1000.0, 60.0, (-25, 25, -25, 25), 16, 16, q=0.3, mode="disk",
+                          r_in=6.0, r_out=20.0)
     with pytest.raises(ValueError):
         srv.submit(rd)
     assert srv.idle() and not be.rounds
+
+
+def test_kerr_and_qmetric_rounds():
+    """A launch holds one space-time: every round is all-Kerr (at the server's
+    precision) or all-q-metric (FP64); while both kinds have rays left the
+    rounds alternate, and every pixel is traced once."""
+    import paper_2202_00086_gb300 as osr
+    rng = np.random.default_rng(9)
+    stream = []
+    for k in range(24):
+        side = int(rng.choice([16, 48, 96]))
+        q = float(rng.choice([-0.5, 0.3])) if k % 3 == 1 else None
+        stream.append((0.0, workloads.render(0.0 if q is not None else 0.7, 1000.0, 60.0,
+                                             (-8, 8, -8, 8), side, side, q=q)))
+    srv, be = _server(round_rays=6000, min_chunk=1000, max_inflight=2)
+    summary = srv.run(stream, realtime=False, poll_s=0)
+    assert summary["renders"] == len(stream)
+    for r in srv.done:
+        assert np.all(r.out["hits"] == 1)
+        assert r.kind == ((osr.SPACETIME_QMETRIC, osr.FP64) if r.render.get("q") is not None
+                          else (osr.SPACETIME_KERR, osr.DF64))
+    kinds = []
+    for qs, prec in be.round_kinds:
+        is_q = [q is not None for q in qs]
+        assert all(is_q) or not any(is_q)
+        assert prec == (osr.FP64 if is_q[0] else osr.DF64)
+        kinds.append(is_q[0])
+    assert any(kinds) and not all(kinds)
+    # alternation: the q-metric renders are not left until the Kerr ones finish
+    last_q = max(i for i, k in enumerate(kinds) if k)
+    last_kerr = max(i for i, k in enumerate(kinds) if not k)
+    first_switch = next(i for i in range(1, len(kinds)) if kinds[i] != kinds[i - 1])
+    assert first_switch == 1
+    both_left = min(last_q, last_kerr)
+    assert all(kinds[i] != kinds[i + 1] for i in range(both_left))
