@@ -164,7 +164,8 @@ int osiris_init_camera(osiris_camera** out, double a, double r_obs, double incl_
  * (-1, -1 + sqrt(3/2)) \ {0} describes naked singularities. The initial data
  * are those of osiris_init_camera for this static metric; rays end at
  * r < r_cap_factor * 2 (the singular surface r = 2) or at the celestial
- * sphere. q-metric renders run in FP64 (OSIRIS_FP64) without a disk.
+ * sphere. q-metric renders run in FP64 or DF64 (not OSIRIS_MIXED), without a
+ * disk.
  *   q          > -1; r_obs > 20; the other arguments as osiris_init_camera. */
 int osiris_init_camera_q(osiris_camera** out, double q, double r_obs, double incl_deg,
                          double x_min, double x_max, double y_min, double y_max, int32_t nx,
@@ -253,7 +254,7 @@ typedef struct osiris_batch_plan osiris_batch_plan;
  * osiris_workspace_bytes(max_requests) bytes) belongs to the plan until it is
  * destroyed and must not be used by other calls meanwhile. The plan allocates
  * max_requests table entries of pinned host memory. Returns OSIRIS_EINVAL
- * (bad arguments, q-metric without FP64), OSIRIS_ENOMEM (workspace too small
+ * (bad arguments, q-metric in MIXED), OSIRIS_ENOMEM (workspace too small
  * or no pinned memory) or OSIRIS_ECUDA; *plan is NULL on error. */
 int osiris_batch_plan_create(osiris_batch_plan** plan, int32_t max_requests, int32_t spacetime,
                              const osiris_trace_opts* opts);
@@ -318,7 +319,7 @@ int osiris_trace_states(double a, double r_obs, const double* states, const doub
  * OSIRIS_SPACETIME_QMETRIC (param = q), and mass2 = 0 for light (H = 0) or
  * 1 for a unit-mass particle on the shell H = -1/2 (time-like geodesics,
  * Sec. 2.1 and Appendix A). max_abs_H then reports max |H - H_shell|. The
- * q-metric needs OSIRIS_FP64 and disk = 0. */
+ * q-metric needs OSIRIS_FP64 or OSIRIS_DF64, and disk = 0. */
 int osiris_trace_states_ex(int32_t spacetime, double param, double r_obs, double mass2,
                            const double* states, const double* E, const double* L, int64_t n,
                            int32_t disk, double r_in, double r_out, const osiris_trace_opts* opts,

@@ -124,11 +124,11 @@ int apply_range(ReqDev& R, const osiris_request& q) {
 
 int cuda_rc(int e) { return e == 0 ? OSIRIS_OK : OSIRIS_ECUDA; }
 
-// The q-metric runs in FP64 without a disk.
+// The q-metric runs in FP64 or DF64, without a disk.
 int check_spacetime(int spacetime, int disk, const osiris_trace_opts* o) {
   if (spacetime == OSIRIS_SPACETIME_KERR) return OSIRIS_OK;
   if (spacetime != OSIRIS_SPACETIME_QMETRIC) return OSIRIS_EINVAL;
-  if (o->precision != OSIRIS_FP64 || disk) return OSIRIS_EINVAL;
+  if ((o->precision != OSIRIS_FP64 && o->precision != OSIRIS_DF64) || disk) return OSIRIS_EINVAL;
   return OSIRIS_OK;
 }
 

@@ -349,6 +349,20 @@ __device__ __forceinline__ double twoH_kerr_direct(const RayK& K, const State& y
   return N * iSig;
 }
 
+// 2H in the q-metric (Appendix A), in FP64 with the library's sin, log, exp
+// and division: the end-point |H| check of the double-float kernels.
+__device__ __forceinline__ double twoH_q_direct(const RayK& K, const State& y) {
+  const double s = sin(y.th);
+  const double rm2 = y.r - 2.0;
+  const double f = rm2 / y.r;
+  const double X = 1.0 + (s * s) / (y.r * rm2);
+  const double fq = exp(K.q * log(f));
+  const double fXk = fq * exp(K.kap * log(X));
+  const double ir2 = 1.0 / (y.r * y.r);
+  return -(K.E * K.E) / (f * fq) + f * fXk * y.pr * y.pr + fXk * ir2 * y.pth * y.pth +
+         fq * ir2 * K.L * K.L / (s * s);
+}
+
 // Metric policies for the FP64 steppers.
 struct KerrMetric {
   static constexpr bool kTrigTable = true;  // rhs64 reads the block's sincos table

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include "df64.cuh"
+#include "explog_df.cuh"
 #include "trace_kernel.cuh"
 
 namespace osiris_impl {
@@ -126,6 +127,95 @@ __device__ __forceinline__ void rhs_df(const RayDF& K, df r, df th, df pr, df pt
   twoH = __fadd_rn(__fsub_rn(NiS.hi, K.twoH0), NiS.lo);
 }
 
+// The q-metric (Appendix A) in df64: rhs_q64's form (trace_device.cuh) with
+// every operation in double-float and f^q, X^k from df_exp and df_log.
+struct RayQDF {
+  df E, L, q, kap, nq1, E2;  // nq1 = -(1 + q), E2 = E^2
+  float twoH0;
+};
+
+__device__ __forceinline__ RayQDF to_qdf(const RayK& K) {
+  RayQDF k;
+  k.E = df_from_double(K.E);
+  k.L = df_from_double(K.L);
+  k.q = df_from_double(K.q);
+  k.kap = df_from_double(K.kap);
+  k.nq1 = df_from_double(-(1.0 + K.q));
+  k.E2 = df_from_double(K.E * K.E);
+  k.twoH0 = 0.0f;
+  return k;
+}
+
+__device__ __forceinline__ void rhs_q_df(const RayQDF& K, df r, df th, df pr, df pth, df& dr,
+                                         df& dth, df& dph, df& dpr, df& dpth, float& twoH) {
+  df s, c;
+  df_sincos(th, s, c);
+  const df rm2 = df_add_f(r, -2.0f);  // renormalised: cancels towards r = 2
+  const df iD = df_rcp(df_mul(r, rm2));
+  const df ir = df_mul(rm2, iD);      // 1/r
+  const df f = df_mul(rm2, ir);       // 1 - 2/r
+  const df s2 = df_sqr(s);
+  const df is2 = df_rcp(s2);
+  const df X = df_add_f(df_mul(s2, iD), 1.0f);
+  const df iX = df_rcp(X);
+  const df fq = df_exp(df_mul(K.q, df_log(f)));
+  const df fXk = df_mul(fq, df_exp(df_mul(K.kap, df_log(X))));
+  const df ir2 = df_sqr(ir);
+  const df gtt = df_neg(df_rcp(df_mul(f, fq)));
+  dr = df_mul(df_mul(f, fXk), pr);
+  dth = df_mul(df_mul(fXk, ir2), pth);
+  dph = df_mul(df_mul(df_mul(fq, ir2), is2), K.L);
+  // the four terms of 2H and their logarithmic derivatives, as in rhs_q64
+  const df Ht = df_mul(gtt, K.E2);
+  const df Hr = df_mul(dr, pr), Hth = df_mul(dth, pth), Hph = df_mul(dph, K.L);
+  const df sum = df_add(df_add_u(Ht, Hr), df_add_u(Hth, Hph));
+  twoH = __fadd_rn(__fsub_rn(sum.hi, K.twoH0), sum.lo);
+  const df iDX = df_mul(iD, iX);
+  const df a1 = df_mul(K.nq1, iD);
+  const df a2 = df_mul(df_mul(df_mul(K.kap, s2), df_add_f_u(r, -1.0f)), df_mul(iD, iDX));
+  const df a3 = df_sub(ir, df_mul(K.q, iD));
+  const df HrHth = df_add_u(Hr, Hth);
+  dpr = df_add(df_mul(a1, df_sub_u(Hr, Ht)),
+               df_add(df_mul(a2, HrHth), df_mul(a3, df_add_u(Hth, Hph))));
+  dpth = df_mul(df_mul(c, s), df_sub(df_mul(Hph, is2), df_mul(df_mul(K.kap, iDX), HrHth)));
+}
+
+// Metric policies of the double-float kernels: the ray constants, the
+// evaluation, the FP64 2H of the end-point check, and the register cap.
+// Registers capped at 128 so that four blocks of 128 threads (16 warps) are
+// resident per SM: the double-float dependency chains need the extra warps
+// more than they lose to the spilled values, which stay in L1 as long as no
+// shared memory is reserved. Measured on the 12 x 1024^2 Kerr set (Mrays/s,
+// Cash-Karp): 168 registers (three blocks) 14.4, 128: 15.5, 112: 15.4,
+// 96: 15.3, 80: 14.7.
+struct KerrDF {
+  using Ray = RayDF;
+  static constexpr int kMaxRegs = 128;
+  static __device__ __forceinline__ Ray ray(const RayK& K) { return to_df(K); }
+  static __device__ __forceinline__ void rhs(const Ray& K, df r, df th, df pr, df pth, df& dr,
+                                             df& dth, df& dph, df& dpr, df& dpth,
+                                             float& twoH) {
+    rhs_df(K, r, th, pr, pth, dr, dth, dph, dpr, dpth, twoH);
+  }
+  static __device__ __forceinline__ double twoH_fp64(const RayK& K, const State& y) {
+    return twoH_kerr_direct(K, y);
+  }
+};
+
+struct QMetricDF {
+  using Ray = RayQDF;
+  static constexpr int kMaxRegs = 128;
+  static __device__ __forceinline__ Ray ray(const RayK& K) { return to_qdf(K); }
+  static __device__ __forceinline__ void rhs(const Ray& K, df r, df th, df pr, df pth, df& dr,
+                                             df& dth, df& dph, df& dpr, df& dpth,
+                                             float& twoH) {
+    rhs_q_df(K, r, th, pr, pth, dr, dth, dph, dpr, dpth, twoH);
+  }
+  static __device__ __forceinline__ double twoH_fp64(const RayK& K, const State& y) {
+    return twoH_q_direct(K, y);
+  }
+};
+
 // Tableaus for the df64 stepper, [integrator][stage]; stage s = 0..6 is the
 // tableau's stage s + 1. kA[i][t][s] = a_{t+1, s+1} in FP32 (the O(h) parts of
 // stage inputs); c_s, b_s and b_s - b*_s as df.
@@ -204,8 +294,8 @@ struct LaneCacheDF<OSIRIS_RKDP45> {
 // solution itself (formed in df64 exactly as o), its derivative is cached as
 // the next k1, and k1 is evaluated here only when the cache is empty. twoH
 // is 2 (H - H0) at y.
-template <int INTEG>
-__device__ __forceinline__ void rk_step_df(const RayDF& K, LaneCacheDF<INTEG>& LC,
+template <class Met, int INTEG>
+__device__ __forceinline__ void rk_step_df(const typename Met::Ray& K, LaneCacheDF<INTEG>& LC,
                                            const StateDF& y, df h, StateDF& o, float d[5],
                                            float& twoH) {
   constexpr int I = (INTEG == OSIRIS_RKDP45) ? 1 : 0;
@@ -265,7 +355,7 @@ __device__ __forceinline__ void rk_step_df(const RayDF& K, LaneCacheDF<INTEG>& L
     }
     df k[5];
     float h2;
-    rhs_df(K, in[0], in[1], in[2], in[3], k[0], k[1], k[2], k[3], k[4], h2);
+    Met::rhs(K, in[0], in[1], in[2], in[3], k[0], k[1], k[2], k[3], k[4], h2);
     if (s == 0) {
       twoH = h2;
 #pragma unroll
@@ -330,7 +420,7 @@ __device__ __forceinline__ void rk_step_df(const RayDF& K, LaneCacheDF<INTEG>& L
 // The lane state machine of trace_body (trace_kernel.cuh) with a df64 state:
 // same modes, same order of tests, same controller; the INTEGRATE path issues
 // no FP64 instruction. Surface location keeps its bracket in FP64.
-template <bool PERSISTENT, int INTEG>
+template <class Met, bool PERSISTENT, int INTEG>
 __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
   const unsigned FULL = 0xffffffffu;
   int mode = MODE_IDLE;
@@ -338,7 +428,7 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
   LaneStats S;
 
   RayInfo I;
-  RayDF KD;
+  typename Met::Ray KD;
   df r_cap, r_esc;
   float tol = 0.0f;
   StateDF y;
@@ -354,7 +444,7 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
     load_ray(A, g, I, y0);
     LC.reset();
     y = to_df(y0);
-    KD = to_df(I.K);
+    KD = Met::ray(I.K);
     KD.twoH0 = (float)(2.0 * I.H0);
     r_cap = df_from_double(I.r_cap);
     r_esc = df_from_double(I.r_esc);
@@ -369,7 +459,7 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
     const State f = to_double(fd);
     double mh = (double)max_abs_H;
     if (status != OSIRIS_STATUS_ERROR) {
-      mh = fmax(mh, fabs(0.5 * twoH_kerr_direct(I.K, f) - I.H0));
+      mh = fmax(mh, fabs(0.5 * Met::twoH_fp64(I.K, f) - I.H0));
       S.rhs += 1;
     }
     write_outputs(A, I, status, f, mh, n_acc, n_rej, S);
@@ -435,7 +525,7 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
     StateDF o;
     float d[5];
     float twoH;
-    rk_step_df<INTEG>(KD, LC, y, hd, o, d, twoH);
+    rk_step_df<Met, INTEG>(KD, LC, y, hd, o, d, twoH);
     S.rhs += 6;
 
     if (mode == MODE_INTEGRATE) {
@@ -520,51 +610,45 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
   flush_stats(A, S);
 }
 
-// Registers capped at 128 so that four blocks of 128 threads (16 warps) are
-// resident per SM: the double-float dependency chains need the extra warps
-// more than they lose to the spilled values, which stay in L1 as long as no
-// shared memory is reserved. Measured on the 12 x 1024^2 Kerr set (Mrays/s,
-// Cash-Karp): 168 registers (three blocks) 14.4, 128: 15.5, 112: 15.4,
-// 96: 15.3, 80: 14.7.
-constexpr int kMaxRegs = 128;
-
-template <int INTEG>
-__global__ void __maxnreg__(kMaxRegs) trace_df64_plain(const __grid_constant__ KernelArgs A) {
-  trace_body_df<false, INTEG>(A);
+template <class Met, int INTEG>
+__global__ void __maxnreg__(Met::kMaxRegs) trace_df64_plain(const __grid_constant__ KernelArgs A) {
+  trace_body_df<Met, false, INTEG>(A);
 }
 
-template <int INTEG>
-__global__ void __maxnreg__(kMaxRegs) trace_df64_persistent(const __grid_constant__ KernelArgs A) {
-  trace_body_df<true, INTEG>(A);
+template <class Met, int INTEG>
+__global__ void __maxnreg__(Met::kMaxRegs)
+    trace_df64_persistent(const __grid_constant__ KernelArgs A) {
+  trace_body_df<Met, true, INTEG>(A);
 }
 
-template <int INTEG>
+template <class Met, int INTEG>
 static const void* df64_kernel(Kernel kind) {
-  return kind == Kernel::kPersistent ? (const void*)trace_df64_persistent<INTEG>
-                                     : (const void*)trace_df64_plain<INTEG>;
+  return kind == Kernel::kPersistent ? (const void*)trace_df64_persistent<Met, INTEG>
+                                     : (const void*)trace_df64_plain<Met, INTEG>;
+}
+
+template <class Met>
+static const void* df64_kernel(Kernel kind, int integrator) {
+  return integrator == OSIRIS_RKDP45 ? df64_kernel<Met, OSIRIS_RKDP45>(kind)
+                                     : df64_kernel<Met, OSIRIS_RKCK45>(kind);
+}
+
+static const void* select_df64(Kernel kind, int integrator, int spacetime) {
+  return spacetime == OSIRIS_SPACETIME_QMETRIC ? df64_kernel<QMetricDF>(kind, integrator)
+                                               : df64_kernel<KerrDF>(kind, integrator);
 }
 
 int launch_trace_df64(const KernelArgs& args, Kernel kind, int integrator, int grid, int block,
                       void* stream) {
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (integrator == OSIRIS_RKDP45) {
-    if (kind == Kernel::kPersistent)
-      trace_df64_persistent<OSIRIS_RKDP45><<<grid, block, 0, s>>>(args);
-    else
-      trace_df64_plain<OSIRIS_RKDP45><<<grid, block, 0, s>>>(args);
-  } else {
-    if (kind == Kernel::kPersistent)
-      trace_df64_persistent<OSIRIS_RKCK45><<<grid, block, 0, s>>>(args);
-    else
-      trace_df64_plain<OSIRIS_RKCK45><<<grid, block, 0, s>>>(args);
-  }
-  return (int)cudaGetLastError();
+  const int spacetime = args.reqs ? args.spacetime : args.single.spacetime;
+  void* params[] = {const_cast<KernelArgs*>(&args)};
+  return (int)cudaLaunchKernel(select_df64(kind, integrator, spacetime), dim3(grid),
+                               dim3(block), params, 0, static_cast<cudaStream_t>(stream));
 }
 
-int occupancy_df64(Kernel kind, int integrator, int, int block, int* blocks_per_sm) {
-  const void* fn = integrator == OSIRIS_RKDP45 ? df64_kernel<OSIRIS_RKDP45>(kind)
-                                               : df64_kernel<OSIRIS_RKCK45>(kind);
-  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, 0);
+int occupancy_df64(Kernel kind, int integrator, int spacetime, int block, int* blocks_per_sm) {
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      blocks_per_sm, select_df64(kind, integrator, spacetime), block, 0);
 }
 
 }  // namespace osiris_impl

@@ -16,8 +16,9 @@ Renders (camera set-ups) arrive over time. The server:
     the completion of its last pixel range.
 
 Round composition: a batched launch holds one space-time and one precision,
-so each render has a kind: Kerr renders run at the server's precision,
-q-metric renders (shadow and lensing; Appendix A) in FP64. A round serves one
+so each render has a kind: Kerr renders run at the server's precision, and
+q-metric renders (shadow and lensing; Appendix A) too, except that a MIXED
+server runs them in FP64 (the q-metric has no MIXED kernel). A round serves one
 kind: that of the oldest render with rays left, or the next kind in that
 order when the previous round served it, so kinds alternate while several
 have work. Within the round every active render of the kind first receives up
@@ -113,15 +114,17 @@ class RenderServer:
     # ---- submission and admission ----
     def submit(self, render, arrival=None):
         """Queue a render (a workloads.render dict). Returns its ServedRender.
-        Kerr renders run at the server's precision, q-metric renders in FP64;
-        a q-metric disk render (the q-metric has no disk model) raises
-        ValueError here, not in a later round."""
+        Kerr and q-metric renders run at the server's precision (q-metric
+        renders in FP64 when it is MIXED); a q-metric disk render (the
+        q-metric has no disk model) raises ValueError here, not in a later
+        round."""
         osr = self.osr
         if render.get("q") is not None:
             if render["mode"] == "disk":
                 raise ValueError("q-metric renders are shadow/lensing renders: the q-metric "
                                  "has no disk model")
-            kind = (osr.SPACETIME_QMETRIC, osr.FP64)
+            kind = (osr.SPACETIME_QMETRIC,
+                    osr.FP64 if self.precision == osr.MIXED else self.precision)
         else:
             kind = (osr.SPACETIME_KERR, self.precision)
         now = self.clock()

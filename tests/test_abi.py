@@ -88,9 +88,9 @@ def test_batch_plan_validation_before_any_cuda_call(osr):
     assert L.osiris_batch_plan_create(ctypes.byref(h), 70000, osr.SPACETIME_KERR,
                                       ctypes.byref(o)) == osr.EINVAL
     assert L.osiris_batch_plan_create(ctypes.byref(h), 4, 7, ctypes.byref(o)) == osr.EINVAL
-    o_df = osr.make_opts(precision=osr.DF64)
+    o_mx = osr.make_opts(precision=osr.MIXED)
     assert L.osiris_batch_plan_create(ctypes.byref(h), 4, osr.SPACETIME_QMETRIC,
-                                      ctypes.byref(o_df)) == osr.EINVAL  # q-metric: FP64 only
+                                      ctypes.byref(o_mx)) == osr.EINVAL  # q-metric: not MIXED
     assert L.osiris_batch_plan_create(ctypes.byref(h), 4, osr.SPACETIME_KERR,
                                       ctypes.byref(osr.make_opts(tol=0.0))) == osr.EINVAL
     assert L.osiris_batch_plan_create(ctypes.byref(h), 4, osr.SPACETIME_KERR,

@@ -1,6 +1,7 @@
 """The q-metric (Appendix A) and time-like geodesics on the GPU, against the
-oracle: q-metric shadow renders (q = 0 equal to the Kerr a = 0 render),
-circular and escaping massive particles, and the mass-shell error."""
+oracle, in FP64 and in double-float (DF64): q-metric shadow renders (q = 0
+equal to the Kerr a = 0 render), circular and escaping massive particles,
+and the mass-shell error."""
 import math
 
 import numpy as np
@@ -11,24 +12,29 @@ import oracle
 import paper_2202_00086_gb300 as osr
 from paper_2202_00086_gb300 import workloads
 
-from _parity import assert_parity, compare, gpu_render, oracle_render
+from _parity import assert_parity, band_mask, compare, gpu_render, oracle_render
 
 pytestmark = pytest.mark.gpu
 
 
+PRECISIONS = [osr.FP64, osr.DF64]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("q", [-0.5, 0.1, 0.5])
 @pytest.mark.parametrize("inc", [30.0, 90.0])
-def test_qmetric_render_parity(q, inc):
+def test_qmetric_render_parity(q, inc, precision):
     rd = workloads.render(0.0, 1000.0, inc, (-8, 8, -8, 8), 32, 32, q=q)
-    rep = compare(rd, gpu_render(rd), oracle_render(rd))
+    rep = compare(rd, gpu_render(rd, precision=precision), oracle_render(rd))
     print(rep)
     assert_parity(rep)
 
 
-def test_qmetric_q0_equals_schwarzschild_on_gpu():
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_qmetric_q0_equals_schwarzschild_on_gpu(precision):
     rq = workloads.render(0.0, 1000.0, 60.0, (-8, 8, -8, 8), 24, 24, q=0.0)
     rk = workloads.render(0.0, 1000.0, 60.0, (-8, 8, -8, 8), 24, 24)
-    gq, gk = gpu_render(rq), gpu_render(rk)
+    gq, gk = gpu_render(rq, precision=precision), gpu_render(rk, precision=precision)
     assert np.array_equal(gq["status"], gk["status"])
     for key in ("r", "theta", "phi"):
         assert np.allclose(gq[key], gk[key], rtol=1e-9, atol=1e-9)
@@ -42,8 +48,9 @@ def _line_element(q, r):
     return -f ** (1 + q), f ** (-1 - q) * X ** -k, f ** -q * r * r
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("q", [0.0, 0.5, -0.5])
-def test_timelike_orbits_parity(q):
+def test_timelike_orbits_parity(q, precision):
     r = 12.0
     # circular orbit from the covariant metric: Omega^2 = -d g_tt / d g_phph
     h = 1e-5 * r
@@ -61,7 +68,7 @@ def test_timelike_orbits_parity(q):
     L = np.array([Lc, Lu])
     out = osr.trace_states(0.0, 100.0, torch.tensor(st, device="cuda"),
                            torch.tensor(E, device="cuda"), torch.tensor(L, device="cuda"),
-                           q=q, mass2=1.0, max_steps=150)
+                           q=q, mass2=1.0, max_steps=150, precision=precision)
     torch.cuda.synchronize()
     ref = oracle.trace_states(0.0, 100.0, st, E, L, spacetime=oracle.QMETRIC, q=q, mass2=1.0,
                               max_steps=150)
@@ -72,19 +79,22 @@ def test_timelike_orbits_parity(q):
     for key in ("r", "theta", "phi"):  # the escape point is located exactly
         assert abs(got[key][1] - ref[key][1]) <= 1e-8 * max(1.0, abs(ref[key][1])), key
     assert got["max_abs_H"].max() < 1e-8
-    assert np.allclose(got["max_abs_H"], ref["max_abs_H"], rtol=0.05, atol=1e-13)
+    # the DF64 kernels track |H - H0| from double-float sums: the same size,
+    # not the same rounding
+    rtol = 0.05 if precision == osr.FP64 else 0.5
+    assert np.allclose(got["max_abs_H"], ref["max_abs_H"], rtol=rtol, atol=1e-13)
 
 
 def test_qmetric_rejects_unsupported_modes():
     cam = osr.Camera(0.0, 1000.0, 60.0, (-8, 8, -8, 8), 8, 8, q=0.5)
-    for kw in (dict(precision=osr.DF64), dict(precision=osr.MIXED)):
-        with pytest.raises(osr.OsirisError):
-            osr.trace(cam, **kw)
+    with pytest.raises(osr.OsirisError):
+        osr.trace(cam, precision=osr.MIXED)
     with pytest.raises(osr.OsirisError):
         osr.render_disk(cam, 6.0, 20.0)
 
 
-def test_qmetric_batch_equals_single_calls():
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_qmetric_batch_equals_single_calls(precision):
     """q-metric renders in one batched persistent launch give the outputs of
     the same renders traced one by one, and a batch may not mix space-times."""
     rds = [workloads.render(0.0, 1000.0, inc, (-8, 8, -8, 8), 20, 16, q=q)
@@ -94,14 +104,38 @@ def test_qmetric_batch_equals_single_calls():
     reqs = [{"camera": c, "out": o, "tol": rd["tol"]} for c, o, rd in zip(cams, outs, rds)]
     ws = torch.empty(osr.workspace_bytes(len(reqs)), dtype=torch.uint8, device="cuda")
     osr.trace_batch(reqs, workspace=ws, cell_deg=rds[0]["cell_deg"],
-                    cell_phase_deg=rds[0]["cell_phase_deg"])
+                    cell_phase_deg=rds[0]["cell_phase_deg"], precision=precision)
     torch.cuda.synchronize()
     for rd, o in zip(rds, outs):
-        alone = gpu_render(rd)
+        alone = gpu_render(rd, precision=precision)
         for f in alone:
             assert np.array_equal(o[f].cpu().numpy(), alone[f]), f
     kerr = osr.Camera.from_render(workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 4, 4))
     mixed = reqs[:1] + [{"camera": kerr, "out": osr.alloc_outputs(16), "tol": 1e-10}]
     with pytest.raises(osr.OsirisError) as e:
-        osr.trace_batch(mixed, workspace=ws)
+        osr.trace_batch(mixed, workspace=ws, precision=precision)
     assert e.value.code == osr.EINVAL
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_full_size_qmetric_batch_sampled(precision):
+    """The six 1024^2 q-metric renders (q in {-0.5, 0.1, 0.5} x inclination
+    {30, 90} deg) in one batched launch, as they are timed; 40 sampled pixels
+    per render against the oracle."""
+    rds = [workloads.render(0.0, 1000.0, inc, (-8, 8, -8, 8), 1024, 1024, q=q)
+           for q in (-0.5, 0.1, 0.5) for inc in (30.0, 90.0)]
+    cams = [osr.Camera.from_render(rd) for rd in rds]
+    outs = [osr.alloc_outputs(c.n_rays) for c in cams]
+    ws = torch.empty(osr.workspace_bytes(len(cams)), dtype=torch.uint8, device="cuda")
+    osr.trace_batch([{"camera": c, "out": o, "tol": rd["tol"]}
+                     for c, o, rd in zip(cams, outs, rds)], workspace=ws, precision=precision,
+                    cell_deg=rds[0]["cell_deg"], cell_phase_deg=rds[0]["cell_phase_deg"])
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(21)
+    for rd, o in zip(rds, outs):
+        gpu = {k: v.cpu().numpy() for k, v in o.items()}
+        pix = np.sort(rng.choice(1024 * 1024, 40, replace=False))
+        ref = oracle_render(rd, pixels=pix)
+        band = band_mask(gpu["status"].reshape(1024, 1024)).reshape(-1)
+        rep = compare(rd, gpu, ref, pixels=pix, band=band)
+        assert_parity(rep)

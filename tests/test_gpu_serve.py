@@ -61,8 +61,8 @@ def test_alone_equals_in_the_mix(precision):
 
 @pytest.mark.parametrize("graphs", [True, False])
 def test_kerr_and_qmetric_in_one_stream(graphs):
-    """q-metric renders (FP64) served next to Kerr renders (DF64), in rounds of
-    one kind each: every render equals the same render traced alone."""
+    """q-metric renders served next to Kerr renders (both DF64), in rounds of
+    one space-time each: every render equals the same render traced alone."""
     phase = workloads.checker_phase_deg(2202)
     rng = np.random.default_rng(3)
     arrivals = []
@@ -83,7 +83,6 @@ def test_kerr_and_qmetric_in_one_stream(graphs):
     by_id = {r.rid: r for r in srv.done}
     for rid, (_, rd) in enumerate(arrivals):
         got = {k: v.cpu().numpy() for k, v in by_id[rid].out.items()}
-        prec = osr.FP64 if rd.get("q") is not None else osr.DF64
-        ref = _alone(rd, prec, phase)
+        ref = _alone(rd, osr.DF64, phase)
         for k in ref:
             assert np.array_equal(got[k], ref[k]), (rid, k)

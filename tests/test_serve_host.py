@@ -124,9 +124,9 @@ def test_qmetric_disk_render_is_refused_at_submission():
 
 
 def test_kerr_and_qmetric_rounds():
-    """A launch holds one space-time: every round is all-Kerr (at the server's
-    precision) or all-q-metric (FP64); while both kinds have rays left the
-    rounds alternate, and every pixel is traced once."""
+    """A launch holds one space-time: every round is all-Kerr or all-q-metric
+    (both at the server's precision, DF64 here); while both kinds have rays
+    left the rounds alternate, and every pixel is traced once."""
     import paper_2202_00086_gb300 as osr
     rng = np.random.default_rng(9)
     stream = []
@@ -140,13 +140,13 @@ def test_kerr_and_qmetric_rounds():
     assert summary["renders"] == len(stream)
     for r in srv.done:
         assert np.all(r.out["hits"] == 1)
-        assert r.kind == ((osr.SPACETIME_QMETRIC, osr.FP64) if r.render.get("q") is not None
+        assert r.kind == ((osr.SPACETIME_QMETRIC, osr.DF64) if r.render.get("q") is not None
                           else (osr.SPACETIME_KERR, osr.DF64))
     kinds = []
     for qs, prec in be.round_kinds:
         is_q = [q is not None for q in qs]
         assert all(is_q) or not any(is_q)
-        assert prec == (osr.FP64 if is_q[0] else osr.DF64)
+        assert prec == osr.DF64
         kinds.append(is_q[0])
     assert any(kinds) and not all(kinds)
     # alternation: the q-metric renders are not left until the Kerr ones finish
@@ -156,3 +156,12 @@ def test_kerr_and_qmetric_rounds():
     assert first_switch == 1
     both_left = min(last_q, last_kerr)
     assert all(kinds[i] != kinds[i + 1] for i in range(both_left))
+
+
+def test_mixed_server_runs_qmetric_in_fp64():
+    import paper_2202_00086_gb300 as osr
+    srv, be = _server(precision=osr.MIXED)
+    r = srv.submit(workloads.render(0.0, 1000.0, 60.0, (-8, 8, -8, 8), 16, 16, q=0.3))
+    k = srv.submit(workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 16, 16))
+    assert r.kind == (osr.SPACETIME_QMETRIC, osr.FP64)
+    assert k.kind == (osr.SPACETIME_KERR, osr.MIXED)
