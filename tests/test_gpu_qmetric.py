@@ -139,3 +139,23 @@ def test_full_size_qmetric_batch_sampled(precision):
         band = band_mask(gpu["status"].reshape(1024, 1024)).reshape(-1)
         rep = compare(rd, gpu, ref, pixels=pix, band=band)
         assert_parity(rep)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("q", [-0.3, 0.1, 0.5])
+def test_qmetric_light_ring_on_gpu(q, precision):
+    """The equatorial light ring of the q-metric, r = 3 + 2q with
+    b = r f^-(1+2q)/2 (the extremum of b^2 = g_phph / -g_tt): a photon started
+    on it stays on it through 60 steps."""
+    r = 3.0 + 2.0 * q
+    b = r * (1.0 - 2.0 / r) ** (-(1.0 + 2.0 * q) / 2.0)
+    st = torch.tensor([[0.0, r, math.pi / 2, 0.0, 0.0, 0.0]], device="cuda", dtype=torch.float64)
+    out = osr.trace_states(0.0, 1000.0, st, torch.ones(1, device="cuda", dtype=torch.float64),
+                           torch.full((1,), b, device="cuda", dtype=torch.float64), q=q,
+                           max_steps=60, precision=precision)
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    assert got["status"][0] == osr.STATUS_MAXSTEP
+    assert abs(got["r"][0] - r) < 1e-8
+    assert got["phi"][0] > 1.0  # it went round
+    assert got["max_abs_H"][0] < 1e-12

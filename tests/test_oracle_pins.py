@@ -763,6 +763,38 @@ def _circular_orbit(q, r):
     return Om, -g[0, 0] * ut, g[3, 3] * Om * ut
 
 
+def qmetric_light_ring(q):
+    """The equatorial circular photon orbit of the q-metric: b^2 = g_phph / -g_tt
+    = r^2 f^-(1+2q) is extremal where 2/r = (1+2q) 2/(r (r-2)), i.e.
+    r = 3 + 2q (X does not enter g_tt or g_phph on the equator); dphi/dt = 1/b.
+    Exists for q > -1/2."""
+    r = 3.0 + 2.0 * q
+    b = r * (1.0 - 2.0 / r) ** (-(1.0 + 2.0 * q) / 2.0)
+    return r, b
+
+
+@pytest.mark.parametrize("q", [-0.3, 0.1, 0.5])
+def test_qmetric_light_ring(q):
+    """Started on r = 3 + 2q with p_r = p_theta = 0 and L/E = b, a photon stays
+    on the circle and goes round at dphi/dt = 1/b: fixes the r-equation of the
+    q-metric (a wrong term in d g^tt/dr or d g^phph/dr moves or breaks the
+    circle)."""
+    r, b = qmetric_light_ring(q)
+    st = np.array([[0.0, r, math.pi / 2, 0.0, 0.0, 0.0]])
+    assert abs(oracle.hamiltonian_sp(oracle.QMETRIC, st[0], 1.0, b, q=q)) < 1e-14
+    res = oracle.trace_states(0.0, R0, st, [1.0], [b], spacetime=oracle.QMETRIC, q=q,
+                              max_steps=60)
+    assert res["status"][0] == oracle.STATUS_MAXSTEP
+    assert res["r"][0] == pytest.approx(r, abs=1e-8)
+    assert res["phi"][0] / res["t"][0] == pytest.approx(1 / b, rel=1e-9)
+    assert res["t"][0] > 10.0
+    # off the ring by 1e-3 the same photon leaves it (the ring is unstable)
+    st[0, 1] = r * (1 + 1e-3)
+    off = oracle.trace_states(0.0, R0, st, [1.0], [b], spacetime=oracle.QMETRIC, q=q,
+                              max_steps=400)
+    assert off["status"][0] in (oracle.STATUS_ESCAPED, oracle.STATUS_CAPTURED)
+
+
 @pytest.mark.parametrize("q", [0.0, 0.5, -0.5])
 def test_timelike_circular_orbits(q):
     r = 12.0
