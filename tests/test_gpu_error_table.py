@@ -1,8 +1,9 @@
 """Error of every output of every precision mode against the FP64 oracle.
 
-Three render kinds (a Kerr shadow with its checkerboard, the Schwarzschild
-thin disk and a Kerr disk from the ISCO) are traced in FP64, DF64 and MIXED
-precision. The reference is the oracle at tol 1e-10 in every case, so the
+Four render kinds (a Kerr shadow with its checkerboard, the Schwarzschild
+thin disk, a Kerr disk from the ISCO, and a q-metric shadow) are traced in
+FP64, DF64 and MIXED precision (the q-metric in FP64 and DF64 only: it has no
+MIXED kernel). The reference is the oracle at tol 1e-10 in every case, so the
 MIXED rows (which run at tol 1e-8 and 1e-7, where FP32 stage evaluations
 are usable) include their tolerance error as well as their precision error.
 Per output the test records:
@@ -27,6 +28,8 @@ RENDERS = {
     "schwarzschild disk 80deg": workloads.schwarzschild_disk(side=48),
     "kerr a=0.9 disk from ISCO": workloads.render(0.9, 1000.0, 60.0, (-25, 25, -25, 25), 48, 48,
                                                   mode="disk", r_in="isco", r_out=20.0),
+    "q-metric q=0.5 60deg shadow": workloads.render(0.0, 1000.0, 60.0, (-8, 8, -8, 8), 48, 48,
+                                                    q=0.5),
 }
 # mode -> (precision, tol, strict). Strict modes must meet the FP64 parity bar
 # (no flag mismatch, positions and g / I / r_hit within 1e-8). The MIXED modes
@@ -54,6 +57,8 @@ def test_error_of_every_output(mode):
     precision, tol, strict = MODES[mode]
     rows = []
     for name, rd in RENDERS.items():
+        if rd.get("q") is not None and precision == osr.MIXED:
+            continue
         ref = _reference(name)
         rep = compare(rd, gpu_render(dict(rd, tol=tol), precision=precision), ref)
         cells = rep.get("cell_mismatch", 0) + rep.get("parity_mismatch", 0)
