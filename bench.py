@@ -38,9 +38,13 @@ UNIT = "rays/s"
 # error estimate, error norm, step clamp).
 F_RHS = 59
 F_STEP = 258
+# The q-metric evaluation (the collected form of Appendix A's equations), with
+# exp, log, sincos and each reciprocal counted as one operation.
+F_RHS_Q = 60
 # Bytes per ray of the shadow outputs copied back in the end-to-end timing:
 # status 1, r/theta/phi/max|H| 4x8, steps 4, cell_i/cell_j 2x2, parity 1.
 SHADOW_BYTES_PER_RAY = 42
+DISK_BYTES_PER_RAY = 66  # + g, intensity, r_hit 3x8
 ORACLE_SAMPLE_STRIDE = 128  # CPU baseline: every 128th pixel of each render
 # DRAM bytes (read + write) of one FP64 trace launch over the 1024^2 set: ncu
 # capture of the same kernel at 512^2 (2.62 MB read + 90.56 MB written), scaled
@@ -48,8 +52,46 @@ ORACLE_SAMPLE_STRIDE = 128  # CPU baseline: every 128th pixel of each render
 FP64_TRAFFIC_BYTES_PER_LAUNCH = 372.7e6
 
 
+# Workloads: the headline Kerr set (default) and the measured "next" rows,
+# each timed under the same rules. --side scales the pixel counts.
+WORKLOADS = {
+    "kerr": (WORKLOAD_NAME, METRIC),
+    "qmetric": ("qmetric_shadow: 6 renders (q in {-0.5,0.1,0.5} x incl in {30,90} deg), "
+                "r_obs=1000, SIDE^2 cell centres on [-8,8]^2, Cash-Karp tol 1e-10, "
+                "r_cap=1.01*2, r_esc=1.1 r_obs, seeded 10-deg checkerboard",
+                "rays/s (q-metric shadow renders, Cash-Karp)"),
+    "disk_l0": ("paper_disk_figure: 3 constant-l0 thin-disk renders, (a, l0) in "
+                "{(0,2.8),(0.5,2.8),(0.998,1.8)}, 85 deg, r_obs=1000, r_in=ISCO(a), r_out=20, "
+                "2*SIDE x SIDE on [-24,24]x[-12,12], Cash-Karp tol 1e-10",
+                "rays/s (constant-l0 disk renders, Cash-Karp)"),
+    "uneven": ("uneven_batch: 256 requests from PCG64(4), side in {1,2,4,8}*SIDE/8, "
+               "a~U[0,0.998], incl~U[5,85] deg, r_obs~U[500,2000], shadow [-8,8]^2 and "
+               "disk (r_in=ISCO, r_out=20, [-25,25]^2) alternating, Cash-Karp tol 1e-10",
+               "rays/s (uneven shadow/disk batch, Cash-Karp)"),
+}
+
+
+def workload_renders(name, side):
+    from paper_2202_00086_gb300 import workloads
+    if name == "qmetric":
+        return workloads.qmetric_shadow_set(side)
+    if name == "disk_l0":
+        return workloads.paper_disk_figure(2 * side, side)
+    if name == "uneven":
+        return workloads.uneven_batch(256, 4, sides=tuple(max(1, side * k // 8)
+                                                            for k in (1, 2, 4, 8)))
+    return workloads.kerr_shadow_ring_set(side)
+
+
+def workload_label(name, side):
+    if name == "kerr":
+        return WORKLOAD_NAME.replace("1024x1024", "%dx%d" % (side, side))
+    return WORKLOADS[name][0].replace("SIDE", str(side))
+
+
 def parse():
     p = argparse.ArgumentParser()
+    p.add_argument("--workload", default="kerr", choices=sorted(WORKLOADS))
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
@@ -148,6 +190,19 @@ def oracle_sample_pixels(rd, stride):
     return np.arange(stride // 2, n, stride, dtype=np.int64)
 
 
+def oracle_options(oracle, rd):
+    """The oracle's options for a render: disk radii and model, space-time."""
+    opts = dict(tol=rd["tol"], cell_deg=rd["cell_deg"], cell_phase_deg=rd["cell_phase_deg"])
+    if rd["mode"] == "disk":
+        r_in = oracle.isco(rd["a"]) if rd["r_in"] == "isco" else rd["r_in"]
+        opts.update(disk=True, r_in=r_in, r_out=rd["r_out"])
+        if rd.get("l0") is not None:
+            opts.update(disk_model=oracle.DISK_CONSTANT_L, l0=rd["l0"])
+    if rd.get("q") is not None:
+        opts.update(spacetime=oracle.QMETRIC, q=rd["q"])
+    return opts
+
+
 def run_oracle_sample(renders, stride):
     import oracle
     cores = os.cpu_count() or 1
@@ -156,8 +211,7 @@ def run_oracle_sample(renders, stride):
     for rd in renders:
         pix = oracle_sample_pixels(rd, stride)
         oracle.trace_pixels(rd["a"], rd["r_obs"], rd["incl_deg"], rd["extent"], rd["nx"],
-                            rd["ny"], pixels=pix, nthreads=cores, tol=rd["tol"],
-                            cell_deg=rd["cell_deg"], cell_phase_deg=rd["cell_phase_deg"])
+                            rd["ny"], pixels=pix, nthreads=cores, **oracle_options(oracle, rd))
         n += pix.size
     dt = time.perf_counter() - t0
     return n, dt, cores
@@ -176,13 +230,14 @@ def reference_arm(args, renders):
         tot_n += n
         tot_t += dt
     value = tot_n / tot_t
-    sample = ("every %dth pixel of each of the 12 renders (%d rays per step), all host cores"
-              % (stride, tot_n // max(1, args.steps)))
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+    sample = ("every %dth pixel of each of the %d renders (%d rays per step), all host cores"
+              % (stride, len(renders), tot_n // max(1, args.steps)))
+    line = {"impl": "reference", "metric": WORKLOADS[args.workload][1], "value": value,
+            "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "sample": sample},
+            "config": {"workload": workload_label(args.workload, args.side), "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -197,8 +252,7 @@ def reference_arm(args, renders):
 
 def main():
     args = parse()
-    from paper_2202_00086_gb300 import workloads
-    renders = workloads.kerr_shadow_ring_set(args.side)
+    renders = workload_renders(args.workload, args.side)
     if args.impl == "reference":
         return reference_arm(args, renders)
 
@@ -218,9 +272,12 @@ def main():
 
     precision = {"fp64": osr.FP64, "mixed": osr.MIXED, "df64": osr.DF64}[args.precision]
     tol = 1e-10
+    f_rhs = F_RHS_Q if args.workload == "qmetric" else F_RHS
     cams = [osr.Camera.from_render(rd) for rd in renders]
     n_rays = sum(c.n_rays for c in cams)
-    outs = [osr.alloc_outputs(c.n_rays) for c in cams]
+    disk = [rd["mode"] == "disk" for rd in renders]
+    outs = [osr.alloc_outputs(c.n_rays, fields=osr.DISK_FIELDS if d else osr.SHADOW_FIELDS)
+            for c, d in zip(cams, disk)]
     ws = torch.empty(osr.workspace_bytes(len(cams)), dtype=torch.uint8, device="cuda")
     stats = osr.new_stats()
     stream = torch.cuda.current_stream()
@@ -228,14 +285,27 @@ def main():
     common = dict(tol=tol, precision=precision, block_size=args.block, workspace=ws,
                   cell_deg=renders[0]["cell_deg"], cell_phase_deg=renders[0]["cell_phase_deg"])
 
+    def request(rd, c, o):
+        r = {"camera": c, "out": o, "tol": rd["tol"]}
+        if rd["mode"] == "disk":
+            r.update(disk=True, r_in=osr.resolve_r_in(rd), r_out=rd["r_out"], l0=rd.get("l0"))
+        return r
+
+    reqs = [request(rd, c, o) for rd, c, o in zip(renders, cams, outs)]
+
+    def trace_one(rd, c, o, **kw):
+        if rd["mode"] == "disk":
+            osr.render_disk(c, osr.resolve_r_in(rd), rd["r_out"], out=o, l0=rd.get("l0"), **kw)
+        else:
+            osr.trace(c, out=o, **kw)
+
     def step(st=None):
         if args.kernel == "batch":
-            reqs = [{"camera": c, "out": o} for c, o in zip(cams, outs)]
             osr.trace_batch(reqs, stats=st, **common)
             launches[0] += 1
         else:
-            for c, o in zip(cams, outs):
-                osr.trace(c, out=o, persistent=(args.kernel == "persistent"), stats=st, **common)
+            for rd, c, o in zip(renders, cams, outs):
+                trace_one(rd, c, o, persistent=(args.kernel == "persistent"), stats=st, **common)
                 launches[0] += 1
 
     # L2 flush buffer (larger than the 129 MB L2), written between timed steps
@@ -288,18 +358,23 @@ def main():
     # ---- end to end through the C interface with host buffers ----
     e2e = None
     if not args.no_e2e:
-        host = [osr.alloc_outputs(c.n_rays, device="cpu", pin_memory=True) for c in cams]
+        host = [osr.alloc_outputs(c.n_rays, device="cpu", pin_memory=True,
+                                  fields=osr.DISK_FIELDS if d else osr.SHADOW_FIELDS)
+                for c, d in zip(cams, disk)]
         h2d = osr.workspace_bytes(len(cams)) - 256 if args.kernel == "batch" else 0
-        d2h = SHADOW_BYTES_PER_RAY * n_rays
+        d2h = sum((DISK_BYTES_PER_RAY if d else SHADOW_BYTES_PER_RAY) * c.n_rays
+                  for c, d in zip(cams, disk))
         e2e_step, e2e_api = step, "per-render calls"
         if args.kernel == "batch":
             # the serving API: a batch plan uploads the request table from its
             # pinned staging table and launches one CUDA graph per step
             ws_plan = torch.empty(osr.workspace_bytes(len(cams)), dtype=torch.uint8,
                                   device="cuda")
-            plan = osr.BatchPlan(len(cams), **dict(common, workspace=ws_plan))
-            plan_reqs = [{"camera": c, "out": o} for c, o in zip(cams, outs)]
-            e2e_step, e2e_api = (lambda: plan.launch(plan_reqs)), "osiris_batch_plan_launch"
+            plan = osr.BatchPlan(len(cams), spacetime=(osr.SPACETIME_QMETRIC
+                                                       if args.workload == "qmetric"
+                                                       else osr.SPACETIME_KERR),
+                                 **dict(common, workspace=ws_plan))
+            e2e_step, e2e_api = (lambda: plan.launch(reqs)), "osiris_batch_plan_launch"
             e2e_step()  # first launch outside the timed region, like the warm-up steps
         barrier()
         torch.cuda.synchronize()
@@ -325,11 +400,10 @@ def main():
 
         def vstep(st=None):
             if args.kernel == "batch":
-                osr.trace_batch([{"camera": c, "out": o} for c, o in zip(cams, outs)], stats=st,
-                                **vcommon)
+                osr.trace_batch(reqs, stats=st, **vcommon)
             else:
-                for c, o in zip(cams, outs):
-                    osr.trace(c, out=o, persistent=(args.kernel == "persistent"), stats=st,
+                for rd, c, o in zip(renders, cams, outs):
+                    trace_one(rd, c, o, persistent=(args.kernel == "persistent"), stats=st,
                               **vcommon)
 
         for _ in range(max(1, args.warmup)):
@@ -353,7 +427,7 @@ def main():
         vms = float(tv.item())
         vs = osr.decode_stats(vstats)
         vatt = vs["accepted"] + vs["rejected"] + vs["root_steps"]
-        vflops = vs["rhs_evals"] * F_RHS + vatt * F_STEP
+        vflops = vs["rhs_evals"] * f_rhs + vatt * F_STEP
         variants["df64"] = {
             "value": world * n_rays * args.steps / (vms * 1e-3), "unit": UNIT,
             "ms_per_step": vms / args.steps,
@@ -371,7 +445,7 @@ def main():
     # ---- served render stream: continuous batching (DF64) vs one render per
     # launch (FP64 plain kernel), same Poisson arrivals ----
     serving = None
-    if args.serve_seconds > 0 and precision == osr.FP64:
+    if args.serve_seconds > 0 and precision == osr.FP64 and args.workload == "kerr":
         from paper_2202_00086_gb300 import serve, workloads as wl
         all_arrivals = wl.served_stream(duration_s=args.serve_seconds)
         offered = sum(rd["nx"] * rd["ny"] for _, rd in all_arrivals) / args.serve_seconds
@@ -405,8 +479,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, dt, cores = run_oracle_sample(renders, ORACLE_SAMPLE_STRIDE)
         cpu = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "every %dth pixel of each of the 12 renders (%d rays), one pass"
-                         % (ORACLE_SAMPLE_STRIDE, n)}
+               "sample": "every %dth pixel of each of the %d renders (%d rays), one pass"
+                         % (ORACLE_SAMPLE_STRIDE, len(renders), n)}
 
     if rank != 0:
         if dist is not None:
@@ -415,17 +489,18 @@ def main():
 
     value = world * n_rays * args.steps / (ms_max * 1e-3)
     attempts = s["accepted"] + s["rejected"] + s["root_steps"]
-    flops = s["rhs_evals"] * F_RHS + attempts * F_STEP
+    flops = s["rhs_evals"] * f_rhs + attempts * F_STEP
     per_launch_ms = ms / max(1, kernel_launches)
     achieved = flops / max(1, kernel_launches) / (per_launch_ms * 1e-3) / 1e12
     peak = peaks["fp64"] if precision == osr.FP64 else peaks["fp32"]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "metric": WORKLOADS[args.workload][1], "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {osr.FP64: "f64", osr.MIXED: "f64+f32", osr.DF64: "f64+df64"}[precision],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "rays_per_step_per_gpu": n_rays,
+        "config": {"workload": workload_label(args.workload, args.side),
+                   "rays_per_step_per_gpu": n_rays,
                    "kernel": args.kernel, "precision": args.precision,
                    "l2": "flushed between timed steps (256 MB write)",
                    "wall_s_timed": t_wall},
@@ -435,18 +510,19 @@ def main():
                           "locate": s["root_steps"] / (n_rays * args.steps)},
         "status_counts_per_step": {k: s[k] // args.steps for k in
                                    ("status_captured", "status_escaped", "status_maxstep",
-                                    "status_error")},
+                                    "status_disk", "status_error")},
         "max_abs_H": s["max_abs_H"],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": (FP64_TRAFFIC_BYTES_PER_LAUNCH
                                  if precision == osr.FP64 and args.side == 1024
-                                 and args.kernel == "batch" else None),
+                                 and args.kernel == "batch" and args.workload == "kerr"
+                                 else None),
                      "peak_source": "FMA probe measured in this process (FP64 pipe)"
                                     if precision == osr.FP64 else
                                     "FMA probe measured in this process (FP32 pipe)",
                      "flops_per_launch": flops / max(1, kernel_launches),
-                     "f_rhs": F_RHS, "f_step": F_STEP},
+                     "f_rhs": f_rhs, "f_step": F_STEP},
         "fma_probe_tflops": peaks,
         "variants": variants,
         "serving": serving,

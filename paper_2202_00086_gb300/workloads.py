@@ -58,6 +58,17 @@ def kerr_shadow_ring_set(side=1024):
             for a in KERR_SPINS for inc in KERR_INCLINATIONS]
 
 
+QMETRIC_QS = (-0.5, 0.1, 0.5)
+QMETRIC_INCLINATIONS = (30.0, 90.0)
+
+
+def qmetric_shadow_set(side=1024):
+    """q-metric shadow set (Appendix A): q in {-0.5, 0.1, 0.5} x inclination
+    {30, 90} deg, r_obs = 1000, side x side on [-8,8]^2, tol 1e-10."""
+    return [render(0.0, 1000.0, inc, (-8.0, 8.0, -8.0, 8.0), side, side, q=q)
+            for q in QMETRIC_QS for inc in QMETRIC_INCLINATIONS]
+
+
 def schwarzschild_disk(side=2048):
     """Thin Keplerian disk around Schwarzschild: r_in=6, r_out=20, 80 deg,
     r_obs=1000, side x side on [-25,25]^2, tol 1e-10."""

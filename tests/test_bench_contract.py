@@ -63,6 +63,19 @@ def test_reference_arm_line():
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
 
 
+@pytest.mark.parametrize("workload,name", [("qmetric", "qmetric_shadow"),
+                                           ("disk_l0", "paper_disk_figure"),
+                                           ("uneven", "uneven_batch")])
+def test_reference_arm_next_workloads(workload, name):
+    """The measured next rows through the same contract: the oracle with each
+    render kind's options (q-metric, constant-l0 disk, mixed shadow/disk)."""
+    d = _run("--impl", "reference", "--workload", workload, "--side", "32", "--steps", "1",
+             "--warmup", "1")
+    _check_common(d, 1, 1)
+    assert d["config"]["workload"].startswith(name)
+    assert "32" in d["config"]["workload"]
+
+
 @pytest.mark.gpu
 def test_gpu_arm_line():
     d = _run("--side", "64", "--steps", "1", "--warmup", "3", "--serve-seconds", "0.5")
@@ -79,3 +92,19 @@ def test_gpu_arm_line():
     assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
     assert d["variants"]["df64"]["value"] > 0
     assert d["serving"]["continuous_batching_df64"]["p99_latency_s"] > 0
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("workload", ["qmetric", "disk_l0", "uneven"])
+def test_gpu_arm_next_workloads(workload):
+    d = _run("--workload", workload, "--side", "32", "--steps", "1", "--warmup", "3",
+             "--serve-seconds", "0.5")
+    _check_common(d, 1, 3)
+    assert d["metric"] != "rays/s (Kerr shadow+ring renders, FP64 Cash-Karp)"
+    assert d["gpu_launches"] == 1
+    assert d["roofline"]["f_rhs"] == (60 if workload == "qmetric" else 59)
+    assert d["roofline"]["traffic"] is None
+    assert d["variants"]["df64"]["value"] > 0
+    assert d["serving"] is None  # the served stream is a Kerr workload
+    if workload != "qmetric":
+        assert d["status_counts_per_step"]["status_disk"] > 0
