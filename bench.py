@@ -68,11 +68,44 @@ WORKLOADS = {
                "a~U[0,0.998], incl~U[5,85] deg, r_obs~U[500,2000], shadow [-8,8]^2 and "
                "disk (r_in=ISCO, r_out=20, [-25,25]^2) alternating, Cash-Karp tol 1e-10",
                "rays/s (uneven shadow/disk batch, Cash-Karp)"),
+    "timelike": ("timelike: SIDE^2 unit-mass particles (E=1.2, L~U[-4,4], theta~U[0.3,pi-0.3], "
+                 "p_theta=0, outward p_r from H=-1/2; PCG64 seed 7) from r=30 in Kerr a=0.9, "
+                 "r_obs=1000, Cash-Karp tol 1e-10, explicit initial data",
+                 "rays/s (time-like geodesics: unit-mass particles in Kerr, Cash-Karp)"),
 }
+
+TIMELIKE_A, TIMELIKE_R0, TIMELIKE_ROBS = 0.9, 30.0, 1000.0
+
+
+def timelike_states(n, seed=7):
+    """Initial data of the time-like workload: (states, E, L) with states rows
+    (t, r, theta, phi, p_r, p_theta); p_r > 0 solves the mass shell
+    g^tt E^2 - 2 g^tphi E L + g^phph L^2 + g^rr p_r^2 = -1 (Kerr, Boyer-Lindquist).
+    Particles for which no real p_r exists are dropped."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    a, r = TIMELIKE_A, TIMELIKE_R0
+    th = rng.uniform(0.3, np.pi - 0.3, n)
+    E = np.full(n, 1.2)
+    L = rng.uniform(-4.0, 4.0, n)
+    s2 = np.sin(th) ** 2
+    sig = r * r + a * a * (1.0 - s2)
+    dlt = r * r - 2.0 * r + a * a
+    big_a = (r * r + a * a) ** 2 - a * a * dlt * s2
+    gtt, gtp = -big_a / (sig * dlt), -2.0 * a * r / (sig * dlt)
+    gpp, grr = (dlt - a * a * s2) / (sig * dlt * s2), dlt / sig
+    rest = -1.0 - (gtt * E * E - 2.0 * gtp * E * L + gpp * L * L)
+    keep = rest > 0.0
+    st = np.zeros((int(keep.sum()), 6))
+    st[:, 1] = r
+    st[:, 2] = th[keep]
+    st[:, 4] = np.sqrt(rest[keep] / grr[keep])
+    return st, E[keep], L[keep]
 
 
 def workload_renders(name, side):
     from paper_2202_00086_gb300 import workloads
+    if name == "timelike":
+        return []
     if name == "qmetric":
         return workloads.qmetric_shadow_set(side)
     if name == "disk_l0":
@@ -217,21 +250,41 @@ def run_oracle_sample(renders, stride):
     return n, dt, cores
 
 
+def run_oracle_states(side, stride):
+    """The time-like workload's oracle sample: every stride-th particle, one
+    thread (the oracle's explicit-data entry is serial)."""
+    import oracle
+    st, E, L = timelike_states(side * side)
+    sel = slice(stride // 2, None, stride)
+    t0 = time.perf_counter()
+    oracle.trace_states(TIMELIKE_A, TIMELIKE_ROBS, st[sel], E[sel], L[sel], mass2=1.0)
+    return int(E[sel].size), time.perf_counter() - t0, 1
+
+
+def oracle_leg(args, renders):
+    """(rays, seconds, cores, description) of one pass of the oracle sample."""
+    stride = ORACLE_SAMPLE_STRIDE
+    if args.workload == "timelike":
+        n, dt, cores = run_oracle_states(args.side, stride)
+        return n, dt, cores, "every %dth particle (%d), one thread" % (stride, n)
+    n, dt, cores = run_oracle_sample(renders, stride)
+    return n, dt, cores, ("every %dth pixel of each of the %d renders (%d rays), all host cores"
+                          % (stride, len(renders), n))
+
+
 def reference_arm(args, renders):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    stride = ORACLE_SAMPLE_STRIDE
     for _ in range(args.warmup):
-        run_oracle_sample(renders, stride)
-    tot_n, tot_t, cores = 0, 0.0, 1
+        oracle_leg(args, renders)
+    tot_n, tot_t, cores, sample = 0, 0.0, 1, ""
     for _ in range(args.steps):
-        n, dt, cores = run_oracle_sample(renders, stride)
+        n, dt, cores, sample = oracle_leg(args, renders)
         tot_n += n
         tot_t += dt
     value = tot_n / tot_t
-    sample = ("every %dth pixel of each of the %d renders (%d rays per step), all host cores"
-              % (stride, len(renders), tot_n // max(1, args.steps)))
+    sample += ", per step"
     line = {"impl": "reference", "metric": WORKLOADS[args.workload][1], "value": value,
             "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -273,17 +326,28 @@ def main():
     precision = {"fp64": osr.FP64, "mixed": osr.MIXED, "df64": osr.DF64}[args.precision]
     tol = 1e-10
     f_rhs = F_RHS_Q if args.workload == "qmetric" else F_RHS
+    timelike = args.workload == "timelike"
     cams = [osr.Camera.from_render(rd) for rd in renders]
-    n_rays = sum(c.n_rays for c in cams)
     disk = [rd["mode"] == "disk" for rd in renders]
-    outs = [osr.alloc_outputs(c.n_rays, fields=osr.DISK_FIELDS if d else osr.SHADOW_FIELDS)
-            for c, d in zip(cams, disk)]
-    ws = torch.empty(osr.workspace_bytes(len(cams)), dtype=torch.uint8, device="cuda")
+    if timelike:
+        st_np, e_np, l_np = timelike_states(args.side * args.side)
+        tl = [torch.tensor(x, device="cuda").contiguous() for x in (st_np, e_np, l_np)]
+        sizes = [int(e_np.size)]
+        outs = [osr.alloc_outputs(sizes[0])]
+    else:
+        sizes = [c.n_rays for c in cams]
+        outs = [osr.alloc_outputs(c.n_rays, fields=osr.DISK_FIELDS if d else osr.SHADOW_FIELDS)
+                for c, d in zip(cams, disk)]
+    n_rays = sum(sizes)
+    ws = torch.empty(osr.workspace_bytes(max(1, len(cams))), dtype=torch.uint8, device="cuda")
     stats = osr.new_stats()
     stream = torch.cuda.current_stream()
     launches = [0]
+    from paper_2202_00086_gb300 import workloads
+    cell_deg = renders[0]["cell_deg"] if renders else 10.0
+    cell_phase = renders[0]["cell_phase_deg"] if renders else workloads.checker_phase_deg(2202)
     common = dict(tol=tol, precision=precision, block_size=args.block, workspace=ws,
-                  cell_deg=renders[0]["cell_deg"], cell_phase_deg=renders[0]["cell_phase_deg"])
+                  cell_deg=cell_deg, cell_phase_deg=cell_phase)
 
     def request(rd, c, o):
         r = {"camera": c, "out": o, "tol": rd["tol"]}
@@ -299,14 +363,21 @@ def main():
         else:
             osr.trace(c, out=o, **kw)
 
-    def step(st=None):
-        if args.kernel == "batch":
-            osr.trace_batch(reqs, stats=st, **common)
+    def launch_all(st, opts):
+        if timelike:
+            osr.trace_states(TIMELIKE_A, TIMELIKE_ROBS, tl[0], tl[1], tl[2], out=outs[0],
+                             mass2=1.0, persistent=True, stats=st, **opts)
+            launches[0] += 1
+        elif args.kernel == "batch":
+            osr.trace_batch(reqs, stats=st, **opts)
             launches[0] += 1
         else:
             for rd, c, o in zip(renders, cams, outs):
-                trace_one(rd, c, o, persistent=(args.kernel == "persistent"), stats=st, **common)
+                trace_one(rd, c, o, persistent=(args.kernel == "persistent"), stats=st, **opts)
                 launches[0] += 1
+
+    def step(st=None):
+        launch_all(st, common)
 
     # L2 flush buffer (larger than the 129 MB L2), written between timed steps
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -358,14 +429,24 @@ def main():
     # ---- end to end through the C interface with host buffers ----
     e2e = None
     if not args.no_e2e:
-        host = [osr.alloc_outputs(c.n_rays, device="cpu", pin_memory=True,
+        host = [osr.alloc_outputs(n, device="cpu", pin_memory=True,
                                   fields=osr.DISK_FIELDS if d else osr.SHADOW_FIELDS)
-                for c, d in zip(cams, disk)]
+                for n, d in zip(sizes, disk if not timelike else [False])]
         h2d = osr.workspace_bytes(len(cams)) - 256 if args.kernel == "batch" else 0
-        d2h = sum((DISK_BYTES_PER_RAY if d else SHADOW_BYTES_PER_RAY) * c.n_rays
-                  for c, d in zip(cams, disk))
+        d2h = sum((DISK_BYTES_PER_RAY if d else SHADOW_BYTES_PER_RAY) * n
+                  for n, d in zip(sizes, disk if not timelike else [False]))
         e2e_step, e2e_api = step, "per-render calls"
-        if args.kernel == "batch":
+        if timelike:
+            # the particles' initial data come from pinned host memory every step
+            tl_host = [torch.from_numpy(x).contiguous().pin_memory() for x in (st_np, e_np, l_np)]
+            h2d = sum(x.numel() * x.element_size() for x in tl_host)
+
+            def e2e_states():
+                for dst, src in zip(tl, tl_host):
+                    dst.copy_(src, non_blocking=True)
+                step()
+            e2e_step, e2e_api = e2e_states, "osiris_trace_states_ex"
+        elif args.kernel == "batch":
             # the serving API: a batch plan uploads the request table from its
             # pinned staging table and launches one CUDA graph per step
             ws_plan = torch.empty(osr.workspace_bytes(len(cams)), dtype=torch.uint8,
@@ -381,8 +462,8 @@ def main():
         t0 = time.perf_counter()
         for k in range(args.steps):
             e2e_step()
-            for c, o, h in zip(cams, outs, host):
-                osr.copy_outputs_to_host(o, h, c.n_rays)
+            for n, o, h in zip(sizes, outs, host):
+                osr.copy_outputs_to_host(o, h, n)
             torch.cuda.synchronize()
         te = time.perf_counter() - t0
         tt = torch.tensor([te], dtype=torch.float64, device="cuda")
@@ -399,12 +480,7 @@ def main():
         vcommon = dict(common, precision=osr.DF64)
 
         def vstep(st=None):
-            if args.kernel == "batch":
-                osr.trace_batch(reqs, stats=st, **vcommon)
-            else:
-                for rd, c, o in zip(renders, cams, outs):
-                    trace_one(rd, c, o, persistent=(args.kernel == "persistent"), stats=st,
-                              **vcommon)
+            launch_all(st, vcommon)
 
         for _ in range(max(1, args.warmup)):
             vstep()
@@ -477,10 +553,9 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n, dt, cores = run_oracle_sample(renders, ORACLE_SAMPLE_STRIDE)
+        n, dt, cores, sample = oracle_leg(args, renders)
         cpu = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "every %dth pixel of each of the %d renders (%d rays), one pass"
-                         % (ORACLE_SAMPLE_STRIDE, len(renders), n)}
+               "sample": sample + ", one pass"}
 
     if rank != 0:
         if dist is not None:

@@ -65,7 +65,8 @@ def test_reference_arm_line():
 
 @pytest.mark.parametrize("workload,name", [("qmetric", "qmetric_shadow"),
                                            ("disk_l0", "paper_disk_figure"),
-                                           ("uneven", "uneven_batch")])
+                                           ("uneven", "uneven_batch"),
+                                           ("timelike", "timelike")])
 def test_reference_arm_next_workloads(workload, name):
     """The measured next rows through the same contract: the oracle with each
     render kind's options (q-metric, constant-l0 disk, mixed shadow/disk)."""
@@ -95,7 +96,7 @@ def test_gpu_arm_line():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("workload", ["qmetric", "disk_l0", "uneven"])
+@pytest.mark.parametrize("workload", ["qmetric", "disk_l0", "uneven", "timelike"])
 def test_gpu_arm_next_workloads(workload):
     d = _run("--workload", workload, "--side", "32", "--steps", "1", "--warmup", "3",
              "--serve-seconds", "0.5")
@@ -106,5 +107,8 @@ def test_gpu_arm_next_workloads(workload):
     assert d["roofline"]["traffic"] is None
     assert d["variants"]["df64"]["value"] > 0
     assert d["serving"] is None  # the served stream is a Kerr workload
-    if workload != "qmetric":
+    if workload in ("disk_l0", "uneven"):
         assert d["status_counts_per_step"]["status_disk"] > 0
+    if workload == "timelike":  # unbound particles launched outwards all escape
+        assert d["status_counts_per_step"]["status_escaped"] == d["config"]["rays_per_step_per_gpu"]
+        assert d["e2e"]["api"] == "osiris_trace_states_ex" and d["e2e"]["h2d_bytes_per_step"] > 0
