@@ -112,3 +112,23 @@ def test_gpu_arm_next_workloads(workload):
     if workload == "timelike":  # unbound particles launched outwards all escape
         assert d["status_counts_per_step"]["status_escaped"] == d["config"]["rays_per_step_per_gpu"]
         assert d["e2e"]["api"] == "osiris_trace_states_ex" and d["e2e"]["h2d_bytes_per_step"] > 0
+
+
+def test_reference_arm_under_torchrun_two_ranks():
+    """The driver's multi-rank launch of the reference arm: rank 0 alone times
+    the oracle and prints one line; the other rank exits 0 without work."""
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    p = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+                        "--nproc-per-node", "2", "--master-addr", "127.0.0.1",
+                        "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+                        "--impl", "reference", "--side", "32", "--steps", "1", "--warmup", "1"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, p.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
