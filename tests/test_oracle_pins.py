@@ -814,6 +814,36 @@ def test_timelike_circular_orbits(q):
     assert res["max_abs_H"][0] < 1e-8
 
 
+def bpt_circular_orbit(a, r):
+    """Prograde equatorial circular orbit of a unit-mass particle in Kerr
+    (Bardeen, Press & Teukolsky 1972, M = 1): energy, angular momentum and
+    angular velocity as closed forms in r and a."""
+    v = math.sqrt(r)
+    den = r ** 0.75 * math.sqrt(r * v - 3.0 * v + 2.0 * a)
+    E = (r * v - 2.0 * v + a) / den
+    L = (r * r - 2.0 * a * v + a * a) / den
+    return E, L, 1.0 / (r * v + a)
+
+
+@pytest.mark.parametrize("a", [0.5, 0.9, 0.998])
+@pytest.mark.parametrize("r_over_isco", [1.2, 3.0])
+def test_kerr_timelike_circular_orbits(a, r_over_isco):
+    """A unit-mass particle started on the closed-form Kerr circular orbit
+    (on the mass shell H = -1/2) stays on it and goes round at
+    dphi/dt = 1/(r^(3/2) + a): pins the Kerr equations of motion with mass,
+    the H0 = -1/2 bookkeeping and the t and phi equations."""
+    r = r_over_isco * oracle.isco(a)
+    E, L, Om = bpt_circular_orbit(a, r)
+    st = np.array([[0.0, r, math.pi / 2, 0.0, 0.0, 0.0]])
+    assert oracle.hamiltonian(a, st[0], E, L) == pytest.approx(-0.5, abs=1e-13)
+    res = oracle.trace_states(a, 1000.0, st, [E], [L], mass2=1.0, max_steps=200)
+    assert res["status"][0] == oracle.STATUS_MAXSTEP
+    assert res["r"][0] == pytest.approx(r, rel=1e-8)
+    assert res["theta"][0] == pytest.approx(math.pi / 2, abs=1e-12)
+    assert res["phi"][0] / res["t"][0] == pytest.approx(Om, rel=1e-9)
+    assert res["max_abs_H"][0] < 1e-10
+
+
 def test_timelike_radial_escape_and_H_shell():
     """An unbound time-like particle (E > 1) in the q-metric escapes, keeping
     |H + 1/2| near the tolerance; the same ray traced as null data fails the
