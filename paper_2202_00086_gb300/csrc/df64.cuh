@@ -118,7 +118,10 @@ __device__ __forceinline__ df df_sqr(df a) {
 __device__ __forceinline__ df df_fma(df a, df b, df c) { return df_add(df_mul(a, b), c); }
 
 // 1 / b: FP32 reciprocal refined by one Newton step, x1 = x0 + x0 (1 - b x0),
-// with the residual formed from both words of b.
+// with the residual formed from both words of b. The seed is 1 / b.hi, so the
+// result keeps df64 precision only when b.lo is a few ulp(b.hi) at most (the
+// error after the step is about (b.lo / b.hi)^2): renormalise a sum that
+// cancelled before taking its reciprocal.
 __device__ __forceinline__ df df_rcp(df b) {
   const float x0 = __fdividef(1.0f, b.hi);
   float e = fmaf(-b.hi, x0, 1.0f);

@@ -2,31 +2,14 @@
 (explog_df.cuh), compiled as host C++ with the FP32 intrinsics mapped to
 plain IEEE single operations, held to 4 units of 2^-48 relative against
 mpmath on the arguments the q-metric feeds them and across their range."""
-import pathlib
-import shutil
 import subprocess
 
 import numpy as np
 import pytest
 
-ROOT = pathlib.Path(__file__).resolve().parent.parent
-CSRC = ROOT / "paper_2202_00086_gb300" / "csrc"
+from _df_host import build
 
 HARNESS = r"""
-#include <math.h>
-#include <cstdint>
-#include <cstring>
-#include <cstdio>
-#define __device__
-#define __forceinline__ inline
-static inline float __fadd_rn(float a, float b) { return a + b; }
-static inline float __fsub_rn(float a, float b) { return a - b; }
-static inline float __fmul_rn(float a, float b) { return a * b; }
-static inline float __fdividef(float a, float b) { return a / b; }
-static inline float __double2float_rn(double x) { return (float)x; }
-static inline unsigned __float_as_uint(float x) { unsigned u; std::memcpy(&u, &x, 4); return u; }
-static inline float __uint_as_float(unsigned u) { float x; std::memcpy(&x, &u, 4); return x; }
-static inline float __int_as_float(int i) { float x; std::memcpy(&x, &i, 4); return x; }
 #include "explog_df.cuh"
 using namespace osiris_impl;
 int main(int argc, char** argv) {
@@ -45,19 +28,13 @@ UNIT = 2.0 ** -48
 
 @pytest.fixture(scope="module")
 def harness(tmp_path_factory):
-    gxx = shutil.which("g++")
-    if gxx is None:
-        pytest.skip("g++ not available")
-    d = tmp_path_factory.mktemp("explog_df")
-    (d / "h.cpp").write_text(HARNESS)
-    subprocess.run([gxx, "-O2", "-std=c++17", "-ffp-contract=off", "-I" + str(CSRC),
-                    str(d / "h.cpp"), "-o", str(d / "h")], check=True)
+    exe = build(tmp_path_factory, "explog_df", HARNESS)
 
     def run(kind, x):
         hi = np.asarray(x, dtype=np.float64).astype(np.float32)
         lo = (x - hi.astype(np.float64)).astype(np.float32)
         a = np.ascontiguousarray(np.stack([hi, lo], 1), dtype=np.float32)
-        p = subprocess.run([str(d / "h"), kind], input=a.tobytes(), capture_output=True,
+        p = subprocess.run([str(exe), kind], input=a.tobytes(), capture_output=True,
                            check=True)
         return a, np.frombuffer(p.stdout, dtype=np.float32).reshape(-1, 2)
     return run
