@@ -23,15 +23,27 @@ import oracle
 from _df_host import build
 
 HARNESS = r"""
+#include <cstdlib>
 #include "rhs_df.cuh"
 using namespace osiris_impl;
 static double d(df x) { return (double)x.hi + (double)x.lo; }
-int main() {
+// x as an unrenormalised pair whose low word is k ulp(hi) away from the
+// renormalised one (hi moved by -k ulp, lo by +k ulp): the stage inputs of the
+// DF64 kernels reach the evaluation in this form.
+static df skew(double x, int k) {
+  df v = df_from_double(x);
+  if (k == 0 || v.hi == 0.0f) return v;
+  const float h = nextafterf(v.hi, k > 0 ? -INFINITY : INFINITY);
+  const float h2 = k > 1 ? nextafterf(h, k > 0 ? -INFINITY : INFINITY) : h;
+  return mk(h2, (float)(x - (double)h2));
+}
+int main(int argc, char** argv) {
+  const int k = argc > 1 ? atoi(argv[1]) : 0;
   double in[9];  // kind (0 Kerr, 1 q-metric), a or q, E, L, H0, r, theta, p_r, p_theta
   while (std::fread(in, sizeof in, 1, stdin) == 1) {
     const double E = in[2], L = in[3], H0 = in[4];
-    const df r = df_from_double(in[5]), th = df_from_double(in[6]);
-    const df pr = df_from_double(in[7]), pth = df_from_double(in[8]);
+    const df r = skew(in[5], k), th = skew(in[6], k);
+    const df pr = skew(in[7], k), pth = skew(in[8], k);
     df dr, dth, dph, dpr, dpth;
     float twoH;
     if (in[0] == 0.0) {  // ray constants formed as the DF64 kernels form them
@@ -70,9 +82,10 @@ int main() {
 def rhs_df(tmp_path_factory):
     exe = build(tmp_path_factory, "rhs_df", HARNESS)
 
-    def run(rows):
+    def run(rows, skew=0):
         inp = np.ascontiguousarray(rows, dtype=np.float64)
-        p = subprocess.run([str(exe)], input=inp.tobytes(), capture_output=True, check=True)
+        p = subprocess.run([str(exe), str(skew)], input=inp.tobytes(), capture_output=True,
+                           check=True)
         return np.frombuffer(p.stdout, dtype=np.float64).reshape(-1, 6)
     return run
 
@@ -137,3 +150,14 @@ def test_massive_particle_shell(rhs_df):
     rows = _points(1, (0.3,), 50, 8)
     rows[:, 4] = -0.5
     _check(rows, rhs_df(rows))
+
+
+def test_unrenormalised_inputs(rhs_df):
+    """Inputs whose low word is two ulp of the high word off the renormalised
+    pair (the form in which the kernels' stage inputs arrive) give the same
+    accuracy, next to the horizon included."""
+    rows = np.concatenate([_points(0, (0.5, 0.998), 150, 9), _points(1, (-0.5, 0.5), 150, 10)])
+    r_h = 1.0 + np.sqrt(1.0 - 0.998 ** 2)
+    near = rows[:, 1] == 0.998
+    rows[near, 5] = r_h * np.random.default_rng(11).uniform(1.02, 1.2, int(near.sum()))
+    _check(rows, rhs_df(rows, skew=2))
