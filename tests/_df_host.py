@@ -38,5 +38,6 @@ def build(tmp_path_factory, name, source):
     d = tmp_path_factory.mktemp(name)
     (d / "h.cpp").write_text(SHIMS + source)
     subprocess.run([gxx, "-O2", "-std=c++17", "-ffp-contract=off", "-I" + str(CSRC),
-                    str(d / "h.cpp"), "-o", str(d / "h")], check=True)
+                    "-I" + str(ROOT / "include"), str(d / "h.cpp"), "-o", str(d / "h")],
+                   check=True)
     return d / "h"
