@@ -6,6 +6,7 @@ import os
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -132,3 +133,26 @@ def test_reference_arm_under_torchrun_two_ranks():
     assert len(lines) == 1, p.stdout
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_workload_inputs():
+    """Each workload's inputs: render counts and sizes, and the time-like
+    particles on the mass shell H = -1/2 (the oracle's Kerr Hamiltonian),
+    moving outwards."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    assert len(bench.workload_renders("kerr", 64)) == 12
+    assert len(bench.workload_renders("qmetric", 64)) == 6
+    assert all(rd["q"] is not None for rd in bench.workload_renders("qmetric", 64))
+    l0 = bench.workload_renders("disk_l0", 64)
+    assert len(l0) == 3 and all((rd["nx"], rd["ny"]) == (128, 64) for rd in l0)
+    un = bench.workload_renders("uneven", 64)
+    assert len(un) == 256 and {rd["nx"] for rd in un} <= {8, 16, 32, 64}
+    assert bench.workload_renders("timelike", 64) == []
+    st, E, L = bench.timelike_states(2000)
+    assert st.shape == (E.size, 6) and E.size > 1900
+    assert np.all(st[:, 4] > 0.0) and np.all(st[:, 5] == 0.0)
+    for k in range(0, E.size, 97):
+        H = oracle.hamiltonian(bench.TIMELIKE_A, st[k], E[k], L[k])
+        assert abs(H + 0.5) < 1e-12, (k, H)
