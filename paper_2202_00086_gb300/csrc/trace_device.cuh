@@ -206,7 +206,11 @@ __device__ __forceinline__ double rcp64(double d) {
   const float f = __int_as_float((int)((b >> 32) & 0x80000000) | (e << 23) |
                                  (int)((b >> 29) & 0x7fffff));
   float rf;
+#ifdef __CUDA_ARCH__
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f));
+#else
+  rf = 1.0f / f;  // host builds of this header (CPU tests): a correctly rounded seed
+#endif
   const double x0 = float_to_double(rf);
   const double eps = fma(-d, x0, 1.0);
   return fma(x0, fma(eps, eps, eps), x0);
