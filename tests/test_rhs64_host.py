@@ -27,8 +27,9 @@ int main(int argc, char** argv) {
   trig_table_init();
   explog_table_init();
   const char op = argv[1][0];
-  double in[8];  // 'e': kind, a or q, E, L, r, theta, p_r, p_theta; 's', 'r': x
-  const int n_in = op == 'e' ? 8 : 1;
+  double in[10];  // 'e': kind, a or q, E, L, r, theta, p_r, p_theta; 's', 'r': x;
+                  // 'k': integrator, a, E, L, r, theta, phi, p_r, p_theta, h
+  const int n_in = op == 'e' ? 8 : op == 'k' ? 10 : 1;
   while (std::fread(in, sizeof(double), n_in, stdin) == (size_t)n_in) {
     if (op == 's') {
       double s, c;
@@ -38,6 +39,32 @@ int main(int argc, char** argv) {
     } else if (op == 'r') {
       const double out = rcp64(in[0]);
       std::fwrite(&out, sizeof out, 1, stdout);
+    } else if (op == 'k') {  // one Kerr attempt of the FP64 kernels' stepper
+      RayK K;
+      K.a = in[1];
+      K.a2 = K.a * K.a;
+      K.q = K.kap = 0.0;
+      K.E = in[2];
+      K.L = in[3];
+      K.aE = K.a * K.E;
+      K.aL = K.a * K.L;
+      K.E2 = K.E + K.E;
+      State y, o, d;
+      y.r = in[4];
+      y.th = in[5];
+      y.ph = in[6];
+      y.pr = in[7];
+      y.pth = in[8];
+      if (in[0] == 0.0) {
+        double twoH;
+        ck_step64<KerrMetric>(K, y, in[9], o, d, twoH);
+      } else {
+        Deriv k1, k7;
+        rhs64_at<KerrMetric>(K, y, k1);
+        dp_step64<KerrMetric>(K, y, in[9], k1, o, d, k7);
+      }
+      const double out[10] = {o.r, o.th, o.ph, o.pr, o.pth, d.r, d.th, d.ph, d.pr, d.pth};
+      std::fwrite(out, sizeof out, 1, stdout);
     } else {
       RayK K;  // as the kernels' load_ray forms it
       K.a = in[0] == 0.0 ? in[1] : 0.0;
@@ -149,3 +176,39 @@ def test_kerr_rhs64_against_oracle(dev):
 def test_qmetric_rhs_q64_against_oracle(dev):
     rows = _points(1, (-0.5, 0.1, 0.5), 300, 5)
     _check(rows, dev("e", rows, 6))
+
+
+def test_fp64_attempt_against_oracle_step(dev):
+    """One Cash-Karp or Dormand-Prince attempt of the FP64 kernels (the
+    derivatives' common factor 1/Sigma folded into the tableau coefficients)
+    against the oracle's step: the fifth-order result within 2e-14 of
+    1 + |y|, and the error norm, at the accept threshold of tol 1e-10,
+    within 2e-5 of the oracle's (measured worst 2.9e-15 and 1.7e-6: the
+    accept/reject decisions are the oracle's)."""
+    rng = np.random.default_rng(6)
+    rows = []
+    for integ in (oracle.RKCK45, oracle.RKDP45):
+        for a in (0.0, 0.5, 0.9, 0.998):
+            r_h = 1.0 + np.sqrt(1.0 - a * a)
+            for _ in range(200):
+                r = np.exp(rng.uniform(np.log(1.1 * r_h), np.log(1000.0)))
+                rows.append([integ, a, 1.0, rng.uniform(-6.0, 6.0), r,
+                             rng.uniform(0.1, np.pi - 0.1), 0.3, -rng.uniform(0.0, 1.0),
+                             3.0 * rng.normal(),
+                             r * np.exp(rng.uniform(np.log(1e-4), np.log(0.05)))])
+    rows = np.array(rows)
+    out = dev("k", rows, 10)
+    n_result = n_threshold = 0
+    for row, o in zip(rows, out):
+        integ, a, E, L, r, th, ph, pr, pth, h = row
+        y6 = np.array([0.0, r, th, ph, pr, pth])
+        y5, d = oracle.rk_step(int(integ), a, y6, E, L, h)
+        scale = 1.0 + np.maximum(np.abs(y6[1:]), np.abs(y5[1:]))
+        errn = np.max(np.abs(d[1:]) / scale)
+        if errn <= 1e-9:
+            n_result += 1
+            assert np.max(np.abs(o[:5] - y5[1:]) / scale) <= 2e-14, (row, o[:5], y5)
+        if 1e-10 <= errn <= 1e-9:
+            n_threshold += 1
+            assert abs(np.max(np.abs(o[5:]) / scale) / errn - 1.0) <= 2e-5, (row, o[5:], d)
+    assert n_result > 800 and n_threshold >= 20
