@@ -19,6 +19,10 @@
 // The six stages run as a loop with one copy of the evaluation of Hamilton's
 // equations (six inlined df64 copies overflow the instruction cache), and
 // every stage sum is kept in registers.
+//
+// The evaluations (Kerr and q-metric) are in rhs_df.cuh, the attempt and its
+// tableaus in step_df.cuh; this file holds the lane state machine, the metric
+// policies and the launchers.
 #include <cuda_runtime.h>
 
 #include "df64.cuh"
