@@ -46,6 +46,7 @@ F_RHS_Q = 60
 SHADOW_BYTES_PER_RAY = 42
 DISK_BYTES_PER_RAY = 66  # + g, intensity, r_hit 3x8
 ORACLE_SAMPLE_STRIDE = 128  # CPU baseline: every 128th pixel of each render
+E2E_STEPS = 5  # end-to-end leg: steps timed with host copies (wall clock)
 # DRAM bytes (read + write) of one FP64 trace launch over the 1024^2 set: ncu
 # capture of the same kernel at 512^2 (2.62 MB read + 90.56 MB written), scaled
 # by the 4x rays (profiles/trace_fp64_persistent_kerr12x512_dram.md).
@@ -136,7 +137,14 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-variants", action="store_true")
-    p.add_argument("--serve-seconds", type=float, default=2.0)
+    p.add_argument("--no-hbar", action="store_true")
+    p.add_argument("--hbar-side", type=int, default=512)
+    p.add_argument("--serve-seconds", type=float, default=60.0)
+    p.add_argument("--serve-rate", type=float, default=50.0)
+    p.add_argument("--serve-baseline-seconds", type=float, default=5.0)
+    p.add_argument("--serve-sustain-rate", default="auto",
+                   help="second stream's arrival rate (renders/s): 'auto' = 85%% of the "
+                        "capacity measured on the first stream; 0 = skip")
     return p.parse_args()
 
 
@@ -303,6 +311,197 @@ def reference_arm(args, renders):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def measure_pipe_peaks(torch, osr, repeats=5):
+    """Rates of the FP64 and FP32 pipes from the library's pipe probes: for
+    each (precision, operation) the best of `repeats` launches that fill every
+    SM, timed with CUDA events. Returns ({"fp64": FMA TFLOP/s, "fp32": FMA
+    TFLOP/s}, details): the FMA rates are the flop peaks (2 operations per
+    instruction), the multiply and add rates show the pipe's instruction rate
+    for the other operations of the kernels."""
+    iters = {osr.FP64: 2048, osr.MIXED: 32768}
+    details = {}
+    for prec, pname in ((osr.FP64, "fp64"), (osr.MIXED, "fp32")):
+        for op, oname in ((osr.PROBE_FMA, "fma"), (osr.PROBE_MUL, "mul"), (osr.PROBE_ADD, "add")):
+            n = osr.pipe_probe_threads(prec, op)
+            out = torch.empty(n, dtype=torch.float64, device="cuda")
+            osr.pipe_probe(prec, op, n, iters[prec], out)
+            torch.cuda.synchronize()
+            best = None
+            for _ in range(repeats):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fl = osr.pipe_probe(prec, op, n, iters[prec], out)
+                e1.record()
+                torch.cuda.synchronize()
+                rate = fl / (e0.elapsed_time(e1) * 1e-3)
+                best = rate if best is None or rate > best else best
+            per_inst = 2.0 if op == osr.PROBE_FMA else 1.0
+            details["%s_%s" % (pname, oname)] = {
+                "tflops": best / 1e12, "warp_inst_per_s": best / per_inst / 32.0,
+                "threads": n}
+    peaks = {"fp64": details["fp64_fma"]["tflops"], "fp32": details["fp32_fma"]["tflops"]}
+    return peaks, details
+
+
+STREAM_LABEL = ("Poisson %g renders/s for %g s (PCG64 seed 5), side log-uniform 64..2048, "
+                "a~U[0,0.998], incl~U[5,85] deg, r_obs=1000, shadow/disk 50/50, "
+                "tol 1e-8/1e-10 50/50")
+
+
+def serve_stream(osr, torch, dist, rank, world, barrier, rate, seconds, phase):
+    """One served stream through the continuous-batching server in DF64
+    (rounds as CUDA-graph launches of batch plans), renders dealt out whole
+    to the GPUs. Returns the merged summary with latency windows."""
+    from paper_2202_00086_gb300 import serve, workloads as wl
+    all_arrivals = wl.served_stream(rate_hz=rate, duration_s=seconds)
+    offered = sum(rd["nx"] * rd["ny"] for _, rd in all_arrivals)
+    arrivals = serve.shard(all_arrivals, rank, world)
+    barrier()
+    srv = serve.RenderServer(precision=osr.DF64, round_rays=1 << 21, cell_phase_deg=phase)
+    summary = srv.run(arrivals, realtime=True)
+    torch.cuda.synchronize()
+    rec = serve.local_record(srv.done, srv.t0)
+    recs = [rec]
+    if dist is not None:
+        recs = [None] * world
+        dist.all_gather_object(recs, rec)
+        summary = dict(serve.merge_records(recs, launches=summary["launches"]),
+                       rejected=summary["rejected"])
+    summary.update(serve.latency_windows(recs, seconds))
+    summary["workload"] = STREAM_LABEL % (rate, seconds)
+    summary["offered_rays_per_s"] = offered / seconds
+    summary["mean_rays_per_render"] = offered / max(1, len(all_arrivals))
+    return summary
+
+
+def serving_leg(args, osr, torch, dist, rank, world, barrier, phase):
+    """The served-stream rows: the stream as specified (Poisson arrivals at
+    --serve-rate for --serve-seconds) through continuous batching in DF64; a
+    second stream at a rate the GPU can sustain (85% of the capacity the
+    first stream measured, rounded down to 5 renders/s) to show bounded p99;
+    and the one-render-per-launch FP64 baseline on the first
+    --serve-baseline-seconds of the first stream."""
+    from paper_2202_00086_gb300 import serve, workloads as wl
+    main = serve_stream(osr, torch, dist, rank, world, barrier, args.serve_rate,
+                        args.serve_seconds, phase)
+    sustained = None
+    if args.serve_sustain_rate != "0":
+        if args.serve_sustain_rate == "auto":
+            cap = main["rays_per_s"] or 0.0
+            rate = 5.0 * int(0.85 * cap / main["mean_rays_per_render"] / 5.0)
+        else:
+            rate = float(args.serve_sustain_rate)
+        if rate > 0:
+            sustained = serve_stream(osr, torch, dist, rank, world, barrier, rate,
+                                     args.serve_seconds, phase)
+            sustained["rate_renders_per_s"] = rate
+            growth = sustained.get("p99_growth")
+            sustained["p99_bounded"] = bool(growth is not None and growth <= 1.5)
+    base_s = min(args.serve_baseline_seconds, args.serve_seconds)
+    first = [x for x in wl.served_stream(rate_hz=args.serve_rate, duration_s=args.serve_seconds)
+             if x[0] < base_s]
+    mine = serve.shard(first, rank, world)
+    barrier()
+    base = serve.run_one_per_launch(mine, precision=osr.FP64, realtime=True,
+                                    cell_phase_deg=phase)
+    if dist is not None:
+        brecs = [None] * world
+        dist.all_gather_object(brecs, base["record"])
+        base = serve.merge_records(brecs, launches=base["launches"])
+    base.pop("record", None)
+    base["workload"] = ("the first %g s of the same stream (%d renders), one plain FP64 "
+                        "launch per render, each waited for" % (base_s, len(first)))
+    return {"continuous_batching_df64": main, "sustained_df64": sustained,
+            "one_render_per_launch_fp64": base,
+            "rays_per_s_ratio": (main["rays_per_s"] / base["rays_per_s"]
+                                 if main["rays_per_s"] and base["rays_per_s"] else None)}
+
+
+def h_distribution(status, max_abs_H, bar=1e-10):
+    """Per-status distribution of the per-ray max |H| (Sec. 3.1, Error =
+    |H_num|): count, p50, p99, max and the share of rays below `bar`."""
+    out = {}
+    for name, code in (("captured", 1), ("escaped", 2), ("disk", 3)):
+        h = max_abs_H[status == code]
+        if h.size == 0:
+            continue
+        out[name] = {"n": int(h.size), "p50": float(np.percentile(h, 50)),
+                     "p99": float(np.percentile(h, 99)), "max": float(h.max()),
+                     "frac_below_bar": float((h < bar).mean())}
+    return out
+
+
+H_BAR = 1e-10  # the |H| bar of the target (Sec. 3.1 reports the error as |H_num|)
+
+
+def h_of_outputs(renders, outs, normalised=True):
+    """Per-status max-|H| distribution over every ray of the renders' device
+    outputs, and (captured rays) the normalised |H| of captured_h_normalised."""
+    st = np.concatenate([o["status"].cpu().numpy() for o in outs])
+    hh = np.concatenate([o["max_abs_H"].cpu().numpy() for o in outs])
+    res = {"by_status": h_distribution(st, hh, H_BAR)}
+    if normalised:
+        parts = [captured_h_normalised(rd, o["status"].cpu().numpy(), o["r"].cpu().numpy(),
+                                       o["theta"].cpu().numpy(), o["max_abs_H"].cpu().numpy())
+                 for rd, o in zip(renders, outs)]
+        v = np.concatenate([x for x in parts if x is not None])
+        if v.size:
+            res["captured_normalised"] = {"p50": float(np.percentile(v, 50)),
+                                          "p99": float(np.percentile(v, 99)),
+                                          "max": float(v.max())}
+    return res
+
+
+def first_tol_meeting(points, bar=H_BAR):
+    """Per integrator, the loosest swept tolerance at which every escaped ray,
+    every captured ray, and every ray keeps max |H| below the bar (None when
+    no swept tolerance does)."""
+    out = {}
+    for iname in sorted({p["integrator"] for p in points}):
+        rows = sorted((p for p in points if p["integrator"] == iname), key=lambda p: -p["tol"])
+        res = {}
+        for cls in ("escaped", "captured", "all"):
+            res[cls] = None
+            for p in rows:
+                bs = p["by_status"]
+                mx = (max(v["max"] for v in bs.values()) if cls == "all"
+                      else bs.get(cls, {"max": 0.0})["max"])
+                if mx < bar:
+                    res[cls] = {"tol": p["tol"], "rays_per_s": p["rays_per_s"]}
+                    break
+        out[iname] = res
+    return out
+
+
+def captured_h_normalised(rd, status, r, theta, max_abs_H):
+    """max |H| of captured rays relative to the size of the terms of 2H at the
+    capture point. With H = N / (2 Sigma), N = Delta p_r^2 + p_theta^2 + W^2
+    - P^2 / Delta and P = (r^2 + a^2) E - a L, the positive terms sum to
+    P^2 / Delta on the constraint surface, so the terms of 2H sum to
+    2 P^2 / (Delta Sigma) and |2H| / sum|terms| = |H| Delta Sigma / P^2.
+    E and L of each pixel are those of the zero-angular-momentum observer
+    of Sec. 2.3 (Kerr metric at the observer)."""
+    cap = status == 1
+    if not cap.any():
+        return None
+    a, r0, th0 = rd["a"], rd["r_obs"], np.radians(rd["incl_deg"])
+    x0, x1, y0, y1 = rd["extent"]
+    nx, ny = rd["nx"], rd["ny"]
+    idx = np.flatnonzero(cap)
+    x = x0 + (idx % nx + 0.5) * (x1 - x0) / nx
+    s2, c2 = np.sin(th0) ** 2, np.cos(th0) ** 2
+    sig0, dlt0 = r0 * r0 + a * a * c2, r0 * r0 - 2 * r0 + a * a
+    g_tph = -2 * a * r0 * s2 / sig0
+    g_pp = s2 * ((r0 * r0 + a * a) ** 2 - a * a * dlt0 * s2) / sig0
+    E = np.sqrt(dlt0 * s2 / g_pp) + x * g_tph / (r0 * np.sqrt(g_pp))
+    L = -x * np.sqrt(g_pp) / r0
+    rr, cc = r[idx], np.cos(theta[idx])
+    sig = rr * rr + a * a * cc * cc
+    dlt = rr * rr - 2 * rr + a * a
+    P = (rr * rr + a * a) * E - a * L
+    return max_abs_H[idx] * dlt * sig / (P * P)
+
+
 def main():
     args = parse()
     renders = workload_renders(args.workload, args.side)
@@ -386,18 +585,9 @@ def main():
         step()
     torch.cuda.synchronize()
 
-    # FP64 / FP32 FMA throughput probe (roofline denominators), same process
-    probe_out = torch.empty(152 * 8 * 256, dtype=torch.float64, device="cuda")
-    peaks = {}
-    for prec, iters, name in ((osr.FP64, 4096, "fp64"), (osr.MIXED, 65536, "fp32")):
-        osr.fma_probe(prec, probe_out.numel(), iters, probe_out)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        fl = sum(osr.fma_probe(prec, probe_out.numel(), iters, probe_out) for _ in range(5))
-        e1.record()
-        torch.cuda.synchronize()
-        peaks[name] = fl / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    # Pipe probes (roofline denominators), same process: 16 independent chains
+    # per thread of one operation, every SM filled with resident blocks
+    peaks, probe = measure_pipe_peaks(torch, osr)
 
     # ---- timed region: K steps, per-step CUDA events, L2 flushed between ----
     clocks = ClockSampler(local)
@@ -425,6 +615,11 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
     s = osr.decode_stats(stats)
+
+    # per-status max |H| of the last timed step (the headline launch itself)
+    hbar = None
+    if not args.no_hbar and args.workload == "kerr" and precision == osr.FP64:
+        hbar = {"bar": H_BAR, "ck45_tol1e-10": h_of_outputs(renders, outs)}
 
     # ---- end to end through the C interface with host buffers ----
     e2e = None
@@ -457,10 +652,12 @@ def main():
                                  **dict(common, workspace=ws_plan))
             e2e_step, e2e_api = (lambda: plan.launch(reqs)), "osiris_batch_plan_launch"
             e2e_step()  # first launch outside the timed region, like the warm-up steps
+        # the same step as the device-timed region, at most E2E_STEPS of them
+        e2e_steps = max(1, min(args.steps, E2E_STEPS))
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for k in range(args.steps):
+        for k in range(e2e_steps):
             e2e_step()
             for n, o, h in zip(sizes, outs, host):
                 osr.copy_outputs_to_host(o, h, n)
@@ -470,8 +667,9 @@ def main():
         if dist is not None:
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         te = float(tt.item())
-        e2e = {"value": world * n_rays * args.steps / te, "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "api": e2e_api}
+        e2e = {"value": world * n_rays * e2e_steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "api": e2e_api,
+               "steps": e2e_steps}
 
     # ---- double-float variant on the same workload (same rules, own timing) ----
     variants = {}
@@ -518,38 +716,44 @@ def main():
                               "locate": vs["root_steps"] / (n_rays * args.steps)},
         }
 
+    # ---- the |H| bar: Dormand-Prince on the same launch, and a tolerance sweep ----
+    if hbar is not None:
+        def one_launch(rds, integrator, tol_):
+            cs = [osr.Camera.from_render(rd) for rd in rds]
+            os_ = [osr.alloc_outputs(c.n_rays) for c in cs]
+            w = torch.empty(osr.workspace_bytes(len(cs)), dtype=torch.uint8, device="cuda")
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            osr.trace_batch([{"camera": c, "out": o} for c, o in zip(cs, os_)], workspace=w,
+                            tol=tol_, integrator=integrator, cell_deg=cell_deg,
+                            cell_phase_deg=cell_phase)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return os_, sum(c.n_rays for c in cs) / (e0.elapsed_time(e1) * 1e-3)
+
+        dp_outs, dp_rate = one_launch(renders, osr.RKDP45, tol)
+        hbar["dp45_tol1e-10"] = h_of_outputs(renders, dp_outs)
+        hbar["dp45_tol1e-10"]["rays_per_s"] = dp_rate
+        del dp_outs
+        side = args.hbar_side
+        small = workloads.kerr_shadow_ring_set(side)
+        sweep = []
+        for integ, iname in ((osr.RKCK45, "ck45"), (osr.RKDP45, "dp45")):
+            for tol_ in (1e-10, 1e-11, 1e-12):
+                o_, rate = one_launch(small, integ, tol_)
+                row = h_of_outputs(small, o_, normalised=False)
+                sweep.append({"integrator": iname, "tol": tol_, "rays_per_s": rate,
+                              "by_status": row["by_status"]})
+        hbar["sweep"] = {"renders": "the same 12 renders at %dx%d" % (side, side),
+                         "points": sweep, "first_tol_meeting_bar": first_tol_meeting(sweep)}
+
     # ---- served render stream: continuous batching (DF64) vs one render per
-    # launch (FP64 plain kernel), same Poisson arrivals ----
+    # launch (FP64 plain kernel), the same Poisson arrivals ----
     serving = None
     if args.serve_seconds > 0 and precision == osr.FP64 and args.workload == "kerr":
-        from paper_2202_00086_gb300 import serve, workloads as wl
-        all_arrivals = wl.served_stream(duration_s=args.serve_seconds)
-        offered = sum(rd["nx"] * rd["ny"] for _, rd in all_arrivals) / args.serve_seconds
-        arrivals = serve.shard(all_arrivals, rank, world)  # whole renders per GPU
-        barrier()
-        srv = serve.RenderServer(precision=osr.DF64, round_rays=1 << 21,
-                                 cell_phase_deg=common["cell_phase_deg"])
-        cb = srv.run(arrivals, realtime=True)
-        torch.cuda.synchronize()
-        cb_rec = serve.local_record(srv.done)
-        barrier()
-        base = serve.run_one_per_launch(arrivals, precision=osr.FP64, realtime=True,
-                                        cell_phase_deg=common["cell_phase_deg"])
-        if dist is not None:
-            recs = [None] * world
-            dist.all_gather_object(recs, cb_rec)
-            cb = serve.merge_records(recs, launches=cb["launches"])
-            brecs = [None] * world
-            dist.all_gather_object(brecs, base["record"])
-            base = serve.merge_records(brecs, launches=base["launches"])
-        base.pop("record", None)
-        serving = {"workload": "Poisson 50 renders/s for %g s (PCG64 seed 5), side log-uniform "
-                               "64..2048, a~U[0,0.998], incl~U[5,85] deg, shadow/disk 50/50, "
-                               "tol 1e-8/1e-10 50/50" % args.serve_seconds,
-                   "offered_rays_per_s": offered,
-                   "continuous_batching_df64": cb, "one_render_per_launch_fp64": base,
-                   "rays_per_s_ratio": (cb["rays_per_s"] / base["rays_per_s"]
-                                        if cb["rays_per_s"] and base["rays_per_s"] else None)}
+        serving = serving_leg(args, osr, torch, dist, rank, world, barrier,
+                              common["cell_phase_deg"])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -593,14 +797,18 @@ def main():
                                  if precision == osr.FP64 and args.side == 1024
                                  and args.kernel == "batch" and args.workload == "kerr"
                                  else None),
-                     "peak_source": "FMA probe measured in this process (FP64 pipe)"
-                                    if precision == osr.FP64 else
-                                    "FMA probe measured in this process (FP32 pipe)",
+                     "peak_source": ("pipe probe measured in this process: FP64 fused "
+                                     "multiply-add, 16 chains per thread, every SM full"
+                                     if precision == osr.FP64 else
+                                     "pipe probe measured in this process: FP32 fused "
+                                     "multiply-add, 16 chains per thread, every SM full"),
                      "flops_per_launch": flops / max(1, kernel_launches),
                      "f_rhs": f_rhs, "f_step": F_STEP},
         "fma_probe_tflops": peaks,
+        "pipe_probes": probe,
         "variants": variants,
         "serving": serving,
+        "hbar": hbar,
         "clocks": clk,
         "gpu_launches": kernel_launches,
         "e2e": e2e,

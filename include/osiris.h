@@ -70,8 +70,14 @@ extern "C" {
 #define OSIRIS_STAT_ROOT_STEPS 3    /* steps spent locating stopping surfaces */
 #define OSIRIS_STAT_RHS_EVALS 4     /* evaluations of Hamilton's equations */
 #define OSIRIS_STAT_STATUS0 5       /* 5..10: rays per status code 0..5 */
-#define OSIRIS_STAT_MAX_ABS_H 11    /* max |H| over all rays, as IEEE-754 bits */
+#define OSIRIS_STAT_MAX_ABS_H 11    /* max |H| over all rays that did not end in
+                                       OSIRIS_STATUS_ERROR, as IEEE-754 bits */
 #define OSIRIS_STAT_FP64_STEPS 12   /* mixed precision: steps taken in FP64 */
+#define OSIRIS_STAT_CHECK_FAILS 13  /* bounds-checked build only: failed index checks */
+#define OSIRIS_STAT_CHECK_WORST 14  /* bounds-checked build only: max over failures of
+                                       (check code << 56) | ray index; codes 1 ray index
+                                       outside the launch, 2 request index, 3 ray outside
+                                       its request's range, 4 pixel / state index */
 #define OSIRIS_STATS_LEN 16
 
 /* Opaque camera: space-time, observer and image plane. Host memory only. */
@@ -338,14 +344,40 @@ double osiris_isco(double a);
 /* Horizon radius r_H = 1 + sqrt(1 - a^2) (Sec. 4.3). Host-only. */
 double osiris_horizon(double a);
 
-/* Throughput probe for the roofline denominators: launches one kernel of
- * n_threads threads, each running 8 independent fused multiply-add chains
- * of `iters` iterations in FP64 (precision = OSIRIS_FP64) or FP32
- * (OSIRIS_MIXED), and stores one value per thread in dev_out (DEVICE,
- * n_threads doubles). *flops receives the floating-point operations of the
- * launch (2 per FMA). n_threads must be a multiple of 256. */
+/* Throughput probes for the roofline denominators (the trace kernels are
+ * bound by the FP64 pipe, and the double-float kernels by the FP32 pipe; the
+ * paper has no counterpart). osiris_pipe_probe launches one kernel of
+ * n_threads threads (256 per block), each running 16 independent chains of
+ * `iters` x 4 operations of one kind:
+ *   op 0  fused multiply-add a = a b + c (2 floating-point operations)
+ *   op 1  multiply a = a b (1)
+ *   op 2  add a = a + c (1)
+ *   op 3  the multiply written as a fused multiply-add with a zero addend (1)
+ *   op 4  the add written as a fused multiply-add by one (1)
+ * in FP64 (precision = OSIRIS_FP64) or FP32 (OSIRIS_MIXED), and stores one
+ * value per thread in dev_out (DEVICE, n_threads doubles). *flops receives
+ * the floating-point operations of the launch. n_threads must be a positive
+ * multiple of 256; osiris_pipe_probe_threads gives the count that fills
+ * every SM of the current device with resident blocks (SMs x resident
+ * blocks x 256), or a negative error code. Time the launch with events on
+ * the stream. */
+int osiris_pipe_probe(int32_t precision, int32_t op, int64_t n_threads, int32_t iters,
+                      double* dev_out, double* flops, void* cuda_stream);
+int64_t osiris_pipe_probe_threads(int32_t precision, int32_t op);
+
+/* osiris_pipe_probe with op 0 (fused multiply-add). */
 int osiris_fma_probe(int32_t precision, int64_t n_threads, int32_t iters, double* dev_out,
                      double* flops, void* cuda_stream);
+
+/* Bounded host wait for the work queued on a stream (the calls above are
+ * asynchronous): polls the stream until it is idle or timeout_s seconds
+ * (>= 0, finite) have passed. Returns OSIRIS_OK when the work is complete,
+ * OSIRIS_ETIMEOUT when the bound ran out first (the work stays queued and
+ * the call may be repeated), OSIRIS_ECUDA when the stream reports an error,
+ * OSIRIS_EINVAL for a negative or non-finite bound. Polls every ~50 us. The
+ * paper has no counterpart: it exists so that a request loop never blocks
+ * without a bound. */
+int osiris_stream_wait(void* cuda_stream, double timeout_s);
 
 /* Human-readable text for a return code. */
 const char* osiris_strerror(int code);

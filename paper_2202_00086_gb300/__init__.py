@@ -60,6 +60,8 @@ class Request(ctypes.Structure):
                 ("n_rays", ctypes.c_int64), ("l0", _d)]
 
 
+LIB_CHECKED_PATH = os.path.join(_HERE, "_build", "libosiris_checked.so")
+
 _lib = None
 
 
@@ -67,44 +69,76 @@ def lib():
     """The loaded libosiris.so. Raises if it has not been built."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libosiris.so is not built (%s); run "
-                               "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
-        L = ctypes.CDLL(LIB_PATH)
-        L.osiris_default_opts.argtypes = [_P(TraceOpts)]
-        L.osiris_init_camera.argtypes = [_P(_vp), _d, _d, _d, _d, _d, _d, _d, ctypes.c_int32,
-                                         ctypes.c_int32]
-        L.osiris_init_camera_q.argtypes = [_P(_vp), _d, _d, _d, _d, _d, _d, _d, ctypes.c_int32,
-                                           ctypes.c_int32]
-        L.osiris_trace_states_ex.argtypes = [ctypes.c_int32, _d, _d, _d, _vp, _vp, _vp,
-                                             ctypes.c_int64, ctypes.c_int32, _d, _d,
-                                             _P(TraceOpts), _P(Outputs), _vp]
-        L.osiris_destroy_camera.argtypes = [_vp]
-        L.osiris_camera_rays.argtypes = [_vp]
-        L.osiris_camera_rays.restype = ctypes.c_int64
-        L.osiris_trace.argtypes = [_vp, _P(TraceOpts), _P(Outputs), _vp]
-        L.osiris_render_disk.argtypes = [_vp, _d, _d, _P(TraceOpts), _P(Outputs), _vp]
-        L.osiris_render_disk_l0.argtypes = [_vp, _d, _d, _d, _P(TraceOpts), _P(Outputs), _vp]
-        L.osiris_workspace_bytes.argtypes = [ctypes.c_int32]
-        L.osiris_workspace_bytes.restype = ctypes.c_size_t
-        L.osiris_trace_batch.argtypes = [_P(Request), ctypes.c_int32, _P(TraceOpts), _vp]
-        L.osiris_batch_plan_create.argtypes = [_P(_vp), ctypes.c_int32, ctypes.c_int32,
-                                               _P(TraceOpts)]
-        L.osiris_batch_plan_launch.argtypes = [_vp, _P(Request), ctypes.c_int32, _vp]
-        L.osiris_batch_plan_destroy.argtypes = [_vp]
-        L.osiris_trace_states.argtypes = [_d, _d, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32,
-                                          _d, _d, _P(TraceOpts), _P(Outputs), _vp]
-        L.osiris_copy_outputs_to_host.argtypes = [_P(Outputs), _P(Outputs), ctypes.c_int64, _vp]
-        L.osiris_isco.argtypes = [_d]
-        L.osiris_isco.restype = _d
-        L.osiris_horizon.argtypes = [_d]
-        L.osiris_horizon.restype = _d
-        L.osiris_fma_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _vp,
-                                       _P(_d), _vp]
-        L.osiris_strerror.argtypes = [ctypes.c_int]
-        L.osiris_strerror.restype = ctypes.c_char_p
-        _lib = L
+        _lib = load(LIB_PATH)
     return _lib
+
+
+def load(path):
+    """Load one build of the library (libosiris.so, or its bounds-checked twin
+    libosiris_checked.so) with the argument types of every entry point."""
+    if not os.path.exists(path):
+        raise RuntimeError("%s is not built; run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+    L = ctypes.CDLL(path)
+    L.osiris_default_opts.argtypes = [_P(TraceOpts)]
+    L.osiris_init_camera.argtypes = [_P(_vp), _d, _d, _d, _d, _d, _d, _d, ctypes.c_int32,
+                                     ctypes.c_int32]
+    L.osiris_init_camera_q.argtypes = [_P(_vp), _d, _d, _d, _d, _d, _d, _d, ctypes.c_int32,
+                                       ctypes.c_int32]
+    L.osiris_trace_states_ex.argtypes = [ctypes.c_int32, _d, _d, _d, _vp, _vp, _vp,
+                                         ctypes.c_int64, ctypes.c_int32, _d, _d,
+                                         _P(TraceOpts), _P(Outputs), _vp]
+    L.osiris_destroy_camera.argtypes = [_vp]
+    L.osiris_camera_rays.argtypes = [_vp]
+    L.osiris_camera_rays.restype = ctypes.c_int64
+    L.osiris_trace.argtypes = [_vp, _P(TraceOpts), _P(Outputs), _vp]
+    L.osiris_render_disk.argtypes = [_vp, _d, _d, _P(TraceOpts), _P(Outputs), _vp]
+    L.osiris_render_disk_l0.argtypes = [_vp, _d, _d, _d, _P(TraceOpts), _P(Outputs), _vp]
+    L.osiris_workspace_bytes.argtypes = [ctypes.c_int32]
+    L.osiris_workspace_bytes.restype = ctypes.c_size_t
+    L.osiris_trace_batch.argtypes = [_P(Request), ctypes.c_int32, _P(TraceOpts), _vp]
+    L.osiris_batch_plan_create.argtypes = [_P(_vp), ctypes.c_int32, ctypes.c_int32,
+                                           _P(TraceOpts)]
+    L.osiris_batch_plan_launch.argtypes = [_vp, _P(Request), ctypes.c_int32, _vp]
+    L.osiris_batch_plan_destroy.argtypes = [_vp]
+    L.osiris_trace_states.argtypes = [_d, _d, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32,
+                                      _d, _d, _P(TraceOpts), _P(Outputs), _vp]
+    L.osiris_copy_outputs_to_host.argtypes = [_P(Outputs), _P(Outputs), ctypes.c_int64, _vp]
+    L.osiris_isco.argtypes = [_d]
+    L.osiris_isco.restype = _d
+    L.osiris_horizon.argtypes = [_d]
+    L.osiris_horizon.restype = _d
+    L.osiris_fma_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _vp,
+                                   _P(_d), _vp]
+    L.osiris_pipe_probe.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                    ctypes.c_int32, _vp, _P(_d), _vp]
+    L.osiris_pipe_probe_threads.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    L.osiris_pipe_probe_threads.restype = ctypes.c_int64
+    L.osiris_strerror.argtypes = [ctypes.c_int]
+    L.osiris_strerror.restype = ctypes.c_char_p
+    L.osiris_stream_wait.argtypes = [_vp, _d]
+    return L
+
+
+class using_library:
+    """Context manager: route every call of this module through another
+    loaded build (e.g. load(LIB_CHECKED_PATH)) and restore the default after.
+    Cameras must be created inside the block (their handles belong to the
+    build that made them)."""
+
+    def __init__(self, L):
+        self.L = L
+
+    def __enter__(self):
+        global _lib
+        self.prev = lib()
+        _lib = self.L
+        return self.L
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.prev
+        return False
 
 
 class OsirisError(RuntimeError):
@@ -346,6 +380,16 @@ def trace_states(a, r_obs, states, E, L, out=None, disk=False, r_in=0.0, r_out=0
     return out
 
 
+def stream_wait(timeout_s, stream=None):
+    """Bounded wait for the work queued on the stream (osiris_stream_wait):
+    returns OK when it is complete or ETIMEOUT when timeout_s ran out first;
+    raises on a stream error."""
+    rc = lib().osiris_stream_wait(_stream_handle(stream), float(timeout_s))
+    if rc not in (OK, ETIMEOUT):
+        _check(rc, "osiris_stream_wait")
+    return rc
+
+
 def copy_outputs_to_host(dev, host, n, stream=None):
     """Asynchronous device-to-host copy of every field present in both dicts."""
     d = outputs_struct(dev)
@@ -362,6 +406,27 @@ def isco(a):
 
 def horizon(a):
     return float(lib().osiris_horizon(float(a)))
+
+
+PROBE_FMA, PROBE_MUL, PROBE_ADD, PROBE_MUL_AS_FMA, PROBE_ADD_AS_FMA = 0, 1, 2, 3, 4
+
+
+def pipe_probe_threads(precision, op=PROBE_FMA):
+    """Threads that fill every SM of the current device with resident probe
+    blocks (osiris_pipe_probe_threads)."""
+    n = int(lib().osiris_pipe_probe_threads(int(precision), int(op)))
+    _check(min(n, 0), "osiris_pipe_probe_threads")
+    return n
+
+
+def pipe_probe(precision, op, n_threads, iters, out, stream=None):
+    """Launch one pipe probe (osiris_pipe_probe); returns the launch's
+    floating-point operation count."""
+    fl = _d()
+    _check(lib().osiris_pipe_probe(int(precision), int(op), int(n_threads), int(iters),
+                                   out.data_ptr(), ctypes.byref(fl), _stream_handle(stream)),
+           "osiris_pipe_probe")
+    return fl.value
 
 
 def fma_probe(precision, n_threads, iters, out, stream=None):

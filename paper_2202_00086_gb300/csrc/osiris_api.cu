@@ -4,9 +4,11 @@
 // the caller.
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <new>
 #include <vector>
 
@@ -481,13 +483,46 @@ double osiris_isco(double a) {
 
 double osiris_horizon(double a) { return horizon(a); }
 
-int osiris_fma_probe(int32_t precision, int64_t n_threads, int32_t iters, double* dev_out,
-                     double* flops, void* cuda_stream) {
+int osiris_pipe_probe(int32_t precision, int32_t op, int64_t n_threads, int32_t iters,
+                      double* dev_out, double* flops, void* cuda_stream) {
   if (!dev_out || n_threads < 256 || n_threads % 256 != 0 || iters < 1) return OSIRIS_EINVAL;
   if (n_threads / 256 > 0x7fffffff) return OSIRIS_EINVAL;
   if (precision != OSIRIS_FP64 && precision != OSIRIS_MIXED) return OSIRIS_EINVAL;
-  if (flops) *flops = 2.0 * 8.0 * static_cast<double>(iters) * static_cast<double>(n_threads);
-  return cuda_rc(osiris_impl::launch_fma_probe(precision, n_threads, iters, dev_out, cuda_stream));
+  if (op < 0 || op >= osiris_impl::kProbeOps) return OSIRIS_EINVAL;
+  if (flops)
+    *flops = (op == 0 ? 2.0 : 1.0) * osiris_impl::kProbeFlopsPerThreadIter *
+             static_cast<double>(iters) * static_cast<double>(n_threads);
+  return cuda_rc(
+      osiris_impl::launch_pipe_probe(precision, op, n_threads, iters, dev_out, cuda_stream));
+}
+
+int64_t osiris_pipe_probe_threads(int32_t precision, int32_t op) {
+  if (precision != OSIRIS_FP64 && precision != OSIRIS_MIXED) return OSIRIS_EINVAL;
+  if (op < 0 || op >= osiris_impl::kProbeOps) return OSIRIS_EINVAL;
+  int sms = 0, per_sm = 0;
+  if (sm_count(&sms) != OSIRIS_OK) return OSIRIS_ECUDA;
+  if (osiris_impl::probe_resident_blocks(precision, op, &per_sm) != 0 || per_sm < 1)
+    return OSIRIS_ECUDA;
+  return static_cast<int64_t>(sms) * per_sm * 256;
+}
+
+int osiris_fma_probe(int32_t precision, int64_t n_threads, int32_t iters, double* dev_out,
+                     double* flops, void* cuda_stream) {
+  return osiris_pipe_probe(precision, 0, n_threads, iters, dev_out, flops, cuda_stream);
+}
+
+int osiris_stream_wait(void* cuda_stream, double timeout_s) {
+  if (!is_fin(timeout_s) || timeout_s < 0.0) return OSIRIS_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaStreamQuery(s);
+    if (e == cudaSuccess) return OSIRIS_OK;
+    if (e != cudaErrorNotReady) return OSIRIS_ECUDA;
+    const std::chrono::duration<double> dt = std::chrono::steady_clock::now() - t0;
+    if (dt.count() >= timeout_s) return OSIRIS_ETIMEOUT;
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
 }
 
 const char* osiris_strerror(int code) {

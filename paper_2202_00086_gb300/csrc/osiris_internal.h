@@ -72,6 +72,13 @@ int launch_trace_df64(const KernelArgs& args, Kernel kind, int integrator, int g
 int occupancy_fp64(Kernel kind, int integrator, int spacetime, int block, int* blocks_per_sm);
 int occupancy_mixed(Kernel kind, int integrator, int spacetime, int block, int* blocks_per_sm);
 int occupancy_df64(Kernel kind, int integrator, int spacetime, int block, int* blocks_per_sm);
-int launch_fma_probe(int precision, int64_t n_threads, int iters, double* out, void* stream);
+// Pipe probes (roofline denominators): 16 chains per thread of one
+// operation (0 FMA, 1 multiply, 2 add, 3 multiply as FMA, 4 add as FMA),
+// 256 threads per block.
+constexpr int kProbeOps = 5;
+constexpr int kProbeFlopsPerThreadIter = 16 * 4;  // operations per thread per loop trip
+int launch_pipe_probe(int precision, int op, int64_t n_threads, int iters, double* out,
+                      void* stream);
+int probe_resident_blocks(int precision, int op, int* blocks_per_sm);
 
 }  // namespace osiris_impl

@@ -181,6 +181,39 @@ __device__ __forceinline__ void sincos_tab(double th, double& s, double& c) {
   c = fma(-sc.x, sx, fma(sc.y, cm, sc.y));
 }
 
+// a b and a + c issued as fused multiply-adds: fma(a, b, -0) = a b and
+// fma(a, 1, c) = a + c exactly (one rounding each, the same result bit for
+// bit, signed zeros included). The -0 and 1 come from constant memory, whose
+// values no compiler pass may assume, so the instruction stays a fused
+// multiply-add instead of being folded back into a multiply or an add.
+#ifdef __CUDACC__
+static __constant__ double kFmaNegZero = -0.0;
+static __constant__ double kFmaOne = 1.0;
+#endif
+
+__device__ __forceinline__ double mul_as_fma(double a, double b) {
+#ifdef __CUDA_ARCH__
+  double r;
+  asm("fma.rn.f64 %0, %1, %2, %3;" : "=d"(r) : "d"(a), "d"(b), "d"(kFmaNegZero));
+  return r;
+#else
+  return a * b;
+#endif
+}
+
+__device__ __forceinline__ double add_as_fma(double a, double c) {
+#ifdef __CUDA_ARCH__
+  double r;
+  asm("fma.rn.f64 %0, %1, %2, %3;" : "=d"(r) : "d"(a), "d"(kFmaOne), "d"(c));
+  return r;
+#else
+  return a + c;
+#endif
+}
+
+__device__ __forceinline__ float mul_as_fma(float a, float b) { return a * b; }
+__device__ __forceinline__ float add_as_fma(float a, float c) { return a + c; }
+
 // A normal FP32 value as a double, by integer operations only.
 __device__ __forceinline__ double float_to_double(float f) {
   const unsigned b = __float_as_uint(f);

@@ -152,7 +152,7 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
 
   auto start_ray = [&](int64_t g) {
     State y0;
-    load_ray(A, g, I, y0);
+    if (!load_ray(A, g, I, y0)) return;  // checked build: index check failed
     LC.reset();
     y = to_df(y0);
     KD = Met::ray(I.K);

@@ -101,26 +101,88 @@ int occupancy_fp64(Kernel kind, int integrator, int spacetime, int block, int* b
       blocks_per_sm, select_fp64(kind, integrator, spacetime), block, 0);
 }
 
-// Roofline probe: 8 independent FMA chains per thread.
-template <typename T>
-__global__ void __launch_bounds__(256) fma_probe_kernel(double* out, T b, T c, int iters) {
-  T a0 = (T)threadIdx.x * (T)1e-3, a1 = a0 + (T)1, a2 = a0 + (T)2, a3 = a0 + (T)3;
-  T a4 = a0 + (T)4, a5 = a0 + (T)5, a6 = a0 + (T)6, a7 = a0 + (T)7;
-  for (int i = 0; i < iters; ++i) {
-    a0 = fma(a0, b, c); a1 = fma(a1, b, c); a2 = fma(a2, b, c); a3 = fma(a3, b, c);
-    a4 = fma(a4, b, c); a5 = fma(a5, b, c); a6 = fma(a6, b, c); a7 = fma(a7, b, c);
-  }
-  out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = (double)(a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7);
+// Roofline probes: kProbeChains independent chains of one arithmetic
+// operation per thread (OP 0: fused multiply-add a = a b + c, 1: multiply
+// a = a b, 2: add a = a + c, 3: the multiply issued as a fused multiply-add
+// with a zero addend, 4: the add issued as a fused multiply-add by one), the
+// chain step unrolled so that each loop trip
+// issues 4 kProbeChains operations back to back. The operands b and c are
+// per-thread values, so the compiler cannot hoist or fold them. This
+// translation unit is compiled with contraction off, so a multiply or an add
+// stays one instruction of the pipe under test.
+constexpr int kProbeChains = 16;
+constexpr int kProbeBlock = 256;
+
+template <typename T, int OP>
+__device__ __forceinline__ T probe_op(T a, T b, T c) {
+  if (OP == 0) return fma(a, b, c);
+  if (OP == 1) return a * b;
+  if (OP == 2) return a + c;
+  if (OP == 3) return mul_as_fma(a, b);
+  return add_as_fma(a, c);
 }
 
-int launch_fma_probe(int precision, int64_t n_threads, int iters, double* out, void* stream) {
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int grid = (int)(n_threads / 256);
-  if (precision == OSIRIS_FP64)
-    fma_probe_kernel<double><<<grid, 256, 0, s>>>(out, 0.999999, 1e-7, iters);
-  else
-    fma_probe_kernel<float><<<grid, 256, 0, s>>>(out, 0.999999f, 1e-7f, iters);
+template <typename T, int OP>
+__global__ void __launch_bounds__(kProbeBlock) pipe_probe_kernel(double* out, T b0, T c0,
+                                                                 int iters) {
+  const T t = (T)threadIdx.x * (T)1e-6;
+  const T b = b0 + t * (T)1e-3, c = c0 + t;
+  T a[kProbeChains];
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) a[k] = t + (T)k;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int k = 0; k < kProbeChains; ++k) a[k] = probe_op<T, OP>(a[k], b, c);
+  }
+  T sum = (T)0;
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) sum += a[k];
+  out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = (double)sum;
+}
+
+template <typename T, int OP>
+static int launch_probe_t(int64_t n_threads, int iters, double* out, cudaStream_t s) {
+  const int grid = (int)(n_threads / kProbeBlock);
+  const T b = (T)0.999999, c = (T)1e-7;
+  pipe_probe_kernel<T, OP><<<grid, kProbeBlock, 0, s>>>(out, b, c, iters);
   return (int)cudaGetLastError();
+}
+
+template <typename T>
+static const void* probe_kernel_t(int op) {
+  switch (op) {
+    case 0: return (const void*)pipe_probe_kernel<T, 0>;
+    case 1: return (const void*)pipe_probe_kernel<T, 1>;
+    case 2: return (const void*)pipe_probe_kernel<T, 2>;
+    case 3: return (const void*)pipe_probe_kernel<T, 3>;
+    default: return (const void*)pipe_probe_kernel<T, 4>;
+  }
+}
+
+template <typename T>
+static int launch_probe_op(int op, int64_t n_threads, int iters, double* out, cudaStream_t s) {
+  switch (op) {
+    case 0: return launch_probe_t<T, 0>(n_threads, iters, out, s);
+    case 1: return launch_probe_t<T, 1>(n_threads, iters, out, s);
+    case 2: return launch_probe_t<T, 2>(n_threads, iters, out, s);
+    case 3: return launch_probe_t<T, 3>(n_threads, iters, out, s);
+    default: return launch_probe_t<T, 4>(n_threads, iters, out, s);
+  }
+}
+
+int launch_pipe_probe(int precision, int op, int64_t n_threads, int iters, double* out,
+                      void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return precision == OSIRIS_FP64 ? launch_probe_op<double>(op, n_threads, iters, out, s)
+                                  : launch_probe_op<float>(op, n_threads, iters, out, s);
+}
+
+int probe_resident_blocks(int precision, int op, int* blocks_per_sm) {
+  const void* fn = precision == OSIRIS_FP64 ? probe_kernel_t<double>(op)
+                                            : probe_kernel_t<float>(op);
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kProbeBlock, 0);
 }
 
 }  // namespace osiris_impl

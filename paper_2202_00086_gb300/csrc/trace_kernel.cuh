@@ -12,6 +12,7 @@
 //   Stepper::twoH(K, y)                       -> 2H at a state (FP64)
 #pragma once
 
+#include "checked.cuh"
 #include "trace_device.cuh"
 
 namespace osiris_impl {
@@ -27,13 +28,39 @@ struct RayInfo {
   int64_t max_steps;
 };
 
+#ifdef OSIRIS_CHECKED
+// Count a failed index check in the caller's stats (checked build only).
+__device__ __forceinline__ void record_check_failure(const KernelArgs& A, unsigned code,
+                                                     int64_t g) {
+  if (A.stats == nullptr) return;
+  atomicAdd(A.stats + OSIRIS_STAT_CHECK_FAILS, 1ull);
+  atomicMax(A.stats + OSIRIS_STAT_CHECK_WORST, check_word(code, g));
+}
+#endif
+
 // Ray g of the launch: its request, constants and initial state (Sec. 2.3,
 // Eq. momentums: pixel centre -> p_theta, L, E, p_r at t = 0, r = r0,
 // theta = theta0, phi = 0; or explicit initial data for the test hook).
-__device__ __forceinline__ void load_ray(const KernelArgs& A, int64_t g, RayInfo& I, State& y) {
+// Returns false (checked build only) when an index check fails: nothing of
+// the ray has been read and the lane must not start it.
+__device__ __forceinline__ bool load_ray(const KernelArgs& A, int64_t g, RayInfo& I, State& y) {
   I.req = find_request(A, g);
+#ifdef OSIRIS_CHECKED
+  if (const unsigned code = check_ray_request(g, A.total_rays, I.req, A.reqs ? A.n_req : 1)) {
+    record_check_failure(A, code, g);
+    return false;
+  }
+#endif
   const ReqDev* R = request_of(A, I.req);
   I.local = g - R->ray_begin + R->pixel_offset;
+#ifdef OSIRIS_CHECKED
+  const int64_t limit =
+      R->explicit_states ? R->pixel_offset + R->n_rays : (int64_t)R->nx * (int64_t)R->ny;
+  if (const unsigned code = check_ray_pixel(g, R->ray_begin, R->n_rays, I.local, limit)) {
+    record_check_failure(A, code, g);
+    return false;
+  }
+#endif
   const double a = R->a;
   I.K.a = a;
   I.K.a2 = a * a;
@@ -73,6 +100,7 @@ __device__ __forceinline__ void load_ray(const KernelArgs& A, int64_t g, RayInfo
   I.tol = R->tol;
   I.max_steps = R->max_steps;
   I.h0 = R->h0;
+  return true;
 }
 
 // Write the outputs of a finished ray (terminal state f, final max |H|) and
@@ -137,7 +165,8 @@ __device__ __forceinline__ void write_outputs(const KernelArgs& A, const RayInfo
   S.status[status] += 1;
   S.acc += n_acc;
   S.rej += n_rej;
-  S.max_abs_H = fmax(S.max_abs_H, max_abs_H);
+  // a ray that ended on a non-finite state may have tracked an infinite |H|
+  if (status != OSIRIS_STATUS_ERROR) S.max_abs_H = fmax(S.max_abs_H, max_abs_H);
 }
 
 // Take the next rays of a persistent grid from the device queue for every
@@ -191,7 +220,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
   State yF, yE;  // state at the upper bracket end; end of the accepted step
 
   auto start_ray = [&](int64_t g) {
-    load_ray(A, g, I, y);
+    if (!load_ray(A, g, I, y)) return;  // checked build: index check failed
     tol32 = (float)I.tol;
     Stepper::prepare(K, RC);
     Stepper::reset(LC);

@@ -27,6 +27,20 @@ then the rest of the round budget goes to the oldest of them. Rays are independe
 render's outputs are the same whether it runs alone or in a mix (the GPU
 tests check this bitwise).
 
+Failure handling (all on the host; nothing waits on the GPU without a
+bound):
+  - cancel(render): a waiting render is dropped at once; an active one gets no
+    further pixel ranges and is retired as cancelled when the ranges already
+    launched complete (its outputs are then partial and released);
+  - a round that has not completed `stall_timeout_s` after its launch stops
+    the server: its renders are retired as timed out (OSIRIS_ETIMEOUT), the
+    other active and waiting renders as abandoned, and nothing more is
+    launched; run() returns with the status in its summary. The GPU work
+    already queued is not recalled (a kernel cannot be interrupted): the
+    server keeps its buffers until close() has waited for the stream;
+  - wait(render, timeout_s) steps the server until the render is retired or
+    the bound runs out, and returns OSIRIS_OK or OSIRIS_ETIMEOUT.
+
 The scheduler is host code; every ray is traced by the CUDA kernels of the
 library. For tests without a GPU the launch, allocation and event functions
 can be replaced.
@@ -40,10 +54,15 @@ SHADOW_BYTES_PER_RAY = 42  # status 1, r/theta/phi/max|H| 32, steps 4, cells 4, 
 DISK_BYTES_PER_RAY = 66    # + g, intensity, r_hit
 
 
+# render states
+WAITING, ACTIVE, DONE, REJECTED, CANCELLED, TIMED_OUT, ABANDONED = (
+    "waiting", "active", "done", "rejected", "cancelled", "timed_out", "abandoned")
+
+
 class ServedRender:
     __slots__ = ("rid", "render", "arrival", "camera", "disk", "r_in", "r_out", "tol",
                  "n_rays", "next_ray", "rays_done", "out", "bytes", "t_submit", "t_admit",
-                 "t_done", "chunks", "kind")
+                 "t_done", "chunks", "kind", "state", "launched")
 
     def __init__(self, rid, render, arrival):
         self.rid = rid
@@ -61,6 +80,8 @@ class ServedRender:
         self.t_submit = self.t_admit = self.t_done = None
         self.chunks = []  # (first_ray, n_rays) in launch order
         self.kind = None  # (space-time, precision) of the launches that trace it
+        self.state = WAITING
+        self.launched = None  # rays launched when it was cancelled
 
 
 class _Round:
@@ -77,7 +98,7 @@ class RenderServer:
     def __init__(self, precision=None, round_rays=1 << 21, min_chunk=1 << 14,
                  hbm_budget_bytes=8 << 30, max_inflight=2, max_entries=4096,
                  keep_outputs=False, cell_deg=10.0, cell_phase_deg=0.0, backend=None,
-                 clock=time.perf_counter, graphs=True):
+                 clock=time.perf_counter, graphs=True, stall_timeout_s=None):
         import paper_2202_00086_gb300 as osr
         self.osr = osr
         self.precision = osr.DF64 if precision is None else precision
@@ -96,6 +117,10 @@ class RenderServer:
         self.inflight = collections.deque()
         self.done = []
         self.rejected = []
+        self.cancelled = []
+        self.failed = []  # timed out or abandoned after a stalled round
+        self.stall_timeout_s = stall_timeout_s
+        self.status = osr.OK
         self.bytes_in_use = 0
         self.rounds = 0
         self.launches = 0
@@ -132,11 +157,41 @@ class RenderServer:
         r.kind = kind
         self._next_id += 1
         r.t_submit = now
-        if r.bytes > self.hbm_budget:
+        if r.bytes > self.hbm_budget or self.status != osr.OK:
+            r.state = REJECTED
             self.rejected.append(r)
             return r
         self.waiting.append(r)
         return r
+
+    def cancel(self, r):
+        """Cancel a submitted render. Returns True if it was waiting or
+        active (it is then retired as cancelled, at once or when its
+        launched pixel ranges complete), False if it had already left."""
+        if r.state == WAITING:
+            self.waiting.remove(r)
+            r.state = CANCELLED
+            r.t_done = self.clock()
+            self.cancelled.append(r)
+            return True
+        if r.state != ACTIVE or r.launched is not None:
+            return False
+        r.launched = r.next_ray
+        r.next_ray = r.n_rays  # no further pixel ranges
+        if r.rays_done == r.launched:
+            self._retire(r, CANCELLED, self.clock())
+        return True
+
+    def _retire(self, r, state, now):
+        r.state = state
+        r.t_done = now
+        self.active.remove(r)
+        self.bytes_in_use -= r.bytes
+        (self.done if state == DONE else
+         self.cancelled if state == CANCELLED else self.failed).append(r)
+        if not self.keep_outputs or state != DONE:
+            r.out = None
+            r.camera = None
 
     def _admit(self):
         while self.waiting and self.bytes_in_use + self.waiting[0].bytes <= self.hbm_budget:
@@ -149,6 +204,7 @@ class RenderServer:
             r.out = self.backend.outputs(r.n_rays, r.disk)
             self.bytes_in_use += r.bytes
             r.t_admit = self.clock()
+            r.state = ACTIVE
             self.active.append(r)
 
     # ---- rounds ----
@@ -231,21 +287,39 @@ class RenderServer:
             self._ws_free.append(rnd.ws_index)
             for r, first, n in rnd.parts:
                 r.rays_done += n
-                if r.rays_done == r.n_rays:
-                    r.t_done = now
-                    self.active.remove(r)
-                    self.done.append(r)
-                    self.bytes_in_use -= r.bytes
-                    if not self.keep_outputs:
-                        r.out = None
-                        r.camera = None
+                if r.launched is not None:
+                    if r.rays_done == r.launched:
+                        self._retire(r, CANCELLED, now)
+                elif r.rays_done == r.n_rays:
+                    self._retire(r, DONE, now)
+            progressed = True
+        if (self.inflight and self.stall_timeout_s is not None
+                and self.clock() - self.inflight[0].t_launch > self.stall_timeout_s):
+            self._stall()
             progressed = True
         return progressed
 
+    def _stall(self):
+        """The oldest round missed its bound: retire its renders as timed out,
+        every other render as abandoned, and launch nothing more."""
+        now = self.clock()
+        self.status = self.osr.ETIMEOUT
+        stalled = {id(r) for r, _, _ in self.inflight[0].parts}
+        for r in list(self.active):
+            self._retire(r, TIMED_OUT if id(r) in stalled else ABANDONED, now)
+        while self.waiting:
+            r = self.waiting.popleft()
+            r.state = ABANDONED
+            r.t_done = now
+            self.failed.append(r)
+
     def step(self):
         """Admit, launch while fewer than max_inflight rounds are queued, and
-        retire finished rounds. Returns True when anything happened."""
+        retire finished rounds. Returns True when anything happened. After a
+        stalled round (status OSIRIS_ETIMEOUT) it launches nothing."""
         progressed = self._poll()
+        if self.status != self.osr.OK:
+            return progressed
         self._admit()
         while len(self.inflight) < self.max_inflight and self._ws_free:
             if not self._launch():
@@ -254,23 +328,56 @@ class RenderServer:
         return progressed
 
     def idle(self):
+        if self.status != self.osr.OK:
+            return True
         return not (self.waiting or self.active or self.inflight)
+
+    def wait(self, r, timeout_s, poll_s=2e-4):
+        """Step the server until render r has left (done, cancelled or
+        failed) or timeout_s has passed. Returns OSIRIS_OK or OSIRIS_ETIMEOUT
+        (the render then stays queued or in flight)."""
+        t0 = self.clock()
+        while r.state in (WAITING, ACTIVE):
+            if self.clock() - t0 > timeout_s:
+                return self.osr.ETIMEOUT
+            if not self.step() and poll_s:
+                time.sleep(poll_s)
+        return self.osr.ETIMEOUT if r.state in (TIMED_OUT, ABANDONED) else self.osr.OK
+
+    def close(self, timeout_s=None):
+        """Wait (bounded when timeout_s is given) for every launched round;
+        returns OSIRIS_OK or OSIRIS_ETIMEOUT."""
+        t0 = self.clock()
+        while self.inflight:
+            if self.inflight[0].event.query():
+                self.inflight.popleft()
+                continue
+            if timeout_s is not None and self.clock() - t0 > timeout_s:
+                return self.osr.ETIMEOUT
+            time.sleep(2e-4)
+        return self.osr.OK
 
     def run(self, arrivals, realtime=True, poll_s=2e-4):
         """Serve a list of (arrival_time_s, render). With realtime, each
         render is submitted when the wall clock reaches its arrival time
-        (measured from the call); otherwise all are submitted at once."""
+        (measured from the call); otherwise all are submitted at once. Stops
+        early when a round stalls (summary "status" OSIRIS_ETIMEOUT)."""
         t0 = self.clock()
+        self.t0 = t0
         pending = collections.deque(sorted(arrivals, key=lambda x: x[0]))
-        while pending or not self.idle():
+        while (pending or not self.idle()) and self.status == self.osr.OK:
             now = self.clock()
             while pending and (not realtime or pending[0][0] <= now - t0):
                 t_arr, rd = pending.popleft()
                 self.submit(rd, arrival=t0 + t_arr if realtime else now)
             if not self.step() and poll_s:
                 time.sleep(poll_s)
-        return summarize(self.done, t0, self.clock(), rejected=len(self.rejected),
-                         launches=self.launches)
+        out = summarize(self.done, t0, self.clock(), rejected=len(self.rejected),
+                        launches=self.launches)
+        out.update(status=self.status, cancelled=len(self.cancelled),
+                   timed_out=sum(r.state == TIMED_OUT for r in self.failed),
+                   abandoned=sum(r.state == ABANDONED for r in self.failed) + len(pending))
+        return out
 
 
 def shard(arrivals, rank, world):
@@ -281,13 +388,52 @@ def shard(arrivals, rank, world):
     return [a for k, a in enumerate(ordered) if k % world == rank]
 
 
-def local_record(done):
-    """Per-GPU part of a multi-GPU summary: latencies, rays and time span."""
+def local_record(done, t0=None):
+    """Per-GPU part of a multi-GPU summary: latencies, rays and time span;
+    with t0 (the clock reading the stream's arrival times count from), also
+    each render's arrival time, its ray count and the time its last pixel
+    range completed, both relative to t0."""
     if not done:
-        return {"latencies": [], "rays": 0, "span": 0.0}
-    return {"latencies": [r.t_done - r.arrival for r in done],
-            "rays": sum(r.n_rays for r in done),
-            "span": max(r.t_done for r in done) - min(r.arrival for r in done)}
+        return {"latencies": [], "rays": 0, "span": 0.0, "arrivals": [], "done_at": [],
+                "n_rays": []}
+    rec = {"latencies": [r.t_done - r.arrival for r in done],
+           "rays": sum(r.n_rays for r in done),
+           "span": max(r.t_done for r in done) - min(r.arrival for r in done)}
+    if t0 is not None:
+        rec["arrivals"] = [r.arrival - t0 for r in done]
+        rec["done_at"] = [r.t_done - t0 for r in done]
+        rec["n_rays"] = [r.n_rays for r in done]
+    return rec
+
+
+def latency_windows(records, duration_s, width_s=10.0):
+    """Latency percentiles of the renders that arrived in each window of
+    width_s seconds of the stream (records: local_record(done, t0) of every
+    GPU), the growth of p99 from the first third of the stream to the last,
+    and the backlog: rays that had arrived but were not yet complete when
+    the last arrival came (duration_s)."""
+    arr = np.array([a for rec in records for a in rec.get("arrivals", [])])
+    lat = np.array([x for rec in records for x in rec["latencies"]])
+    done_at = np.array([a for rec in records for a in rec.get("done_at", [])])
+    n_rays = np.array([a for rec in records for a in rec.get("n_rays", [])])
+    if arr.size == 0:
+        return {"windows": [], "p99_growth": None, "backlog_rays_at_last_arrival": None}
+    windows = []
+    w0 = 0.0
+    while w0 < duration_s:
+        m = (arr >= w0) & (arr < w0 + width_s)
+        if m.any():
+            windows.append({"from_s": w0, "renders": int(m.sum()),
+                            "p50_latency_s": float(np.percentile(lat[m], 50)),
+                            "p99_latency_s": float(np.percentile(lat[m], 99))})
+        w0 += width_s
+    first = arr < duration_s / 3
+    last = arr >= 2 * duration_s / 3
+    growth = None
+    if first.any() and last.any():
+        growth = float(np.percentile(lat[last], 99) / np.percentile(lat[first], 99))
+    backlog = int(n_rays[(arr <= duration_s) & (done_at > duration_s)].sum())
+    return {"windows": windows, "p99_growth": growth, "backlog_rays_at_last_arrival": backlog}
 
 
 def merge_records(records, launches=0):

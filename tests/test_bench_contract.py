@@ -80,7 +80,8 @@ def test_reference_arm_next_workloads(workload, name):
 
 @pytest.mark.gpu
 def test_gpu_arm_line():
-    d = _run("--side", "64", "--steps", "1", "--warmup", "3", "--serve-seconds", "0.5")
+    d = _run("--side", "64", "--steps", "1", "--warmup", "3", "--serve-seconds", "0.5",
+             "--hbar-side", "32")
     _check_common(d, 1, 3)
     assert "impl" not in d or d["impl"] != "reference"
     r = d["roofline"]
@@ -93,7 +94,18 @@ def test_gpu_arm_line():
     assert d["e2e"]["api"] == "osiris_batch_plan_launch"
     assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
     assert d["variants"]["df64"]["value"] > 0
-    assert d["serving"]["continuous_batching_df64"]["p99_latency_s"] > 0
+    sv = d["serving"]
+    assert sv["continuous_batching_df64"]["p99_latency_s"] > 0
+    assert "0.5 s" in sv["continuous_batching_df64"]["workload"]
+    assert "windows" in sv["continuous_batching_df64"]
+    assert sv["one_render_per_launch_fp64"]["renders"] > 0
+    p = d["pipe_probes"]
+    assert p["fp64_fma"]["tflops"] == pytest.approx(r["peak"], rel=1e-12)
+    assert p["fp32_fma"]["tflops"] > p["fp64_fma"]["tflops"]
+    hb = d["hbar"]
+    assert hb["bar"] == 1e-10
+    assert set(hb["ck45_tol1e-10"]["by_status"]) <= {"captured", "escaped", "disk"}
+    assert len(hb["sweep"]["points"]) == 6
 
 
 @pytest.mark.gpu

@@ -8,7 +8,7 @@ import torch
 import paper_2202_00086_gb300 as osr
 from paper_2202_00086_gb300 import workloads
 
-from _parity import assert_parity, band_mask, compare, gpu_render, oracle_render
+from _parity import assert_parity, compare, gpu_render, oracle_render, oracle_sampled
 
 pytestmark = pytest.mark.gpu
 
@@ -17,7 +17,8 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("case", [0, 1, 2])
 def test_paper_disk_figure_subsampled(precision, case):
     rd = workloads.paper_disk_figure(nx=96, ny=48)[case]
-    rep = compare(rd, gpu_render(rd, precision=precision), oracle_render(rd))
+    rep = compare(rd, gpu_render(rd, precision=precision), oracle_render(rd),
+                  precision=precision)
     print(rep)
     assert_parity(rep)
     assert rep["n_disk"] > 300
@@ -28,9 +29,8 @@ def test_paper_disk_figure_full_size_sampled():
     gpu = gpu_render(rd, precision=osr.DF64, persistent=True)
     rng = np.random.default_rng(31)
     pix = np.sort(rng.choice(rd["nx"] * rd["ny"], 300, replace=False))
-    ref = oracle_render(rd, pixels=pix)
-    band = band_mask(gpu["status"].reshape(rd["ny"], rd["nx"])).reshape(-1)
-    rep = compare(rd, gpu, ref, pixels=pix, band=band)
+    ref, band = oracle_sampled(rd, pix)
+    rep = compare(rd, gpu, ref, pixels=pix, band=band, precision=osr.DF64)
     print(rep)
     assert_parity(rep)
     assert rep["n_disk"] > 20

@@ -10,7 +10,7 @@ import oracle
 import paper_2202_00086_gb300 as osr
 from paper_2202_00086_gb300 import workloads
 
-from _parity import assert_parity, band_mask, compare, gpu_render, oracle_render
+from _parity import assert_parity, compare, gpu_render, oracle_render, oracle_sampled
 
 pytestmark = pytest.mark.gpu
 DP = osr.RKDP45
@@ -22,7 +22,8 @@ DP = osr.RKDP45
 def test_dp45_kerr_subsampled(precision, a, inc):
     rd = workloads.render(a, 1000.0, inc, (-8, 8, -8, 8), 32, 32)
     ref = oracle_render(rd, integrator=oracle.RKDP45)
-    rep = compare(rd, gpu_render(rd, precision=precision, integrator=DP), ref)
+    rep = compare(rd, gpu_render(rd, precision=precision, integrator=DP), ref,
+                  precision=precision)
     print(rep)
     assert_parity(rep)
 
@@ -33,7 +34,8 @@ def test_dp45_disks(precision):
                workloads.render(0.9, 1000.0, 60.0, (-25, 25, -25, 25), 40, 40, mode="disk",
                                 r_in="isco", r_out=20.0)):
         ref = oracle_render(rd, integrator=oracle.RKDP45)
-        rep = compare(rd, gpu_render(rd, precision=precision, integrator=DP), ref)
+        rep = compare(rd, gpu_render(rd, precision=precision, integrator=DP), ref,
+                      precision=precision)
         print(rep)
         assert_parity(rep)
         assert rep["n_disk"] > 100
@@ -61,9 +63,8 @@ def test_dp45_full_size_sampled():
     gpu = gpu_render(rd, precision=osr.DF64, integrator=DP, persistent=True)
     rng = np.random.default_rng(21)
     pix = np.sort(rng.choice(1024 * 1024, 300, replace=False))
-    ref = oracle_render(rd, pixels=pix, integrator=oracle.RKDP45)
-    band = band_mask(gpu["status"].reshape(1024, 1024)).reshape(-1)
-    rep = compare(rd, gpu, ref, pixels=pix, band=band)
+    ref, band = oracle_sampled(rd, pix, integrator=oracle.RKDP45)
+    rep = compare(rd, gpu, ref, pixels=pix, band=band, precision=osr.DF64)
     print(rep)
     assert_parity(rep)
 

@@ -13,7 +13,7 @@ import oracle
 import paper_2202_00086_gb300 as osr
 from paper_2202_00086_gb300 import workloads
 
-from _parity import assert_parity, band_mask, compare, gpu_render, oracle_render
+from _parity import assert_parity, band_mask, compare, gpu_render, oracle_render, oracle_sampled
 
 pytestmark = pytest.mark.gpu
 
@@ -194,8 +194,7 @@ def test_full_size_kerr_sampled():
     gpu = gpu_render(rd, persistent=True)
     rng = np.random.default_rng(11)
     pix = np.sort(rng.choice(1024 * 1024, 600, replace=False))
-    ref = oracle_render(rd, pixels=pix)
-    band = band_mask(gpu["status"].reshape(1024, 1024)).reshape(-1)
+    ref, band = oracle_sampled(rd, pix)
     rep = compare(rd, gpu, ref, pixels=pix, band=band)
     print(rep)
     assert_parity(rep)
@@ -212,9 +211,8 @@ def test_full_size_schwarzschild_disk_sampled(precision):
     assert int((gpu["status"] == 0).sum()) == 0
     rng = np.random.default_rng(13)
     pix = np.sort(rng.choice(2048 * 2048, 2000, replace=False))
-    ref = oracle_render(rd, pixels=pix)
-    band = band_mask(gpu["status"].reshape(2048, 2048)).reshape(-1)
-    rep = compare(rd, gpu, ref, pixels=pix, band=band)
+    ref, band = oracle_sampled(rd, pix)
+    rep = compare(rd, gpu, ref, pixels=pix, band=band, precision=precision)
     print(rep)
     assert_parity(rep)
     assert rep["n_disk"] > 200

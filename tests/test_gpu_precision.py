@@ -12,7 +12,7 @@ import torch
 import paper_2202_00086_gb300 as osr
 from paper_2202_00086_gb300 import workloads
 
-from _parity import assert_parity, band_mask, compare, gpu_render, oracle_render
+from _parity import assert_parity, compare, gpu_render, oracle_render, oracle_sampled
 
 pytestmark = pytest.mark.gpu
 
@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("inc", workloads.KERR_INCLINATIONS)
 def test_df64_kerr_subsampled(a, inc):
     rd = workloads.render(a, 1000.0, inc, (-8, 8, -8, 8), 32, 32)
-    rep = compare(rd, gpu_render(rd, precision=osr.DF64), oracle_render(rd))
+    rep = compare(rd, gpu_render(rd, precision=osr.DF64), oracle_render(rd), precision=osr.DF64)
     print(rep)
     assert_parity(rep)
     assert rep["theta_max_rel"] < 1e-9 and rep["phi_max_rel"] < 1e-9
@@ -31,7 +31,8 @@ def test_df64_disks():
     for rd in (workloads.schwarzschild_disk(side=64),
                workloads.render(0.9, 1000.0, 60.0, (-25, 25, -25, 25), 40, 40, mode="disk",
                                 r_in="isco", r_out=20.0)):
-        rep = compare(rd, gpu_render(rd, precision=osr.DF64), oracle_render(rd))
+        rep = compare(rd, gpu_render(rd, precision=osr.DF64), oracle_render(rd),
+                      precision=osr.DF64)
         print(rep)
         assert_parity(rep)
         assert rep["n_disk"] > 100 and rep["g_max_rel"] < 1e-9
@@ -43,7 +44,7 @@ def test_df64_persistent_matches_plain_and_ragged():
     b = gpu_render(rd, precision=osr.DF64, persistent=True, block_size=64)
     for k in a:
         assert np.array_equal(a[k], b[k]), k
-    assert_parity(compare(rd, a, oracle_render(rd)))
+    assert_parity(compare(rd, a, oracle_render(rd), precision=osr.DF64))
 
 
 def test_df64_max_steps_and_states():
@@ -71,9 +72,9 @@ def test_full_size_batch_sampled(precision):
     for rd, o in zip(rds, outs):
         gpu = {k: v.cpu().numpy() for k, v in o.items()}
         pix = np.sort(rng.choice(1024 * 1024, 50, replace=False))
-        ref = oracle_render(rd, pixels=pix)
-        band = band_mask(gpu["status"].reshape(1024, 1024)).reshape(-1)
-        rep = compare(rd, gpu, ref, pixels=pix, band=band)
+        ref, band = oracle_sampled(rd, pix)
+        rep = compare(rd, gpu, ref, pixels=pix, band=band, precision=precision)
+        print(rep)
         assert_parity(rep)
 
 
@@ -82,7 +83,8 @@ def test_mixed_error_bound(tol):
     rd = dict(workloads.schwarzschild_disk(side=48))
     rd["tol"] = tol
     ref = oracle_render(dict(rd, tol=1e-10))
-    rep = compare(rd, gpu_render(rd, precision=osr.MIXED), ref, coord_rtol=1e-5, g_rtol=1e-5)
+    rep = compare(rd, gpu_render(rd, precision=osr.MIXED), ref, coord_rtol=1e-5, g_rtol=1e-5,
+                  precision=osr.MIXED)
     print(rep)
     assert_parity(rep)
     assert rep["n_disk"] > 150

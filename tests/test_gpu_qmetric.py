@@ -12,7 +12,7 @@ import oracle
 import paper_2202_00086_gb300 as osr
 from paper_2202_00086_gb300 import workloads
 
-from _parity import assert_parity, band_mask, compare, gpu_render, oracle_render
+from _parity import assert_parity, compare, gpu_render, oracle_render, oracle_sampled
 
 pytestmark = pytest.mark.gpu
 
@@ -25,7 +25,8 @@ PRECISIONS = [osr.FP64, osr.DF64]
 @pytest.mark.parametrize("inc", [30.0, 90.0])
 def test_qmetric_render_parity(q, inc, precision):
     rd = workloads.render(0.0, 1000.0, inc, (-8, 8, -8, 8), 32, 32, q=q)
-    rep = compare(rd, gpu_render(rd, precision=precision), oracle_render(rd))
+    rep = compare(rd, gpu_render(rd, precision=precision), oracle_render(rd),
+                  precision=precision)
     print(rep)
     assert_parity(rep)
 
@@ -135,9 +136,9 @@ def test_full_size_qmetric_batch_sampled(precision):
     for rd, o in zip(rds, outs):
         gpu = {k: v.cpu().numpy() for k, v in o.items()}
         pix = np.sort(rng.choice(1024 * 1024, 40, replace=False))
-        ref = oracle_render(rd, pixels=pix)
-        band = band_mask(gpu["status"].reshape(1024, 1024)).reshape(-1)
-        rep = compare(rd, gpu, ref, pixels=pix, band=band)
+        ref, band = oracle_sampled(rd, pix)
+        rep = compare(rd, gpu, ref, pixels=pix, band=band, precision=precision)
+        print(rep)
         assert_parity(rep)
 
 

@@ -165,3 +165,90 @@ def test_mixed_server_runs_qmetric_in_fp64():
     k = srv.submit(workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 16, 16))
     assert r.kind == (osr.SPACETIME_QMETRIC, osr.FP64)
     assert k.kind == (osr.SPACETIME_KERR, osr.MIXED)
+
+
+class StuckEvent:
+    """A round that never completes (a stalled poll made on the host)."""
+
+    def query(self):
+        return False
+
+
+class StuckBackend(FakeBackend):
+    def launch(self, entries, ws, **opts):
+        super().launch(entries, ws, **opts)
+        return StuckEvent()
+
+
+class TickClock:
+    """Deterministic clock: every reading advances it by `dt` seconds."""
+
+    def __init__(self, dt=0.01):
+        self.t = 0.0
+        self.dt = dt
+
+    def __call__(self):
+        self.t += self.dt
+        return self.t
+
+
+def test_cancel_waiting_and_active_renders():
+    import paper_2202_00086_gb300 as osr
+    big = [workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 128, 128) for _ in range(3)]
+    srv, be = _server(round_rays=4096, min_chunk=1024, max_inflight=1, max_entries=8)
+    rs = [srv.submit(rd, arrival=0.0) for rd in big]
+    srv.step()  # admits all three, launches the first round
+    assert all(r.state == serve.ACTIVE for r in rs)
+    waiting = srv.submit(workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 16, 16))
+    assert srv.cancel(waiting) and waiting.state == serve.CANCELLED and waiting not in srv.waiting
+    launched_before = rs[1].next_ray
+    assert 0 < launched_before < rs[1].n_rays
+    assert srv.cancel(rs[1])
+    assert not srv.cancel(rs[1])  # only once
+    while not srv.idle():
+        srv.step()
+    assert rs[1].state == serve.CANCELLED and rs[1] in srv.cancelled
+    assert rs[1].rays_done == launched_before  # no range launched after the cancel
+    assert sum(n for first, n in rs[1].chunks) == launched_before
+    for r in (rs[0], rs[2]):
+        assert r.state == serve.DONE and np.all(r.out["hits"] == 1)
+    assert srv.bytes_in_use == 0 and srv.status == osr.OK
+    assert not srv.cancel(rs[0])  # already done
+
+
+def test_stalled_round_times_out_without_waiting_forever():
+    import paper_2202_00086_gb300 as osr
+    ref = [None]
+    be = StuckBackend(ref)
+    clock = TickClock(0.01)
+    srv = serve.RenderServer(backend=be, keep_outputs=True, clock=clock, stall_timeout_s=1.0,
+                             round_rays=2048, min_chunk=512, max_inflight=2)
+    ref[0] = srv
+    stream = [(0.0, workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 64, 64))
+              for _ in range(5)]
+    summary = srv.run(stream, realtime=False, poll_s=0)
+    assert summary["status"] == osr.ETIMEOUT
+    assert summary["renders"] == 0
+    assert summary["timed_out"] >= 1
+    assert summary["timed_out"] + summary["abandoned"] == len(stream)
+    assert srv.idle() and srv.bytes_in_use == 0
+    n_rounds = len(be.rounds)
+    assert srv.submit(stream[0][1]).state == serve.REJECTED  # a stopped server takes nothing
+    srv.step()
+    assert len(be.rounds) == n_rounds  # and launches nothing
+    assert srv.close(timeout_s=0.5) == osr.ETIMEOUT  # the stuck rounds are never waited out
+
+
+def test_bounded_wait_for_one_render():
+    import paper_2202_00086_gb300 as osr
+    srv, be = _server(round_rays=1 << 16, max_inflight=1)
+    srv.clock = TickClock(0.001)
+    r = srv.submit(workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 32, 32))
+    assert srv.wait(r, timeout_s=10.0, poll_s=0) == osr.OK and r.state == serve.DONE
+    ref = [None]
+    stuck = StuckBackend(ref)
+    srv2 = serve.RenderServer(backend=stuck, clock=TickClock(0.001), max_inflight=1)
+    ref[0] = srv2
+    r2 = srv2.submit(workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 32, 32))
+    assert srv2.wait(r2, timeout_s=0.05, poll_s=0) == osr.ETIMEOUT
+    assert r2.state == serve.ACTIVE  # still in flight: nothing was waited for without bound

@@ -20,8 +20,6 @@ from paper_2202_00086_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
 
-COORD_RTOL = 1e-8  # the parity tolerance of the other GPU tests
-
 
 def _batch(seed):
     """A small uneven batch: shadow and disk renders of different sizes."""
@@ -58,16 +56,14 @@ def _host(reqs):
 
 
 def _assert_same(a, b):
+    """Bit-identical outputs: the two entry points run the same kernel on the
+    same request table, so any difference means a table or queue that was not
+    what the caller asked for."""
     for qa, qb in zip(a, b):
-        assert np.array_equal(qa["status"], qb["status"])
-        for key in ("r", "theta", "phi"):
-            err = np.abs(qa[key] - qb[key]) / np.maximum(np.abs(qb[key]), 1.0)
-            assert err.max() <= COORD_RTOL, key
-        for key in ("g", "intensity", "r_hit"):
-            if key in qa:
-                assert np.allclose(qa[key], qb[key], rtol=COORD_RTOL, atol=0.0), key
-        for key in ("cell_i", "cell_j", "parity", "steps"):
-            assert np.array_equal(qa[key], qb[key]), key
+        assert qa.keys() == qb.keys()
+        for key in qa:
+            assert qa[key].dtype == qb[key].dtype, key
+            assert np.array_equal(qa[key].view(np.uint8), qb[key].view(np.uint8)), key
 
 
 def test_static_batch_matches_workspace_batch_twice():
