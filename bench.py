@@ -47,10 +47,15 @@ SHADOW_BYTES_PER_RAY = 42
 DISK_BYTES_PER_RAY = 66  # + g, intensity, r_hit 3x8
 ORACLE_SAMPLE_STRIDE = 128  # CPU baseline: every 128th pixel of each render
 E2E_STEPS = 5  # end-to-end leg: steps timed with host copies (wall clock)
-# DRAM bytes (read + write) of one FP64 trace launch over the 1024^2 set: ncu
-# capture of the same kernel at 512^2 (2.62 MB read + 90.56 MB written), scaled
-# by the 4x rays (profiles/trace_fp64_persistent_kerr12x512_dram.md).
-FP64_TRAFFIC_BYTES_PER_LAUNCH = 372.7e6
+# DRAM bytes (read + write) of one FP64 trace launch over the 1024^2 set, from
+# an ncu capture of the current kernel (None while the kernel has changed since
+# the counters were taken).
+FP64_TRAFFIC_BYTES_PER_LAUNCH = None
+# FP32-pipe (FMA heavy + lite) thread instructions per double-float Cash-Karp
+# attempt on the Kerr set: ncu capture of trace_df64_persistent on the 12
+# renders at 256x256 (3.625e10 FMA-pipe warp instructions x 28.33 active lanes
+# over 2.73e8 attempts), profiles/trace_df64_persistent_kerr12x256_ncu.md.
+DF64_FP32_INST_PER_ATTEMPT = 3761
 
 
 # Workloads: the headline Kerr set (default) and the measured "next" rows,
@@ -710,6 +715,19 @@ def main():
             "dtype": "f64+df64",
             "fp64_equivalent_tflops": vflops / (vms * 1e-3) / 1e12,
             "fp64_equivalent_frac_of_fp64_peak": vflops / (vms * 1e-3) / 1e12 / peaks["fp64"],
+            # the pipe the double-float kernel runs on: FP32-pipe thread
+            # instructions per attempt (ncu) x attempts/s over the FP32 probe's
+            # thread-instruction rate
+            "roofline": ({
+                "bound": "alu", "pipe": "FP32 (FMA heavy + lite)",
+                "achieved": vatt * DF64_FP32_INST_PER_ATTEMPT / (vms * 1e-3) / 1e12,
+                "peak": probe["fp32_fma"]["warp_inst_per_s"] * 32 / 1e12,
+                "unit": "T thread-instructions/s",
+                "frac": (vatt * DF64_FP32_INST_PER_ATTEMPT / (vms * 1e-3)) /
+                        (probe["fp32_fma"]["warp_inst_per_s"] * 32),
+                "inst_per_attempt": DF64_FP32_INST_PER_ATTEMPT,
+                "peak_source": "FP32 pipe probe measured in this process"}
+                if args.workload == "kerr" else None),
             "max_abs_H": vs["max_abs_H"],
             "steps_per_ray": {"accepted": vs["accepted"] / (n_rays * args.steps),
                               "rejected": vs["rejected"] / (n_rays * args.steps),

@@ -108,6 +108,13 @@ typedef struct {
                               that may run at the same time. */
     size_t workspace_bytes;
     int32_t integrator;    /* OSIRIS_RKCK45 (default) or OSIRIS_RKDP45 */
+    int32_t rays_per_lane; /* rays a lane takes at once, 0..64 (0 = 1): a plain
+                              launch gives each thread this many consecutive
+                              pixels; a persistent grid claims this many per
+                              idle lane with each queue atomic */
+    int32_t refill_lanes;  /* persistent grid, 0..32 (0 = 1): a warp whose other
+                              lanes are still integrating refills its idle
+                              lanes only once at least this many are idle */
 } osiris_trace_opts;
 
 /* Per-ray outputs: DEVICE arrays with one entry per ray (NULL = not wanted).
@@ -142,7 +149,8 @@ typedef struct {
 
 /* Sets the defaults: tol 1e-10, max_steps 1e6, FP64, Cash-Karp,
  * non-persistent, r_cap_factor 1.01, r_esc_factor 1.1, 10-degree cells,
- * phase 0, library block size, no stats, no workspace. */
+ * phase 0, library block size, no stats, no workspace, one ray per lane at a
+ * time, refill as soon as one lane is idle. */
 void osiris_default_opts(osiris_trace_opts* opts);
 
 /* Create a camera (Sec. 2.3, Eq. momentums; observer at t0 = 0, phi0 = 0):

@@ -38,7 +38,8 @@ class TraceOpts(ctypes.Structure):
                 ("persistent", ctypes.c_int32), ("r_cap_factor", _d), ("r_esc_factor", _d),
                 ("cell_deg", _d), ("cell_phase_deg", _d), ("block_size", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("stats", _vp), ("workspace", _vp),
-                ("workspace_bytes", ctypes.c_size_t), ("integrator", ctypes.c_int32)]
+                ("workspace_bytes", ctypes.c_size_t), ("integrator", ctypes.c_int32),
+                ("rays_per_lane", ctypes.c_int32), ("refill_lanes", ctypes.c_int32)]
 
 
 OUTPUT_FIELDS = [("status", torch.uint8), ("r", torch.float64), ("theta", torch.float64),
@@ -207,7 +208,8 @@ def workspace_bytes(n_requests=1):
 
 def make_opts(tol=1e-10, max_steps=1_000_000, precision=FP64, persistent=False,
               r_cap_factor=1.01, r_esc_factor=1.1, cell_deg=10.0, cell_phase_deg=0.0,
-              block_size=0, blocks_per_sm=0, stats=None, workspace=None, integrator=RKCK45):
+              block_size=0, blocks_per_sm=0, stats=None, workspace=None, integrator=RKCK45,
+              rays_per_lane=0, refill_lanes=0):
     o = TraceOpts()
     lib().osiris_default_opts(ctypes.byref(o))
     o.tol, o.max_steps = float(tol), int(max_steps)
@@ -217,6 +219,7 @@ def make_opts(tol=1e-10, max_steps=1_000_000, precision=FP64, persistent=False,
     o.cell_deg, o.cell_phase_deg = float(cell_deg), float(cell_phase_deg)
     o.block_size, o.blocks_per_sm = int(block_size), int(blocks_per_sm)
     o.integrator = int(integrator)
+    o.rays_per_lane, o.refill_lanes = int(rays_per_lane), int(refill_lanes)
     o.stats = stats.data_ptr() if stats is not None else None
     if workspace is not None:
         o.workspace = workspace.data_ptr()

@@ -1,18 +1,17 @@
-"""Launch-shape autotuner for the persistent trace kernels.
+"""Launch autotuner for the persistent trace kernels.
 
-Times every candidate (threads per block x resident blocks per SM) of a
-precision / integrator pair on a sample render set, keeps the fastest and
-caches it per GPU model in a JSON file. `tuned_opts` returns the cached
-choice as keyword arguments for the trace calls.
-
-Two launch parameters are fixed by the kernel design rather than tuned:
-  - rays per thread = 1: a lane's whole ray state lives in registers, and the
-    register budget (FP64: ~200, DF64: 128 per thread) leaves no room for a
-    second ray;
-  - refill granularity = 1 warp-wide atomic as soon as any lane is idle: a
-    ray start costs about one evaluation of the equations against ~350
-    attempts per ray, so waiting for more idle lanes would only add idle
-    lane-cycles.
+Times candidate launches of a precision / integrator pair on a sample render
+set (one batched persistent launch each), keeps the fastest and caches it
+per GPU model in a JSON file. `tuned_opts` returns the cached choice as
+keyword arguments for the trace calls. The search has two stages:
+  1. launch shape: threads per block x resident blocks per SM (0 = the
+     occupancy limit), with one ray per lane and immediate refills;
+  2. work granularity at the best shape: rays per lane (a lane claims that
+     many consecutive rays from the device queue with each warp atomic) x
+     refill granularity (a warp whose other lanes are still integrating
+     refills its idle lanes only once at least that many are idle).
+Rays are independent, so every candidate gives the same outputs; only the
+time differs.
 """
 import json
 import os
@@ -21,18 +20,28 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(_HERE, "_build", "autotune.json")
 BLOCKS = (64, 96, 128, 192, 256)
 PER_SM = (0, 1, 2, 3, 4)  # 0 = the occupancy limit
+RAYS_PER_LANE = (1, 2, 4, 8)
+REFILL_LANES = (1, 4, 16, 32)
+KEYS = ("block_size", "blocks_per_sm", "rays_per_lane", "refill_lanes")
 
 
 def candidates(blocks=BLOCKS, per_sm=PER_SM):
+    """Launch shapes of the first stage: (block, blocks per SM)."""
     return [(b, k) for b in blocks for k in per_sm]
 
 
+def granularity_candidates(rays=RAYS_PER_LANE, refill=REFILL_LANES):
+    """Work granularities of the second stage: (rays per lane, refill lanes)."""
+    return [(r, f) for r in rays for f in refill]
+
+
 def choose(timings):
-    """Fastest candidate from {(block, per_sm): seconds}; ties go to the
-    smaller block, then to the occupancy-limited grid (per_sm = 0)."""
+    """Fastest candidate from {candidate tuple: seconds}; ties go to the
+    smaller tuple (smaller block, the occupancy-limited grid, one ray per
+    lane, immediate refills)."""
     if not timings:
         raise ValueError("no candidate ran")
-    return min(timings, key=lambda c: (timings[c], c[0], c[1]))
+    return min(timings, key=lambda c: (timings[c], c))
 
 
 def _key(device_name, precision, integrator):
@@ -55,29 +64,44 @@ def save_cache(cache, path=DEFAULT_CACHE):
     os.replace(tmp, path)
 
 
-def autotune(precision=None, integrator=0, renders=None, cands=None, repeats=2,
+def autotune(precision=None, integrator=0, renders=None, cands=None, grans=None, repeats=2,
              cache_path=DEFAULT_CACHE, timer=None):
-    """Time each candidate on `renders` (default: the 12-render Kerr set at
-    256x256) in one batched persistent launch; return (best, timings) and
-    store best in the cache. `timer(block, per_sm)` may replace the GPU
+    """Time each launch shape of `cands` (stage 1), then each work
+    granularity of `grans` at the fastest shape (stage 2), on `renders`
+    (default: the 12-render Kerr set at 256x256) in one batched persistent
+    launch per timing. Returns (best, timings): best = (block, blocks per
+    SM, rays per lane, refill lanes), timings keyed by such 4-tuples. The
+    best candidate, its time and the spread of all timings go to the cache.
+    `timer(block, per_sm, rays_per_lane, refill_lanes)` may replace the GPU
     timing (tests)."""
     import paper_2202_00086_gb300 as osr
     precision = osr.DF64 if precision is None else precision
     cands = candidates() if cands is None else cands
+    grans = granularity_candidates() if grans is None else grans
     if timer is None:
         timer, device = _gpu_timer(osr, precision, integrator, renders, repeats)
     else:
         device = "test-device"
     timings = {}
-    for b, k in cands:
+
+    def run(c):
         try:
-            timings[(b, k)] = timer(b, k)
+            timings[c] = timer(*c)
         except osr.OsirisError:
-            continue  # e.g. more blocks per SM than the registers allow
-    best = choose(timings)
+            pass  # e.g. more blocks per SM than the registers allow
+
+    for b, k in cands:
+        run((b, k, 1, 1))
+    b, k, _, _ = choose(timings)
+    for r, f in grans:
+        if (b, k, r, f) not in timings:
+            run((b, k, r, f))
+    best = choose({c: t for c, t in timings.items() if c[:2] == (b, k)})
     cache = load_cache(cache_path)
-    cache[_key(device, precision, integrator)] = {"block_size": best[0], "blocks_per_sm": best[1],
-                                                 "seconds": timings[best]}
+    entry = dict(zip(KEYS, best))
+    entry.update(seconds=timings[best], slowest_seconds=max(timings.values()),
+                 candidates=len(timings))
+    cache[_key(device, precision, integrator)] = entry
     save_cache(cache, cache_path)
     return best, timings
 
@@ -90,7 +114,7 @@ def tuned_opts(precision, integrator=0, cache_path=DEFAULT_CACHE, device_name=No
     entry = load_cache(cache_path).get(_key(device_name, precision, integrator))
     if not entry:
         return {}
-    return {"block_size": entry["block_size"], "blocks_per_sm": entry["blocks_per_sm"]}
+    return {k: entry[k] for k in KEYS if k in entry}
 
 
 def _gpu_timer(osr, precision, integrator, renders, repeats):
@@ -103,14 +127,15 @@ def _gpu_timer(osr, precision, integrator, renders, repeats):
     ws = torch.empty(osr.workspace_bytes(len(cams)), dtype=torch.uint8, device="cuda")
     reqs = [{"camera": c, "out": o, "tol": rd["tol"]} for c, o, rd in zip(cams, outs, renders)]
 
-    def timer(block, per_sm):
+    def timer(block, per_sm, rays_per_lane=1, refill_lanes=1):
         best = float("inf")
         for _ in range(repeats):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
             osr.trace_batch(reqs, workspace=ws, precision=precision, integrator=integrator,
-                            block_size=block, blocks_per_sm=per_sm)
+                            block_size=block, blocks_per_sm=per_sm, rays_per_lane=rays_per_lane,
+                            refill_lanes=refill_lanes)
             e1.record()
             torch.cuda.synchronize()
             best = min(best, e0.elapsed_time(e1) * 1e-3)

@@ -58,6 +58,8 @@ int check_opts(const osiris_trace_opts* o) {
       (o->block_size < 32 || o->block_size > 256 || o->block_size % 32 != 0))
     return OSIRIS_EINVAL;
   if (o->blocks_per_sm < 0) return OSIRIS_EINVAL;
+  if (o->rays_per_lane < 0 || o->rays_per_lane > 64) return OSIRIS_EINVAL;
+  if (o->refill_lanes < 0 || o->refill_lanes > 32) return OSIRIS_EINVAL;
   if (o->workspace && (reinterpret_cast<uintptr_t>(o->workspace) & 255u)) return OSIRIS_EINVAL;
   return OSIRIS_OK;
 }
@@ -169,14 +171,22 @@ int persistent_shape(const osiris_trace_opts* o, int spacetime, int* block,
   return OSIRIS_OK;
 }
 
+// Work-distribution knobs of a launch (0 in the options = 1).
+void set_granularity(KernelArgs& args, const osiris_trace_opts* o) {
+  args.rays_per_lane = o->rays_per_lane > 0 ? o->rays_per_lane : 1;
+  args.refill_lanes = o->refill_lanes > 0 ? o->refill_lanes : 1;
+}
+
 // Launch the trace kernel for the requests in args (args.reqs / single).
 int launch(KernelArgs& args, const osiris_trace_opts* o, void* stream) {
   if (args.total_rays == 0) return OSIRIS_OK;
   const bool persistent = o->persistent != 0 || args.reqs != nullptr;
   const Launcher launcher = launcher_of(o);
+  set_granularity(args, o);
   if (!persistent) {
     const int block = o->block_size ? o->block_size : kDefaultBlock;
-    const int64_t grid = (args.total_rays + block - 1) / block;
+    const int64_t per_block = static_cast<int64_t>(block) * args.rays_per_lane;
+    const int64_t grid = (args.total_rays + per_block - 1) / per_block;
     if (grid > 0x7fffffff) return OSIRIS_EINVAL;
     args.queue = nullptr;
     return cuda_rc(
@@ -187,7 +197,8 @@ int launch(KernelArgs& args, const osiris_trace_opts* o, void* stream) {
   int64_t grid = 0;
   const int spacetime = args.reqs ? args.spacetime : args.single.spacetime;
   if (int rc = persistent_shape(o, spacetime, &block, &grid)) return rc;
-  const int64_t needed = (args.total_rays + block - 1) / block;
+  const int64_t per_block = static_cast<int64_t>(block) * args.rays_per_lane;
+  const int64_t needed = (args.total_rays + per_block - 1) / per_block;
   if (grid > needed) grid = needed;
   args.queue = static_cast<unsigned long long*>(o->workspace);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -658,6 +669,7 @@ int record_plan(osiris_batch_plan* p) {
   args.total_rays = 1;
   args.stats = reinterpret_cast<unsigned long long*>(p->opts.stats);
   args.queue = static_cast<unsigned long long*>(p->opts.workspace);
+  set_granularity(args, &p->opts);
   // An external event record node: the host waits on it before rewriting the
   // staging table.
   if (cudaMemcpyAsync(p->dev_table, p->staging,
@@ -757,7 +769,9 @@ int osiris_batch_plan_launch(osiris_batch_plan* p, const osiris_request* reqs, i
   args.total_rays = total;
   args.stats = reinterpret_cast<unsigned long long*>(p->opts.stats);
   args.queue = static_cast<unsigned long long*>(p->opts.workspace);
-  int64_t grid = (total + p->block - 1) / p->block;
+  set_granularity(args, &p->opts);
+  const int64_t per_block = static_cast<int64_t>(p->block) * args.rays_per_lane;
+  int64_t grid = (total + per_block - 1) / per_block;
   if (grid > p->full_grid) grid = p->full_grid;
   cudaKernelNodeParams k = p->kernel;
   void* argv[] = {&args};

@@ -54,6 +54,9 @@ struct KernelArgs {
   int64_t total_rays;
   unsigned long long* queue;       // persistent grids: next ray index (device)
   unsigned long long* stats;       // optional OSIRIS_STATS_LEN counters (device)
+  int32_t rays_per_lane;           // rays a lane claims at once (plain: per thread), >= 1
+  int32_t refill_lanes;            // persistent: idle lanes a warp waits for before it
+                                   // refills (unless none of its lanes is busy), 1..32
   ReqDev single;
 };
 

@@ -215,20 +215,24 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
     }
   };
 
-  if (!PERSISTENT) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < A.total_rays) start_ray(g);
-  }
+  // rays claimed by this lane and not yet started: [g_next, g_end)
+  int64_t g_next = 0, g_end = 0;
+  if (!PERSISTENT) plain_range(A, g_next, g_end);
 
   for (;;) {
+    if (mode == MODE_IDLE && g_next < g_end) start_ray(g_next++);
     if (PERSISTENT) {
-      const int64_t g = refill(A, (mode == MODE_IDLE) && !drained);
-      if (g >= 0)
-        start_ray(g);
-      else if (g == -2)
+      int64_t first = 0;
+      const int got = refill(A, (mode == MODE_IDLE) && !drained, mode != MODE_IDLE, first);
+      if (got > 0) {
+        g_next = first;
+        g_end = first + got;
+        start_ray(g_next++);
+      } else if (got < 0) {
         drained = true;
+      }
     }
-    if (!__any_sync(FULL, mode != MODE_IDLE)) break;
+    if (!__any_sync(FULL, mode != MODE_IDLE || g_next < g_end)) break;
     if (mode == MODE_IDLE) continue;
 
     const float hs_f = fminf(h, 0.1f * y.r.hi);

@@ -169,21 +169,40 @@ __device__ __forceinline__ void write_outputs(const KernelArgs& A, const RayInfo
   if (status != OSIRIS_STATUS_ERROR) S.max_abs_H = fmax(S.max_abs_H, max_abs_H);
 }
 
-// Take the next rays of a persistent grid from the device queue for every
-// lane that needs one (one atomic per warp). Returns the ray index for this
-// lane, or -1 when the queue is drained or the lane needs none.
-__device__ __forceinline__ int64_t refill(const KernelArgs& A, bool need) {
+// Take the next rays of a persistent grid from the device queue for the lanes
+// that need one: one atomic per warp claims rays_per_lane consecutive rays
+// for each such lane. A warp with busy lanes refills only when at least
+// refill_lanes of its lanes need rays (a warp with no busy lane always
+// refills, so no warp waits forever). Returns the number of rays claimed by
+// this lane (their first index in `first`), 0 when it claimed none this time,
+// or -1 when the queue is drained.
+__device__ __forceinline__ int refill(const KernelArgs& A, bool need, bool busy,
+                                      int64_t& first) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned m = __ballot_sync(FULL, need);
-  if (!m) return -1;
+  const unsigned b = __ballot_sync(FULL, busy);
+  if (!m || (b && __popc(m) < A.refill_lanes)) return 0;
   const int leader = __ffs(m) - 1;
+  const unsigned long long per = (unsigned long long)A.rays_per_lane;
   unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(A.queue, (unsigned long long)__popc(m));
+  if (lane == leader) base = atomicAdd(A.queue, (unsigned long long)__popc(m) * per);
   base = __shfl_sync(FULL, base, leader);
-  if (!need) return -1;
-  const unsigned long long g = base + __popc(m & ((1u << lane) - 1u));
-  return g < (unsigned long long)A.total_rays ? (int64_t)g : -2;
+  if (!need) return 0;
+  const unsigned long long g = base + __popc(m & ((1u << lane) - 1u)) * per;
+  const unsigned long long total = (unsigned long long)A.total_rays;
+  if (g >= total) return -1;
+  first = (int64_t)g;
+  return (int)(total - g < per ? total - g : per);
+}
+
+// The rays a plain (one launch thread per ray range) launch gives this
+// thread: rays_per_lane consecutive rays from thread index x rays_per_lane.
+__device__ __forceinline__ void plain_range(const KernelArgs& A, int64_t& next, int64_t& end) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  next = t * A.rays_per_lane;
+  end = next + A.rays_per_lane;
+  if (end > A.total_rays) end = A.total_rays;
 }
 
 template <class Stepper, bool PERSISTENT>
@@ -274,20 +293,24 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
     }
   };
 
-  if (!PERSISTENT) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < A.total_rays) start_ray(g);
-  }
+  // rays claimed by this lane and not yet started: [g_next, g_end)
+  int64_t g_next = 0, g_end = 0;
+  if (!PERSISTENT) plain_range(A, g_next, g_end);
 
   for (;;) {
+    if (mode == MODE_IDLE && g_next < g_end) start_ray(g_next++);
     if (PERSISTENT) {
-      const int64_t g = refill(A, (mode == MODE_IDLE) && !drained);
-      if (g >= 0)
-        start_ray(g);
-      else if (g == -2)
+      int64_t first = 0;
+      const int got = refill(A, (mode == MODE_IDLE) && !drained, mode != MODE_IDLE, first);
+      if (got > 0) {
+        g_next = first;
+        g_end = first + got;
+        start_ray(g_next++);
+      } else if (got < 0) {
         drained = true;
+      }
     }
-    if (!__any_sync(FULL, mode != MODE_IDLE)) break;
+    if (!__any_sync(FULL, mode != MODE_IDLE || g_next < g_end)) break;
     if (mode == MODE_IDLE) continue;
 
     const double hs = (mode == MODE_LOCATE) ? h_try : fmin(h, 0.1 * y.r);
