@@ -47,10 +47,11 @@ SHADOW_BYTES_PER_RAY = 42
 DISK_BYTES_PER_RAY = 66  # + g, intensity, r_hit 3x8
 ORACLE_SAMPLE_STRIDE = 128  # CPU baseline: every 128th pixel of each render
 E2E_STEPS = 5  # end-to-end leg: steps timed with host copies (wall clock)
-# DRAM bytes (read + write) of one FP64 trace launch over the 1024^2 set, from
-# an ncu capture of the current kernel (None while the kernel has changed since
-# the counters were taken).
-FP64_TRAFFIC_BYTES_PER_LAUNCH = None
+# DRAM bytes (read + write) of one FP64 trace launch over the 1024^2 set: ncu
+# capture (one pass) of the timed launch of the current kernel, 40.99 MB read
+# + 523.18 MB written (profiles/trace_fp64_persistent_kerr12x1024_dram.md);
+# the outputs alone are 528.5 MB (42 B per ray).
+FP64_TRAFFIC_BYTES_PER_LAUNCH = 564.17e6
 # FP32-pipe (FMA heavy + lite) thread instructions per double-float Cash-Karp
 # attempt on the Kerr set: ncu capture of trace_df64_persistent on the 12
 # renders at 256x256 (3.625e10 FMA-pipe warp instructions x 28.33 active lanes
@@ -139,6 +140,8 @@ def parse():
     p.add_argument("--kernel", default="batch", choices=["batch", "persistent", "plain"])
     p.add_argument("--side", type=int, default=1024)
     p.add_argument("--block", type=int, default=0)
+    p.add_argument("--rays-per-lane", type=int, default=0)
+    p.add_argument("--refill-lanes", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-variants", action="store_true")
@@ -551,7 +554,8 @@ def main():
     cell_deg = renders[0]["cell_deg"] if renders else 10.0
     cell_phase = renders[0]["cell_phase_deg"] if renders else workloads.checker_phase_deg(2202)
     common = dict(tol=tol, precision=precision, block_size=args.block, workspace=ws,
-                  cell_deg=cell_deg, cell_phase_deg=cell_phase)
+                  cell_deg=cell_deg, cell_phase_deg=cell_phase,
+                  rays_per_lane=args.rays_per_lane, refill_lanes=args.refill_lanes)
 
     def request(rd, c, o):
         r = {"camera": c, "out": o, "tol": rd["tol"]}

@@ -112,9 +112,11 @@ typedef struct {
                               launch gives each thread this many consecutive
                               pixels; a persistent grid claims this many per
                               idle lane with each queue atomic */
-    int32_t refill_lanes;  /* persistent grid, 0..32 (0 = 1): a warp whose other
-                              lanes are still integrating refills its idle
-                              lanes only once at least this many are idle */
+    int32_t refill_lanes;  /* persistent grid, 0..32 (0 = library default, 4): a
+                              warp whose other lanes are still integrating
+                              refills its idle lanes only once at least this
+                              many are idle (a warp with no busy lane always
+                              refills) */
 } osiris_trace_opts;
 
 /* Per-ray outputs: DEVICE arrays with one entry per ray (NULL = not wanted).
@@ -149,8 +151,9 @@ typedef struct {
 
 /* Sets the defaults: tol 1e-10, max_steps 1e6, FP64, Cash-Karp,
  * non-persistent, r_cap_factor 1.01, r_esc_factor 1.1, 10-degree cells,
- * phase 0, library block size, no stats, no workspace, one ray per lane at a
- * time, refill as soon as one lane is idle. */
+ * phase 0, library block size, no stats, no workspace, library work
+ * distribution (one ray per lane at a time, refill once four lanes of a warp
+ * are idle). */
 void osiris_default_opts(osiris_trace_opts* opts);
 
 /* Create a camera (Sec. 2.3, Eq. momentums; observer at t0 = 0, phi0 = 0):

@@ -5,7 +5,7 @@ set (one batched persistent launch each), keeps the fastest and caches it
 per GPU model in a JSON file. `tuned_opts` returns the cached choice as
 keyword arguments for the trace calls. The search has two stages:
   1. launch shape: threads per block x resident blocks per SM (0 = the
-     occupancy limit), with one ray per lane and immediate refills;
+     occupancy limit), with the library's default work distribution;
   2. work granularity at the best shape: rays per lane (a lane claims that
      many consecutive rays from the device queue with each warp atomic) x
      refill granularity (a warp whose other lanes are still integrating
@@ -20,8 +20,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(_HERE, "_build", "autotune.json")
 BLOCKS = (64, 96, 128, 192, 256)
 PER_SM = (0, 1, 2, 3, 4)  # 0 = the occupancy limit
-RAYS_PER_LANE = (1, 2, 4, 8)
-REFILL_LANES = (1, 4, 16, 32)
+RAYS_PER_LANE = (1, 2, 4)
+REFILL_LANES = (1, 2, 4, 8, 16)
+DEFAULT_GRANULARITY = (0, 0)  # the library's default (one ray per lane, refill at 4 idle lanes)
 KEYS = ("block_size", "blocks_per_sm", "rays_per_lane", "refill_lanes")
 
 
@@ -37,8 +38,8 @@ def granularity_candidates(rays=RAYS_PER_LANE, refill=REFILL_LANES):
 
 def choose(timings):
     """Fastest candidate from {candidate tuple: seconds}; ties go to the
-    smaller tuple (smaller block, the occupancy-limited grid, one ray per
-    lane, immediate refills)."""
+    smaller tuple (smaller block, the occupancy-limited grid, the library's
+    default work distribution)."""
     if not timings:
         raise ValueError("no candidate ran")
     return min(timings, key=lambda c: (timings[c], c))
@@ -91,7 +92,7 @@ def autotune(precision=None, integrator=0, renders=None, cands=None, grans=None,
             pass  # e.g. more blocks per SM than the registers allow
 
     for b, k in cands:
-        run((b, k, 1, 1))
+        run((b, k) + DEFAULT_GRANULARITY)
     b, k, _, _ = choose(timings)
     for r, f in grans:
         if (b, k, r, f) not in timings:
@@ -127,7 +128,7 @@ def _gpu_timer(osr, precision, integrator, renders, repeats):
     ws = torch.empty(osr.workspace_bytes(len(cams)), dtype=torch.uint8, device="cuda")
     reqs = [{"camera": c, "out": o, "tol": rd["tol"]} for c, o, rd in zip(cams, outs, renders)]
 
-    def timer(block, per_sm, rays_per_lane=1, refill_lanes=1):
+    def timer(block, per_sm, rays_per_lane=0, refill_lanes=0):
         best = float("inf")
         for _ in range(repeats):
             e0 = torch.cuda.Event(enable_timing=True)

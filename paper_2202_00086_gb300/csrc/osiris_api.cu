@@ -171,10 +171,16 @@ int persistent_shape(const osiris_trace_opts* o, int spacetime, int* block,
   return OSIRIS_OK;
 }
 
-// Work-distribution knobs of a launch (0 in the options = 1).
+// Work-distribution knobs of a launch (0 in the options = the library
+// default: one ray per lane; refill once 4 lanes of a busy warp are idle).
+// Measured on the 12 x 1024^2 Kerr set: refill granularity 1 / 4 / 8 gave
+// 16.2 / 18.5 / 18.1 Mrays/s in DF64 and 3.59 / 3.61 / 3.50 in FP64.
+constexpr int kDefaultRaysPerLane = 1;
+constexpr int kDefaultRefillLanes = 4;
+
 void set_granularity(KernelArgs& args, const osiris_trace_opts* o) {
-  args.rays_per_lane = o->rays_per_lane > 0 ? o->rays_per_lane : 1;
-  args.refill_lanes = o->refill_lanes > 0 ? o->refill_lanes : 1;
+  args.rays_per_lane = o->rays_per_lane > 0 ? o->rays_per_lane : kDefaultRaysPerLane;
+  args.refill_lanes = o->refill_lanes > 0 ? o->refill_lanes : kDefaultRefillLanes;
 }
 
 // Launch the trace kernel for the requests in args (args.reqs / single).

@@ -215,24 +215,24 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
     }
   };
 
-  // rays claimed by this lane and not yet started: [g_next, g_end)
-  int64_t g_next = 0, g_end = 0;
-  if (!PERSISTENT) plain_range(A, g_next, g_end);
+  init_claim<PERSISTENT>(A);
 
   for (;;) {
-    if (mode == MODE_IDLE && g_next < g_end) start_ray(g_next++);
+    if (mode == MODE_IDLE) {
+      const int64_t g = next_claimed(A);
+      if (g >= 0) start_ray(g);
+    }
     if (PERSISTENT) {
       int64_t first = 0;
       const int got = refill(A, (mode == MODE_IDLE) && !drained, mode != MODE_IDLE, first);
       if (got > 0) {
-        g_next = first;
-        g_end = first + got;
-        start_ray(g_next++);
+        set_claim(first + 1, got - 1);
+        start_ray(first);
       } else if (got < 0) {
         drained = true;
       }
     }
-    if (!__any_sync(FULL, mode != MODE_IDLE || g_next < g_end)) break;
+    if (!__any_sync(FULL, mode != MODE_IDLE || has_claim())) break;
     if (mode == MODE_IDLE) continue;
 
     const float hs_f = fminf(h, 0.1f * y.r.hi);

@@ -196,13 +196,57 @@ __device__ __forceinline__ int refill(const KernelArgs& A, bool need, bool busy,
   return (int)(total - g < per ? total - g : per);
 }
 
-// The rays a plain (one launch thread per ray range) launch gives this
-// thread: rays_per_lane consecutive rays from thread index x rays_per_lane.
-__device__ __forceinline__ void plain_range(const KernelArgs& A, int64_t& next, int64_t& end) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  next = t * A.rays_per_lane;
-  end = next + A.rays_per_lane;
-  if (end > A.total_rays) end = A.total_rays;
+// Rays a lane has claimed and not yet started, [next, end), one slot per
+// thread of the block (at most 256). They live in shared memory, and are
+// read and written only by the lane itself when it is idle, so no register
+// holds them across the attempt loop. Volatile: the accesses stay in memory.
+constexpr int kClaimSlots = 256;
+
+struct LaneClaims {
+  volatile long long next[kClaimSlots], end[kClaimSlots];
+};
+
+__device__ __forceinline__ LaneClaims& lane_claims() {
+  __shared__ LaneClaims claims;
+  return claims;
+}
+
+// The lane's first claim: a plain launch (one launch thread per ray range)
+// gives each thread rays_per_lane consecutive rays from thread index x
+// rays_per_lane; a persistent grid starts with none and refills.
+template <bool PERSISTENT>
+__device__ __forceinline__ void init_claim(const KernelArgs& A) {
+  LaneClaims& C = lane_claims();
+  long long next = 0, end = 0;
+  if (!PERSISTENT) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    next = t * A.rays_per_lane;
+    end = next + A.rays_per_lane;
+    if (end > A.total_rays) end = A.total_rays;
+  }
+  C.next[threadIdx.x] = next;
+  C.end[threadIdx.x] = end;
+}
+
+// Next claimed ray of an idle lane (-1 when its claim is used up).
+__device__ __forceinline__ int64_t next_claimed(const KernelArgs&) {
+  LaneClaims& C = lane_claims();
+  const long long g = C.next[threadIdx.x];
+  if (g >= C.end[threadIdx.x]) return -1;
+  C.next[threadIdx.x] = g + 1;
+  return g;
+}
+
+// True when the lane still holds claimed rays (idle lanes only ask).
+__device__ __forceinline__ bool has_claim() {
+  LaneClaims& C = lane_claims();
+  return C.next[threadIdx.x] < C.end[threadIdx.x];
+}
+
+__device__ __forceinline__ void set_claim(int64_t first, int count) {
+  LaneClaims& C = lane_claims();
+  C.next[threadIdx.x] = first;
+  C.end[threadIdx.x] = first + count;
 }
 
 template <class Stepper, bool PERSISTENT>
@@ -293,24 +337,24 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
     }
   };
 
-  // rays claimed by this lane and not yet started: [g_next, g_end)
-  int64_t g_next = 0, g_end = 0;
-  if (!PERSISTENT) plain_range(A, g_next, g_end);
+  init_claim<PERSISTENT>(A);
 
   for (;;) {
-    if (mode == MODE_IDLE && g_next < g_end) start_ray(g_next++);
+    if (mode == MODE_IDLE) {
+      const int64_t g = next_claimed(A);
+      if (g >= 0) start_ray(g);
+    }
     if (PERSISTENT) {
       int64_t first = 0;
       const int got = refill(A, (mode == MODE_IDLE) && !drained, mode != MODE_IDLE, first);
       if (got > 0) {
-        g_next = first;
-        g_end = first + got;
-        start_ray(g_next++);
+        set_claim(first + 1, got - 1);
+        start_ray(first);
       } else if (got < 0) {
         drained = true;
       }
     }
-    if (!__any_sync(FULL, mode != MODE_IDLE || g_next < g_end)) break;
+    if (!__any_sync(FULL, mode != MODE_IDLE || has_claim())) break;
     if (mode == MODE_IDLE) continue;
 
     const double hs = (mode == MODE_LOCATE) ? h_try : fmin(h, 0.1 * y.r);

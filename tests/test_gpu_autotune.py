@@ -21,7 +21,7 @@ def test_autotune_small_sample(tmp_path):
     path = os.path.join(tmp_path, "tune.json")
     rds = [workloads.render(a, 1000.0, 60.0, (-8, 8, -8, 8), 48, 48) for a in (0.0, 0.9)]
     cands = [(64, 0), (128, 0), (128, 2), (256, 1)]
-    grans = [(1, 1), (2, 4), (4, 32)]
+    grans = [(0, 0), (2, 4), (4, 32)]
     best, timings = autotune.autotune(osr.DF64, 0, renders=rds, cands=cands, grans=grans,
                                       cache_path=path)
     assert best[:2] in cands and best[2:] in grans
