@@ -71,7 +71,7 @@ constexpr double PIO2_LO = 6.123233995736766e-17;
 constexpr double TWO_PI = 6.283185307179586;
 constexpr double PI_D = 3.141592653589793;
 
-enum : int { MODE_IDLE = 0, MODE_INTEGRATE = 1, MODE_LOCATE = 2 };
+enum : int { MODE_IDLE = 0, MODE_INTEGRATE = 1, MODE_LOCATE = 2, MODE_DONE = 3 };
 enum : int { SURF_EQUATOR = 0, SURF_CAPTURE = 1, SURF_ESCAPE = 2 };
 
 struct State {  // evolved coordinates and momenta (t does not feed back; not integrated)

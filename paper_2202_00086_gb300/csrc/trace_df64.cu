@@ -166,14 +166,25 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
     mode = MODE_INTEGRATE;
   };
 
+  // The ray has ended with `status` at state fd: keep both and wait (DONE)
+  // until complete() writes its outputs together with other lanes' (see
+  // complete_finished in trace_kernel.cuh).
+  int done_status = 0;
   auto finish = [&](int status, const StateDF& fd) {
-    const State f = to_double(fd);
+    done_status = status;
+    yF = fd;
+    mode = MODE_DONE;
+  };
+
+  // The FP64 end-point |H| check and the outputs of a DONE lane; retires it.
+  auto complete = [&]() {
+    const State f = to_double(yF);
     double mh = (double)max_abs_H;
-    if (status != OSIRIS_STATUS_ERROR) {
+    if (done_status != OSIRIS_STATUS_ERROR) {
       mh = fmax(mh, fabs(0.5 * Met::twoH_fp64(I.K, f) - I.H0));
       S.rhs += 1;
     }
-    write_outputs(A, I, status, f, mh, n_acc, n_rej, S);
+    write_outputs(A, I, done_status, f, mh, n_acc, n_rej, S);
     mode = MODE_IDLE;
   };
 
@@ -218,13 +229,15 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
   init_claim<PERSISTENT>(A);
 
   for (;;) {
+    if (complete_finished(A, mode)) complete();
+    const bool busy = (mode == MODE_INTEGRATE) || (mode == MODE_LOCATE);
     if (mode == MODE_IDLE) {
       const int64_t g = next_claimed(A);
       if (g >= 0) start_ray(g);
     }
     if (PERSISTENT) {
       int64_t first = 0;
-      const int got = refill(A, (mode == MODE_IDLE) && !drained, mode != MODE_IDLE, first);
+      const int got = refill(A, (mode == MODE_IDLE) && !drained, busy, first);
       if (got > 0) {
         set_claim(first + 1, got - 1);
         start_ray(first);
@@ -233,7 +246,7 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
       }
     }
     if (!__any_sync(FULL, mode != MODE_IDLE || has_claim())) break;
-    if (mode == MODE_IDLE) continue;
+    if (mode != MODE_INTEGRATE && mode != MODE_LOCATE) continue;
 
     const float hs_f = fminf(h, 0.1f * y.r.hi);
     const df hd = (mode == MODE_LOCATE) ? df_from_double(h_try) : mk(hs_f, 0.0f);

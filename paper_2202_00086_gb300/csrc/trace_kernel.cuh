@@ -196,6 +196,20 @@ __device__ __forceinline__ int refill(const KernelArgs& A, bool need, bool busy,
   return (int)(total - g < per ? total - g : per);
 }
 
+// Lanes whose ray has ended (DONE) complete it (end-point check, outputs)
+// together: once refill_lanes of the warp are DONE, or when no lane of the
+// warp is still integrating. Their warp instructions, FP64 for the most part,
+// are then shared by several lanes instead of being issued for one lane at a
+// time as each ray ends. Warp-uniform decision; returns true for the lanes
+// that complete now.
+__device__ __forceinline__ bool complete_finished(const KernelArgs& A, int mode) {
+  const unsigned FULL = 0xffffffffu;
+  const unsigned done = __ballot_sync(FULL, mode == MODE_DONE);
+  if (!done) return false;
+  const unsigned busy = __ballot_sync(FULL, mode == MODE_INTEGRATE || mode == MODE_LOCATE);
+  return (mode == MODE_DONE) && (!busy || __popc(done) >= A.refill_lanes);
+}
+
 // Rays a lane has claimed and not yet started, [next, end), one slot per
 // thread of the block (at most 256). They live in shared memory, and are
 // read and written only by the lane itself when it is idle, so no register
@@ -293,13 +307,23 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
     mode = MODE_INTEGRATE;
   };
 
-  // Write the ray's outputs and retire the lane.
+  // The ray has ended with `status` at state f: keep both and wait (DONE)
+  // until complete() writes its outputs together with other lanes' (see
+  // complete_finished).
+  int done_status = 0;
   auto finish = [&](int status, const State& f) {
-    if (status != OSIRIS_STATUS_ERROR) {
-      track_abs_H(max_abs_H, Stepper::twoH(K, f), I.H0);
+    done_status = status;
+    yF = f;
+    mode = MODE_DONE;
+  };
+
+  // The end-point |H| check and the outputs of a DONE lane; retires it.
+  auto complete = [&]() {
+    if (done_status != OSIRIS_STATUS_ERROR) {
+      track_abs_H(max_abs_H, Stepper::twoH(K, yF), I.H0);
       S.rhs += 1;
     }
-    write_outputs(A, I, status, f, __longlong_as_double(max_abs_H), n_acc, n_rej, S);
+    write_outputs(A, I, done_status, yF, __longlong_as_double(max_abs_H), n_acc, n_rej, S);
     mode = MODE_IDLE;
   };
 
@@ -340,13 +364,15 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
   init_claim<PERSISTENT>(A);
 
   for (;;) {
+    if (complete_finished(A, mode)) complete();
+    const bool busy = (mode == MODE_INTEGRATE) || (mode == MODE_LOCATE);
     if (mode == MODE_IDLE) {
       const int64_t g = next_claimed(A);
       if (g >= 0) start_ray(g);
     }
     if (PERSISTENT) {
       int64_t first = 0;
-      const int got = refill(A, (mode == MODE_IDLE) && !drained, mode != MODE_IDLE, first);
+      const int got = refill(A, (mode == MODE_IDLE) && !drained, busy, first);
       if (got > 0) {
         set_claim(first + 1, got - 1);
         start_ray(first);
@@ -355,7 +381,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
       }
     }
     if (!__any_sync(FULL, mode != MODE_IDLE || has_claim())) break;
-    if (mode == MODE_IDLE) continue;
+    if (mode != MODE_INTEGRATE && mode != MODE_LOCATE) continue;
 
     const double hs = (mode == MODE_LOCATE) ? h_try : fmin(h, 0.1 * y.r);
     State o, d;
