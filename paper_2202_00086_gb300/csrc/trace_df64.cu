@@ -100,9 +100,13 @@ __device__ __forceinline__ RayQDF to_qdf(const RayK& K) {
 // shared memory is reserved. Measured on the 12 x 1024^2 Kerr set (Mrays/s,
 // Cash-Karp): 168 registers (three blocks) 14.4, 128: 15.5, 112: 15.4,
 // 96: 15.3, 80: 14.7.
+#ifndef OSIRIS_DF64_MAXREGS
+#define OSIRIS_DF64_MAXREGS 128
+#endif
+
 struct KerrDF {
   using Ray = RayDF;
-  static constexpr int kMaxRegs = 128;
+  static constexpr int kMaxRegs = OSIRIS_DF64_MAXREGS;
   static __device__ __forceinline__ Ray ray(const RayK& K) { return to_df(K); }
   static __device__ __forceinline__ void rhs(const Ray& K, df r, df th, df pr, df pth, df& dr,
                                              df& dth, df& dph, df& dpr, df& dpth,
@@ -116,7 +120,7 @@ struct KerrDF {
 
 struct QMetricDF {
   using Ray = RayQDF;
-  static constexpr int kMaxRegs = 128;
+  static constexpr int kMaxRegs = OSIRIS_DF64_MAXREGS;
   static __device__ __forceinline__ Ray ray(const RayK& K) { return to_qdf(K); }
   static __device__ __forceinline__ void rhs(const Ray& K, df r, df th, df pr, df pth, df& dr,
                                              df& dth, df& dph, df& dpr, df& dpth,
