@@ -47,10 +47,11 @@ SHADOW_BYTES_PER_RAY = 42
 DISK_BYTES_PER_RAY = 66  # + g, intensity, r_hit 3x8
 ORACLE_SAMPLE_STRIDE = 128  # CPU baseline: every 128th pixel of each render
 E2E_STEPS = 5  # end-to-end leg: steps timed with host copies (wall clock)
-# DRAM bytes (read + write) of one FP64 trace launch over the 1024^2 set, from
-# an ncu capture of the current kernel (None while the kernel has changed
-# since the counters were taken).
-FP64_TRAFFIC_BYTES_PER_LAUNCH = None
+# DRAM bytes (read + write) of one FP64 trace launch over the 1024^2 set: ncu
+# capture (one pass) of the timed launch of the current kernel, 48.34 MB read
+# + 535.75 MB written (profiles/trace_fp64_persistent_kerr12x1024_dram.md);
+# the outputs alone are 528.5 MB (42 B per ray).
+FP64_TRAFFIC_BYTES_PER_LAUNCH = 584.09e6
 # FP32-pipe (FMA heavy + lite) thread instructions per double-float Cash-Karp
 # attempt on the Kerr set: ncu capture of trace_df64_persistent on the 12
 # renders at 256x256 (3.6286e10 FMA-pipe warp instructions x 28.65 active

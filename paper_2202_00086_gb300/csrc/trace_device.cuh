@@ -401,6 +401,10 @@ __device__ __forceinline__ double twoH_q_direct(const RayK& K, const State& y) {
 }
 
 // Metric policies for the FP64 steppers.
+#ifndef OSIRIS_FP64_MAXREGS
+#define OSIRIS_FP64_MAXREGS 255
+#endif
+
 struct KerrMetric {
   static constexpr bool kTrigTable = true;  // rhs64 reads the block's sincos table
   static constexpr bool kExpLogTable = false;
@@ -408,7 +412,7 @@ struct KerrMetric {
   // SM): measured on the 12 x 1024^2 Kerr set, 3.09 Mrays/s uncapped against
   // 2.95 at 168 registers (three blocks) and 2.90 at 152 or 128 (three or
   // four blocks). The FP64 pipe needs the scheduling freedom more than warps.
-  static constexpr int kMaxRegs = 255;
+  static constexpr int kMaxRegs = OSIRIS_FP64_MAXREGS;
   static __device__ __forceinline__ void rhs(const RayK& K, double r, double th, double pr,
                                              double pth, double& dr, double& dth, double& dph,
                                              double& dpr, double& dpth, double& twoH,
@@ -419,7 +423,7 @@ struct KerrMetric {
 struct QMetric {
   static constexpr bool kTrigTable = true;  // rhs_q64 reads the block's sincos table
   static constexpr bool kExpLogTable = true;  // and the exp/log tables
-  static constexpr int kMaxRegs = 255;
+  static constexpr int kMaxRegs = OSIRIS_FP64_MAXREGS;
   static __device__ __forceinline__ void rhs(const RayK& K, double r, double th, double pr,
                                              double pth, double& dr, double& dth, double& dph,
                                              double& dpr, double& dpth, double& twoH,

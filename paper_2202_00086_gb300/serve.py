@@ -121,6 +121,7 @@ class RenderServer:
         self.failed = []  # timed out or abandoned after a stalled round
         self.stall_timeout_s = stall_timeout_s
         self.status = osr.OK
+        self._held = []  # buffers of renders retired while their rounds may still run
         self.bytes_in_use = 0
         self.rounds = 0
         self.launches = 0
@@ -189,6 +190,10 @@ class RenderServer:
         self.bytes_in_use -= r.bytes
         (self.done if state == DONE else
          self.cancelled if state == CANCELLED else self.failed).append(r)
+        if state in (TIMED_OUT, ABANDONED):
+            # launched ranges may still be running: their output buffers stay
+            # allocated until close() has seen every round complete
+            self._held.append((r.out, r.camera))
         if not self.keep_outputs or state != DONE:
             r.out = None
             r.camera = None
@@ -345,8 +350,10 @@ class RenderServer:
         return self.osr.ETIMEOUT if r.state in (TIMED_OUT, ABANDONED) else self.osr.OK
 
     def close(self, timeout_s=None):
-        """Wait (bounded when timeout_s is given) for every launched round;
-        returns OSIRIS_OK or OSIRIS_ETIMEOUT."""
+        """Wait (bounded when timeout_s is given) for every launched round,
+        then release the buffers of renders retired while their rounds were
+        still running; returns OSIRIS_OK or OSIRIS_ETIMEOUT (the buffers are
+        then kept)."""
         t0 = self.clock()
         while self.inflight:
             if self.inflight[0].event.query():
@@ -355,6 +362,7 @@ class RenderServer:
             if timeout_s is not None and self.clock() - t0 > timeout_s:
                 return self.osr.ETIMEOUT
             time.sleep(2e-4)
+        self._held = []
         return self.osr.OK
 
     def run(self, arrivals, realtime=True, poll_s=2e-4):

@@ -106,3 +106,28 @@ def test_oracle_library_loads():
     lib = oracle.lib()
     for n in ("oracle_trace_pixels", "oracle_trace_states", "oracle_init_ray"):
         assert hasattr(lib, n)
+
+
+def test_new_entry_points_validate_before_any_cuda_call(osr):
+    """Argument errors of the pipe probes, the bounded stream wait and the
+    work-distribution options are refused on the host (no GPU here)."""
+    L = osr.lib()
+    fl = ctypes.c_double()
+    buf = ctypes.c_void_p(1)  # never dereferenced: the arguments are refused first
+    for prec, op, n, iters in ((7, 0, 256, 1), (osr.FP64, 5, 256, 1), (osr.FP64, -1, 256, 1),
+                               (osr.FP64, 0, 100, 1), (osr.FP64, 0, 256, 0)):
+        assert L.osiris_pipe_probe(prec, op, n, iters, buf, ctypes.byref(fl), None) == osr.EINVAL
+    assert L.osiris_pipe_probe(osr.FP64, 0, 256, 1, None, ctypes.byref(fl), None) == osr.EINVAL
+    assert L.osiris_pipe_probe_threads(7, 0) == osr.EINVAL
+    assert L.osiris_pipe_probe_threads(osr.FP64, 9) == osr.EINVAL
+    assert L.osiris_stream_wait(None, -1.0) == osr.EINVAL
+    assert L.osiris_stream_wait(None, float("nan")) == osr.EINVAL
+    cam = osr.Camera(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 8, 8)
+    out = osr.Outputs()
+    for bad in (dict(rays_per_lane=-1), dict(rays_per_lane=65), dict(refill_lanes=-1),
+                dict(refill_lanes=33)):
+        o = osr.make_opts(**bad)
+        assert osr.lib().osiris_trace(cam.handle, ctypes.byref(o), ctypes.byref(out),
+                                      None) == osr.EINVAL, bad
+    o = osr.make_opts()
+    assert (o.rays_per_lane, o.refill_lanes) == (0, 0)  # 0 = the library default

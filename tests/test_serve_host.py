@@ -237,6 +237,12 @@ def test_stalled_round_times_out_without_waiting_forever():
     srv.step()
     assert len(be.rounds) == n_rounds  # and launches nothing
     assert srv.close(timeout_s=0.5) == osr.ETIMEOUT  # the stuck rounds are never waited out
+    # the retired renders' output buffers stay held while their rounds may still run
+    held = {id(out) for out, _ in srv._held}
+    assert len(held) == len(stream) and all(r.out is None for r in srv.failed)
+    for rnd in srv.inflight:  # the rounds finally complete: close() releases them
+        rnd.event = FakeEvent(0)
+    assert srv.close(timeout_s=0.5) == osr.OK and srv._held == []
 
 
 def test_bounded_wait_for_one_render():
