@@ -150,7 +150,8 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
   float h = 0.0f, max_abs_H = 0.0f;
   unsigned n_acc = 0, n_rej = 0;
   int kind = 0, side = 0, iters = 0;
-  double lo = 0, hi = 0, flo = 0, fhi = 0, h_try = 0, h_step = 0;
+  double lo = 0, hi = 0, h_try = 0, h_step = 0;
+  float flo = 0.0f, fhi = 0.0f;
   StateDF yF, yE;
   LaneCacheDF<INTEG> LC;
 
@@ -192,11 +193,24 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
     mode = MODE_IDLE;
   };
 
-  // FP64 value whose sign tells the side of the surface (see surface_value)
-  auto surf = [&](int k, const StateDF& s) -> double {
-    if (k == SURF_EQUATOR) return (PIO2_HI - df_to_double(s.th)) + PIO2_LO;
-    if (k == SURF_CAPTURE) return df_to_double(s.r) - I.r_cap;
-    return df_to_double(s.r) - I.r_esc;
+  // Signed distance to the surface (pi/2 - theta, r - r_cap or r - r_esc),
+  // formed in double-float (the difference of nearby values is exact) and
+  // rounded to FP32: its sign and its size relative to the tolerance are all
+  // surface location needs, so no FP64 instruction is spent on it.
+  auto surf = [&](int k, const StateDF& s) -> float {
+    const df d = (k == SURF_EQUATOR) ? df_sub(mk(dfc::P1, dfc::P2), s.th)
+                                     : df_sub(s.r, k == SURF_CAPTURE ? r_cap : r_esc);
+    return __fadd_rn(d.hi, d.lo);
+  };
+
+  // Next trial step length of the bracket [lo, hi]: the regula falsi point
+  // lo + (hi - lo) t, t = f_lo / (f_lo - f_hi) in FP32 (f_lo, f_hi have
+  // opposite signs, so t is in (0, 1) without cancellation); the midpoint if
+  // rounding put it on an end.
+  auto next_trial = [&]() {
+    const float t = __fdividef(flo, __fsub_rn(flo, fhi));
+    h_try = fma(hi - lo, (double)t, lo);
+    if (!(h_try > lo && h_try < hi)) h_try = 0.5 * (lo + hi);
   };
 
   auto begin_locate = [&](int k, double hs, const StateDF& o) {
@@ -208,8 +222,7 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
     yF = o;
     side = 0;
     iters = 0;
-    h_try = (lo * fhi - hi * flo) / (fhi - flo);
-    if (!(h_try > lo && h_try < hi)) h_try = 0.5 * (lo + hi);
+    next_trial();
     mode = MODE_LOCATE;
   };
 
@@ -304,28 +317,27 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
         continue;
       }
       const double hs = h_try;
-      const double f = surf(kind, o);
-      const bool to_lo = (f != 0.0) && ((f > 0.0) == (flo > 0.0));
+      const float f = surf(kind, o);
+      const bool to_lo = (f != 0.0f) && ((f > 0.0f) == (flo > 0.0f));
       if (to_lo) {
         lo = hs;
         flo = f;
-        if (side == -1) fhi *= 0.5;
+        if (side == -1) fhi *= 0.5f;
         side = -1;
       } else {
         hi = hs;
         fhi = f;
         yF = o;
-        if (side == +1) flo *= 0.5;
+        if (side == +1) flo *= 0.5f;
         side = +1;
       }
-      const double ftol = (kind == SURF_EQUATOR)
-                              ? 1e-15
-                              : 1e-14 * (kind == SURF_CAPTURE ? I.r_cap : I.r_esc);
-      const bool done = (f == 0.0) || (!to_lo && fabs(f) <= ftol) || (hi - lo <= 4e-16 * hi) ||
-                        iters >= 64;
+      const float ftol = (kind == SURF_EQUATOR)
+                             ? 1e-15f
+                             : 1e-14f * (kind == SURF_CAPTURE ? r_cap.hi : r_esc.hi);
+      const bool done = (f == 0.0f) || (!to_lo && fabsf(f) <= ftol) ||
+                        (hi - lo <= 4e-16 * hi) || iters >= 64;
       if (!done) {
-        h_try = (lo * fhi - hi * flo) / (fhi - flo);
-        if (!(h_try > lo && h_try < hi)) h_try = 0.5 * (lo + hi);
+        next_trial();
       } else if (kind == SURF_CAPTURE) {
         finish(OSIRIS_STATUS_CAPTURED, yF);
       } else if (kind == SURF_ESCAPE) {
