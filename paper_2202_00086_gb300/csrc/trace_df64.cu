@@ -2,9 +2,10 @@
 // in df64 arithmetic (pairs of FP32, 48-bit significand) on the FP32 pipe,
 // which on GB300 is ~70x the FP64 pipe: the six evaluations of Hamilton's
 // equations, the stage sums, the increment, the error estimate, the error
-// test and the stopping-surface tests. The state between steps is a df64
-// vector too. FP64 is used only once per ray (initial data, the terminal
-// state and its |H|, the observables) and inside surface location.
+// test, the stopping-surface tests and the end-point |H|. The state between
+// steps is a df64 vector too. FP64 is used only once per ray (initial data,
+// the terminal state and the observables) and for the step-length bracket of
+// surface location.
 //
 // Stage sums. With d_j = k_j - k_1 (j >= 2), the Cash-Karp combinations are
 //   stage input  y_i = y + c_i h k_1 + h sum_j a_ij d_j      (sum_j a_ij = c_i)
@@ -93,7 +94,7 @@ __device__ __forceinline__ RayQDF to_qdf(const RayK& K) {
 }
 
 // Metric policies of the double-float kernels: the ray constants, the
-// evaluation, the FP64 2H of the end-point check, and the register cap.
+// evaluation, and the register cap.
 // Registers capped at 128 so that four blocks of 128 threads (16 warps) are
 // resident per SM: the double-float dependency chains need the extra warps
 // more than they lose to the spilled values, which stay in L1 as long as no
@@ -113,9 +114,6 @@ struct KerrDF {
                                              float& twoH) {
     rhs_df(K, r, th, pr, pth, dr, dth, dph, dpr, dpth, twoH);
   }
-  static __device__ __forceinline__ double twoH_fp64(const RayK& K, const State& y) {
-    return twoH_kerr_direct(K, y);
-  }
 };
 
 struct QMetricDF {
@@ -126,9 +124,6 @@ struct QMetricDF {
                                              df& dth, df& dph, df& dpr, df& dpth,
                                              float& twoH) {
     rhs_q_df(K, r, th, pr, pth, dr, dth, dph, dpr, dpth, twoH);
-  }
-  static __device__ __forceinline__ double twoH_fp64(const RayK& K, const State& y) {
-    return twoH_q_direct(K, y);
   }
 };
 
@@ -181,15 +176,21 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
     mode = MODE_DONE;
   };
 
-  // The FP64 end-point |H| check and the outputs of a DONE lane; retires it.
+  // The end-point |H| check and the outputs of a DONE lane; retires it. The
+  // check evaluates 2 (H - H0) at the final state with the same double-float
+  // equations as every step (error ~2^-48 of the terms of 2H), on the FP32
+  // pipe; only the outputs are formed in FP64.
   auto complete = [&]() {
     const State f = to_double(yF);
-    double mh = (double)max_abs_H;
+    float mh = max_abs_H;
     if (done_status != OSIRIS_STATUS_ERROR) {
-      mh = fmax(mh, fabs(0.5 * Met::twoH_fp64(I.K, f) - I.H0));
+      df dr, dth, dph, dpr, dpth;
+      float twoH;
+      Met::rhs(KD, yF.r, yF.th, yF.pr, yF.pth, dr, dth, dph, dpr, dpth, twoH);
+      mh = fmaxf(mh, fabsf(0.5f * twoH));
       S.rhs += 1;
     }
-    write_outputs(A, I, done_status, f, mh, n_acc, n_rej, S);
+    write_outputs(A, I, done_status, f, (double)mh, n_acc, n_rej, S);
     mode = MODE_IDLE;
   };
 
