@@ -146,6 +146,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-hbar", action="store_true")
+    p.add_argument("--no-other-configs", action="store_true")
     p.add_argument("--hbar-side", type=int, default=512)
     p.add_argument("--serve-seconds", type=float, default=60.0)
     p.add_argument("--serve-rate", type=float, default=50.0)
@@ -423,6 +424,62 @@ def serving_leg(args, osr, torch, dist, rank, world, barrier, phase):
             "one_render_per_launch_fp64": base,
             "rays_per_s_ratio": (main["rays_per_s"] / base["rays_per_s"]
                                  if main["rays_per_s"] and base["rays_per_s"] else None)}
+
+
+def other_configs(osr, torch, flush, stream, phase):
+    """The target's other single-GPU configurations, each one launch timed
+    with CUDA events after the L2 flush (a warm-up launch first, except for
+    the 256-request batch, whose FP64 launch alone takes ~26 s), in FP64 and
+    DF64: the 64^2 Schwarzschild shadow, the 2048^2 Schwarzschild thin disk
+    (persistent grid) and the 256 uneven requests of PCG64(4) in one batched
+    launch."""
+    from paper_2202_00086_gb300 import workloads as wl
+
+    def timed(fn, warm=True):
+        if warm:
+            fn()
+            torch.cuda.synchronize()
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+
+    res = {}
+    ws = torch.empty(osr.workspace_bytes(256), dtype=torch.uint8, device="cuda")
+    for key, rd in (("config1_schwarzschild_shadow_64x64", wl.schwarzschild_shadow_64()),
+                    ("config3_schwarzschild_disk_2048x2048", wl.schwarzschild_disk())):
+        cam = osr.Camera.from_render(rd)
+        disk = rd["mode"] == "disk"
+        out = osr.alloc_outputs(cam.n_rays, fields=osr.DISK_FIELDS if disk else osr.SHADOW_FIELDS)
+        row = {"rays": cam.n_rays}
+        for prec, pn in ((osr.FP64, "fp64"), (osr.DF64, "df64")):
+            kw = dict(out=out, tol=rd["tol"], precision=prec, persistent=True, workspace=ws,
+                      cell_phase_deg=rd["cell_phase_deg"])
+            if disk:
+                t = timed(lambda: osr.render_disk(cam, rd["r_in"], rd["r_out"], **kw))
+            else:
+                t = timed(lambda: osr.trace(cam, **kw))
+            row[pn + "_rays_per_s"] = cam.n_rays / t
+        res[key] = row
+    rds = wl.uneven_batch()
+    cams = [osr.Camera.from_render(rd) for rd in rds]
+    outs = [osr.alloc_outputs(c.n_rays, fields=osr.DISK_FIELDS if rd["mode"] == "disk"
+                              else osr.SHADOW_FIELDS) for c, rd in zip(cams, rds)]
+    reqs = [{"camera": c, "out": o, "tol": rd["tol"], "disk": rd["mode"] == "disk",
+             "r_in": osr.resolve_r_in(rd) if rd["mode"] == "disk" else 0.0,
+             "r_out": rd["r_out"] if rd["mode"] == "disk" else 0.0}
+            for c, o, rd in zip(cams, outs, rds)]
+    n = sum(c.n_rays for c in cams)
+    row = {"rays": n, "requests": len(rds)}
+    for prec, pn in ((osr.FP64, "fp64"), (osr.DF64, "df64")):
+        t = timed(lambda: osr.trace_batch(reqs, workspace=ws, precision=prec,
+                                          cell_phase_deg=phase), warm=False)
+        row[pn + "_rays_per_s"] = n / t
+    res["config4_uneven_256_requests_sides_128_to_1024"] = row
+    return res
 
 
 def h_distribution(status, max_abs_H, bar=1e-10):
@@ -770,6 +827,12 @@ def main():
         hbar["sweep"] = {"renders": "the same 12 renders at %dx%d" % (side, side),
                          "points": sweep, "first_tol_meeting_bar": first_tol_meeting(sweep)}
 
+    # ---- the other single-GPU configurations (one timed launch each) ----
+    configs = None
+    if (not args.no_other_configs and args.workload == "kerr" and precision == osr.FP64
+            and args.side == 1024):
+        configs = other_configs(osr, torch, flush, stream, cell_phase)
+
     # ---- served render stream: continuous batching (DF64) vs one render per
     # launch (FP64 plain kernel), the same Poisson arrivals ----
     serving = None
@@ -831,6 +894,7 @@ def main():
         "variants": variants,
         "serving": serving,
         "hbar": hbar,
+        "other_configs": configs,
         "clocks": clk,
         "gpu_launches": kernel_launches,
         "e2e": e2e,

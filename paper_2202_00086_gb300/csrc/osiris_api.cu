@@ -91,6 +91,7 @@ void fill_common(ReqDev& R, double a, double r0, const osiris_trace_opts* o, dou
   R.h0 = 0.01 * r0;
   R.max_steps = o->max_steps;
   R.cell_rad = o->cell_deg * kPi / 180.0;
+  R.inv_cell = 1.0 / R.cell_rad;
   R.phase_rad = o->cell_phase_deg * kPi / 180.0;
   R.n_th_cells = static_cast<int32_t>(std::ceil(180.0 / o->cell_deg - 1e-9));
   R.n_ph_cells = static_cast<int32_t>(std::ceil(360.0 / o->cell_deg - 1e-9));

@@ -39,7 +39,7 @@ struct alignas(16) ReqDev {
   double tol, h0;
   int64_t max_steps;
   // celestial checkerboard
-  double cell_rad, phase_rad;
+  double cell_rad, phase_rad, inv_cell;  // inv_cell = 1 / cell_rad
   int32_t n_th_cells, n_ph_cells;
   // position in the launch's global ray queue; pixel index of its first ray
   int64_t ray_begin, n_rays, pixel_offset;

@@ -103,6 +103,16 @@ __device__ __forceinline__ bool load_ray(const KernelArgs& A, int64_t g, RayInfo
   return true;
 }
 
+// x reduced into [0, 2 pi): x - 2 pi floor(x / (2 pi)) with one rounding in
+// the fused multiply-add (error a few ulp of x), then the ends fixed.
+__device__ __forceinline__ double wrap_2pi(double x) {
+  constexpr double INV_TWO_PI = 0.15915494309189535;
+  double t = fma(-TWO_PI, floor(x * INV_TWO_PI), x);
+  if (t < 0.0) t += TWO_PI;
+  if (t >= TWO_PI) t -= TWO_PI;
+  return t;
+}
+
 // Write the outputs of a finished ray (terminal state f, final max |H|) and
 // fold it into the lane's counters.
 __device__ __forceinline__ void write_outputs(const KernelArgs& A, const RayInfo& I, int status,
@@ -120,17 +130,18 @@ __device__ __forceinline__ void write_outputs(const KernelArgs& A, const RayInfo
   int ci = -1, cj = -1, par = 0;
   if (status == OSIRIS_STATUS_ESCAPED) {
     // celestial checkerboard: fold theta into [0, pi], wrap phi into [0, 2pi)
-    double t = fmod(f.th, TWO_PI);
-    if (t < 0.0) t += TWO_PI;
+    // (angles reduced by floor instead of the library fmod, cells by the
+    // host's reciprocal of the cell size: a cell index can differ from the
+    // divided one only within ~1e-15 rad of an edge)
+    double t = wrap_2pi(f.th);
     double p = f.ph;
     if (t > PI_D) {
       t = TWO_PI - t;
       p += PI_D;
     }
-    double q = fmod(p + R->phase_rad, TWO_PI);
-    if (q < 0.0) q += TWO_PI;
-    ci = (int)floor(t / R->cell_rad);
-    cj = (int)floor(q / R->cell_rad);
+    const double q = wrap_2pi(p + R->phase_rad);
+    ci = (int)floor(t * R->inv_cell);
+    cj = (int)floor(q * R->inv_cell);
     ci = min(max(ci, 0), R->n_th_cells - 1);
     cj = ((cj % R->n_ph_cells) + R->n_ph_cells) % R->n_ph_cells;
     par = (ci + cj) & 1;

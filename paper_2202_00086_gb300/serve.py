@@ -2,7 +2,8 @@
 
 Renders (camera set-ups) arrive over time. The server:
   - admits a waiting render when its output buffers fit in an HBM budget
-    (outputs stay on the device until the render completes);
+    (by default 80 % of the device memory free when the server starts;
+    outputs stay on the device until the render completes);
   - runs rounds: each round is ONE persistent batched launch over pixel
     ranges of every active render, so renders that arrive while others are on
     the GPU join the next round and their rays share launches with the older
@@ -52,6 +53,7 @@ import numpy as np
 
 SHADOW_BYTES_PER_RAY = 42  # status 1, r/theta/phi/max|H| 32, steps 4, cells 4, parity 1
 DISK_BYTES_PER_RAY = 66    # + g, intensity, r_hit
+HBM_SHARE = 0.8  # default admission budget: this share of the free device memory
 
 
 # render states
@@ -96,7 +98,7 @@ class _Round:
 
 class RenderServer:
     def __init__(self, precision=None, round_rays=1 << 21, min_chunk=1 << 14,
-                 hbm_budget_bytes=8 << 30, max_inflight=2, max_entries=4096,
+                 hbm_budget_bytes=None, max_inflight=2, max_entries=4096,
                  keep_outputs=False, cell_deg=10.0, cell_phase_deg=0.0, backend=None,
                  clock=time.perf_counter, graphs=True, stall_timeout_s=None):
         import paper_2202_00086_gb300 as osr
@@ -104,6 +106,11 @@ class RenderServer:
         self.precision = osr.DF64 if precision is None else precision
         self.round_rays = int(round_rays)
         self.min_chunk = int(min_chunk)
+        self.backend = backend if backend is not None else _CudaBackend(osr)
+        if hbm_budget_bytes is None:
+            # the renders' device outputs may take this share of the memory that
+            # is free when the server starts (the rest is left to the caller)
+            hbm_budget_bytes = int(HBM_SHARE * self.backend.free_bytes())
         self.hbm_budget = int(hbm_budget_bytes)
         self.max_inflight = int(max_inflight)
         self.max_entries = int(max_entries)
@@ -111,7 +118,6 @@ class RenderServer:
         self.cell_deg = cell_deg
         self.cell_phase_deg = cell_phase_deg
         self.clock = clock
-        self.backend = backend if backend is not None else _CudaBackend(osr)
         self.waiting = collections.deque()
         self.active = []
         self.inflight = collections.deque()
@@ -511,6 +517,13 @@ class _CudaBackend:
 
     def workspace(self, nbytes):
         return self.torch.empty(nbytes, dtype=self.torch.uint8, device="cuda")
+
+    def free_bytes(self):
+        """Device memory free now (cudaMemGetInfo), plus what torch's caching
+        allocator holds but does not use."""
+        free, _ = self.torch.cuda.mem_get_info()
+        cached = self.torch.cuda.memory_reserved() - self.torch.cuda.memory_allocated()
+        return free + cached
 
     def camera(self, rd):
         return self.osr.Camera.from_render(rd)

@@ -106,6 +106,7 @@ def test_gpu_arm_line():
     assert hb["bar"] == 1e-10
     assert set(hb["ck45_tol1e-10"]["by_status"]) <= {"captured", "escaped", "disk"}
     assert len(hb["sweep"]["points"]) == 6
+    assert d["other_configs"] is None  # the other configurations run only at the full size
 
 
 @pytest.mark.gpu

@@ -28,6 +28,9 @@ class FakeBackend:
     def workspace(self, nbytes):
         return object()
 
+    def free_bytes(self):
+        return 10 << 30
+
     def camera(self, rd):
         return ("camera", rd["nx"], rd["ny"], rd.get("q"))
 
@@ -258,3 +261,10 @@ def test_bounded_wait_for_one_render():
     r2 = srv2.submit(workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 32, 32))
     assert srv2.wait(r2, timeout_s=0.05, poll_s=0) == osr.ETIMEOUT
     assert r2.state == serve.ACTIVE  # still in flight: nothing was waited for without bound
+
+
+def test_default_budget_is_a_share_of_free_memory():
+    srv, be = _server()
+    assert srv.hbm_budget == int(serve.HBM_SHARE * (10 << 30))
+    big = workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 16384, 16384)  # 11.3 GB of outputs
+    assert srv.submit(big).state == serve.REJECTED
