@@ -116,8 +116,10 @@ def trace_pixels(a, r_obs, incl_deg, extent, nx, ny, pixels=None, M=1.0, nthread
 
     extent = (x_min, x_max, y_min, y_max); pixels = linear indices j*nx + i
     (default: the whole image). Returns a dict of numpy arrays, one entry per
-    traced pixel.  Parity unpinned for generic Kerr rays' final coordinates
-    (no closed form); the pinned parts are listed in tests/test_oracle_pins.py.
+    traced pixel. Generic Kerr escape points are pinned to the quadratures of
+    the first integrals (Mino time); parity unpinned for generic q-metric rays
+    (q != 0: no Carter constant, no quadrature). The pins are listed in
+    tests/test_oracle_pins.py.
     """
     L = lib()
     if pixels is None:
