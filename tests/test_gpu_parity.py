@@ -220,15 +220,15 @@ def test_full_size_schwarzschild_disk_sampled(precision):
 
 @pytest.mark.parametrize("precision", [osr.FP64, osr.DF64])
 def test_kerr_escape_points_against_first_integrals(precision):
-    """The GPU's escape points of generic Kerr rays (a = 0.9, 0.998, 0.5;
-    inclinations 60, 17, 90 deg), traced at tol 1e-12 from the oracle's
-    initial data, against the exact escape points from the quadratures of
-    the first integrals (tests/test_oracle_pins.py): cos theta and phi within
-    1e-8 (the oracle itself agrees to 2e-11)."""
-    from test_oracle_pins import _kerr_escape_point
-    for a, inc, pix in [(0.9, 60.0, [(6.5, 1.0), (-7.5, 2.0), (2.0, -6.8)]),
-                        (0.998, 17.0, [(6.0, 1.5), (-4.5, 5.5)]),
-                        (0.5, 90.0, [(0.8, 6.5), (-6.0, -2.0)])]:
+    """The GPU's end points of generic Kerr rays (a = 0.9, 0.998, 0.5;
+    inclinations 60, 17, 90 deg; escaping and captured), traced at tol 1e-12
+    from the oracle's initial data, against the exact end points from the
+    quadratures of the first integrals (tests/test_oracle_pins.py): cos theta
+    and phi within 1e-8 (the oracle itself agrees to 2e-11)."""
+    from test_oracle_pins import KERR_END_POINT_RAYS, _kerr_escape_point
+    for a, inc, esc, cap in KERR_END_POINT_RAYS:
+        pix = esc + cap
+        r_cap = 1.01 * (1.0 + math.sqrt(1.0 - a * a))
         st = np.array([oracle.init_ray(a, 1000.0, inc, x, y) for x, y in pix])
         out = osr.trace_states(a, 1000.0, torch.tensor(st[:, :6], device="cuda").contiguous(),
                                torch.tensor(st[:, 6], device="cuda"),
@@ -236,8 +236,9 @@ def test_kerr_escape_points_against_first_integrals(precision):
                                precision=precision)
         torch.cuda.synchronize()
         got = {k: v.cpu().numpy() for k, v in out.items()}
-        assert np.all(got["status"] == osr.STATUS_ESCAPED)
+        assert got["status"].tolist() == ([osr.STATUS_ESCAPED] * len(esc) +
+                                          [osr.STATUS_CAPTURED] * len(cap))
         for k in range(len(pix)):
-            uf, phif = _kerr_escape_point(a, 1100.0, st[k])
+            uf, phif = _kerr_escape_point(a, 1100.0, st[k], r_cap=r_cap)
             assert abs(math.cos(got["theta"][k]) - uf) < 1e-8, (a, pix[k])
             assert abs(got["phi"][k] - phif) < 1e-8 * max(1.0, abs(phif)), (a, pix[k])

@@ -866,15 +866,17 @@ def test_timelike_radial_escape_and_H_shell():
 # Generic Kerr escape points from the first integrals (Mino-time quadratures)
 # ---------------------------------------------------------------------------
 
-def _kerr_escape_point(a, r_esc, st):
-    """Final (cos theta, phi) at r = r_esc of an escaping Kerr null geodesic,
-    from its first integrals alone (Carter 1968), with E = 1, xi = L/E and
+def _kerr_escape_point(a, r_esc, st, r_cap=None):
+    """Final (cos theta, phi) at r = r_esc of an escaping Kerr null geodesic
+    or, when it has no radial turning point outside r_cap, at r = r_cap where
+    it is captured: from its first integrals alone (Carter 1968), with E = 1, xi = L/E and
     eta = Q/E^2, in Mino time tau (d tau = d lambda / Sigma):
       (dr/dtau)^2 = R(r) = (r^2 + a^2 - a xi)^2 - Delta (eta + (xi - a)^2),
       (du/dtau)^2 = U(u) = eta - (eta + xi^2 - a^2) u^2 - a^2 u^4,  u = cos theta,
       dphi/dtau  = a (r^2 + a^2 - a xi) / Delta - a + xi / (1 - u^2).
     The radial leg runs in from r0 to the turning point r_min (largest root of
-    R) and out to r_esc; its Mino time is how far u travels along its
+    R) and out to r_esc (or, captured, from r0 to r_cap); its Mino time is how
+    far u travels along its
     oscillation between -u+ and +u+, starting in the direction opposite to the
     sign of p_theta. Every integral is a one-dimensional quadrature (mpmath,
     30 digits) with the potentials factored at their turning points, so the
@@ -889,15 +891,22 @@ def _kerr_escape_point(a, r_esc, st):
     # R(r) = r^4 + c2 r^2 + c1 r + c0 and its largest real root
     c2, c1, c0 = a * a - xi * xi - eta, 2 * (eta + (xi - a) ** 2), -a * a * eta
     roots = mp.polyroots([1, 0, c2, c1, c0], maxsteps=400, extraprec=200)
-    r_min = max(mp.re(z) for z in roots if abs(mp.im(z)) < mp.mpf(10) ** -20)
-    assert r_min > 1 + mp.sqrt(1 - a * a)  # a turning point outside the horizon: it escapes
-    b2 = r_min                       # R = (r - r_min) (r^3 + b2 r^2 + b1 r + b0)
-    b1 = c2 + r_min * b2
-    b0 = c1 + r_min * b1
+    real = [mp.re(z) for z in roots if abs(mp.im(z)) < mp.mpf(10) ** -20]
+    r_min = max(real) if real else None
+    if r_min is not None and r_min > (r_cap if r_cap is not None else 1):
+        b2 = r_min                   # R = (r - r_min) (r^3 + b2 r^2 + b1 r + b0)
+        b1 = c2 + r_min * b2
+        b0 = c1 + r_min * b1
 
-    def radial(f):
-        g = lambda r: f(r) / mp.sqrt((r - r_min) * (((r + b2) * r + b1) * r + b0))
-        return mp.quad(g, [r_min, r0]) + mp.quad(g, [r_min, r_esc])
+        def radial(f):
+            g = lambda r: f(r) / mp.sqrt((r - r_min) * (((r + b2) * r + b1) * r + b0))
+            return mp.quad(g, [r_min, r0]) + mp.quad(g, [r_min, r_esc])
+    else:  # no turning point before the capture radius: one inward leg
+        assert r_cap is not None
+
+        def radial(f):
+            g = lambda r: f(r) / mp.sqrt((((r * r + c2) * r + c1) * r + c0))
+            return mp.quad(g, [mp.mpf(r_cap), r0])
 
     tau = radial(lambda r: 1)
     phi = radial(lambda r: a * (r * r + a * a - a * xi) / (r * r - 2 * r + a * a) - a)
@@ -925,22 +934,28 @@ def _kerr_escape_point(a, r_esc, st):
         u, s = end, -s
 
 
-@pytest.mark.parametrize("a,inc,pixels", [
-    (0.9, 60.0, [(6.5, 1.0), (-7.5, 2.0), (2.0, -6.8)]),
-    (0.998, 17.0, [(6.0, 1.5), (-4.5, 5.5)]),
-    (0.5, 90.0, [(0.8, 6.5), (-6.0, -2.0)]),
-])
-def test_kerr_escape_point_from_first_integrals(a, inc, pixels):
+KERR_END_POINT_RAYS = [  # (a, inclination, escaping pixels, captured pixels)
+    (0.9, 60.0, [(6.5, 1.0), (-7.5, 2.0), (2.0, -6.8)], [(1.0, 0.5), (-2.5, -1.0)]),
+    (0.998, 17.0, [(6.0, 1.5), (-4.5, 5.5)], [(0.5, 2.0)]),
+    (0.5, 90.0, [(0.8, 6.5), (-6.0, -2.0)], [(-1.5, 3.0)]),
+]
+
+
+@pytest.mark.parametrize("a,inc,pixels,captured", KERR_END_POINT_RAYS)
+def test_kerr_escape_point_from_first_integrals(a, inc, pixels, captured):
     """Generic Kerr rays (a != 0, off the equator, several passes through the
-    polar turning points): the oracle's escape point (cos theta, phi) at
-    r_esc = 1.1 r0, integrated at tol 1e-12, agrees with the quadratures of
-    the first integrals to 1e-8. A slip in any derivative of the oracle's
-    equations of motion moves the escape point by far more."""
+    polar turning points): the oracle's end point (cos theta, phi) at
+    r_esc = 1.1 r0 for escaping rays and at r_cap = 1.01 r_H for captured
+    ones, integrated at tol 1e-12, agrees with the quadratures of the first
+    integrals to 1e-8. A slip in any derivative of the oracle's equations of
+    motion moves the end point by far more."""
     r0 = 1000.0
-    for x, y in pixels:
+    r_cap = 1.01 * (1.0 + math.sqrt(1.0 - a * a))
+    for (x, y), fate in [(p, oracle.STATUS_ESCAPED) for p in pixels] + \
+                        [(p, oracle.STATUS_CAPTURED) for p in captured]:
         st = oracle.init_ray(a, r0, inc, x, y)
         res = oracle.trace_states(a, r0, st[None, :6], [st[6]], [st[7]], tol=1e-12)
-        assert res["status"][0] == oracle.STATUS_ESCAPED, (a, inc, x, y)
-        uf, phif = _kerr_escape_point(a, 1.1 * r0, st)
+        assert res["status"][0] == fate, (a, inc, x, y)
+        uf, phif = _kerr_escape_point(a, 1.1 * r0, st, r_cap=r_cap)
         assert abs(math.cos(res["theta"][0]) - uf) < 1e-8, (x, y, math.cos(res["theta"][0]), uf)
         assert abs(res["phi"][0] - phif) < 1e-8 * max(1.0, abs(phif)), (x, y, res["phi"][0], phif)
