@@ -222,23 +222,25 @@ def test_full_size_schwarzschild_disk_sampled(precision):
 def test_kerr_escape_points_against_first_integrals(precision):
     """The GPU's end points of generic Kerr rays (a = 0.9, 0.998, 0.5;
     inclinations 60, 17, 90 deg; escaping and captured), traced at tol 1e-12
-    from the oracle's initial data, against the exact end points from the
-    quadratures of the first integrals (tests/test_oracle_pins.py): cos theta
-    and phi within 1e-8 (the oracle itself agrees to 2e-11)."""
-    from test_oracle_pins import KERR_END_POINT_RAYS, _kerr_escape_point
-    for a, inc, esc, cap in KERR_END_POINT_RAYS:
-        pix = esc + cap
-        r_cap = 1.01 * (1.0 + math.sqrt(1.0 - a * a))
-        st = np.array([oracle.init_ray(a, 1000.0, inc, x, y) for x, y in pix])
+    from the oracle's initial data, against their exact end points from the
+    quadratures of the first integrals (tests/golden/kerr_end_points.json,
+    written by its script from oracle/first_integrals.py): cos theta and phi
+    within 1e-8 (the oracle's own integration agrees to 2.4e-11)."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "kerr_end_points.json")) as f:
+        rays = json.load(f)["rays"]
+    for a in sorted({r["a"] for r in rays}):
+        rows = [r for r in rays if r["a"] == a]
+        st = np.array([oracle.init_ray(a, 1000.0, r["incl_deg"], r["x"], r["y"]) for r in rows])
         out = osr.trace_states(a, 1000.0, torch.tensor(st[:, :6], device="cuda").contiguous(),
                                torch.tensor(st[:, 6], device="cuda"),
                                torch.tensor(st[:, 7], device="cuda"), tol=1e-12,
                                precision=precision)
         torch.cuda.synchronize()
         got = {k: v.cpu().numpy() for k, v in out.items()}
-        assert got["status"].tolist() == ([osr.STATUS_ESCAPED] * len(esc) +
-                                          [osr.STATUS_CAPTURED] * len(cap))
-        for k in range(len(pix)):
-            uf, phif = _kerr_escape_point(a, 1100.0, st[k], r_cap=r_cap)
-            assert abs(math.cos(got["theta"][k]) - uf) < 1e-8, (a, pix[k])
-            assert abs(got["phi"][k] - phif) < 1e-8 * max(1.0, abs(phif)), (a, pix[k])
+        for k, r in enumerate(rows):
+            fate = osr.STATUS_ESCAPED if r["fate"] == "escaped" else osr.STATUS_CAPTURED
+            assert got["status"][k] == fate, (a, r)
+            assert abs(math.cos(got["theta"][k]) - r["cos_theta"]) < 1e-8, (a, r)
+            assert abs(got["phi"][k] - r["phi"]) < 1e-8 * max(1.0, abs(r["phi"])), (a, r)
