@@ -116,9 +116,10 @@ def trace_pixels(a, r_obs, incl_deg, extent, nx, ny, pixels=None, M=1.0, nthread
 
     extent = (x_min, x_max, y_min, y_max); pixels = linear indices j*nx + i
     (default: the whole image). Returns a dict of numpy arrays, one entry per
-    traced pixel. Generic Kerr escape points are pinned to the quadratures of
-    the first integrals (Mino time); parity unpinned for generic q-metric rays
-    (q != 0: no Carter constant, no quadrature). The pins are listed in
+    traced pixel. Generic Kerr end points are pinned to the quadratures of
+    the first integrals (Mino time); generic q-metric end points (no Carter
+    constant, no quadrature) to the second-order geodesic equation of the
+    line element, integrated independently. The pins are listed in
     tests/test_oracle_pins.py.
     """
     L = lib()
