@@ -6,8 +6,9 @@ the CUDA library and never calls it.
 
 Every function follows a passage of Velasquez-Cadavid et al., "OSIRIS"
 (arXiv:2202.00086); see the header of osiris_oracle.cpp for the list.
-Functions whose result has no closed form to check against are marked
-"parity unpinned" below.
+Every function is pinned to something other than itself (closed forms,
+reductions, first integrals, an independent geodesic integration); the one
+quantity with no such pin is the size of the integration error |H| itself.
 """
 import ctypes
 import os
