@@ -23,7 +23,7 @@ struct StateDF {
 
 // Tableaus for the df64 stepper, [integrator][stage]; stage s = 0..6 is the
 // tableau's stage s + 1. kA[i][t][s] = a_{t+1, s+1} in FP32 (the O(h) parts of
-// stage inputs); c_s, b_s and b_s - b*_s as df.
+// stage inputs); c_s and b_s as df, b_s - b*_s in FP32.
 OSIRIS_DF_TABLEAU float kA[2][7][7] = {
     {{0, 0, 0, 0, 0, 0, 0},
      {0, 0, 0, 0, 0, 0, 0},
@@ -58,17 +58,13 @@ OSIRIS_DF_TABLEAU float kBL[2][7] = {
      0.0f},
     {0.0f, 0.0f, -5.2749844492439024e-09f, -1.9868215517249155e-08f, 1.2370775515080368e-08f,
      -7.095791065836465e-09f, 0.0f}};
-// b_s - b*_s for s >= 2 (zero for s = 1 in both)
+// b_s - b*_s for s >= 2 (zero for s = 1 in both), in FP32 (the error sum is
+// an FP32 sum, see rk_step_df)
 OSIRIS_DF_TABLEAU float kDH[2][7] = {
     {0.0f, 0.0f, 0.018668586388230324f, -0.03415502607822418f, -0.01932198740541935f,
      0.03910220041871071f, 0.0f},
     {0.0f, 0.0f, -0.004252770449966192f, 0.03697916492819786f, -0.05086379870772362f,
      0.041904762387275696f, -0.02500000037252903f}};
-OSIRIS_DF_TABLEAU float kDL[2][7] = {
-    {0.0f, 0.0f, -2.943724985993157e-10f, -7.525838841004884e-10f, 7.982765004577175e-10f,
-     1.726969678372825e-09f, 0.0f},
-    {0.0f, 0.0f, 1.5946005627043291e-10f, 1.73846881335038e-09f, 1.5379122420000613e-09f,
-     -4.825138066877344e-10f, 3.7252903539730653e-10f}};
 
 struct DerivDF {
   df r, th, ph, pr, pth;
@@ -91,26 +87,40 @@ struct LaneCacheDF<OSIRIS_RKDP45> {
 };
 
 // One embedded Runge-Kutta attempt of length h from y, all in df64: o =
-// fifth-order result, d = fifth minus fourth order (FP32 is enough for the
-// error test). The stages share one copy of the equations; as soon as stage
-// s gives d_s = k_s - k_1 it is folded into the FP32 sums of the later stage
-// inputs, the df64 increment sum and the df64 error sum, so no stage value is
-// kept in memory. Dormand-Prince: the seventh stage input is the fifth-order
-// solution itself (formed in df64 exactly as o), its derivative is cached as
-// the next k1, and k1 is evaluated here only when the cache is empty. twoH
-// is 2 (H - H0) at y.
+// fifth-order result, d = fifth minus fourth order. The stages share one copy
+// of the equations; as soon as stage s gives d_s = k_s - k_1 it is folded
+// into the FP32 sums of the later stage inputs, the df64 increment sum and
+// the FP32 error sum, so no stage value is kept in memory.
+//
+// The error sum h sum_s (b_s - b*_s) d_s cancels from terms of size
+// T ~ h |d_s| / 30 to the local error D ~ tol |y|. Each d_s is exact to
+// df64 precision (k_s and k_1 are df64 values), so summing its leading word
+// in FP32 costs only the FP32 rounding of the terms, ~2^-24 T; with
+// |d_s| ~ (h / tau) |k| and D ~ (h / tau)^5 |y| (tau: time scale of the
+// solution, |y| ~ tau |k|) that is a relative error of ~2^-24 (h / tau)^-3 / 30
+// in D: about 0.2 % at tol = 1e-10 and 3 % at 1e-12, inside the
+// controller's safety factor. (An FP32 evaluation of the equations, by
+// contrast, would put the rounding of k itself, 2^-24 |k|, into every d_s.)
+//
+// Dormand-Prince: the seventh stage input is the fifth-order solution itself
+// (formed in df64 exactly as o), its derivative is cached as the next k1, and
+// k1 is evaluated here only when the cache is empty. twoH is 2 (H - H0) at y.
 template <class Met, int INTEG>
 __device__ __forceinline__ void rk_step_df(const typename Met::Ray& K, LaneCacheDF<INTEG>& LC,
                                            const StateDF& y, df h, StateDF& o, float d[5],
                                            float& twoH) {
   constexpr int I = (INTEG == OSIRIS_RKDP45) ? 1 : 0;
   constexpr int NS = (INTEG == OSIRIS_RKDP45) ? 7 : 6;
-  df k1[5], hk1[5], sb[5], sd[5];
+  df k1[5], hk1[5], sb[5];
+  float sd[5];
   float acc[4][4];  // FP32 sums sum_j a_tj d_j of stages t = 2..5; (r, theta, p_r, p_theta)
   bool need_k1 = true;
   twoH = 0.0f;
 #pragma unroll
-  for (int c = 0; c < 5; ++c) k1[c] = hk1[c] = sb[c] = sd[c] = mk(0.0f, 0.0f);
+  for (int c = 0; c < 5; ++c) {
+    k1[c] = hk1[c] = sb[c] = mk(0.0f, 0.0f);
+    sd[c] = 0.0f;
+  }
   if constexpr (INTEG == OSIRIS_RKDP45) {
     need_k1 = !LC.valid;
     if (!need_k1) {
@@ -194,12 +204,12 @@ __device__ __forceinline__ void rk_step_df(const typename Met::Ray& K, LaneCache
     }
     if (s >= 2) {
       const df bw = mk(kBH[I][s], kBL[I][s]);
-      const df dw = mk(kDH[I][s], kDL[I][s]);
+      const float dw = kDH[I][s];
       const bool has_b = (bw.hi != 0.0f);
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
         if (has_b) sb[c] = df_add_u(sb[c], df_mul(e[c], bw));
-        sd[c] = df_add_u(sd[c], df_mul(e[c], dw));
+        sd[c] = fmaf(dw, e[c].hi, sd[c]);
       }
     }
   }
@@ -219,7 +229,7 @@ __device__ __forceinline__ void rk_step_df(const typename Met::Ray& K, LaneCache
     o.pth = df_add(y.pth, df_add(hk1[4], df_mul(h, sb[4])));
   }
 #pragma unroll
-  for (int c = 0; c < 5; ++c) d[c] = df_mul(h, sd[c]).hi;
+  for (int c = 0; c < 5; ++c) d[c] = __fmul_rn(h.hi, sd[c]);
 }
 
 }  // namespace osiris_impl

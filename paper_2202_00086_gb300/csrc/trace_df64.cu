@@ -11,11 +11,13 @@
 //   stage input  y_i = y + c_i h k_1 + h sum_j a_ij d_j      (sum_j a_ij = c_i)
 //   increment        = h k_1 + h sum_i b_i d_i                (sum_i b_i = 1)
 //   error estimate   = h sum_i (b_i - b*_i) d_i               (sum = 0)
-// The increment and the error estimate are formed in df64 with df64 weights
-// (the error estimate cancels to O(h^5) and needs the extra digits). In a
-// stage input the part h sum_j a_ij d_j is O(h/T) smaller than the stage's
-// step (T: time scale of the solution) and reaches the result only through
-// one more factor h/T, so it is summed in FP32.
+// The increment is formed in df64 with df64 weights. The error estimate
+// cancels to O(h^5), but every d_i is exact to df64 precision, so the leading
+// words summed in FP32 keep its relative error near 2^-24 (h/T)^-3 / 30 (T:
+// time scale of the solution), a fraction of a percent at tol 1e-10 (the
+// derivation is at rk_step_df). In a stage input the part h sum_j a_ij d_j
+// is O(h/T) smaller than the stage's step and reaches the result only
+// through one more factor h/T, so it is summed in FP32 too.
 //
 // The six stages run as a loop with one copy of the evaluation of Hamilton's
 // equations (six inlined df64 copies overflow the instruction cache), and

@@ -11,8 +11,12 @@ Renders (camera set-ups) arrive over time. The server:
     (osiris_batch_plan_*): table upload, queue reset and kernel recorded once
     as a CUDA graph, so a round is one graph launch with patched arguments;
     without, a round is one osiris_trace_batch call;
-  - keeps up to `max_inflight` rounds queued on the stream, so the GPU never
-    waits for the host between rounds;
+  - keeps up to `max_inflight` rounds in flight, each on the stream of its
+    slot (`overlap`, the default), so the GPU never waits for the host
+    between rounds and the next round's blocks take the SMs that the
+    current round's last, longest rays leave idle (a persistent launch ends
+    only when its slowest lane does); with overlap=False every round goes to
+    the current stream and runs after the previous one;
   - detects round completion with CUDA events and timestamps each render at
     the completion of its last pixel range.
 
@@ -100,7 +104,7 @@ class RenderServer:
     def __init__(self, precision=None, round_rays=1 << 21, min_chunk=1 << 14,
                  hbm_budget_bytes=None, max_inflight=2, max_entries=4096,
                  keep_outputs=False, cell_deg=10.0, cell_phase_deg=0.0, backend=None,
-                 clock=time.perf_counter, graphs=True, stall_timeout_s=None):
+                 clock=time.perf_counter, graphs=True, stall_timeout_s=None, overlap=True):
         import paper_2202_00086_gb300 as osr
         self.osr = osr
         self.precision = osr.DF64 if precision is None else precision
@@ -126,6 +130,7 @@ class RenderServer:
         self.cancelled = []
         self.failed = []  # timed out or abandoned after a stalled round
         self.stall_timeout_s = stall_timeout_s
+        self.overlap = bool(overlap)
         self.status = osr.OK
         self._held = []  # buffers of renders retired while their rounds may still run
         self.bytes_in_use = 0
@@ -277,10 +282,11 @@ class RenderServer:
                             "tol": r.tol, "out": r.out, "first_ray": first, "n_rays": n,
                             "l0": r.render.get("l0") if r.disk else None})
             r.chunks.append((first, n))
+        slot = k if self.overlap else None  # None: the current stream
         if self._plans is not None:
-            event = self.backend.launch_plan(self._plan(k, kind), entries)
+            event = self.backend.launch_plan(self._plan(k, kind), entries, slot=slot)
         else:
-            event = self.backend.launch(entries, self._ws[k], precision=kind[1],
+            event = self.backend.launch(entries, self._ws[k], slot=slot, precision=kind[1],
                                         cell_deg=self.cell_deg,
                                         cell_phase_deg=self.cell_phase_deg)
         self._last_kind = kind
@@ -290,10 +296,15 @@ class RenderServer:
         self.launches += 1
         return True
 
+    def _finished_rounds(self):
+        """In-flight rounds whose event has completed, oldest first (rounds on
+        different slot streams may complete out of launch order)."""
+        return [rnd for rnd in self.inflight if rnd.event.query()]
+
     def _poll(self):
         progressed = False
-        while self.inflight and self.inflight[0].event.query():
-            rnd = self.inflight.popleft()
+        for rnd in self._finished_rounds():
+            self.inflight.remove(rnd)
             now = self.clock()
             self._ws_free.append(rnd.ws_index)
             for r, first, n in rnd.parts:
@@ -362,8 +373,10 @@ class RenderServer:
         then kept)."""
         t0 = self.clock()
         while self.inflight:
-            if self.inflight[0].event.query():
-                self.inflight.popleft()
+            finished = self._finished_rounds()
+            for rnd in finished:
+                self.inflight.remove(rnd)
+            if finished:
                 continue
             if timeout_s is not None and self.clock() - t0 > timeout_s:
                 return self.osr.ETIMEOUT
@@ -514,6 +527,20 @@ class _CudaBackend:
         import torch
         self.osr = osr
         self.torch = torch
+        self._streams = {}
+
+    def _stream(self, slot):
+        """The stream of an in-flight slot (None: the current stream). A slot
+        stream first waits for the work queued so far on the current stream,
+        so a round never overtakes what the caller queued before it."""
+        cur = self.torch.cuda.current_stream()
+        if slot is None:
+            return cur
+        s = self._streams.get(slot)
+        if s is None:
+            s = self._streams[slot] = self.torch.cuda.Stream()
+        s.wait_stream(cur)
+        return s
 
     def workspace(self, nbytes):
         return self.torch.empty(nbytes, dtype=self.torch.uint8, device="cuda")
@@ -535,19 +562,21 @@ class _CudaBackend:
         return self.osr.alloc_outputs(n, fields=self.osr.DISK_FIELDS if disk
                                       else self.osr.SHADOW_FIELDS)
 
-    def launch(self, entries, ws, **opts):
-        self.osr.trace_batch(entries, workspace=ws, **opts)
+    def launch(self, entries, ws, slot=None, **opts):
+        s = self._stream(slot)
+        self.osr.trace_batch(entries, workspace=ws, stream=s, **opts)
         ev = self.torch.cuda.Event()
-        ev.record()
+        ev.record(s)
         return ev
 
     def plan(self, ws, max_entries, **opts):
         return self.osr.BatchPlan(max_entries, workspace=ws, **opts)
 
-    def launch_plan(self, plan, entries):
-        plan.launch(entries)
+    def launch_plan(self, plan, entries, slot=None):
+        s = self._stream(slot)  # a plan belongs to one slot, so to one stream
+        plan.launch(entries, stream=s)
         ev = self.torch.cuda.Event()
-        ev.record()
+        ev.record(s)
         return ev
 
     def single(self, r, **opts):

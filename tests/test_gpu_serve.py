@@ -39,12 +39,16 @@ def _alone(rd, precision, phase):
     return {k: v.cpu().numpy() for k, v in out.items()}
 
 
-@pytest.mark.parametrize("precision", [osr.DF64, osr.FP64])
-def test_alone_equals_in_the_mix(precision):
+@pytest.mark.parametrize("precision,overlap", [(osr.DF64, True), (osr.FP64, True),
+                                               (osr.DF64, False)])
+def test_alone_equals_in_the_mix(precision, overlap):
+    """Rounds on per-slot streams (overlap: the next round's blocks start in
+    the current round's tail) or all on one stream."""
     phase = workloads.checker_phase_deg(2202)
     arrivals = _stream()
     srv = serve.RenderServer(precision=precision, round_rays=3000, min_chunk=500,
-                             keep_outputs=True, cell_phase_deg=phase, max_inflight=2)
+                             keep_outputs=True, cell_phase_deg=phase, max_inflight=2,
+                             overlap=overlap)
     summary = srv.run(arrivals, realtime=True)
     torch.cuda.synchronize()
     assert summary["renders"] == len(arrivals)

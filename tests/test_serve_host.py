@@ -268,3 +268,43 @@ def test_default_budget_is_a_share_of_free_memory():
     assert srv.hbm_budget == int(serve.HBM_SHARE * (10 << 30))
     big = workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 16384, 16384)  # 11.3 GB of outputs
     assert srv.submit(big).state == serve.REJECTED
+
+
+class ReorderBackend(FakeBackend):
+    """Rounds on different slot streams: every second round completes before
+    the round launched ahead of it; records the slot of every launch."""
+
+    def __init__(self, server_ref):
+        super().__init__(server_ref)
+        self.slots = []
+
+    def launch(self, entries, ws, slot=None, **opts):
+        super().launch(entries, ws, **opts)
+        self.slots.append(slot)
+        return FakeEvent(1 if len(self.slots) % 2 == 0 else 6)
+
+
+def test_rounds_completing_out_of_order():
+    ref = [None]
+    be = ReorderBackend(ref)
+    srv = serve.RenderServer(backend=be, keep_outputs=True, round_rays=3000, min_chunk=3000,
+                             max_inflight=2)
+    ref[0] = srv
+    reqs = [workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 40, 40) for _ in range(6)]
+    rs = [srv.submit(rd, arrival=0.0) for rd in reqs]
+    order = []
+    while not srv.idle():
+        srv.step()
+        order += [r.rid for r in srv.done if r.rid not in order]
+    assert all(r.state == serve.DONE and np.all(r.out["hits"] == 1) for r in rs)
+    assert order != sorted(order)  # a later round's render retired first
+    assert set(be.slots) == {0, 1}  # each in-flight slot launches on its own stream
+    assert srv.bytes_in_use == 0 and not srv.inflight
+
+    ref2 = [None]
+    be2 = ReorderBackend(ref2)
+    srv2 = serve.RenderServer(backend=be2, keep_outputs=True, round_rays=3000, max_inflight=2,
+                              overlap=False)
+    ref2[0] = srv2
+    srv2.run([(0.0, rd) for rd in reqs], realtime=False, poll_s=0)
+    assert set(be2.slots) == {None}  # every round on the current stream
