@@ -47,17 +47,20 @@ extern "C" {
 
 /* ---- precision of the integrator -------------------------------------- */
 #define OSIRIS_FP64 0  /* every operation in double precision */
-#define OSIRIS_MIXED 1 /* FP32 stage evaluations, FP64 state and controller;
-                          FP64 steps near the horizon (r < 4) and at polar
-                          turning points; for tolerances of 1e-7 and looser */
-#define OSIRIS_DF64 2  /* stage evaluations in double-float (pairs of FP32,
-                          48-bit significand) on the FP32 pipe; FP64 state
-                          and controller */
+#define OSIRIS_MIXED 1 /* stage evaluations of Hamilton's equations in FP32,
+                          inside the DF64 stepper: double-float state, stage
+                          sums, error estimate and controller, end-point |H|
+                          in double-float; Kerr only; for tolerances of 1e-8
+                          and looser (FP32 rounding of the stages swamps the
+                          error estimate of tighter ones) */
+#define OSIRIS_DF64 2  /* every operation of the integration in double-float
+                          (pairs of FP32, 48-bit significand) on the FP32
+                          pipe; FP64 for initial data and outputs */
 
 /* ---- integrator (Sec. 3.1) -------------------------------------------- */
 #define OSIRIS_RKCK45 0 /* Cash-Karp 4(5), six evaluations per attempt */
 #define OSIRIS_RKDP45 1 /* Dormand-Prince 5(4), first same as last: six new
-                           evaluations per attempt (FP64 and DF64 only) */
+                           evaluations per attempt */
 
 /* ---- space-times ------------------------------------------------------- */
 #define OSIRIS_SPACETIME_KERR 0    /* Kerr, Boyer-Lindquist (Sec. 4.3), spin a */
@@ -72,7 +75,9 @@ extern "C" {
 #define OSIRIS_STAT_STATUS0 5       /* 5..10: rays per status code 0..5 */
 #define OSIRIS_STAT_MAX_ABS_H 11    /* max |H| over all rays that did not end in
                                        OSIRIS_STATUS_ERROR, as IEEE-754 bits */
-#define OSIRIS_STAT_FP64_STEPS 12   /* mixed precision: steps taken in FP64 */
+#define OSIRIS_STAT_FP64_STEPS 12   /* reserved: steps a reduced-precision kernel
+                                       took in FP64 (0: neither MIXED nor DF64
+                                       takes any) */
 #define OSIRIS_STAT_CHECK_FAILS 13  /* bounds-checked build only: failed index checks */
 #define OSIRIS_STAT_CHECK_WORST 14  /* bounds-checked build only: max over failures of
                                        (check code << 56) | ray index; codes 1 ray index

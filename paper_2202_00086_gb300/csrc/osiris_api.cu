@@ -49,7 +49,6 @@ int check_opts(const osiris_trace_opts* o) {
   if (o->precision != OSIRIS_FP64 && o->precision != OSIRIS_MIXED && o->precision != OSIRIS_DF64)
     return OSIRIS_EINVAL;
   if (o->integrator != OSIRIS_RKCK45 && o->integrator != OSIRIS_RKDP45) return OSIRIS_EINVAL;
-  if (o->integrator == OSIRIS_RKDP45 && o->precision == OSIRIS_MIXED) return OSIRIS_EINVAL;
   if (!(o->r_cap_factor > 1.0) || !is_fin(o->r_cap_factor)) return OSIRIS_EINVAL;
   if (!(o->r_esc_factor > 1.0) || !is_fin(o->r_esc_factor)) return OSIRIS_EINVAL;
   if (!(o->cell_deg > 0.0 && o->cell_deg <= 180.0)) return OSIRIS_EINVAL;

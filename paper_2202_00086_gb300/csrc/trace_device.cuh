@@ -367,39 +367,6 @@ __device__ __forceinline__ void rhs_q64(const RayK& K, double r, double th, doub
   dpth = (c * s) * fma(-K.kap * iDX, Hr + Hth, Hph * is2);
 }
 
-// 2H = N / Sigma in Kerr, in FP64, without the derivatives and without the
-// block's sine table (library sincos, correctly rounded reciprocal): usable
-// from kernels that do not fill the table (the double-float and mixed
-// kernels check |H| at a ray's end point with it).
-__device__ __forceinline__ double twoH_kerr_direct(const RayK& K, const State& y) {
-  double s, c;
-  sincos(y.th, &s, &c);
-  const double Delta = fma(y.r, y.r - 2.0, K.a2);
-  const double Sigma = fma(K.a2 * c, c, y.r * y.r);
-  const double P = fma(fma(y.r, y.r, K.a2), K.E, -K.aL);
-  const double DS = Delta * Sigma;
-  const double inv = __drcp_rn(DS * s);
-  const double iSig = (Delta * s) * inv;
-  const double iDel = (Sigma * s) * inv;
-  const double W = fma(K.L, DS * inv, -K.aE * s);
-  const double N = fma(Delta * y.pr, y.pr, fma(y.pth, y.pth, fma(W, W, -P * (P * iDel))));
-  return N * iSig;
-}
-
-// 2H in the q-metric (Appendix A), in FP64 with the library's sin, log, exp
-// and division: the end-point |H| check of the double-float kernels.
-__device__ __forceinline__ double twoH_q_direct(const RayK& K, const State& y) {
-  const double s = sin(y.th);
-  const double rm2 = y.r - 2.0;
-  const double f = rm2 / y.r;
-  const double X = 1.0 + (s * s) / (y.r * rm2);
-  const double fq = exp(K.q * log(f));
-  const double fXk = fq * exp(K.kap * log(X));
-  const double ir2 = 1.0 / (y.r * y.r);
-  return -(K.E * K.E) / (f * fq) + f * fXk * y.pr * y.pr + fXk * ir2 * y.pth * y.pth +
-         fq * ir2 * K.L * K.L / (s * s);
-}
-
 // Metric policies for the FP64 steppers.
 #ifndef OSIRIS_FP64_MAXREGS
 #define OSIRIS_FP64_MAXREGS 255

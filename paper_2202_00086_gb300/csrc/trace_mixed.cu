@@ -1,151 +1,115 @@
-// Mixed-precision trace kernels. The six stage evaluations of Hamilton's
-// equations run in FP32 (the GB300 FP32 pipe is ~70x the FP64 pipe); the
-// state, the accumulation of each accepted increment, the error scale and
-// the |H| constraint stay in FP64, and a step that starts near the horizon
-// (r < 4) or at a polar turning point (|p_theta| < 1e-3) is taken entirely
-// in FP64, where FP32 cancellation in N = Delta p_r^2 - P^2/Delta + ... is
-// severe.
+// Mixed-precision trace kernels (OSIRIS_MIXED): the lane state machine and
+// the double-float stepper of the DF64 kernels (trace_df_body.cuh,
+// step_df.cuh) with the six evaluations of Hamilton's equations of every
+// attempt in FP32 (rhs_f32.cuh). The state, the stage inputs, the increment,
+// the error estimate and the controller keep df64 precision (FP32 with
+// compensated sums); only the stage derivatives carry FP32 rounding, ~1e-7 of
+// |k|. Nothing in the integration runs on the FP64 pipe.
+//
+// Tolerance range. The embedded error estimate h sum_s (b_s - b*_s)(k_s - k_1)
+// then carries a noise of ~1e-8 h |k| ~ 1e-8 (h/tau) |y| (tau: time scale of
+// the solution), against the local error tol (1 + |y|) that the controller
+// compares it with. At tol 1e-8 the accepted steps have h/tau ~ 0.03 and the
+// noise is a few percent of the estimate; at 1e-10 it is as large as the
+// estimate and the controller would shrink the steps to chase it. MIXED is
+// meant for tolerances of 1e-8 and looser; DF64 covers the tighter ones.
+//
+// |H|. The FP32 evaluations' own 2H carries the rounding of its largest terms
+// (P^2 / Delta grows without bound towards the horizon), so it does not track
+// the constraint; a ray's |H| output is that of its end point, evaluated in
+// double-float (rhs_df) as in the DF64 kernels.
+//
+// Surface location. A trial step's end point carries the FP32 rounding of its
+// stage derivatives, ~1e-7 h |k|, so the step-length bracket is resolved to a
+// relative width of 2e-7, not to the DF64 kernels' 4e-16.
 #include <cuda_runtime.h>
 
-#include "trace_kernel.cuh"
+#include "rhs_f32.cuh"
+#include "trace_df_body.cuh"
 
 namespace osiris_impl {
 
-constexpr double kMixedFP64Radius = 4.0;
-constexpr double kMixedFP64Ptheta = 1e-3;
+// Registers capped as in the DF64 kernels: four blocks of 128 threads per SM.
+#ifndef OSIRIS_MIXED_MAXREGS
+#define OSIRIS_MIXED_MAXREGS 128
+#endif
 
-struct RayK32 {
-  float a, a2, aE, aL, E, L;
-};
-
-// The separated form of Hamilton's equations (see rhs64) in FP32.
-__device__ __forceinline__ void rhs32(const RayK32& K, float r, float th, float pr, float pth,
-                                      float& dr, float& dth, float& dph, float& dpr,
-                                      float& dpth) {
-  float s, c;
-  sincosf(th, &s, &c);
-  const float r2 = r * r;
-  const float Delta = fmaf(r, r - 2.0f, K.a2);
-  const float Sigma = fmaf(K.a2 * c, c, r2);
-  const float P = fmaf(fmaf(r, r, K.a2), K.E, -K.aL);
-  const float DS = Delta * Sigma;
-  const float inv = __frcp_rn(DS * s);
-  const float iSig = (Delta * s) * inv;
-  const float iDel = (Sigma * s) * inv;
-  const float is = DS * inv;
-  const float W = fmaf(K.L, is, -K.aE * s);
-  const float u = P * iDel;
-  const float Dpr = Delta * pr;
-  const float N = fmaf(Dpr, pr, fmaf(pth, pth, fmaf(W, W, -P * u)));
-  const float NiS = N * iSig;
-  dr = Dpr * iSig;
-  dth = pth * iSig;
-  dph = fmaf(W, is, K.a * u) * iSig;
-  dpr = iSig * fmaf(1.0f - r, fmaf(u, u, pr * pr), fmaf(r, NiS, (r + r) * K.E * u));
-  dpth = (c * iSig) * fmaf(W, fmaf(K.L, is * is, K.aE), -(K.a2 * s) * NiS);
-}
-
-struct StepperMixed {
-  // FP32 stage values put ~1e-7 relative noise on a trial step's end point;
-  // a bracket narrower than that cannot be resolved further
+struct KerrMixed {
+  using Ray = RayF32;
+  static constexpr int kMaxRegs = OSIRIS_MIXED_MAXREGS;
+  static constexpr bool kTrackH = false;
   static constexpr double kLocateRel = 2e-7;
-  static constexpr bool kTrigTable = true;  // its FP64 steps use rhs64
-  static constexpr bool kExpLogTable = false;
-  struct RayCache {};
-  struct LaneCache {};
-  static __device__ __forceinline__ void prepare(const RayK&, RayCache&) {}
-  static __device__ __forceinline__ void reset(LaneCache&) {}
-  static __device__ __forceinline__ void accepted(LaneCache&) {}
-  static __device__ __forceinline__ bool attempt(const RayK& K, const RayCache&, LaneCache&,
-                                                 const State& y, double h,
-                                                 State& o, State& d, double& twoH) {
-    if (y.r < kMixedFP64Radius || fabs(y.pth) < kMixedFP64Ptheta) {
-      ck_step64(K, y, h, o, d, twoH);
-      return true;
-    }
-    using namespace ck;
-    const RayK32 k{(float)K.a, (float)K.a2, (float)K.aE, (float)K.aL, (float)K.E, (float)K.L};
-    const float hf = (float)h;
-    const float yr = (float)y.r, yt = (float)y.th, ypr = (float)y.pr, ypt = (float)y.pth;
-    float k1r, k1t, k1p, k1pr, k1pt;
-    rhs32(k, yr, yt, ypr, ypt, k1r, k1t, k1p, k1pr, k1pt);
-    float k2r, k2t, k2p, k2pr, k2pt;
-    rhs32(k, fmaf(hf, (float)A21 * k1r, yr), fmaf(hf, (float)A21 * k1t, yt),
-          fmaf(hf, (float)A21 * k1pr, ypr), fmaf(hf, (float)A21 * k1pt, ypt), k2r, k2t, k2p, k2pr,
-          k2pt);
-#define M3(c, y0) fmaf(hf, fmaf((float)A32, k2##c, (float)A31 * k1##c), y0)
-    float k3r, k3t, k3p, k3pr, k3pt;
-    rhs32(k, M3(r, yr), M3(t, yt), M3(pr, ypr), M3(pt, ypt), k3r, k3t, k3p, k3pr, k3pt);
-#undef M3
-#define M4(c, y0) fmaf(hf, fmaf((float)A43, k3##c, fmaf((float)A42, k2##c, (float)A41 * k1##c)), y0)
-    float k4r, k4t, k4p, k4pr, k4pt;
-    rhs32(k, M4(r, yr), M4(t, yt), M4(pr, ypr), M4(pt, ypt), k4r, k4t, k4p, k4pr, k4pt);
-#undef M4
-#define M5(c, y0)                                                                       \
-  fmaf(hf, fmaf((float)A54, k4##c, fmaf((float)A53, k3##c, fmaf((float)A52, k2##c,     \
-                                                                 (float)A51 * k1##c))), \
-       y0)
-    float k5r, k5t, k5p, k5pr, k5pt;
-    rhs32(k, M5(r, yr), M5(t, yt), M5(pr, ypr), M5(pt, ypt), k5r, k5t, k5p, k5pr, k5pt);
-#undef M5
-#define M6(c, y0)                                                                            \
-  fmaf(hf,                                                                                   \
-       fmaf((float)A65, k5##c,                                                               \
-            fmaf((float)A64, k4##c,                                                          \
-                 fmaf((float)A63, k3##c, fmaf((float)A62, k2##c, (float)A61 * k1##c)))), \
-       y0)
-    float k6r, k6t, k6p, k6pr, k6pt;
-    rhs32(k, M6(r, yr), M6(t, yt), M6(pr, ypr), M6(pt, ypt), k6r, k6t, k6p, k6pr, k6pt);
-#undef M6
-#define INC(c) (hf * fmaf((float)B6, k6##c, fmaf((float)B4, k4##c, fmaf((float)B3, k3##c, (float)B1 * k1##c))))
-#define DLT(c)                                                                              \
-  (hf * fmaf((float)D6, k6##c,                                                              \
-             fmaf((float)D5, k5##c,                                                         \
-                  fmaf((float)D4, k4##c, fmaf((float)D3, k3##c, (float)D1 * k1##c)))))
-    o.r = y.r + (double)INC(r);
-    o.th = y.th + (double)INC(t);
-    o.ph = y.ph + (double)INC(p);
-    o.pr = y.pr + (double)INC(pr);
-    o.pth = y.pth + (double)INC(pt);
-    d.r = (double)DLT(r);
-    d.th = (double)DLT(t);
-    d.ph = (double)DLT(p);
-    d.pr = (double)DLT(pr);
-    d.pth = (double)DLT(pt);
-#undef INC
-#undef DLT
-    twoH = twoH_kerr_direct(K, y);
-    return false;
+  static __device__ __forceinline__ Ray ray(const RayK& K) {
+    Ray k;
+    k.a = (float)K.a;
+    k.a2 = (float)K.a2;
+    k.aE = (float)K.aE;
+    k.aL = (float)K.aL;
+    k.E = (float)K.E;
+    k.L = (float)K.L;
+    k.twoE = (float)(2.0 * K.E);
+    const double sq = sqrt(fmax(0.0, 1.0 - K.a2));
+    k.rp = df_from_double(1.0 + sq);
+    k.rm = (float)(1.0 - sq);
+    k.twoH0 = 0.0f;
+    return k;
   }
-  static __device__ __forceinline__ double twoH(const RayK& K, const State& y) {
-    return twoH_kerr_direct(K, y);
+  static __device__ __forceinline__ void rhs(const Ray& K, df r, df th, df pr, df pth, df& dr,
+                                             df& dth, df& dph, df& dpr, df& dpth,
+                                             float& twoH) {
+    float fr, ft, fp, fpr, fpt;
+    rhs_f32(K, r, th, pr, pth, fr, ft, fp, fpr, fpt, twoH);
+    dr = mk(fr, 0.0f);
+    dth = mk(ft, 0.0f);
+    dph = mk(fp, 0.0f);
+    dpr = mk(fpr, 0.0f);
+    dpth = mk(fpt, 0.0f);
+  }
+  // 2 (H - H0) at the end point with the double-float equations of DF64.
+  static __device__ __forceinline__ float end_twoH(const Ray& KD, const RayK& K,
+                                                   const StateDF& y) {
+    RayDF k = to_df(K);
+    k.twoH0 = KD.twoH0;
+    df dr, dth, dph, dpr, dpth;
+    float twoH;
+    rhs_df(k, y.r, y.th, y.pr, y.pth, dr, dth, dph, dpr, dpth, twoH);
+    return twoH;
   }
 };
 
-constexpr int kMaxBlock = 256;
-
-__global__ void __launch_bounds__(kMaxBlock) trace_mixed_plain(const __grid_constant__ KernelArgs A) {
-  trace_body<StepperMixed, false>(A);
+template <int INTEG>
+__global__ void __maxnreg__(KerrMixed::kMaxRegs)
+    trace_mixed_plain(const __grid_constant__ KernelArgs A) {
+  trace_body_df<KerrMixed, false, INTEG>(A);
 }
 
-__global__ void __launch_bounds__(kMaxBlock) trace_mixed_persistent(const __grid_constant__ KernelArgs A) {
-  trace_body<StepperMixed, true>(A);
+template <int INTEG>
+__global__ void __maxnreg__(KerrMixed::kMaxRegs)
+    trace_mixed_persistent(const __grid_constant__ KernelArgs A) {
+  trace_body_df<KerrMixed, true, INTEG>(A);
 }
 
-int launch_trace_mixed(const KernelArgs& args, Kernel kind, int, int grid, int block,
+template <int INTEG>
+static const void* mixed_kernel(Kernel kind) {
+  return kind == Kernel::kPersistent ? (const void*)trace_mixed_persistent<INTEG>
+                                     : (const void*)trace_mixed_plain<INTEG>;
+}
+
+static const void* select_mixed(Kernel kind, int integrator) {
+  return integrator == OSIRIS_RKDP45 ? mixed_kernel<OSIRIS_RKDP45>(kind)
+                                     : mixed_kernel<OSIRIS_RKCK45>(kind);
+}
+
+int launch_trace_mixed(const KernelArgs& args, Kernel kind, int integrator, int grid, int block,
                        void* stream) {
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (kind == Kernel::kPersistent)
-    trace_mixed_persistent<<<grid, block, 0, s>>>(args);
-  else
-    trace_mixed_plain<<<grid, block, 0, s>>>(args);
-  return (int)cudaGetLastError();
+  void* params[] = {const_cast<KernelArgs*>(&args)};
+  return (int)cudaLaunchKernel(select_mixed(kind, integrator), dim3(grid), dim3(block), params,
+                               0, static_cast<cudaStream_t>(stream));
 }
 
-int occupancy_mixed(Kernel kind, int, int, int block, int* blocks_per_sm) {
-  const void* fn = (kind == Kernel::kPersistent) ? (const void*)trace_mixed_persistent
-                                                 : (const void*)trace_mixed_plain;
-  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, 0);
+int occupancy_mixed(Kernel kind, int integrator, int, int block, int* blocks_per_sm) {
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      blocks_per_sm, select_mixed(kind, integrator), block, 0);
 }
 
 }  // namespace osiris_impl

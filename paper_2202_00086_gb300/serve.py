@@ -21,9 +21,11 @@ Renders (camera set-ups) arrive over time. The server:
     the completion of its last pixel range.
 
 Round composition: a batched launch holds one space-time and one precision,
-so each render has a kind: Kerr renders run at the server's precision, and
-q-metric renders (shadow and lensing; Appendix A) too, except that a MIXED
-server runs them in FP64 (the q-metric has no MIXED kernel). A round serves one
+so each render has a kind: Kerr renders run at the server's precision, or at
+`loose_precision` when one is given and the render's tolerance is at least
+`loose_tol` (e.g. MIXED, FP32 stage evaluations, for the renders at 1e-8);
+q-metric renders (shadow and lensing; Appendix A) run at the same precision,
+in DF64 where that is MIXED (the q-metric has no MIXED kernel). A round serves one
 kind: that of the oldest render with rays left, or the next kind in that
 order when the previous round served it, so kinds alternate while several
 have work. Within the round every active render of the kind first receives up
@@ -104,10 +106,13 @@ class RenderServer:
     def __init__(self, precision=None, round_rays=1 << 21, min_chunk=1 << 14,
                  hbm_budget_bytes=None, max_inflight=2, max_entries=4096,
                  keep_outputs=False, cell_deg=10.0, cell_phase_deg=0.0, backend=None,
-                 clock=time.perf_counter, graphs=True, stall_timeout_s=None, overlap=True):
+                 clock=time.perf_counter, graphs=True, stall_timeout_s=None, overlap=True,
+                 loose_precision=None, loose_tol=1e-8):
         import paper_2202_00086_gb300 as osr
         self.osr = osr
         self.precision = osr.DF64 if precision is None else precision
+        self.loose_precision = loose_precision
+        self.loose_tol = float(loose_tol)
         self.round_rays = int(round_rays)
         self.min_chunk = int(min_chunk)
         self.backend = backend if backend is not None else _CudaBackend(osr)
@@ -151,19 +156,21 @@ class RenderServer:
     # ---- submission and admission ----
     def submit(self, render, arrival=None):
         """Queue a render (a workloads.render dict). Returns its ServedRender.
-        Kerr and q-metric renders run at the server's precision (q-metric
-        renders in FP64 when it is MIXED); a q-metric disk render (the
-        q-metric has no disk model) raises ValueError here, not in a later
-        round."""
+        Renders run at the server's precision, or at its loose precision when
+        their tolerance is loose enough (q-metric renders in DF64 where that
+        is MIXED); a q-metric disk render (the q-metric has no disk model)
+        raises ValueError here, not in a later round."""
         osr = self.osr
+        prec = self.precision
+        if self.loose_precision is not None and render["tol"] >= self.loose_tol:
+            prec = self.loose_precision
         if render.get("q") is not None:
             if render["mode"] == "disk":
                 raise ValueError("q-metric renders are shadow/lensing renders: the q-metric "
                                  "has no disk model")
-            kind = (osr.SPACETIME_QMETRIC,
-                    osr.FP64 if self.precision == osr.MIXED else self.precision)
+            kind = (osr.SPACETIME_QMETRIC, osr.DF64 if prec == osr.MIXED else prec)
         else:
-            kind = (osr.SPACETIME_KERR, self.precision)
+            kind = (osr.SPACETIME_KERR, prec)
         now = self.clock()
         r = ServedRender(self._next_id, render, now if arrival is None else arrival)
         r.kind = kind

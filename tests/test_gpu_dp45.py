@@ -69,8 +69,12 @@ def test_dp45_full_size_sampled():
     assert_parity(rep)
 
 
-def test_dp45_not_offered_in_mixed():
-    cam = osr.Camera(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 8, 8)
-    with pytest.raises(osr.OsirisError) as e:
-        osr.trace(cam, precision=osr.MIXED, integrator=DP)
-    assert e.value.code == osr.EINVAL
+def test_dp45_mixed_error_bound():
+    """Dormand-Prince with FP32 stage evaluations (MIXED) at tol 1e-8 against
+    the oracle's Dormand-Prince at 1e-10: the MIXED error bound."""
+    rd = dict(workloads.render(0.9, 1000.0, 60.0, (-8, 8, -8, 8), 40, 40), tol=1e-8)
+    ref = oracle_render(dict(rd, tol=1e-10), integrator=oracle.RKDP45)
+    rep = compare(rd, gpu_render(rd, precision=osr.MIXED, integrator=DP), ref, coord_rtol=1e-5,
+                  precision=osr.MIXED)
+    print(rep)
+    assert_parity(rep)

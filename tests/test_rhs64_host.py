@@ -29,7 +29,7 @@ int main(int argc, char** argv) {
   const char op = argv[1][0];
   double in[10];  // 'e': kind, a or q, E, L, r, theta, p_r, p_theta; 's', 'r': x;
                   // 'k': integrator, a, E, L, r, theta, phi, p_r, p_theta, h
-  const int n_in = (op == 'e' || op == 'h') ? 8 : op == 'k' ? 10 : 1;
+  const int n_in = op == 'e' ? 8 : op == 'k' ? 10 : 1;
   while (std::fread(in, sizeof(double), n_in, stdin) == (size_t)n_in) {
     if (op == 's') {
       double s, c;
@@ -38,25 +38,6 @@ int main(int argc, char** argv) {
       std::fwrite(out, sizeof out, 1, stdout);
     } else if (op == 'r') {
       const double out = rcp64(in[0]);
-      std::fwrite(&out, sizeof out, 1, stdout);
-    } else if (op == 'h') {  // 2H of the DF64 kernels' end-point check (library functions)
-      RayK K;
-      K.a = in[0] == 0.0 ? in[1] : 0.0;
-      K.a2 = K.a * K.a;
-      K.q = in[0] == 0.0 ? 0.0 : in[1];
-      K.kap = K.q * (2.0 + K.q);
-      K.E = in[2];
-      K.L = in[3];
-      K.aE = K.a * K.E;
-      K.aL = K.a * K.L;
-      K.E2 = K.E + K.E;
-      State y;
-      y.r = in[4];
-      y.th = in[5];
-      y.ph = 0.0;
-      y.pr = in[6];
-      y.pth = in[7];
-      const double out = in[0] == 0.0 ? twoH_kerr_direct(K, y) : twoH_q_direct(K, y);
       std::fwrite(&out, sizeof out, 1, stdout);
     } else if (op == 'k') {  // one Kerr attempt of the FP64 kernels' stepper
       RayK K;
@@ -232,21 +213,3 @@ def test_fp64_attempt_against_oracle_step(dev):
             assert abs(np.max(np.abs(o[5:]) / scale) / errn - 1.0) <= 2e-5, (row, o[5:], d)
     assert n_result > 800 and n_threshold >= 20
 
-
-def test_end_point_twoH(dev):
-    """2H as the DF64 kernels evaluate it at a ray's end point (FP64 with the
-    library's functions, no shared tables): Kerr and the q-metric against the
-    oracle's Hamiltonian, within 1e-14 of the terms of H."""
-    for kind, params, seed in ((0, (0.0, 0.5, 0.9, 0.998), 7), (1, (-0.5, 0.1, 0.5), 8)):
-        rows = _points(kind, params, 150, seed)
-        out = dev("h", rows, 1)[:, 0]
-        for row, got in zip(rows, out):
-            k, prm, E, L, r, th, pr, pth = row
-            sp = oracle.KERR if k == 0 else oracle.QMETRIC
-            kw = dict(a=prm) if k == 0 else dict(q=prm)
-            y6 = np.array([0.0, r, th, 0.0, pr, pth])
-            g = oracle.metric_sp(sp, r, th, **kw)[1]
-            terms = (abs(g[0, 0]) * E * E + 2 * abs(g[0, 3] * E * L) + abs(g[3, 3]) * L * L
-                     + abs(g[1, 1]) * pr * pr + abs(g[2, 2]) * pth * pth)
-            want = 2.0 * oracle.hamiltonian_sp(sp, y6, E, L, **kw)
-            assert abs(got - want) <= 1e-14 * terms, (row, got, want, terms)

@@ -1,0 +1,135 @@
+"""The FP32 evaluation of Hamilton's equations used by the MIXED kernels
+(rhs_f32.cuh: Kerr in the separated form of the FP64 kernels), compiled as
+host C++, against the oracle's component-form equations at random
+phase-space points, off the constraint surface and down to 1.02 horizon
+radii, and its sine and cosine against numpy next to the poles.
+
+FP32 carries 24 significand bits, so each derivative must agree with the
+oracle to 2e-6 of the size of the terms it is summed from (the largest
+derivative, and (u^2 + p_r^2) r / Sigma with u = P / Delta, the terms that
+cancel in p_r' next to the horizon), and r' and theta' (no cancellation)
+to 2e-6 relative: which holds next to the horizon only because Delta is
+formed as (r - r+)(r - r-) from both words of the df64 radius (in FP32,
+r^2 - 2r + a^2 keeps no correct digit at 1.02 r+ for a = 0.998). sin and cos
+must keep 1e-6 relative accuracy from 1e-8 to 1e-5 away from the poles and
+the equator, where the quadrant reduction works from both words of theta
+(its absolute floor, the FP32 rounding of theta.lo - k P2, is ~1e-14; a ray
+passes within 1e-8 of a pole almost never). Measured worst: 6.4e-7 of the
+terms, 2.8e-7 relative."""
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from _df_host import build
+
+HARNESS = r"""
+#include <cstdlib>
+#include "rhs_f32.cuh"
+using namespace osiris_impl;
+int main(int argc, char** argv) {
+  const char op = argv[1][0];
+  double in[9];  // 'e': a, E, L, r, theta, p_r, p_theta; 's': theta
+  const int n = op == 'e' ? 7 : 1;
+  while (std::fread(in, sizeof(double) * n, 1, stdin) == 1) {
+    if (op == 's') {
+      float s, c;
+      sincos_f32(df_from_double(in[0]), s, c);
+      const double out[2] = {s, c};
+      std::fwrite(out, sizeof out, 1, stdout);
+      continue;
+    }
+    const double a = in[0], E = in[1], L = in[2];
+    RayF32 k;  // ray constants formed as the MIXED kernels form them
+    k.a = (float)a;
+    k.a2 = (float)(a * a);
+    k.aE = (float)(a * E);
+    k.aL = (float)(a * L);
+    k.E = (float)E;
+    k.L = (float)L;
+    k.twoE = (float)(2.0 * E);
+    const double sq = std::sqrt(std::fmax(0.0, 1.0 - a * a));
+    k.rp = df_from_double(1.0 + sq);
+    k.rm = (float)(1.0 - sq);
+    k.twoH0 = 0.0f;
+    float d[5], twoH;
+    rhs_f32(k, df_from_double(in[3]), df_from_double(in[4]), df_from_double(in[5]),
+            df_from_double(in[6]), d[0], d[1], d[2], d[3], d[4], twoH);
+    const double out[6] = {d[0], d[1], d[2], d[3], d[4], twoH};
+    std::fwrite(out, sizeof out, 1, stdout);
+  }
+  return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def dev(tmp_path_factory):
+    exe = build(tmp_path_factory, "rhs_f32", HARNESS)
+
+    def run(op, rows, width):
+        inp = np.ascontiguousarray(rows, dtype=np.float64)
+        p = subprocess.run([str(exe), op], input=inp.tobytes(), capture_output=True, check=True)
+        return np.frombuffer(p.stdout, dtype=np.float64).reshape(-1, width)
+    return run
+
+
+def _points(n, seed):
+    rng = np.random.default_rng(seed)
+    rows = []
+    for a in (0.0, 0.5, 0.9, 0.998):
+        r_min = 1.02 * (1.0 + np.sqrt(1.0 - a * a))
+        for _ in range(n):
+            rows.append([a, 1.0, rng.uniform(-8.0, 8.0),
+                         np.exp(rng.uniform(np.log(r_min), np.log(1000.0))),
+                         rng.uniform(0.05, np.pi - 0.05), 2.0 * rng.normal(), 5.0 * rng.normal()])
+    return np.array(rows)
+
+
+def _errors(rows, out):
+    worst_terms = worst_rel = 0.0
+    for row, o in zip(rows, out):
+        a, E, L, r, th, pr, pth = row
+        y6 = np.array([0.0, r, th, 0.0, pr, pth])
+        dy = oracle.rhs_sp(oracle.KERR, y6, E, L, a=a)
+        delta = r * r - 2.0 * r + a * a
+        sigma = r * r + a * a * np.cos(th) ** 2
+        u = ((r * r + a * a) * E - a * L) / delta
+        scale = np.abs(dy[1:]).max() + (u * u + pr * pr) * max(r, 1.0) / sigma
+        err = np.abs(o[:5] - dy[1:])
+        worst_terms = max(worst_terms, err.max() / scale)
+        worst_rel = max(worst_rel, err[0] / abs(dy[1]), err[1] / abs(dy[2]))
+    return worst_terms, worst_rel
+
+
+def test_kerr_rhs_f32_against_oracle(dev):
+    rows = _points(150, 11)
+    worst_terms, worst_rel = _errors(rows, dev("e", rows, 6))
+    assert worst_terms <= 2e-6 and worst_rel <= 2e-6, (worst_terms, worst_rel)
+
+
+def test_kerr_rhs_f32_next_to_the_horizon(dev):
+    rng = np.random.default_rng(12)
+    rows = []
+    for a in (0.0, 0.9, 0.998):
+        r_h = 1.0 + np.sqrt(1.0 - a * a)
+        for f in (1.0001, 1.001, 1.01, 1.02):
+            for _ in range(20):
+                rows.append([a, 1.0, rng.uniform(-4.0, 4.0), f * r_h, rng.uniform(0.3, 2.8),
+                             rng.normal(), 3.0 * rng.normal()])
+    rows = np.array(rows)
+    worst_terms, worst_rel = _errors(rows, dev("e", rows, 6))
+    assert worst_terms <= 2e-6 and worst_rel <= 2e-6, (worst_terms, worst_rel)
+
+
+def test_sincos_f32_next_to_poles_and_equator(dev):
+    rng = np.random.default_rng(13)
+    centres = (0.0, 0.5 * np.pi, np.pi, 1.5 * np.pi, -0.5 * np.pi)
+    th = np.concatenate([c + np.exp(rng.uniform(np.log(1e-8), np.log(1e-5), 60))
+                         * rng.choice([-1.0, 1.0], 60) for c in centres])
+    th = np.concatenate([th, rng.uniform(-np.pi, 2.0 * np.pi, 300)])
+    out = dev("s", th[:, None], 2)
+    rel_s = np.abs(out[:, 0] - np.sin(th)) / np.abs(np.sin(th))
+    rel_c = np.abs(out[:, 1] - np.cos(th)) / np.abs(np.cos(th))
+    assert rel_s.max() <= 1e-6 and rel_c.max() <= 1e-6, (rel_s.max(), rel_c.max())

@@ -161,13 +161,32 @@ def test_kerr_and_qmetric_rounds():
     assert all(kinds[i] != kinds[i + 1] for i in range(both_left))
 
 
-def test_mixed_server_runs_qmetric_in_fp64():
+def test_mixed_server_runs_qmetric_in_df64():
     import paper_2202_00086_gb300 as osr
     srv, be = _server(precision=osr.MIXED)
     r = srv.submit(workloads.render(0.0, 1000.0, 60.0, (-8, 8, -8, 8), 16, 16, q=0.3))
     k = srv.submit(workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 16, 16))
-    assert r.kind == (osr.SPACETIME_QMETRIC, osr.FP64)
+    assert r.kind == (osr.SPACETIME_QMETRIC, osr.DF64)
     assert k.kind == (osr.SPACETIME_KERR, osr.MIXED)
+
+
+def test_loose_tolerance_renders_take_the_loose_precision():
+    import paper_2202_00086_gb300 as osr
+    srv, be = _server(precision=osr.DF64, loose_precision=osr.MIXED, loose_tol=1e-8)
+    base = workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 16, 16)
+    tight = srv.submit(dict(base, tol=1e-10))
+    loose = srv.submit(dict(base, tol=1e-8))
+    looser = srv.submit(dict(base, tol=1e-6))
+    q = srv.submit(dict(workloads.render(0.0, 1000.0, 60.0, (-8, 8, -8, 8), 16, 16, q=0.3),
+                        tol=1e-8))
+    assert tight.kind == (osr.SPACETIME_KERR, osr.DF64)
+    assert loose.kind == looser.kind == (osr.SPACETIME_KERR, osr.MIXED)
+    assert q.kind == (osr.SPACETIME_QMETRIC, osr.DF64)
+    while not srv.idle():
+        srv.step()
+    for r in (tight, loose, looser, q):
+        assert r.state == serve.DONE and (r.out["hits"] == 1).all()
+    assert {p for _, p in be.round_kinds} == {osr.DF64, osr.MIXED}
 
 
 class StuckEvent:
