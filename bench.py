@@ -124,10 +124,12 @@ def workload_renders(name, side):
     return workloads.kerr_shadow_ring_set(side)
 
 
-def workload_label(name, side):
+def workload_label(name, side, tol=None):
     if name == "kerr":
-        return WORKLOAD_NAME.replace("1024x1024", "%dx%d" % (side, side))
-    return WORKLOADS[name][0].replace("SIDE", str(side))
+        label = WORKLOAD_NAME.replace("1024x1024", "%dx%d" % (side, side))
+    else:
+        label = WORKLOADS[name][0].replace("SIDE", str(side))
+    return label if tol is None else label.replace("tol 1e-10", "tol %g" % tol)
 
 
 def parse():
@@ -140,6 +142,8 @@ def parse():
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "df64"])
     p.add_argument("--kernel", default="batch", choices=["batch", "persistent", "plain"])
     p.add_argument("--side", type=int, default=1024)
+    p.add_argument("--tol", type=float, default=None,
+                   help="Cash-Karp tolerance of every render (default: the workload's, 1e-10)")
     p.add_argument("--block", type=int, default=0)
     p.add_argument("--rays-per-lane", type=int, default=0)
     p.add_argument("--refill-lanes", type=int, default=0)
@@ -153,8 +157,9 @@ def parse():
     p.add_argument("--serve-rate", type=float, default=50.0)
     p.add_argument("--serve-baseline-seconds", type=float, default=5.0)
     p.add_argument("--serve-sustain-rate", default="auto",
-                   help="second stream's arrival rate (renders/s): 'auto' = 85%% of the "
-                        "capacity measured on the first stream; 0 = skip")
+                   help="second stream's arrival rate (renders/s): 'auto' = 10 above the "
+                        "first stream's rate if the server kept up with it, else 85%% of "
+                        "the capacity it measured; 0 = skip")
     return p.parse_args()
 
 
@@ -308,7 +313,8 @@ def reference_arm(args, renders):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_label(args.workload, args.side), "sample": sample},
+            "config": {"workload": workload_label(args.workload, args.side, args.tol),
+                       "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -358,16 +364,23 @@ STREAM_LABEL = ("Poisson %g renders/s for %g s (PCG64 seed 5), side log-uniform 
                 "tol 1e-8/1e-10 50/50")
 
 
+SERVED_FORM = ("DF64 for the renders at tol 1e-10, MIXED (FP32 stage evaluations in the "
+               "double-float stepper) for those at tol 1e-8")
+
+
 def serve_stream(osr, torch, dist, rank, world, barrier, rate, seconds, phase):
-    """One served stream through the continuous-batching server in DF64
-    (rounds as CUDA-graph launches of batch plans), renders dealt out whole
-    to the GPUs. Returns the merged summary with latency windows."""
+    """One served stream through the continuous-batching server in its served
+    form (DF64, and MIXED for the renders at LOOSE_TOL; rounds as CUDA-graph
+    launches of batch plans, each in-flight round on its own stream), renders
+    dealt out whole to the GPUs. Returns the merged summary with latency
+    windows."""
     from paper_2202_00086_gb300 import serve, workloads as wl
     all_arrivals = wl.served_stream(rate_hz=rate, duration_s=seconds)
     offered = sum(rd["nx"] * rd["ny"] for _, rd in all_arrivals)
     arrivals = serve.shard(all_arrivals, rank, world)
     barrier()
-    srv = serve.RenderServer(precision=osr.DF64, round_rays=1 << 21, cell_phase_deg=phase)
+    srv = serve.RenderServer(precision=osr.DF64, loose_precision=osr.MIXED, loose_tol=LOOSE_TOL,
+                             round_rays=1 << 21, cell_phase_deg=phase)
     summary = srv.run(arrivals, realtime=True)
     torch.cuda.synchronize()
     rec = serve.local_record(srv.done, srv.t0)
@@ -379,34 +392,43 @@ def serve_stream(osr, torch, dist, rank, world, barrier, rate, seconds, phase):
                        rejected=summary["rejected"])
     summary.update(serve.latency_windows(recs, seconds))
     summary["workload"] = STREAM_LABEL % (rate, seconds)
+    summary["precision"] = SERVED_FORM
     summary["offered_rays_per_s"] = offered / seconds
     summary["mean_rays_per_render"] = offered / max(1, len(all_arrivals))
+    # kept up: what had arrived by the last arrival was done within 2 s of it
+    cap = max(summary["rays_per_s"] or 0.0, summary["offered_rays_per_s"])
+    backlog = summary.get("backlog_rays_at_last_arrival")
+    summary["kept_up"] = bool(backlog is not None and backlog <= 2.0 * cap)
     return summary
 
 
 def serving_leg(args, osr, torch, dist, rank, world, barrier, phase):
     """The served-stream rows: the stream as specified (Poisson arrivals at
-    --serve-rate for --serve-seconds) through continuous batching in DF64; a
-    second stream at a rate the GPU can sustain (85% of the capacity the
-    first stream measured, rounded down to 5 renders/s) to show bounded p99;
-    and the one-render-per-launch FP64 baseline on the first
-    --serve-baseline-seconds of the first stream."""
+    --serve-rate for --serve-seconds) through continuous batching in the
+    served form; a second stream that brackets the sustainable rate (with
+    --serve-sustain-rate auto: 10 renders/s above the first stream's rate if
+    the server kept up with it, else 85% of the capacity it measured, rounded
+    down to 5 renders/s); and the one-render-per-launch FP64 baseline on the
+    first --serve-baseline-seconds of the first stream. A stream is kept up
+    with when the rays that had arrived by its last arrival were done within
+    2 s of it."""
     from paper_2202_00086_gb300 import serve, workloads as wl
     main = serve_stream(osr, torch, dist, rank, world, barrier, args.serve_rate,
                         args.serve_seconds, phase)
-    sustained = None
+    second = None
     if args.serve_sustain_rate != "0":
         if args.serve_sustain_rate == "auto":
-            cap = main["rays_per_s"] or 0.0
-            rate = 5.0 * int(0.85 * cap / main["mean_rays_per_render"] / 5.0)
+            if main["kept_up"]:
+                rate = args.serve_rate + 10.0
+            else:
+                cap = main["rays_per_s"] or 0.0
+                rate = 5.0 * int(0.85 * cap / main["mean_rays_per_render"] / 5.0)
         else:
             rate = float(args.serve_sustain_rate)
         if rate > 0:
-            sustained = serve_stream(osr, torch, dist, rank, world, barrier, rate,
-                                     args.serve_seconds, phase)
-            sustained["rate_renders_per_s"] = rate
-            growth = sustained.get("p99_growth")
-            sustained["p99_bounded"] = bool(growth is not None and growth <= 1.5)
+            second = serve_stream(osr, torch, dist, rank, world, barrier, rate,
+                                  args.serve_seconds, phase)
+            second["rate_renders_per_s"] = rate
     base_s = min(args.serve_baseline_seconds, args.serve_seconds)
     first = [x for x in wl.served_stream(rate_hz=args.serve_rate, duration_s=args.serve_seconds)
              if x[0] < base_s]
@@ -421,7 +443,7 @@ def serving_leg(args, osr, torch, dist, rank, world, barrier, phase):
     base.pop("record", None)
     base["workload"] = ("the first %g s of the same stream (%d renders), one plain FP64 "
                         "launch per render, each waited for" % (base_s, len(first)))
-    return {"continuous_batching_df64": main, "sustained_df64": sustained,
+    return {"continuous_batching": main, "second_rate": second,
             "one_render_per_launch_fp64": base,
             "rays_per_s_ratio": (main["rays_per_s"] / base["rays_per_s"]
                                  if main["rays_per_s"] and base["rays_per_s"] else None)}
@@ -571,6 +593,8 @@ def captured_h_normalised(rd, status, r, theta, max_abs_H):
 def main():
     args = parse()
     renders = workload_renders(args.workload, args.side)
+    if args.tol is not None:
+        renders = [dict(rd, tol=args.tol) for rd in renders]
     if args.impl == "reference":
         return reference_arm(args, renders)
 
@@ -589,7 +613,7 @@ def main():
             dist.barrier()
 
     precision = {"fp64": osr.FP64, "mixed": osr.MIXED, "df64": osr.DF64}[args.precision]
-    tol = 1e-10
+    tol = 1e-10 if args.tol is None else args.tol
     f_rhs = F_RHS_Q if args.workload == "qmetric" else F_RHS
     timelike = args.workload == "timelike"
     cams = [osr.Camera.from_render(rd) for rd in renders]
@@ -850,8 +874,8 @@ def main():
             and args.side == 1024):
         configs = other_configs(osr, torch, flush, stream, cell_phase)
 
-    # ---- served render stream: continuous batching (DF64) vs one render per
-    # launch (FP64 plain kernel), the same Poisson arrivals ----
+    # ---- served render stream: continuous batching (DF64 + MIXED) vs one
+    # render per launch (FP64 plain kernel), the same Poisson arrivals ----
     serving = None
     if args.serve_seconds > 0 and precision == osr.FP64 and args.workload == "kerr":
         serving = serving_leg(args, osr, torch, dist, rank, world, barrier,
@@ -880,7 +904,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {osr.FP64: "f64", osr.MIXED: "f64+f32", osr.DF64: "f64+df64"}[precision],
         "data": "synthetic",
-        "config": {"workload": workload_label(args.workload, args.side),
+        "config": {"workload": workload_label(args.workload, args.side, args.tol),
                    "rays_per_step_per_gpu": n_rays,
                    "kernel": args.kernel, "precision": args.precision,
                    "l2": "flushed between timed steps (256 MB write)",

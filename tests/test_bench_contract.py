@@ -95,9 +95,10 @@ def test_gpu_arm_line():
     assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
     assert d["variants"]["df64"]["value"] > 0
     sv = d["serving"]
-    assert sv["continuous_batching_df64"]["p99_latency_s"] > 0
-    assert "0.5 s" in sv["continuous_batching_df64"]["workload"]
-    assert "windows" in sv["continuous_batching_df64"]
+    assert sv["continuous_batching"]["p99_latency_s"] > 0
+    assert "0.5 s" in sv["continuous_batching"]["workload"]
+    assert "windows" in sv["continuous_batching"]
+    assert isinstance(sv["continuous_batching"]["kept_up"], bool)
     assert sv["one_render_per_launch_fp64"]["renders"] > 0
     p = d["pipe_probes"]
     assert p["fp64_fma"]["tflops"] == pytest.approx(r["peak"], rel=1e-12)
