@@ -89,7 +89,9 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
   float h = 0.0f, max_abs_H = 0.0f;
   unsigned n_acc = 0, n_rej = 0;
   int kind = 0, side = 0, iters = 0;
-  double lo = 0, hi = 0, h_try = 0, h_step = 0;
+  double lo = 0, hi = 0, h_try = 0;  // surface location: the step-length bracket
+  df h_try_df = mk(0.0f, 0.0f);       // h_try as the stepper takes it
+  float h_step = 0.0f;                // length of the last accepted step
   float flo = 0.0f, fhi = 0.0f;
   StateDF yF, yE;
   LaneCacheDF<INTEG> LC;
@@ -153,9 +155,10 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
     const float t = __fdividef(flo, __fsub_rn(flo, fhi));
     h_try = fma(hi - lo, (double)t, lo);
     if (!(h_try > lo && h_try < hi)) h_try = 0.5 * (lo + hi);
+    h_try_df = df_from_double(h_try);
   };
 
-  auto begin_locate = [&](int k, double hs, const StateDF& o) {
+  auto begin_locate = [&](int k, float hs, const StateDF& o) {
     kind = k;
     lo = 0.0;
     hi = hs;
@@ -169,7 +172,7 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
   };
 
   // `fresh`: the last attempt was the accepted step itself.
-  auto after_accept = [&](double hs, const StateDF& o, bool fresh) {
+  auto after_accept = [&](float hs, const StateDF& o, bool fresh) {
     if (df_lt(o.r, r_cap)) {
       begin_locate(SURF_CAPTURE, hs, o);
     } else if (df_lt(r_esc, o.r)) {
@@ -208,7 +211,8 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
     if (mode != MODE_INTEGRATE && mode != MODE_LOCATE) continue;
 
     const float hs_f = fminf(h, 0.1f * y.r.hi);
-    const df hd = (mode == MODE_LOCATE) ? df_from_double(h_try) : mk(hs_f, 0.0f);
+    // the step length: no FP64 instruction on the integration path
+    const df hd = (mode == MODE_LOCATE) ? h_try_df : mk(hs_f, 0.0f);
     StateDF o;
     float d[5];
     float twoH;
@@ -237,7 +241,7 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
         ++n_acc;
         const float grow = fminf(5.0f, fmaxf(0.2f, 0.9f * exp2f(-0.2f * log2f(err))));
         h = hs_f * grow;
-        h_step = (double)hs_f;
+        h_step = hs_f;
         yE = o;
         if (I.disk && ((df_side(y.th) > 0.0f && df_side(o.th) <= 0.0f) ||
                        (df_side(y.th) < 0.0f && df_side(o.th) >= 0.0f)))

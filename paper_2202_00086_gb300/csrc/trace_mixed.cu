@@ -4,7 +4,9 @@
 // attempt in FP32 (rhs_f32.cuh). The state, the stage inputs, the increment,
 // the error estimate and the controller keep df64 precision (FP32 with
 // compensated sums); only the stage derivatives carry FP32 rounding, ~1e-7 of
-// |k|. Nothing in the integration runs on the FP64 pipe.
+// |k|. No step of the integration runs on the FP64 pipe: FP64 only sets up
+// each ray, keeps the step-length bracket of surface location and forms the
+// outputs.
 //
 // Tolerance range. The embedded error estimate h sum_s (b_s - b*_s)(k_s - k_1)
 // then carries a noise of ~1e-8 h |k| ~ 1e-8 (h/tau) |y| (tau: time scale of
@@ -29,9 +31,14 @@
 
 namespace osiris_impl {
 
-// Registers capped as in the DF64 kernels: four blocks of 128 threads per SM.
+// Registers capped at 96 so that five blocks of 128 threads (20 warps) are
+// resident per SM: the FP32 evaluations leave the same double-float stepper
+// state as DF64 but fewer live temporaries, and the extra warps hide more of
+// the dependent FP32 chains than the added spills (L1 hits) cost. Measured on
+// the 12 x 1024^2 Kerr set at tol 1e-8 (Mrays/s, Cash-Karp): 192 registers
+// 46.7, 160: 52.6, 128: 59.9, 112: 60.7, 96: 64.7.
 #ifndef OSIRIS_MIXED_MAXREGS
-#define OSIRIS_MIXED_MAXREGS 128
+#define OSIRIS_MIXED_MAXREGS 96
 #endif
 
 struct KerrMixed {
