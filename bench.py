@@ -58,6 +58,11 @@ FP64_TRAFFIC_BYTES_PER_LAUNCH = 584.09e6
 # renders at 256x256 (3.6286e10 FMA-pipe warp instructions x 28.65 active
 # lanes over 2.7318e8 attempts), profiles/trace_df64_persistent_kerr12x256_ncu.md.
 DF64_FP32_INST_PER_ATTEMPT = 3806
+# The same for the MIXED kernel (FP32 evaluations in the double-float stepper)
+# at tol 1e-8: ncu capture of trace_mixed_persistent on the 12 renders at
+# 256x256 (8.424e9 FMA-pipe warp instructions x 26.87 active lanes over
+# 1.4604e8 attempts), profiles/trace_mixed_persistent_kerr12x256_ncu.md.
+MIXED_FP32_INST_PER_ATTEMPT = 1550
 
 
 # Workloads: the headline Kerr set (default) and the measured "next" rows,
@@ -833,6 +838,18 @@ def main():
                            "ms_per_step": lms / args.steps,
                            "accepted_per_ray": ls["accepted"] / (n_rays * args.steps),
                            "rejected_per_ray": ls["rejected"] / (n_rays * args.steps)}
+            if prec in (osr.DF64, osr.MIXED):
+                # against the FP32 pipe the double-float stepper runs on, as variants.df64
+                ipa = (MIXED_FP32_INST_PER_ATTEMPT if prec == osr.MIXED
+                       else DF64_FP32_INST_PER_ATTEMPT)
+                latt = ls["accepted"] + ls["rejected"] + ls["root_steps"]
+                rate = latt * ipa / (lms * 1e-3)
+                peak32 = probe["fp32_fma"]["warp_inst_per_s"] * 32
+                loose[name]["roofline"] = {
+                    "bound": "alu", "pipe": "FP32 (FMA heavy + lite)", "achieved": rate / 1e12,
+                    "peak": peak32 / 1e12, "unit": "T thread-instructions/s",
+                    "frac": rate / peak32, "inst_per_attempt": ipa,
+                    "peak_source": "FP32 pipe probe measured in this process"}
         loose["mixed_vs_df64"] = loose["mixed"]["value"] / loose["df64"]["value"]
         variants["tol_%g" % LOOSE_TOL] = loose
 
