@@ -49,20 +49,20 @@ ORACLE_SAMPLE_STRIDE = 128  # CPU baseline: every 128th pixel of each render
 E2E_STEPS = 5  # end-to-end leg: steps timed with host copies (wall clock)
 LOOSE_TOL = 1e-8  # the served stream's looser tolerance, where MIXED is meant to run
 # DRAM bytes (read + write) of one FP64 trace launch over the 1024^2 set: ncu
-# capture (one pass) of the timed launch of the current kernel, 48.34 MB read
-# + 535.75 MB written (profiles/trace_fp64_persistent_kerr12x1024_dram.md);
+# capture (one pass) of the timed launch of the current kernel, 46.47 MB read
+# + 528.11 MB written (profiles/trace_fp64_persistent_kerr12x1024_dram.md);
 # the outputs alone are 528.5 MB (42 B per ray).
-FP64_TRAFFIC_BYTES_PER_LAUNCH = 584.09e6
+FP64_TRAFFIC_BYTES_PER_LAUNCH = 574.58e6
 # FP32-pipe (FMA heavy + lite) thread instructions per double-float Cash-Karp
 # attempt on the Kerr set: ncu capture of trace_df64_persistent on the 12
-# renders at 256x256 (3.6286e10 FMA-pipe warp instructions x 28.65 active
-# lanes over 2.7318e8 attempts), profiles/trace_df64_persistent_kerr12x256_ncu.md.
-DF64_FP32_INST_PER_ATTEMPT = 3806
+# renders at 256x256 (3.5559e10 FMA-pipe warp instructions x 28.73 active
+# lanes over 2.7322e8 attempts), profiles/trace_df64_persistent_kerr12x256_ncu.md.
+DF64_FP32_INST_PER_ATTEMPT = 3739
 # The same for the MIXED kernel (FP32 evaluations in the double-float stepper)
 # at tol 1e-8: ncu capture of trace_mixed_persistent on the 12 renders at
-# 256x256 (8.424e9 FMA-pipe warp instructions x 26.87 active lanes over
-# 1.4604e8 attempts), profiles/trace_mixed_persistent_kerr12x256_ncu.md.
-MIXED_FP32_INST_PER_ATTEMPT = 1550
+# 256x256 (8.3947e9 FMA-pipe warp instructions x 26.41 active lanes over
+# 1.4603e8 attempts), profiles/trace_mixed_persistent_kerr12x256_ncu.md.
+MIXED_FP32_INST_PER_ATTEMPT = 1518
 
 
 # Workloads: the headline Kerr set (default) and the measured "next" rows,
