@@ -21,6 +21,7 @@
 
 #include <cstdint>
 
+#include "df64.cuh"
 #include "explog.cuh"
 #include "osiris_internal.h"
 
@@ -98,13 +99,18 @@ struct RayK {
 // k pi/512 (the node index found in FP32), so that x = theta - N_k is exact
 // (Sterbenz) and |x| <= pi/1024 (+ FP32 rounding). sin and cos of the node
 // itself (not of k pi/512) come from a per-block shared-memory table filled
-// with the library sincos; sin x and cos x - 1 from their Taylor series
+// with the library sincos; sin x - x and cos x - 1 from their Taylor series
 // (truncation below 0.01 ulp at |x| = 0.0031):
-//   sin x = x + x^3 (-1/6 + x^2/120),   cos x - 1 = x^2 (-1/2 + x^2/24),
-//   sin theta = S_k + (S_k (cos x - 1) + C_k sin x), cos similarly:
-// 11 FP64 instructions. The table covers theta in [-pi/16, 17 pi/16], which
-// holds every ray except one passing almost exactly over a pole; outside it
-// the library sincos is used.
+//   sin x - x = x^3 (-1/6 + x^2/120),   cos x - 1 = x^2 (-1/2 + x^2/24),
+//   sin theta = (S_k + C_k x) + [C_k (sin x - x) + S_k (cos x - 1)],
+//   cos theta = (C_k - S_k x) + [C_k (cos x - 1) - S_k (sin x - x)].
+// The bracketed corrections are at most 5e-6 of the result and need only
+// ~1e-11 relative accuracy, so they are formed in double-float on the FP32
+// pipe from x split into two floats by integer operations; the FP64 pipe does
+// x itself, C_k x added to S_k and the correction's two words added on: 7 FP64
+// instructions for both results, each within ~1.5 ulp. The table covers theta
+// in [-pi/16, 17 pi/16], which holds every ray except one passing almost
+// exactly over a pole; outside it the library sincos is used.
 // ---------------------------------------------------------------------------
 constexpr int kTrigPerPi = 512;                      // nodes per pi
 constexpr int kTrigFirst = -kTrigPerPi / 16;         // node index of the first entry
@@ -112,6 +118,7 @@ constexpr int kTrigNodes = kTrigPerPi + 2 * (kTrigPerPi / 16) + 1;
 
 struct TrigTable {
   double2 sc[kTrigNodes];  // sin N_k, cos N_k
+  float4 scf[kTrigNodes];  // the same as double-float pairs (sin hi, lo, cos hi, lo)
   double n[kTrigNodes];    // N_k
 };
 
@@ -129,6 +136,8 @@ __device__ __forceinline__ void trig_table_init() {
     double s, c;
     sincos(n, &s, &c);
     t.sc[i] = make_double2(s, c);
+    const float sh = (float)s, ch = (float)c;
+    t.scf[i] = make_float4(sh, (float)(s - (double)sh), ch, (float)(c - (double)ch));
     t.n[i] = n;
   }
   __syncthreads();
@@ -162,24 +171,6 @@ __device__ __forceinline__ float to_float_rz(double x) {
   return __int_as_float(sign | (e << 23) | (int)((b >> 29) & 0x7fffff));
 }
 
-__device__ __forceinline__ void sincos_tab(double th, double& s, double& c) {
-  // nearest node in FP32: 1.5 * 2^23 added to round to an integer
-  const float tk = fmaf(to_float_rz(th), (float)(kTrigPerPi / 3.14159265358979323846),
-                        12582912.0f);
-  const int idx = (__float_as_int(tk) - 0x4B400000) - kTrigFirst;
-  if ((unsigned)idx >= (unsigned)kTrigNodes) {  // also NaN / inf
-    sincos(th, &s, &c);
-    return;
-  }
-  const TrigTable& t = trig_table();
-  const double2 sc = t.sc[idx];
-  const double x = th - t.n[idx];
-  const double x2 = x * x;
-  const double sx = fma(x * x2, fma(x2, 1.0 / 120.0, -1.0 / 6.0), x);
-  const double cm = x2 * fma(x2, 1.0 / 24.0, -0.5);
-  s = fma(sc.y, sx, fma(sc.x, cm, sc.x));
-  c = fma(-sc.x, sx, fma(sc.y, cm, sc.y));
-}
 
 // a b and a + c issued as fused multiply-adds: fma(a, b, -0) = a b and
 // fma(a, 1, c) = a + c exactly (one rounding each, the same result bit for
@@ -220,6 +211,58 @@ __device__ __forceinline__ double float_to_double(float f) {
   const long long e = (long long)((b >> 23) & 0xff) - 127 + 1023;
   return __longlong_as_double((long long)(b & 0x80000000u) << 32 | e << 52 |
                               (long long)(b & 0x7fffffu) << 29);
+}
+
+// An FP32 value as a double, by integer operations only: zero (and FP32
+// denormals, below 1.2e-38) give zero.
+__device__ __forceinline__ double float_to_double0(float f) {
+  return (__float_as_uint(f) & 0x7f800000u) ? float_to_double(f) : 0.0;
+}
+
+// x (|x| < 2^-8) as a double-float pair by integer operations only: hi is x
+// truncated to 24 significant bits, lo the 29 bits below them truncated to
+// 24, so hi + lo = x to 2^-46 |x|; lo is zero below 2^-74.
+__device__ __forceinline__ df split_small(double x) {
+  const long long b = __double_as_longlong(x);
+  const float hi = to_float_rz(x);
+  const long long m = b & ((1LL << 29) - 1);  // the significand bits below hi's
+  const int e = (int)((b >> 52) & 0x7ff);     // biased exponent of x
+  const int lead = 63 - __clzll(m | 1);       // leading bit of m (m = 0: no bits, see below)
+  const int fe = lead + e - 1075 + 127;        // FP32 biased exponent of the leading bit
+  const unsigned frac = (unsigned)((lead >= 23) ? (m >> (lead - 23)) : (m << (23 - lead)));
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const float lo = (m != 0 && fe > 0) ? __uint_as_float(sign | ((unsigned)fe << 23) |
+                                                         (frac & 0x7fffffu))
+                                      : 0.0f;
+  return mk(hi, lo);
+}
+
+__device__ __forceinline__ void sincos_tab(double th, double& s, double& c) {
+  using namespace dfc;
+  // nearest node in FP32: 1.5 * 2^23 added to round to an integer
+  const float tk = fmaf(to_float_rz(th), (float)(kTrigPerPi / 3.14159265358979323846),
+                        12582912.0f);
+  const int idx = (__float_as_int(tk) - 0x4B400000) - kTrigFirst;
+  if ((unsigned)idx >= (unsigned)kTrigNodes) {  // also NaN / inf
+    sincos(th, &s, &c);
+    return;
+  }
+  const TrigTable& t = trig_table();
+  const double2 sc = t.sc[idx];
+  const float4 scf = t.scf[idx];
+  const double x = th - t.n[idx];  // exact
+  // the corrections in double-float
+  const df xd = split_small(x);
+  const df u = df_sqr(xd);                                                    // x^2
+  const df q = df_add_f_u(mk(-I3H, -I3L), __fmul_rn(u.hi, 1.0f / 120.0f));    // -1/6 + x^2/120
+  const df ds = df_mul(df_mul(xd, u), q);                                     // sin x - x
+  const df cm = df_add_f_u(df_scale(u, -0.5f),
+                           __fmul_rn(__fmul_rn(u.hi, u.hi), 1.0f / 24.0f));   // cos x - 1
+  const df S = mk(scf.x, scf.y), C = mk(scf.z, scf.w);
+  const df corr_s = df_add_u(df_mul(C, ds), df_mul(S, cm));
+  const df corr_c = df_sub_u(df_mul(C, cm), df_mul(S, ds));
+  s = fma(sc.y, x, sc.x + float_to_double0(corr_s.hi)) + float_to_double0(corr_s.lo);
+  c = fma(-sc.x, x, sc.y + float_to_double0(corr_c.hi)) + float_to_double0(corr_c.lo);
 }
 
 // max |H - H0| kept as the bit pattern of a non-negative double: |v| and the

@@ -42,6 +42,11 @@ static const osiris_dim3 blockDim = {1, 1, 1};
 static inline void __syncthreads() {}
 struct double2 { double x, y; };
 static inline double2 make_double2(double x, double y) { double2 r; r.x = x; r.y = y; return r; }
+struct float4 { float x, y, z, w; };
+static inline float4 make_float4(float x, float y, float z, float w) {
+  float4 r; r.x = x; r.y = y; r.z = z; r.w = w; return r;
+}
+static inline int __clzll(long long v) { return v == 0 ? 64 : __builtin_clzll((unsigned long long)v); }
 static inline long long __double_as_longlong(double x) {
   long long b; std::memcpy(&b, &x, 8); return b;
 }
