@@ -75,9 +75,8 @@ extern "C" {
 #define OSIRIS_STAT_STATUS0 5       /* 5..10: rays per status code 0..5 */
 #define OSIRIS_STAT_MAX_ABS_H 11    /* max |H| over all rays that did not end in
                                        OSIRIS_STATUS_ERROR, as IEEE-754 bits */
-#define OSIRIS_STAT_FP64_STEPS 12   /* reserved: steps a reduced-precision kernel
-                                       took in FP64 (0: neither MIXED nor DF64
-                                       takes any) */
+#define OSIRIS_STAT_FP64_STEPS 12   /* attempts taken in FP64: every attempt of
+                                       the FP64 kernels, none in MIXED or DF64 */
 #define OSIRIS_STAT_CHECK_FAILS 13  /* bounds-checked build only: failed index checks */
 #define OSIRIS_STAT_CHECK_WORST 14  /* bounds-checked build only: max over failures of
                                        (check code << 56) | ray index; codes 1 ray index
