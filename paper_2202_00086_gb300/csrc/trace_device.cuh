@@ -79,12 +79,6 @@ struct State {  // evolved coordinates and momenta (t does not feed back; not in
   double r, th, ph, pr, pth;
 };
 
-// The embedded error estimate of an FP64 attempt, per component, as
-// double-float pairs (formed on the FP32 pipe; see rk_attempt64).
-struct ErrDF {
-  df r, th, ph, pr, pth;
-};
-
 // Per-ray constants of the Hamiltonian (Kerr: a and its products; q-metric:
 // q and kap = q (2 + q)).
 struct RayK {
@@ -225,12 +219,10 @@ __device__ __forceinline__ double float_to_double0(float f) {
   return (__float_as_uint(f) & 0x7f800000u) ? float_to_double(f) : 0.0;
 }
 
-// x as a double-float pair by integer operations only: hi is x truncated to
-// 24 significant bits, lo the 29 bits below them truncated to 24, so
-// hi + lo = x to 2^-46 |x| for |x| in FP32's normal range (hi is zero below
-// it and infinite above it, NaN and infinities included); lo is zero where
-// its bits fall below FP32's normal range.
-__device__ __forceinline__ df split_df(double x) {
+// x (|x| < 2^-8) as a double-float pair by integer operations only: hi is x
+// truncated to 24 significant bits, lo the 29 bits below them truncated to
+// 24, so hi + lo = x to 2^-46 |x|; lo is zero below 2^-74.
+__device__ __forceinline__ df split_small(double x) {
   const long long b = __double_as_longlong(x);
   const float hi = to_float_rz(x);
   const long long m = b & ((1LL << 29) - 1);  // the significand bits below hi's
@@ -260,7 +252,7 @@ __device__ __forceinline__ void sincos_tab(double th, double& s, double& c) {
   const float4 scf = t.scf[idx];
   const double x = th - t.n[idx];  // exact
   // the corrections in double-float
-  const df xd = split_df(x);
+  const df xd = split_small(x);
   const df u = df_sqr(xd);                                                    // x^2
   const df q = df_add_f_u(mk(-I3H, -I3L), __fmul_rn(u.hi, 1.0f / 120.0f));    // -1/6 + x^2/120
   const df ds = df_mul(df_mul(xd, u), q);                                     // sin x - x
@@ -495,18 +487,10 @@ struct Tableau64 {
 
 // Stages 1 .. NS-1 (stage 0, k[0], is given), o and d. FSAL: the last
 // stage is evaluated at o.
-//
-// d = h sum_j e_j scale_j k_j only decides accept or reject, so it is formed
-// in double-float on the FP32 and integer pipes (each k_j split into two
-// floats by split_df): its terms cancel by up to ~(h/T)^-3 / 30 (T: time
-// scale of the solution; ~1e5 at tol 1e-12), and at ~2^-47 per term d keeps
-// ~1e-10 relative accuracy, far inside the 1e-5 band around the accept
-// threshold that the exact test resolves (trace_body). That takes the 30
-// FP64 instructions of the sum off the FP64 pipe, which bounds this kernel.
 template <class Met, int NS, bool FSAL>
 __device__ __forceinline__ void rk_attempt64(const Tableau64<NS>& T, const RayK& K,
                                              const State& y, double h, Deriv (&k)[NS],
-                                             State& o, ErrDF& d) {
+                                             State& o, State& d) {
   double w[NS];
   w[0] = h * k[0].scale;
   constexpr int NI = FSAL ? NS - 1 : NS;  // stages whose input is a stage sum
@@ -542,31 +526,29 @@ __device__ __forceinline__ void rk_attempt64(const Tableau64<NS>& T, const RayK&
     rhs64_at<Met>(K, o, k[NS - 1]);
     w[NS - 1] = h * k[NS - 1].scale;
   }
-  ErrDF acc;
-  acc.r = acc.th = acc.ph = acc.pr = acc.pth = mk(0.0f, 0.0f);
+  const double c0 = T.e[0] * w[0];
+  d.r = c0 * k[0].r;
+  d.th = c0 * k[0].th;
+  d.ph = c0 * k[0].ph;
+  d.pr = c0 * k[0].pr;
+  d.pth = c0 * k[0].pth;
 #pragma unroll
-  for (int j = 0; j < NS; ++j) {
+  for (int j = 1; j < NS; ++j) {
     if (T.e[j] != 0.0) {
-      const df c = df_mul(split_df(T.e[j]), split_df(k[j].scale));  // e_j scale_j
-      acc.r = df_add_u(acc.r, df_mul(c, split_df(k[j].r)));
-      acc.th = df_add_u(acc.th, df_mul(c, split_df(k[j].th)));
-      acc.ph = df_add_u(acc.ph, df_mul(c, split_df(k[j].ph)));
-      acc.pr = df_add_u(acc.pr, df_mul(c, split_df(k[j].pr)));
-      acc.pth = df_add_u(acc.pth, df_mul(c, split_df(k[j].pth)));
+      const double c = T.e[j] * w[j];
+      d.r = fma(c, k[j].r, d.r);
+      d.th = fma(c, k[j].th, d.th);
+      d.ph = fma(c, k[j].ph, d.ph);
+      d.pr = fma(c, k[j].pr, d.pr);
+      d.pth = fma(c, k[j].pth, d.pth);
     }
   }
-  const df hd = split_df(h);
-  d.r = df_norm(df_mul(hd, acc.r));
-  d.th = df_norm(df_mul(hd, acc.th));
-  d.ph = df_norm(df_mul(hd, acc.ph));
-  d.pr = df_norm(df_mul(hd, acc.pr));
-  d.pth = df_norm(df_mul(hd, acc.pth));
 }
 
 // One Cash-Karp attempt of length h from y (Sec. 3.1, RKCK45).
 template <class Met = KerrMetric>
 __device__ __forceinline__ void ck_step64(const RayK& K, const State& y, double h, State& o,
-                                          ErrDF& d, double& twoH) {
+                                          State& d, double& twoH) {
   constexpr Tableau64<6> T = {
       {{0, 0, 0, 0, 0, 0},
        {ck::A21, 0, 0, 0, 0, 0},
@@ -587,7 +569,7 @@ __device__ __forceinline__ void ck_step64(const RayK& K, const State& y, double 
 // step if this one is accepted.
 template <class Met = KerrMetric>
 __device__ __forceinline__ void dp_step64(const RayK& K, const State& y, double h,
-                                          const Deriv& k1, State& o, ErrDF& d, Deriv& k7) {
+                                          const Deriv& k1, State& o, State& d, Deriv& k7) {
   constexpr Tableau64<7> T = {
       {{0, 0, 0, 0, 0, 0, 0},
        {dp::A21, 0, 0, 0, 0, 0, 0},
@@ -614,18 +596,10 @@ __device__ __forceinline__ bool state_not_finite(const State& s) {
          not_finite(s.pth);
 }
 
-__device__ __forceinline__ bool err_not_finite(const ErrDF& d) {
-  const unsigned inf = 0x7f800000u;
-  return ((__float_as_uint(d.r.hi) & inf) == inf) | ((__float_as_uint(d.th.hi) & inf) == inf) |
-         ((__float_as_uint(d.ph.hi) & inf) == inf) | ((__float_as_uint(d.pr.hi) & inf) == inf) |
-         ((__float_as_uint(d.pth.hi) & inf) == inf);
-}
-
 // Error test of one component: accept needs |d| <= tol (1 + max(|y|, |o|));
 // the ratio (for the step-size controller only) is formed in FP32.
-__device__ __forceinline__ void err_component(double y, double o, df dd, double tol,
+__device__ __forceinline__ void err_component(double y, double o, double d, double tol,
                                               bool& ok, float& err) {
-  const double d = float_to_double0(dd.hi) + float_to_double0(dd.lo);
   const double scale = tol * (1.0 + fmax(fabs(y), fabs(o)));
   const double ad = fabs(d);
   ok = ok && (ad <= scale);
@@ -648,11 +622,11 @@ __device__ __forceinline__ float abs_to_float_rz(double x) {
 // within a relative 1e-6 of the FP64 one. The caller decides accept/reject
 // from it and falls back to the exact FP64 test (err_component) only when it
 // lies within 1e-5 of 1, so the decision is always the FP64 one.
-__device__ __forceinline__ float err_norm32(const State& y, const State& o, const ErrDF& d,
+__device__ __forceinline__ float err_norm32(const State& y, const State& o, const State& d,
                                             float tol32) {
   float err = 0.0f;
 #define OSIRIS_ERR32(c)                                                                  \
-  err = fmaxf(err, __fdividef(fabsf(d.c.hi),                                            \
+  err = fmaxf(err, __fdividef(abs_to_float_rz(d.c),                                     \
                               tol32 * (1.0f + fmaxf(abs_to_float_rz(y.c),               \
                                                     abs_to_float_rz(o.c)))))
   OSIRIS_ERR32(r);

@@ -20,7 +20,7 @@ struct StepperFP64<OSIRIS_RKCK45, Met> {
   static __device__ __forceinline__ void reset(LaneCache&) {}
   static __device__ __forceinline__ void accepted(LaneCache&) {}
   static __device__ __forceinline__ bool attempt(const RayK& K, const RayCache&, LaneCache&,
-                                                 const State& y, double h, State& o, ErrDF& d,
+                                                 const State& y, double h, State& o, State& d,
                                                  double& twoH) {
     ck_step64<Met>(K, y, h, o, d, twoH);
     return true;
@@ -47,7 +47,7 @@ struct StepperFP64<OSIRIS_RKDP45, Met> {
   static __device__ __forceinline__ void reset(LaneCache& c) { c.valid = false; }
   static __device__ __forceinline__ void accepted(LaneCache& c) { c.k1 = c.k7; }
   static __device__ __forceinline__ bool attempt(const RayK& K, const RayCache&, LaneCache& c,
-                                                 const State& y, double h, State& o, ErrDF& d,
+                                                 const State& y, double h, State& o, State& d,
                                                  double& twoH) {
     if (!c.valid) {
       rhs64_at<Met>(K, y, c.k1);

@@ -395,8 +395,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
     if (mode != MODE_INTEGRATE && mode != MODE_LOCATE) continue;
 
     const double hs = (mode == MODE_LOCATE) ? h_try : fmin(h, 0.1 * y.r);
-    State o;
-    ErrDF d;
+    State o, d;
     double twoH;
     const bool fp64_step = Stepper::attempt(K, RC, LC, y, hs, o, d, twoH);
     S.rhs += 6;
@@ -404,7 +403,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& A) {
 
     if (mode == MODE_INTEGRATE) {
       track_abs_H(max_abs_H, twoH, I.H0);
-      if (state_not_finite(o) || err_not_finite(d)) {
+      if (state_not_finite(o) || state_not_finite(d)) {
         finish(OSIRIS_STATUS_ERROR, y);
         continue;
       }

@@ -49,8 +49,7 @@ int main(int argc, char** argv) {
       K.aE = K.a * K.E;
       K.aL = K.a * K.L;
       K.E2 = K.E + K.E;
-      State y, o;
-      ErrDF d;
+      State y, o, d;
       y.r = in[4];
       y.th = in[5];
       y.ph = in[6];
@@ -64,9 +63,7 @@ int main(int argc, char** argv) {
         rhs64_at<KerrMetric>(K, y, k1);
         dp_step64<KerrMetric>(K, y, in[9], k1, o, d, k7);
       }
-      auto v = [](df x) { return (double)x.hi + (double)x.lo; };
-      const double out[10] = {o.r, o.th, o.ph, o.pr, o.pth, v(d.r), v(d.th), v(d.ph), v(d.pr),
-                              v(d.pth)};
+      const double out[10] = {o.r, o.th, o.ph, o.pr, o.pth, d.r, d.th, d.ph, d.pr, d.pth};
       std::fwrite(out, sizeof out, 1, stdout);
     } else {
       RayK K;  // as the kernels' load_ray forms it
