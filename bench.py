@@ -49,10 +49,10 @@ ORACLE_SAMPLE_STRIDE = 128  # CPU baseline: every 128th pixel of each render
 E2E_STEPS = 5  # end-to-end leg: steps timed with host copies (wall clock)
 LOOSE_TOL = 1e-8  # the served stream's looser tolerance, where MIXED is meant to run
 # DRAM bytes (read + write) of one FP64 trace launch over the 1024^2 set: ncu
-# capture (one pass) of the timed launch of the current kernel, 46.47 MB read
-# + 528.11 MB written (profiles/trace_fp64_persistent_kerr12x1024_dram.md);
+# capture (one pass) of the timed launch of the current kernel, 47.60 MB read
+# + 528.18 MB written (profiles/trace_fp64_persistent_kerr12x1024_dram.md);
 # the outputs alone are 528.5 MB (42 B per ray).
-FP64_TRAFFIC_BYTES_PER_LAUNCH = 574.58e6
+FP64_TRAFFIC_BYTES_PER_LAUNCH = 575.78e6
 # FP32-pipe (FMA heavy + lite) thread instructions per double-float Cash-Karp
 # attempt on the Kerr set: ncu capture of trace_df64_persistent on the 12
 # renders at 256x256 (3.5559e10 FMA-pipe warp instructions x 28.73 active
