@@ -827,7 +827,7 @@ def main():
         }
 
     # ---- the three precisions at the looser tolerance MIXED is meant for ----
-    if (precision == osr.FP64 and not args.no_variants and args.workload == "kerr"
+    if (precision == osr.FP64 and not args.no_variants and args.workload in ("kerr", "qmetric")
             and args.kernel == "batch"):
         reqs_loose = [dict(r, tol=LOOSE_TOL) for r in reqs]
         loose = {"workload": "the same renders at Cash-Karp tol %g" % LOOSE_TOL}
@@ -838,7 +838,7 @@ def main():
                            "ms_per_step": lms / args.steps,
                            "accepted_per_ray": ls["accepted"] / (n_rays * args.steps),
                            "rejected_per_ray": ls["rejected"] / (n_rays * args.steps)}
-            if prec in (osr.DF64, osr.MIXED):
+            if prec in (osr.DF64, osr.MIXED) and args.workload == "kerr":
                 # against the FP32 pipe the double-float stepper runs on, as variants.df64
                 ipa = (MIXED_FP32_INST_PER_ATTEMPT if prec == osr.MIXED
                        else DF64_FP32_INST_PER_ATTEMPT)

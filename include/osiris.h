@@ -50,9 +50,9 @@ extern "C" {
 #define OSIRIS_MIXED 1 /* stage evaluations of Hamilton's equations in FP32,
                           inside the DF64 stepper: double-float state, stage
                           sums, error estimate and controller, end-point |H|
-                          in double-float; Kerr only; for tolerances of 1e-8
-                          and looser (FP32 rounding of the stages swamps the
-                          error estimate of tighter ones) */
+                          in double-float; for tolerances of 1e-8 and looser
+                          (FP32 rounding of the stages swamps the error
+                          estimate of tighter ones) */
 #define OSIRIS_DF64 2  /* every operation of the integration in double-float
                           (pairs of FP32, 48-bit significand) on the FP32
                           pipe; FP64 for initial data and outputs */
@@ -185,8 +185,7 @@ int osiris_init_camera(osiris_camera** out, double a, double r_obs, double incl_
  * (-1, -1 + sqrt(3/2)) \ {0} describes naked singularities. The initial data
  * are those of osiris_init_camera for this static metric; rays end at
  * r < r_cap_factor * 2 (the singular surface r = 2) or at the celestial
- * sphere. q-metric renders run in FP64 or DF64 (not OSIRIS_MIXED), without a
- * disk.
+ * sphere. q-metric renders run in every precision, without a disk.
  *   q          > -1; r_obs > 20; the other arguments as osiris_init_camera. */
 int osiris_init_camera_q(osiris_camera** out, double q, double r_obs, double incl_deg,
                          double x_min, double x_max, double y_min, double y_max, int32_t nx,
@@ -275,7 +274,7 @@ typedef struct osiris_batch_plan osiris_batch_plan;
  * osiris_workspace_bytes(max_requests) bytes) belongs to the plan until it is
  * destroyed and must not be used by other calls meanwhile. The plan allocates
  * max_requests table entries of pinned host memory. Returns OSIRIS_EINVAL
- * (bad arguments, q-metric in MIXED), OSIRIS_ENOMEM (workspace too small
+ * (bad arguments), OSIRIS_ENOMEM (workspace too small
  * or no pinned memory) or OSIRIS_ECUDA; *plan is NULL on error. */
 int osiris_batch_plan_create(osiris_batch_plan** plan, int32_t max_requests, int32_t spacetime,
                              const osiris_trace_opts* opts);

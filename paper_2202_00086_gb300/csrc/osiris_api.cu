@@ -132,7 +132,7 @@ int cuda_rc(int e) { return e == 0 ? OSIRIS_OK : OSIRIS_ECUDA; }
 int check_spacetime(int spacetime, int disk, const osiris_trace_opts* o) {
   if (spacetime == OSIRIS_SPACETIME_KERR) return OSIRIS_OK;
   if (spacetime != OSIRIS_SPACETIME_QMETRIC) return OSIRIS_EINVAL;
-  if ((o->precision != OSIRIS_FP64 && o->precision != OSIRIS_DF64) || disk) return OSIRIS_EINVAL;
+  if (disk) return OSIRIS_EINVAL;  // the q-metric has no disk model
   return OSIRIS_OK;
 }
 

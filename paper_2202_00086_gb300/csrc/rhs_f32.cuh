@@ -11,8 +11,11 @@
 //     from the leading word exactly (as in df_sincos), so sin theta keeps its
 //     relative accuracy next to the poles.
 // Every other operation has FP32 relative accuracy (~1e-7), the accuracy of
-// the derivatives this returns. Like rhs_df it uses no CUDA built-in beyond
-// the FP32 intrinsics, so it also compiles as host C++ for the CPU tests.
+// the derivatives this returns. The q-metric evaluation (rhs_q_f32, Appendix
+// A) does the same with r - 2, the factor of f = 1 - 2/r that vanishes at its
+// inner surface, and takes the powers f^q and X^k from the FP32 exp and log
+// intrinsics. Like rhs_df it uses no CUDA built-in beyond the FP32
+// intrinsics, so it also compiles as host C++ for the CPU tests.
 #pragma once
 
 #include "df64.cuh"
@@ -36,7 +39,8 @@ __device__ __forceinline__ void sincos_f32(df th, float& s, float& c) {
   const float u = __fmul_rn(t, t);
   const float ps = fmaf(u, fmaf(u, fmaf(u, fmaf(u, I9H, -I7H), I5H), -I3H), 1.0f);
   const float st = __fmul_rn(t, ps);
-  const float ct = fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, -I10, I8H), -I6H), I4H), -0.5f), 1.0f);
+  const float ct =
+      fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, -I10, I8H), -I6H), I4H), -0.5f), 1.0f);
   const int q = ((int)k) & 3;
   if (q == 0) {
     s = st;
@@ -91,6 +95,53 @@ __device__ __forceinline__ void rhs_f32(const RayF32& K, df r, df th, df pr, df 
   dpr = __fmul_rn(iSig, fmaf(rf, __fsub_rn(X, Y), Y));
   dpth = __fmul_rn(__fmul_rn(c, iSig), fmaf(W, fmaf(Lis, is, K.aE), -__fmul_rn(a2s, NiS)));
   twoH = __fsub_rn(NiS, K.twoH0);
+}
+
+struct RayQF32 {
+  float E, L, q, kap, nq1, E2;  // kap = q (2 + q), nq1 = -(1 + q), E2 = E^2
+  float twoH0;
+};
+
+// The q-metric (Appendix A) in FP32: the collected form of rhs_q_df
+// (rhs_df.cuh) and rhs_q64, the derivatives from the four terms of 2H and
+// their logarithmic derivatives, with f = (r - 2) / r and X = 1 + sin^2 / D,
+// D = r (r - 2).
+__device__ __forceinline__ void rhs_q_f32(const RayQF32& K, df r, df th, df pr, df pth,
+                                          float& dr, float& dth, float& dph, float& dpr,
+                                          float& dpth, float& twoH) {
+  float s, c;
+  sincos_f32(th, s, c);
+  const float rf = __fadd_rn(r.hi, r.lo);
+  const float prf = __fadd_rn(pr.hi, pr.lo);
+  const float ptf = __fadd_rn(pth.hi, pth.lo);
+  const float rm2 = __fadd_rn(__fsub_rn(r.hi, 2.0f), r.lo);  // r - 2, exact next to r = 2
+  const float iD = __fdividef(1.0f, __fmul_rn(rf, rm2));
+  const float ir = __fmul_rn(rm2, iD);  // 1/r
+  const float f = __fmul_rn(rm2, ir);   // 1 - 2/r
+  const float s2 = __fmul_rn(s, s);
+  const float is2 = __fdividef(1.0f, s2);
+  const float X = fmaf(s2, iD, 1.0f);
+  const float iX = __fdividef(1.0f, X);
+  const float fq = __expf(__fmul_rn(K.q, __logf(f)));
+  const float fXk = __fmul_rn(fq, __expf(__fmul_rn(K.kap, __logf(X))));
+  const float ir2 = __fmul_rn(ir, ir);
+  const float gtt = -__fdividef(1.0f, __fmul_rn(f, fq));
+  dr = __fmul_rn(__fmul_rn(f, fXk), prf);
+  dth = __fmul_rn(__fmul_rn(fXk, ir2), ptf);
+  dph = __fmul_rn(__fmul_rn(__fmul_rn(fq, ir2), is2), K.L);
+  // the four terms of 2H and their logarithmic derivatives
+  const float Ht = __fmul_rn(gtt, K.E2);
+  const float Hr = __fmul_rn(dr, prf), Hth = __fmul_rn(dth, ptf), Hph = __fmul_rn(dph, K.L);
+  twoH = __fsub_rn(__fadd_rn(__fadd_rn(Ht, Hr), __fadd_rn(Hth, Hph)), K.twoH0);
+  const float iDX = __fmul_rn(iD, iX);
+  const float a1 = __fmul_rn(K.nq1, iD);
+  const float a2 = __fmul_rn(__fmul_rn(__fmul_rn(K.kap, s2), __fsub_rn(rf, 1.0f)),
+                             __fmul_rn(iD, iDX));
+  const float a3 = fmaf(-K.q, iD, ir);
+  const float HrHth = __fadd_rn(Hr, Hth);
+  dpr = fmaf(a1, __fsub_rn(Hr, Ht), fmaf(a2, HrHth, __fmul_rn(a3, __fadd_rn(Hth, Hph))));
+  dpth = __fmul_rn(__fmul_rn(c, s),
+                   fmaf(-__fmul_rn(K.kap, iDX), HrHth, __fmul_rn(Hph, is2)));
 }
 
 }  // namespace osiris_impl

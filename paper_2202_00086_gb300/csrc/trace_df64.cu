@@ -30,18 +30,6 @@
 
 namespace osiris_impl {
 
-__device__ __forceinline__ RayQDF to_qdf(const RayK& K) {
-  RayQDF k;
-  k.E = df_from_double(K.E);
-  k.L = df_from_double(K.L);
-  k.q = df_from_double(K.q);
-  k.kap = df_from_double(K.kap);
-  k.nq1 = df_from_double(-(1.0 + K.q));
-  k.E2 = df_from_double(K.E * K.E);
-  k.twoH0 = 0.0f;
-  return k;
-}
-
 // Metric policies of the double-float kernels: the ray constants, the
 // evaluation, and the register cap.
 // Registers capped at 128 so that four blocks of 128 threads (16 warps) are

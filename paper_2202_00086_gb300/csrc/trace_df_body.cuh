@@ -49,6 +49,18 @@ __device__ __forceinline__ State to_double(const StateDF& d) {
   return s;
 }
 
+__device__ __forceinline__ RayQDF to_qdf(const RayK& K) {
+  RayQDF k;
+  k.E = df_from_double(K.E);
+  k.L = df_from_double(K.L);
+  k.q = df_from_double(K.q);
+  k.kap = df_from_double(K.kap);
+  k.nq1 = df_from_double(-(1.0 + K.q));
+  k.E2 = df_from_double(K.E * K.E);
+  k.twoH0 = 0.0f;
+  return k;
+}
+
 // a < b for normalised df values
 __device__ __forceinline__ bool df_lt(df a, df b) {
   return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);

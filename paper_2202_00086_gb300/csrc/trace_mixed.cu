@@ -1,7 +1,7 @@
-// Mixed-precision trace kernels (OSIRIS_MIXED): the lane state machine and
-// the double-float stepper of the DF64 kernels (trace_df_body.cuh,
-// step_df.cuh) with the six evaluations of Hamilton's equations of every
-// attempt in FP32 (rhs_f32.cuh). The state, the stage inputs, the increment,
+// Mixed-precision trace kernels (OSIRIS_MIXED), Kerr and the q-metric: the
+// lane state machine and the double-float stepper of the DF64 kernels
+// (trace_df_body.cuh, step_df.cuh) with the six evaluations of Hamilton's
+// equations of every attempt in FP32 (rhs_f32.cuh). The state, the stage inputs, the increment,
 // the error estimate and the controller keep df64 precision (FP32 with
 // compensated sums); only the stage derivatives carry FP32 rounding, ~1e-7 of
 // |k|. No step of the integration runs on the FP64 pipe: FP64 only sets up
@@ -84,39 +84,85 @@ struct KerrMixed {
   }
 };
 
-template <int INTEG>
-__global__ void __maxnreg__(KerrMixed::kMaxRegs)
-    trace_mixed_plain(const __grid_constant__ KernelArgs A) {
-  trace_body_df<KerrMixed, false, INTEG>(A);
+// The q-metric (Appendix A) with the same stepper; its end-point |H| from
+// the double-float q-metric equations (rhs_q_df).
+struct QMetricMixed {
+  using Ray = RayQF32;
+  static constexpr int kMaxRegs = OSIRIS_MIXED_MAXREGS;
+  static constexpr bool kTrackH = false;
+  static constexpr double kLocateRel = 2e-7;
+  static __device__ __forceinline__ Ray ray(const RayK& K) {
+    Ray k;
+    k.E = (float)K.E;
+    k.L = (float)K.L;
+    k.q = (float)K.q;
+    k.kap = (float)K.kap;
+    k.nq1 = (float)(-(1.0 + K.q));
+    k.E2 = (float)(K.E * K.E);
+    k.twoH0 = 0.0f;
+    return k;
+  }
+  static __device__ __forceinline__ void rhs(const Ray& K, df r, df th, df pr, df pth, df& dr,
+                                             df& dth, df& dph, df& dpr, df& dpth,
+                                             float& twoH) {
+    float fr, ft, fp, fpr, fpt;
+    rhs_q_f32(K, r, th, pr, pth, fr, ft, fp, fpr, fpt, twoH);
+    dr = mk(fr, 0.0f);
+    dth = mk(ft, 0.0f);
+    dph = mk(fp, 0.0f);
+    dpr = mk(fpr, 0.0f);
+    dpth = mk(fpt, 0.0f);
+  }
+  static __device__ __forceinline__ float end_twoH(const Ray& KD, const RayK& K,
+                                                   const StateDF& y) {
+    RayQDF k = to_qdf(K);
+    k.twoH0 = KD.twoH0;
+    df dr, dth, dph, dpr, dpth;
+    float twoH;
+    rhs_q_df(k, y.r, y.th, y.pr, y.pth, dr, dth, dph, dpr, dpth, twoH);
+    return twoH;
+  }
+};
+
+template <class Met, int INTEG>
+__global__ void __maxnreg__(Met::kMaxRegs) trace_mixed_plain(const __grid_constant__ KernelArgs A) {
+  trace_body_df<Met, false, INTEG>(A);
 }
 
-template <int INTEG>
-__global__ void __maxnreg__(KerrMixed::kMaxRegs)
+template <class Met, int INTEG>
+__global__ void __maxnreg__(Met::kMaxRegs)
     trace_mixed_persistent(const __grid_constant__ KernelArgs A) {
-  trace_body_df<KerrMixed, true, INTEG>(A);
+  trace_body_df<Met, true, INTEG>(A);
 }
 
-template <int INTEG>
+template <class Met, int INTEG>
 static const void* mixed_kernel(Kernel kind) {
-  return kind == Kernel::kPersistent ? (const void*)trace_mixed_persistent<INTEG>
-                                     : (const void*)trace_mixed_plain<INTEG>;
+  return kind == Kernel::kPersistent ? (const void*)trace_mixed_persistent<Met, INTEG>
+                                     : (const void*)trace_mixed_plain<Met, INTEG>;
 }
 
-static const void* select_mixed(Kernel kind, int integrator) {
-  return integrator == OSIRIS_RKDP45 ? mixed_kernel<OSIRIS_RKDP45>(kind)
-                                     : mixed_kernel<OSIRIS_RKCK45>(kind);
+template <class Met>
+static const void* mixed_kernel(Kernel kind, int integrator) {
+  return integrator == OSIRIS_RKDP45 ? mixed_kernel<Met, OSIRIS_RKDP45>(kind)
+                                     : mixed_kernel<Met, OSIRIS_RKCK45>(kind);
+}
+
+static const void* select_mixed(Kernel kind, int integrator, int spacetime) {
+  return spacetime == OSIRIS_SPACETIME_QMETRIC ? mixed_kernel<QMetricMixed>(kind, integrator)
+                                               : mixed_kernel<KerrMixed>(kind, integrator);
 }
 
 int launch_trace_mixed(const KernelArgs& args, Kernel kind, int integrator, int grid, int block,
                        void* stream) {
+  const int spacetime = args.reqs ? args.spacetime : args.single.spacetime;
   void* params[] = {const_cast<KernelArgs*>(&args)};
-  return (int)cudaLaunchKernel(select_mixed(kind, integrator), dim3(grid), dim3(block), params,
-                               0, static_cast<cudaStream_t>(stream));
+  return (int)cudaLaunchKernel(select_mixed(kind, integrator, spacetime), dim3(grid),
+                               dim3(block), params, 0, static_cast<cudaStream_t>(stream));
 }
 
-int occupancy_mixed(Kernel kind, int integrator, int, int block, int* blocks_per_sm) {
+int occupancy_mixed(Kernel kind, int integrator, int spacetime, int block, int* blocks_per_sm) {
   return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      blocks_per_sm, select_mixed(kind, integrator), block, 0);
+      blocks_per_sm, select_mixed(kind, integrator, spacetime), block, 0);
 }
 
 }  // namespace osiris_impl

@@ -24,8 +24,7 @@ Round composition: a batched launch holds one space-time and one precision,
 so each render has a kind: Kerr renders run at the server's precision, or at
 `loose_precision` when one is given and the render's tolerance is at least
 `loose_tol` (e.g. MIXED, FP32 stage evaluations, for the renders at 1e-8);
-q-metric renders (shadow and lensing; Appendix A) run at the same precision,
-in DF64 where that is MIXED (the q-metric has no MIXED kernel). A round serves one
+q-metric renders (shadow and lensing; Appendix A) likewise. A round serves one
 kind: that of the oldest render with rays left, or the next kind in that
 order when the previous round served it, so kinds alternate while several
 have work. Within the round every active render of the kind first receives up
@@ -157,9 +156,8 @@ class RenderServer:
     def submit(self, render, arrival=None):
         """Queue a render (a workloads.render dict). Returns its ServedRender.
         Renders run at the server's precision, or at its loose precision when
-        their tolerance is loose enough (q-metric renders in DF64 where that
-        is MIXED); a q-metric disk render (the q-metric has no disk model)
-        raises ValueError here, not in a later round."""
+        their tolerance is loose enough; a q-metric disk render (the q-metric
+        has no disk model) raises ValueError here, not in a later round."""
         osr = self.osr
         prec = self.precision
         if self.loose_precision is not None and render["tol"] >= self.loose_tol:
@@ -168,7 +166,7 @@ class RenderServer:
             if render["mode"] == "disk":
                 raise ValueError("q-metric renders are shadow/lensing renders: the q-metric "
                                  "has no disk model")
-            kind = (osr.SPACETIME_QMETRIC, osr.DF64 if prec == osr.MIXED else prec)
+            kind = (osr.SPACETIME_QMETRIC, prec)
         else:
             kind = (osr.SPACETIME_KERR, prec)
         now = self.clock()

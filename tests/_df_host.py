@@ -25,6 +25,10 @@ static inline float __fadd_rn(float a, float b) { return a + b; }
 static inline float __fsub_rn(float a, float b) { return a - b; }
 static inline float __fmul_rn(float a, float b) { return a * b; }
 static inline float __fdividef(float a, float b) { return a / b; }
+static inline float osiris_host_expf(float x) { return expf(x); }
+static inline float osiris_host_logf(float x) { return logf(x); }
+#define __expf osiris_host_expf
+#define __logf osiris_host_logf
 static inline float __double2float_rn(double x) { return (float)x; }
 static inline unsigned __float_as_uint(float x) { unsigned u; std::memcpy(&u, &x, 4); return u; }
 static inline float __uint_as_float(unsigned u) { float x; std::memcpy(&x, &u, 4); return x; }

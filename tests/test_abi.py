@@ -88,9 +88,10 @@ def test_batch_plan_validation_before_any_cuda_call(osr):
     assert L.osiris_batch_plan_create(ctypes.byref(h), 70000, osr.SPACETIME_KERR,
                                       ctypes.byref(o)) == osr.EINVAL
     assert L.osiris_batch_plan_create(ctypes.byref(h), 4, 7, ctypes.byref(o)) == osr.EINVAL
-    o_mx = osr.make_opts(precision=osr.MIXED)
+    o_bad = osr.make_opts()
+    o_bad.precision = 7
     assert L.osiris_batch_plan_create(ctypes.byref(h), 4, osr.SPACETIME_QMETRIC,
-                                      ctypes.byref(o_mx)) == osr.EINVAL  # q-metric: not MIXED
+                                      ctypes.byref(o_bad)) == osr.EINVAL  # no such precision
     assert L.osiris_batch_plan_create(ctypes.byref(h), 4, osr.SPACETIME_KERR,
                                       ctypes.byref(osr.make_opts(tol=0.0))) == osr.EINVAL
     assert L.osiris_batch_plan_create(ctypes.byref(h), 4, osr.SPACETIME_KERR,

@@ -2,9 +2,8 @@
 
 Four render kinds (a Kerr shadow with its checkerboard, the Schwarzschild
 thin disk, a Kerr disk from the ISCO, and a q-metric shadow) are traced in
-FP64, DF64 and MIXED precision (the q-metric in FP64 and DF64 only: it has no
-MIXED kernel). The reference is the oracle at tol 1e-10 in every case, so the
-rows at tol 1e-8 and 1e-7 (MIXED, where FP32 stage evaluations are usable,
+FP64, DF64 and MIXED precision. The reference is the oracle at tol 1e-10 in
+every case, so the rows at tol 1e-8 and 1e-7 (MIXED, where FP32 stage evaluations are usable,
 and the served DF64 form at the served stream's looser tolerance) include
 their tolerance error as well as their precision error; the FP64 row at
 tol 1e-8 shows the tolerance error alone.
@@ -63,8 +62,6 @@ def test_error_of_every_output(mode):
     precision, tol, strict = MODES[mode]
     rows = []
     for name, rd in RENDERS.items():
-        if rd.get("q") is not None and precision == osr.MIXED:
-            continue
         ref = _reference(name)
         rep = compare(rd, gpu_render(dict(rd, tol=tol), precision=precision), ref,
                       precision=precision if strict else osr.MIXED)

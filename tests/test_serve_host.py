@@ -161,12 +161,12 @@ def test_kerr_and_qmetric_rounds():
     assert all(kinds[i] != kinds[i + 1] for i in range(both_left))
 
 
-def test_mixed_server_runs_qmetric_in_df64():
+def test_mixed_server_runs_both_spacetimes_in_mixed():
     import paper_2202_00086_gb300 as osr
     srv, be = _server(precision=osr.MIXED)
     r = srv.submit(workloads.render(0.0, 1000.0, 60.0, (-8, 8, -8, 8), 16, 16, q=0.3))
     k = srv.submit(workloads.render(0.5, 1000.0, 60.0, (-8, 8, -8, 8), 16, 16))
-    assert r.kind == (osr.SPACETIME_QMETRIC, osr.DF64)
+    assert r.kind == (osr.SPACETIME_QMETRIC, osr.MIXED)
     assert k.kind == (osr.SPACETIME_KERR, osr.MIXED)
 
 
@@ -181,7 +181,7 @@ def test_loose_tolerance_renders_take_the_loose_precision():
                         tol=1e-8))
     assert tight.kind == (osr.SPACETIME_KERR, osr.DF64)
     assert loose.kind == looser.kind == (osr.SPACETIME_KERR, osr.MIXED)
-    assert q.kind == (osr.SPACETIME_QMETRIC, osr.DF64)
+    assert q.kind == (osr.SPACETIME_QMETRIC, osr.MIXED)
     while not srv.idle():
         srv.step()
     for r in (tight, loose, looser, q):
