@@ -169,3 +169,51 @@ def test_qmetric_light_ring_on_gpu(q, precision):
     assert abs(got["r"][0] - r) < 1e-8
     assert got["phi"][0] > 1.0  # it went round
     assert got["max_abs_H"][0] < 1e-12
+
+
+@pytest.mark.parametrize("q", [None, 0.5])
+def test_mixed_timelike_particles(q):
+    """Unit-mass particles (H = -1/2) in MIXED at tol 1e-8, Kerr a = 0.9 or the
+    q-metric, launched outwards from r = 30 with the bench's recipe: the same
+    fates as the oracle at 1e-10 and escape points within 1e-5; the end-point
+    |H + 1/2| comes from the double-float equations."""
+    rng = np.random.default_rng(31)
+    n = 64
+    a = 0.0 if q is not None else 0.9
+    E = np.full(n, 1.2)
+    L = rng.uniform(-4.0, 4.0, n)
+    # the q-metric particles start on the equator, where _line_element holds
+    th = rng.uniform(0.3, math.pi - 0.3, n) if q is None else np.full(n, math.pi / 2)
+    r0 = 30.0
+    st = np.zeros((n, 6))
+    st[:, 1], st[:, 2] = r0, th
+    for i in range(n):  # outward p_r on the mass shell H = -1/2, p_theta = 0
+        if q is None:
+            s2 = math.sin(th[i]) ** 2
+            sig = r0 * r0 + a * a * (1 - s2)
+            dlt = r0 * r0 - 2 * r0 + a * a
+            A = (r0 * r0 + a * a) ** 2 - a * a * dlt * s2
+            gtt, gtp = -A / (sig * dlt), -2 * a * r0 / (sig * dlt)
+            gpp = (dlt - a * a * s2) / (sig * dlt * s2)
+            grr = dlt / sig
+            rest = gtt * E[i] ** 2 - 2 * gtp * E[i] * L[i] + gpp * L[i] ** 2 + 1.0
+        else:
+            g = _line_element(q, r0)
+            grr = 1.0 / g[1]
+            rest = E[i] ** 2 / g[0] + L[i] ** 2 / (g[2] * math.sin(th[i]) ** 2) + 1.0
+        st[i, 4] = math.sqrt(max(0.0, -rest / grr))
+    kw = dict(q=q) if q is not None else {}
+    dev = [torch.tensor(x, device="cuda") for x in (st, E, L)]
+    out = osr.trace_states(a, 100.0, *dev, mass2=1.0, tol=1e-8, precision=osr.MIXED, **kw)
+    torch.cuda.synchronize()
+    okw = dict(spacetime=oracle.QMETRIC, q=q) if q is not None else {}
+    ref = oracle.trace_states(a, 100.0, st, E, L, mass2=1.0, **okw)
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    assert got["status"].tolist() == ref["status"].tolist()
+    esc = ref["status"] == oracle.STATUS_ESCAPED
+    assert esc.sum() > n // 2
+    for key in ("r", "theta", "phi"):
+        err = np.abs(got[key][esc] - ref[key][esc])
+        assert np.all(err <= 1e-5 * np.maximum(1.0, np.abs(ref[key][esc]))), (key, err.max())
+    assert np.all(got["max_abs_H"][esc] < 1e-5)
+
