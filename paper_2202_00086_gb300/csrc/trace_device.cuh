@@ -90,10 +90,12 @@ struct RayK {
 // ---------------------------------------------------------------------------
 // FP64 sine/cosine and reciprocal with few FP64-pipe instructions.
 //
-// GB300 issues about one FP64 warp instruction per 19 SM cycles, while its
-// FP32, integer and shared-memory pipes are nearly idle in this kernel; the
-// two helpers below move the argument reduction, table look-up and seeds onto
-// those pipes and keep only the accuracy-critical FP64 arithmetic.
+// GB300's FP64 pipe takes one warp instruction per 16 SM cycles (a fused
+// multiply-add; a separate multiply or add takes 19), while its FP32, integer
+// and shared-memory pipes are nearly idle in this kernel; the helpers below
+// move the argument reduction, table look-up, seeds and the small sine/cosine
+// corrections onto those pipes and keep only the accuracy-critical FP64
+// arithmetic.
 //
 // sincos_tab: theta = N_k + x, where the node N_k is the double nearest to
 // k pi/512 (the node index found in FP32), so that x = theta - N_k is exact
