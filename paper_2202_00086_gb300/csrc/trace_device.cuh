@@ -21,6 +21,7 @@
 
 #include <cstdint>
 
+#include "convert.cuh"
 #include "df64.cuh"
 #include "explog.cuh"
 #include "osiris_internal.h"
@@ -161,17 +162,6 @@ __device__ __forceinline__ void explog_table_init() {
   __syncthreads();
 }
 
-// x as FP32, significand truncated with integer operations only (relative
-// error < 2^-23); zero below the FP32 normal range, +-inf above it.
-__device__ __forceinline__ float to_float_rz(double x) {
-  const long long b = __double_as_longlong(x);
-  const int hi = (int)(b >> 32);
-  const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;
-  const int sign = hi & (int)0x80000000;
-  if (e <= 0) return __int_as_float(sign);
-  if (e >= 255) return __int_as_float(sign | 0x7f800000);
-  return __int_as_float(sign | (e << 23) | (int)((b >> 29) & 0x7fffff));
-}
 
 
 // a b and a + c issued as fused multiply-adds: fma(a, b, -0) = a b and
@@ -207,37 +197,8 @@ __device__ __forceinline__ double add_as_fma(double a, double c) {
 __device__ __forceinline__ float mul_as_fma(float a, float b) { return a * b; }
 __device__ __forceinline__ float add_as_fma(float a, float c) { return a + c; }
 
-// A normal FP32 value as a double, by integer operations only.
-__device__ __forceinline__ double float_to_double(float f) {
-  const unsigned b = __float_as_uint(f);
-  const long long e = (long long)((b >> 23) & 0xff) - 127 + 1023;
-  return __longlong_as_double((long long)(b & 0x80000000u) << 32 | e << 52 |
-                              (long long)(b & 0x7fffffu) << 29);
-}
 
-// An FP32 value as a double, by integer operations only: zero (and FP32
-// denormals, below 1.2e-38) give zero.
-__device__ __forceinline__ double float_to_double0(float f) {
-  return (__float_as_uint(f) & 0x7f800000u) ? float_to_double(f) : 0.0;
-}
 
-// x (|x| < 2^-8) as a double-float pair by integer operations only: hi is x
-// truncated to 24 significant bits, lo the 29 bits below them truncated to
-// 24, so hi + lo = x to 2^-46 |x|; lo is zero below 2^-74.
-__device__ __forceinline__ df split_small(double x) {
-  const long long b = __double_as_longlong(x);
-  const float hi = to_float_rz(x);
-  const long long m = b & ((1LL << 29) - 1);  // the significand bits below hi's
-  const int e = (int)((b >> 52) & 0x7ff);     // biased exponent of x
-  const int lead = 63 - __clzll(m | 1);       // leading bit of m (m = 0: no bits, see below)
-  const int fe = lead + e - 1075 + 127;        // FP32 biased exponent of the leading bit
-  const unsigned frac = (unsigned)((lead >= 23) ? (m >> (lead - 23)) : (m << (23 - lead)));
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  const float lo = (m != 0 && fe > 0) ? __uint_as_float(sign | ((unsigned)fe << 23) |
-                                                         (frac & 0x7fffffu))
-                                      : 0.0f;
-  return mk(hi, lo);
-}
 
 __device__ __forceinline__ void sincos_tab(double th, double& s, double& c) {
   using namespace dfc;
@@ -254,7 +215,7 @@ __device__ __forceinline__ void sincos_tab(double th, double& s, double& c) {
   const float4 scf = t.scf[idx];
   const double x = th - t.n[idx];  // exact
   // the corrections in double-float
-  const df xd = split_small(x);
+  const df xd = split_df(x);
   const df u = df_sqr(xd);                                                    // x^2
   const df q = df_add_f_u(mk(-I3H, -I3L), __fmul_rn(u.hi, 1.0f / 120.0f));    // -1/6 + x^2/120
   const df ds = df_mul(df_mul(xd, u), q);                                     // sin x - x
