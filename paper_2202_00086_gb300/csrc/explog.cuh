@@ -20,10 +20,15 @@
 // device code copies them into shared memory once per block. Arguments
 // outside the reduced forms' range
 // (exp: |y| >= 700 or NaN; log: x outside [2^-1000, 2^1000] or NaN) go to the
-// library functions. Both stay within 2 ulp of the exact value (measured
-// worst cases 1.3 ulp for exp, 1.6 ulp for log, where log(F/2) and log1p(u)
-// partly cancel). The functions also compile as host C++, which is how that
-// bound is tested, against mpmath and libm.
+// library functions. The higher-order parts of the two series,
+// exp(r) - 1 - r (< 1.5e-5) and log1p(u) - u (< 7.7e-6), are small against
+// the results, so they are formed in double-float on the FP32 pipe
+// (convert.cuh, df64.cuh; their own leading terms in two words) and added to
+// r or u in FP64: 7 FP64 instructions for exp and 8 for log instead of 10 and
+// 13. Both stay within 2 ulp of the
+// exact value (measured worst cases are in tests/test_explog_host.py, where
+// log(F/2) and log1p(u) partly cancel). The functions also compile as host
+// C++, which is how that bound is tested, against mpmath and libm.
 #pragma once
 
 #include <cmath>
@@ -36,6 +41,8 @@
 #define __device__
 #define __forceinline__ inline
 #endif
+
+#include "convert.cuh"
 
 namespace osiris_explog {
 
@@ -93,22 +100,31 @@ constexpr double kLn2Lo = 0x1.abc9e3b39803fp-56;
 constexpr double kShift = 0x1.8p52;
 constexpr long long kShiftBits = 0x4338000000000000LL;
 
-__host__ __device__ __forceinline__ double exp_tab(double y, const double* t2) {
+// 1/3 as a float pair, for the log1p series
+constexpr float kThirdH = 0.3333333432674408f, kThirdL = -9.934107758624577e-09f;
+
+__device__ __forceinline__ double exp_tab(double y, const double* t2) {
+  using namespace osiris_impl;
   if (!(fabs(y) < 700.0)) return exp(y);
   const double t = fma(y, kInvL, kShift);
   const int n = (int)(to_bits(t) & 0xffffffffLL);  // y * 64/ln2 rounded, mod 2^32
   const double nd = t - kShift;
   const double r = fma(-nd, kL2, fma(-nd, kL1, y));
-  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-  q = fma(q, r, 1.0 / 6.0);
-  q = fma(q, r, 0.5);
-  const double p = fma(r * r, q, r);
+  // exp(r) - 1 = r + c, c = r^2 (1/2 + r/6 + r^2/24 + r^3/120), in double-float:
+  // the r/6 term as a product with 1/6 in two words, the rest in FP32
+  const df rd = split_df(r);
+  const float rf = rd.hi;
+  const float small = __fmul_rn(__fmul_rn(rf, rf), fmaf(rf, 1.0f / 120.0f, 1.0f / 24.0f));
+  const df q = df_add_f_u(df_add_f_u(df_mul(rd, mk(dfc::I3H, dfc::I3L)), small), 0.5f);
+  const df c = df_mul(df_sqr(rd), q);
+  const double p = (r + float_to_double0(c.hi)) + float_to_double0(c.lo);
   const double T = t2[n & (kExpN - 1)];
   const double e = fma(T, p, T);  // in [0.99, 2.02): scaling by 2^m stays normal
   return from_bits(to_bits(e) + (long long)(n >> 6) * (1LL << 52));
 }
 
-__host__ __device__ __forceinline__ double log_tab(double x, const LogEntry* lg) {
+__device__ __forceinline__ double log_tab(double x, const LogEntry* lg) {
+  using namespace osiris_impl;
   if (!(x >= 0x1p-1000 && x <= 0x1p+1000)) return log(x);
   const long long b = to_bits(x);
   const int hi = (int)(b >> 32);
@@ -117,12 +133,19 @@ __host__ __device__ __forceinline__ double log_tab(double x, const LogEntry* lg)
   const double F = from_bits(0x3ff0000000000000LL + ((long long)j << 45));
   const LogEntry E = lg[j];
   const double u = (m - F) * E.rcpF;  // m - F is exact
-  double q = fma(u, 1.0 / 7.0, -1.0 / 6.0);
-  q = fma(q, u, 1.0 / 5.0);
-  q = fma(q, u, -0.25);
-  q = fma(q, u, 1.0 / 3.0);
-  q = fma(q, u, -0.5);
-  const double l1p = fma(u * u, q, u);
+  // log1p(u) = u + c, c = u^2 (-1/2 + u/3 - u^2/4 + u^3/5 - u^4/6 + u^5/7), in
+  // double-float. The result is ~u, so c needs ~2^-53 / |u| relative accuracy:
+  // the u/3 and u^2/4 terms in two words, from u^3 on in FP32.
+  const df ud = split_df(u);
+  const float uf = ud.hi;
+  const df usq = df_sqr(ud);
+  const float small = __fmul_rn(__fmul_rn(uf, __fmul_rn(uf, uf)),
+                                fmaf(uf, fmaf(uf, 1.0f / 7.0f, -1.0f / 6.0f), 1.0f / 5.0f));
+  const df q = df_add_f_u(
+      df_add_f_u(df_add_u(df_mul(ud, mk(kThirdH, kThirdL)), df_scale(usq, -0.25f)), small),
+      -0.5f);
+  const df c = df_mul(usq, q);
+  const double l1p = (u + float_to_double0(c.hi)) + float_to_double0(c.lo);
   const int k = (hi >> 20) - 1023 + (j >= kLogHalf ? 1 : 0);
   const double kd = from_bits(kShiftBits + k) - kShift;
   return fma(kd, kLn2Hi, E.logF) + fma(kd, kLn2Lo, l1p);
