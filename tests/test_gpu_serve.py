@@ -39,25 +39,31 @@ def _alone(rd, precision, phase):
     return {k: v.cpu().numpy() for k, v in out.items()}
 
 
-@pytest.mark.parametrize("precision,overlap", [(osr.DF64, True), (osr.FP64, True),
-                                               (osr.DF64, False)])
-def test_alone_equals_in_the_mix(precision, overlap):
+@pytest.mark.parametrize("precision,overlap,loose", [(osr.DF64, True, None),
+                                                     (osr.FP64, True, None),
+                                                     (osr.DF64, False, None),
+                                                     (osr.DF64, True, osr.MIXED)])
+def test_alone_equals_in_the_mix(precision, overlap, loose):
     """Rounds on per-slot streams (overlap: the next round's blocks start in
-    the current round's tail) or all on one stream."""
+    the current round's tail) or all on one stream; with a loose precision,
+    the renders at tol 1e-8 run in MIXED, the others at the server's."""
     phase = workloads.checker_phase_deg(2202)
     arrivals = _stream()
     srv = serve.RenderServer(precision=precision, round_rays=3000, min_chunk=500,
                              keep_outputs=True, cell_phase_deg=phase, max_inflight=2,
-                             overlap=overlap)
+                             overlap=overlap, loose_precision=loose, loose_tol=1e-8)
     summary = srv.run(arrivals, realtime=True)
     torch.cuda.synchronize()
     assert summary["renders"] == len(arrivals)
     assert srv.rounds > 3
     assert max(srv.round_entries) > 1  # renders shared launches
     by_id = {r.rid: r for r in srv.done}
+    if loose is not None:
+        assert {r.kind[1] for r in srv.done} == {precision, loose}
     for rid, (_, rd) in enumerate(arrivals):
         got = {k: v.cpu().numpy() for k, v in by_id[rid].out.items()}
-        ref = _alone(rd, precision, phase)
+        ref = _alone(rd, loose if loose is not None and rd["tol"] >= 1e-8 else precision,
+                     phase)
         for k in ref:
             assert np.array_equal(got[k], ref[k]), (rid, k)
     assert summary["p99_latency_s"] >= summary["p50_latency_s"] > 0
