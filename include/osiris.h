@@ -314,8 +314,7 @@ void osiris_batch_plan_destroy(osiris_batch_plan* plan);
  *   - n_requests must be in [1, OSIRIS_STATIC_MAX_REQUESTS]; more returns
  *     OSIRIS_EINVAL before anything is launched.
  *   - The first call on a device looks up the device address of the array
- *     (once per device, with that device current); make that first call
- *     before any stream capture begins.
+ *     (once per device, with that device current).
  *   - All calls share the one array, which keeps the last call's contents;
  *     each call resets the queue counter and rewrites the request table on
  *     its stream. Calls whose work may overlap on the GPU (different streams
