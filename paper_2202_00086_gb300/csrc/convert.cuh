@@ -86,30 +86,4 @@ __device__ __forceinline__ df split_df(double x) {
   return mk(hi, lo);
 }
 
-// hi + lo (any two floats) as a double, by integer operations only: both
-// significands on a common 64-bit fixed point, summed, renormalised and
-// truncated to 53 bits (relative error below 2^-52 of the sum). Zero words
-// (and FP32 denormals) count as zero. Used where the sum is a small
-// correction added to an FP64 value, so its own truncation does not show.
-__device__ __forceinline__ double df_to_double(float hi, float lo) {
-  const unsigned bh = __float_as_uint(hi), bl = __float_as_uint(lo);
-  const int eh = (int)((bh >> 23) & 0xff), el = (int)((bl >> 23) & 0xff);
-  if (el == 0) return float_to_double0(hi);
-  if (eh == 0) return float_to_double0(lo);
-  // the word with the larger exponent leads; its significand's top bit sits at bit 61
-  const bool swap = el > eh;
-  const unsigned ba = swap ? bl : bh, bb = swap ? bh : bl;
-  const int ea = swap ? el : eh, d = swap ? el - eh : eh - el;
-  const long long ma = (long long)((ba & 0x7fffffu) | 0x800000u) << 38;
-  const long long mb = d < 62 ? ((long long)((bb & 0x7fffffu) | 0x800000u) << 38) >> d : 0;
-  const long long sum = ((ba >> 31) ? -ma : ma) + ((bb >> 31) ? -mb : mb);
-  if (sum == 0) return 0.0;
-  const unsigned long long mag = (unsigned long long)(sum < 0 ? -sum : sum);
-  const int lz = clz64((long long)mag);  // 2 when no bit was gained or lost
-  const unsigned long long norm = mag << lz;
-  const long long e = (long long)(ea + 2 - lz) - 127 + 1023;
-  return double_of((sum < 0 ? (1LL << 63) : 0LL) | (e << 52) |
-                   (long long)((norm >> 11) & ((1ULL << 52) - 1)));
-}
-
 }  // namespace osiris_impl

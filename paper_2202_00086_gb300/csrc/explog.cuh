@@ -23,9 +23,9 @@
 // library functions. The higher-order parts of the two series,
 // exp(r) - 1 - r (< 1.5e-5) and log1p(u) - u (< 7.7e-6), are small against
 // the results, so they are formed in double-float on the FP32 pipe
-// (convert.cuh, df64.cuh; their own leading terms in two words), turned into
-// one double by integer operations and added to r or u in FP64: 6 FP64
-// instructions for exp and 7 for log instead of 10 and 13. Both stay within 2 ulp of the
+// (convert.cuh, df64.cuh; their own leading terms in two words) and added to
+// r or u in FP64: 7 FP64 instructions for exp and 8 for log instead of 10 and
+// 13. Both stay within 2 ulp of the
 // exact value (measured worst cases are in tests/test_explog_host.py, where
 // log(F/2) and log1p(u) partly cancel). The functions also compile as host
 // C++, which is how that bound is tested, against mpmath and libm.
@@ -117,7 +117,7 @@ __device__ __forceinline__ double exp_tab(double y, const double* t2) {
   const float small = __fmul_rn(__fmul_rn(rf, rf), fmaf(rf, 1.0f / 120.0f, 1.0f / 24.0f));
   const df q = df_add_f_u(df_add_f_u(df_mul(rd, mk(dfc::I3H, dfc::I3L)), small), 0.5f);
   const df c = df_mul(df_sqr(rd), q);
-  const double p = r + df_to_double(c.hi, c.lo);
+  const double p = (r + float_to_double0(c.hi)) + float_to_double0(c.lo);
   const double T = t2[n & (kExpN - 1)];
   const double e = fma(T, p, T);  // in [0.99, 2.02): scaling by 2^m stays normal
   return from_bits(to_bits(e) + (long long)(n >> 6) * (1LL << 52));
@@ -145,7 +145,7 @@ __device__ __forceinline__ double log_tab(double x, const LogEntry* lg) {
       df_add_f_u(df_add_u(df_mul(ud, mk(kThirdH, kThirdL)), df_scale(usq, -0.25f)), small),
       -0.5f);
   const df c = df_mul(usq, q);
-  const double l1p = u + df_to_double(c.hi, c.lo);
+  const double l1p = (u + float_to_double0(c.hi)) + float_to_double0(c.lo);
   const int k = (hi >> 20) - 1023 + (j >= kLogHalf ? 1 : 0);
   const double kd = from_bits(kShiftBits + k) - kShift;
   return fma(kd, kLn2Hi, E.logF) + fma(kd, kLn2Lo, l1p);

@@ -109,10 +109,9 @@ struct RayK {
 //   cos theta = (C_k - S_k x) + [C_k (cos x - 1) - S_k (sin x - x)].
 // The bracketed corrections are at most 5e-6 of the result and need only
 // ~1e-11 relative accuracy, so they are formed in double-float on the FP32
-// pipe from x split into two floats by integer operations, and turned into
-// one double by integer operations; the FP64 pipe does x itself, the
-// correction added to S_k and the fused multiply-add with C_k x: 5 FP64
-// instructions for both results, each within ~1 ulp. The table covers theta
+// pipe from x split into two floats by integer operations; the FP64 pipe does
+// x itself, C_k x added to S_k and the correction's two words added on: 7 FP64
+// instructions for both results, each within ~1.5 ulp. The table covers theta
 // in [-pi/16, 17 pi/16], which holds every ray except one passing almost
 // exactly over a pole; outside it the library sincos is used.
 // ---------------------------------------------------------------------------
@@ -225,8 +224,8 @@ __device__ __forceinline__ void sincos_tab(double th, double& s, double& c) {
   const df S = mk(scf.x, scf.y), C = mk(scf.z, scf.w);
   const df corr_s = df_add_u(df_mul(C, ds), df_mul(S, cm));
   const df corr_c = df_sub_u(df_mul(C, cm), df_mul(S, ds));
-  s = fma(sc.y, x, sc.x + df_to_double(corr_s.hi, corr_s.lo));
-  c = fma(-sc.x, x, sc.y + df_to_double(corr_c.hi, corr_c.lo));
+  s = fma(sc.y, x, sc.x + float_to_double0(corr_s.hi)) + float_to_double0(corr_s.lo);
+  c = fma(-sc.x, x, sc.y + float_to_double0(corr_c.hi)) + float_to_double0(corr_c.lo);
 }
 
 // max |H - H0| kept as the bit pattern of a non-negative double: |v| and the
