@@ -116,7 +116,8 @@ typedef struct {
                               launch gives each thread this many consecutive
                               pixels; a persistent grid claims this many per
                               idle lane with each queue atomic */
-    int32_t refill_lanes;  /* persistent grid, 0..32 (0 = library default, 4): a
+    int32_t refill_lanes;  /* persistent grid, 0..32 (0 = library default: 4,
+                              32 in OSIRIS_MIXED): a
                               warp whose other lanes are still integrating
                               refills its idle lanes only once at least this
                               many are idle (a warp with no busy lane always

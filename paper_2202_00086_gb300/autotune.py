@@ -21,8 +21,9 @@ DEFAULT_CACHE = os.path.join(_HERE, "_build", "autotune.json")
 BLOCKS = (64, 96, 128, 192, 256)
 PER_SM = (0, 1, 2, 3, 4)  # 0 = the occupancy limit
 RAYS_PER_LANE = (1, 2, 4)
-REFILL_LANES = (1, 2, 4, 8, 16)
-DEFAULT_GRANULARITY = (0, 0)  # the library's default (one ray per lane, refill at 4 idle lanes)
+REFILL_LANES = (1, 2, 4, 8, 16, 32)
+DEFAULT_GRANULARITY = (0, 0)  # the library's default (one ray per lane; refill at 4 idle
+#                               lanes, 32 in MIXED)
 KEYS = ("block_size", "blocks_per_sm", "rays_per_lane", "refill_lanes")
 
 

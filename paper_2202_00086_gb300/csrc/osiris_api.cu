@@ -172,15 +172,23 @@ int persistent_shape(const osiris_trace_opts* o, int spacetime, int* block,
 }
 
 // Work-distribution knobs of a launch (0 in the options = the library
-// default: one ray per lane; refill once 4 lanes of a busy warp are idle).
-// Measured on the 12 x 1024^2 Kerr set: refill granularity 1 / 4 / 8 gave
-// 16.2 / 18.5 / 18.1 Mrays/s in DF64 and 3.59 / 3.61 / 3.50 in FP64.
+// default: one ray per lane; refill once 4 lanes of a busy warp are idle, or
+// in MIXED once all 32 are). Measured on the 12 x 1024^2 Kerr set, refill
+// granularity 1 / 4 / 8 / 16 / 32: DF64 16.2 / 18.5-19.0 / 18.1 / 18.5 / 18.9
+// Mrays/s, FP64 3.59 / 3.79 / 3.69 / 3.70 / 3.75; MIXED at tol 1e-8 49.0 /
+// 65.3 / 65.5 / 67.5 / 70.2. A MIXED ray takes about half the attempts of a
+// DF64 ray at tol 1e-10, so its start and end (FP64 work, one warp instruction
+// however many lanes share it) weigh more, and starting a warp's rays together
+// also keeps neighbouring pixels in one warp.
 constexpr int kDefaultRaysPerLane = 1;
 constexpr int kDefaultRefillLanes = 4;
+constexpr int kDefaultRefillLanesMixed = 32;
 
 void set_granularity(KernelArgs& args, const osiris_trace_opts* o) {
   args.rays_per_lane = o->rays_per_lane > 0 ? o->rays_per_lane : kDefaultRaysPerLane;
-  args.refill_lanes = o->refill_lanes > 0 ? o->refill_lanes : kDefaultRefillLanes;
+  args.refill_lanes = o->refill_lanes > 0 ? o->refill_lanes
+                      : o->precision == OSIRIS_MIXED ? kDefaultRefillLanesMixed
+                                                     : kDefaultRefillLanes;
 }
 
 // Launch the trace kernel for the requests in args (args.reqs / single).

@@ -35,7 +35,7 @@ def test_autotune_small_sample(tmp_path):
         assert np.array_equal(a[k], b[k]), k
 
 
-@pytest.mark.parametrize("precision", [osr.FP64, osr.DF64])
+@pytest.mark.parametrize("precision", [osr.FP64, osr.DF64, osr.MIXED])
 def test_granularity_does_not_change_outputs(precision):
     """37x29 render (ragged against every block and claim size): plain
     launches with 1, 3 and 8 rays per thread and persistent launches with
