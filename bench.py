@@ -60,9 +60,9 @@ FP64_TRAFFIC_BYTES_PER_LAUNCH = 575.78e6
 DF64_FP32_INST_PER_ATTEMPT = 3739
 # The same for the MIXED kernel (FP32 evaluations in the double-float stepper)
 # at tol 1e-8: ncu capture of trace_mixed_persistent on the 12 renders at
-# 256x256 (8.3947e9 FMA-pipe warp instructions x 26.41 active lanes over
+# 256x256 (8.7459e9 FMA-pipe warp instructions x 26.18 active lanes over
 # 1.4603e8 attempts), profiles/trace_mixed_persistent_kerr12x256_ncu.md.
-MIXED_FP32_INST_PER_ATTEMPT = 1518
+MIXED_FP32_INST_PER_ATTEMPT = 1568
 
 
 # Workloads: the headline Kerr set (default) and the measured "next" rows,
