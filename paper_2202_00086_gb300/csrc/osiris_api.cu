@@ -129,7 +129,8 @@ int apply_range(ReqDev& R, const osiris_request& q) {
 int cuda_rc(int e) { return e == 0 ? OSIRIS_OK : OSIRIS_ECUDA; }
 
 // The q-metric runs in FP64 or DF64, without a disk.
-int check_spacetime(int spacetime, int disk, const osiris_trace_opts* o) {
+// Every precision traces both space-times; the q-metric has no disk model.
+int check_spacetime(int spacetime, int disk) {
   if (spacetime == OSIRIS_SPACETIME_KERR) return OSIRIS_OK;
   if (spacetime != OSIRIS_SPACETIME_QMETRIC) return OSIRIS_EINVAL;
   if (disk) return OSIRIS_EINVAL;  // the q-metric has no disk model
@@ -234,7 +235,7 @@ int build_table(const osiris_request* reqs, int32_t n, const osiris_trace_opts* 
     if (q.disk < OSIRIS_DISK_NONE || q.disk > OSIRIS_DISK_CONSTANT_L || !is_fin(q.l0))
       return OSIRIS_EINVAL;
     if (q.camera->spacetime != reqs[0].camera->spacetime) return OSIRIS_EINVAL;
-    if (int rc = check_spacetime(q.camera->spacetime, q.disk, o)) return rc;
+    if (int rc = check_spacetime(q.camera->spacetime, q.disk)) return rc;
     const double r_esc = o->r_esc_factor * q.camera->r0;
     if (q.disk)
       if (int rc = check_disk(q.camera->a, o->r_cap_factor, r_esc, q.r_in, q.r_out)) return rc;
@@ -259,7 +260,7 @@ int run_camera(const osiris_camera* cam, int disk, double r_in, double r_out, do
   if (disk)
     if (int rc = check_disk(cam->a, o->r_cap_factor, r_esc, r_in, r_out)) return rc;
   if (!is_fin(l0)) return OSIRIS_EINVAL;
-  if (int rc = check_spacetime(cam->spacetime, disk, o)) return rc;
+  if (int rc = check_spacetime(cam->spacetime, disk)) return rc;
   KernelArgs args;
   std::memset(&args, 0, sizeof(args));
   ReqDev& R = args.single;
@@ -448,7 +449,7 @@ int osiris_trace_states_ex(int32_t spacetime, double param, double r_obs, double
     return OSIRIS_EINVAL;
   }
   if (int rc = check_opts(o)) return rc;
-  if (int rc = check_spacetime(spacetime, disk, o)) return rc;
+  if (int rc = check_spacetime(spacetime, disk)) return rc;
   if (disk)
     if (int rc = check_disk(a, o->r_cap_factor, o->r_esc_factor * r_obs, r_in, r_out)) return rc;
   KernelArgs args;
@@ -731,7 +732,7 @@ int osiris_batch_plan_create(osiris_batch_plan** out, int32_t max_requests, int3
   if (!out || !opts || max_requests < 1 || max_requests > 65536) return OSIRIS_EINVAL;
   *out = nullptr;
   if (int rc = check_opts(opts)) return rc;
-  if (int rc = check_spacetime(spacetime, OSIRIS_DISK_NONE, opts)) return rc;
+  if (int rc = check_spacetime(spacetime, OSIRIS_DISK_NONE)) return rc;
   if (!opts->workspace || opts->workspace_bytes < osiris_workspace_bytes(max_requests))
     return OSIRIS_ENOMEM;
   osiris_batch_plan* p = new (std::nothrow) osiris_batch_plan;
