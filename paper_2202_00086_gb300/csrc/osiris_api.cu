@@ -128,12 +128,11 @@ int apply_range(ReqDev& R, const osiris_request& q) {
 
 int cuda_rc(int e) { return e == 0 ? OSIRIS_OK : OSIRIS_ECUDA; }
 
-// The q-metric runs in FP64 or DF64, without a disk.
 // Every precision traces both space-times; the q-metric has no disk model.
 int check_spacetime(int spacetime, int disk) {
   if (spacetime == OSIRIS_SPACETIME_KERR) return OSIRIS_OK;
   if (spacetime != OSIRIS_SPACETIME_QMETRIC) return OSIRIS_EINVAL;
-  if (disk) return OSIRIS_EINVAL;  // the q-metric has no disk model
+  if (disk) return OSIRIS_EINVAL;
   return OSIRIS_OK;
 }
 
