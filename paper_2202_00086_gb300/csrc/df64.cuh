@@ -77,6 +77,15 @@ __device__ __forceinline__ df df_add_u(df a, df b) {
 
 __device__ __forceinline__ df df_sub_u(df a, df b) { return df_add_u(a, df_neg(b)); }
 
+// df_add_u for operands whose order of magnitude is known, |a.hi| >= |b.hi|:
+// Dekker's FastTwoSum of the leading words is then exact too, at half the
+// instructions and dependency depth of TwoSum.
+__device__ __forceinline__ df df_add_ord_u(df a, df b) {
+  df s = fast_two_sum(a.hi, b.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return s;
+}
+
 __device__ __forceinline__ df df_norm(df a) { return fast_two_sum(a.hi, a.lo); }
 
 __device__ __forceinline__ df df_add_f(df a, float b) {
@@ -88,6 +97,20 @@ __device__ __forceinline__ df df_add_f(df a, float b) {
 // df_add_f without the final renormalisation (see df_add_u).
 __device__ __forceinline__ df df_add_f_u(df a, float b) {
   df s = two_sum(a.hi, b);
+  s.lo = __fadd_rn(s.lo, a.lo);
+  return s;
+}
+
+// df_add_f_u for |a.hi| >= |b| (FastTwoSum, see df_add_ord_u).
+__device__ __forceinline__ df df_add_f_ord_u(df a, float b) {
+  df s = fast_two_sum(a.hi, b);
+  s.lo = __fadd_rn(s.lo, a.lo);
+  return s;
+}
+
+// b + a for a float b with |b| >= |a.hi| (FastTwoSum, see df_add_ord_u).
+__device__ __forceinline__ df df_add_to_f_u(float b, df a) {
+  df s = fast_two_sum(b, a.hi);
   s.lo = __fadd_rn(s.lo, a.lo);
   return s;
 }
@@ -174,23 +197,25 @@ __device__ __forceinline__ void df_sincos(df x, df& s, df& c) {
   t.lo = __fadd_rn(t.lo, fmaf(-k, P3, b.lo));
   t = fast_two_sum(t.hi, t.lo);
   // The series steps and the results are left unrenormalised: their only
-  // consumers are products and further sums.
+  // consumers are products and further sums. With u = t^2 <= (pi/4)^2 < 0.62
+  // every step adds a term smaller than the one it is added to (the largest
+  // ratio is u/2 < 0.31, in cos t = 1 + u (...)), so each takes FastTwoSum.
   const df u = df_sqr(t);
   const float uf = u.hi;
   // sin t = t (1 - u/3! + u^2/5! - ... ): inner terms in FP32
   float ps = fmaf(uf, fmaf(uf, -I15, I13), -I11);  // -1/11! + u/13! - u^2/15!
-  df qs = df_add_f_u(mk(I9H, I9L), __fmul_rn(uf, ps));          // 1/9! - u/11! + ...
-  qs = df_add_u(mk(-I7H, -I7L), df_mul(u, qs));
-  qs = df_add_u(mk(I5H, I5L), df_mul(u, qs));
-  qs = df_add_u(mk(-I3H, -I3L), df_mul(u, qs));
-  const df st = df_add_u(t, df_mul(df_mul(t, u), qs));
+  df qs = df_add_f_ord_u(mk(I9H, I9L), __fmul_rn(uf, ps));      // 1/9! - u/11! + ...
+  qs = df_add_ord_u(mk(-I7H, -I7L), df_mul(u, qs));
+  qs = df_add_ord_u(mk(I5H, I5L), df_mul(u, qs));
+  qs = df_add_ord_u(mk(-I3H, -I3L), df_mul(u, qs));
+  const df st = df_add_ord_u(t, df_mul(df_mul(t, u), qs));
   // cos t = 1 - u/2 + u^2/4! - ...
   float pc = fmaf(uf, fmaf(uf, fmaf(uf, I16, -I14), I12), -I10);  // -1/10! + ...
-  df qc = df_add_f_u(mk(I8H, I8L), __fmul_rn(uf, pc));
-  qc = df_add_u(mk(-I6H, -I6L), df_mul(u, qc));
-  qc = df_add_u(mk(I4H, I4L), df_mul(u, qc));
-  qc = df_add_f_u(df_mul(u, qc), -0.5f);
-  const df ct = df_add_f_u(df_mul(u, qc), 1.0f);
+  df qc = df_add_f_ord_u(mk(I8H, I8L), __fmul_rn(uf, pc));
+  qc = df_add_ord_u(mk(-I6H, -I6L), df_mul(u, qc));
+  qc = df_add_ord_u(mk(I4H, I4L), df_mul(u, qc));
+  qc = df_add_to_f_u(-0.5f, df_mul(u, qc));
+  const df ct = df_add_to_f_u(1.0f, df_mul(u, qc));
   // quadrant
   const int q = ((int)k) & 3;
   if (q == 0) {

@@ -26,12 +26,12 @@ __device__ __forceinline__ void rhs_df(const RayDF& K, df r, df th, df pr, df pt
   // k - k1.
   df s, c;
   df_sincos(th, s, c);
-  const df ra2 = df_add_u(df_sqr(r), K.a2);  // r^2 + a^2
+  const df ra2 = df_add_ord_u(df_sqr(r), K.a2);  // r^2 + a^2 (r > 1 >= a)
   const df a2s = df_mul(K.a2, s);
   // renormalised: Delta cancels next to the horizon, and df_rcp below seeds
   // its Newton step from the leading word alone
   const df Delta = df_add(df_mul(r, df_add_f(r, -2.0f)), K.a2);
-  const df Sigma = df_sub_u(ra2, df_mul(a2s, s));  // r^2 + a^2 cos^2 (r > a: no cancellation)
+  const df Sigma = df_add_ord_u(ra2, df_neg(df_mul(a2s, s)));  // r^2 + a^2 cos^2 (r > a)
   const df P = df_sub_u(df_mul(ra2, K.E), K.aL);
   const df DS = df_mul(Delta, Sigma);
   const df inv = df_rcp(df_mul(DS, s));

@@ -149,11 +149,11 @@ __device__ __forceinline__ void rk_step_df(const typename Met::Ray& K, LaneCache
       for (int c = 0; c < 4; ++c) in[c] = y4[c];
     } else if (INTEG == OSIRIS_RKDP45 && s == NS - 1) {
       // the fifth-order solution (first same as last)
-      o.r = df_add(y.r, df_add(hk1[0], df_mul(h, sb[0])));
-      o.th = df_add(y.th, df_add(hk1[1], df_mul(h, sb[1])));
-      o.ph = df_add(y.ph, df_add(hk1[2], df_mul(h, sb[2])));
-      o.pr = df_add(y.pr, df_add(hk1[3], df_mul(h, sb[3])));
-      o.pth = df_add(y.pth, df_add(hk1[4], df_mul(h, sb[4])));
+      o.r = df_add(y.r, df_mul(h, df_add_u(k1[0], sb[0])));
+      o.th = df_add(y.th, df_mul(h, df_add_u(k1[1], sb[1])));
+      o.ph = df_add(y.ph, df_mul(h, df_add_u(k1[2], sb[2])));
+      o.pr = df_add(y.pr, df_mul(h, df_add_u(k1[3], sb[3])));
+      o.pth = df_add(y.pth, df_mul(h, df_add_u(k1[4], sb[4])));
       in[0] = o.r;
       in[1] = o.th;
       in[2] = o.pr;
@@ -222,11 +222,11 @@ __device__ __forceinline__ void rk_step_df(const typename Met::Ray& K, LaneCache
     LC.k1.pth = k1[4];
     LC.k1.twoH = twoH;
   } else {
-    o.r = df_add(y.r, df_add(hk1[0], df_mul(h, sb[0])));
-    o.th = df_add(y.th, df_add(hk1[1], df_mul(h, sb[1])));
-    o.ph = df_add(y.ph, df_add(hk1[2], df_mul(h, sb[2])));
-    o.pr = df_add(y.pr, df_add(hk1[3], df_mul(h, sb[3])));
-    o.pth = df_add(y.pth, df_add(hk1[4], df_mul(h, sb[4])));
+    o.r = df_add(y.r, df_mul(h, df_add_u(k1[0], sb[0])));
+    o.th = df_add(y.th, df_mul(h, df_add_u(k1[1], sb[1])));
+    o.ph = df_add(y.ph, df_mul(h, df_add_u(k1[2], sb[2])));
+    o.pr = df_add(y.pr, df_mul(h, df_add_u(k1[3], sb[3])));
+    o.pth = df_add(y.pth, df_mul(h, df_add_u(k1[4], sb[4])));
   }
 #pragma unroll
   for (int c = 0; c < 5; ++c) d[c] = __fmul_rn(h.hi, sd[c]);
