@@ -86,6 +86,12 @@ __device__ __forceinline__ df df_add_ord_u(df a, df b) {
   return s;
 }
 
+// df_add for |a.hi| >= |b.hi| (renormalised).
+__device__ __forceinline__ df df_add_ord(df a, df b) {
+  const df s = df_add_ord_u(a, b);
+  return fast_two_sum(s.hi, s.lo);
+}
+
 __device__ __forceinline__ df df_norm(df a) { return fast_two_sum(a.hi, a.lo); }
 
 __device__ __forceinline__ df df_add_f(df a, float b) {

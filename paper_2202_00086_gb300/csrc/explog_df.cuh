@@ -11,7 +11,7 @@
 //        terms below 2^-48 in FP32; k ln2 with ln2 split into three floats
 //        (the first of 15 bits, so k times it is exact).
 // Both stay within 4 units of 2^-48 relative of the exact value (measured
-// worst cases 1.7 for exp, 2.5 for log) for -69 < y < 80 and x in
+// worst cases 1.6 for exp, 2.4 for log) for -69 < y < 80 and x in
 // [2^-100, 2^100]. Below y = -69 the low word of the result is subnormal and
 // the relative precision falls towards 2^-35 at y = -80; for |y| >= 80, x
 // outside that range, or NaN, they return the FP32 library value. A ray
@@ -66,13 +66,15 @@ __device__ __forceinline__ df df_exp(df y) {
   const float t = fmaf(-n, L1, y.hi);
   const df nl = two_prod(n, L2);
   const df r = df_sub(two_sum(t, y.lo), mk(nl.hi, fmaf(n, L3, nl.lo)));
+  // |r| <= ln2/128: each sum below adds a term smaller than the one it is
+  // added to, so it takes FastTwoSum (df_add_ord and its variants)
   const float q4 = fmaf(r.hi, 1.0f / 120.0f, 1.0f / 24.0f);
-  df q = df_add_f_u(mk(I3H, I3L), __fmul_rn(r.hi, q4));  // 1/6 + r/24 + r^2/120
-  q = df_add_f_u(df_mul(r, q), 0.5f);
-  const df p = df_add(r, df_mul(df_sqr(r), q));          // exp(r) - 1
+  df q = df_add_f_ord_u(mk(I3H, I3L), __fmul_rn(r.hi, q4));  // 1/6 + r/24 + r^2/120
+  q = df_add_to_f_u(0.5f, df_mul(r, q));
+  const df p = df_add_ord(r, df_mul(df_sqr(r), q));          // exp(r) - 1
   const ExpEntryDF te = kT2DF[ni & 63];  // one 8-byte load, cached in L1
   const df T = mk(te.hi, te.lo);
-  const df e = df_add(T, df_mul(T, p));
+  const df e = df_add_ord(T, df_mul(T, p));
   // times 2^m, |m| <= 115
   return df_scale(e, __int_as_float((127 + (ni >> 6)) << 23));
 }
@@ -89,9 +91,10 @@ __device__ __forceinline__ df df_log(df x) {
   const df u = df_mul(two_sum(__fsub_rn(m.hi, F), m.lo), E.rcpF);      // m.hi - F exact
   const float uf = u.hi;
   const float c4 = fmaf(uf, fmaf(uf, fmaf(uf, 1.0f / 7.0f, -1.0f / 6.0f), 0.2f), -0.25f);
-  df c = df_add_f_u(mk(T3H, T3L), __fmul_rn(uf, c4));  // 1/3 - u/4 + u^2/5 - ...
-  c = df_add_f_u(df_mul(u, c), -0.5f);
-  const df l1p = df_add(u, df_mul(df_sqr(u), c));        // log1p(u)
+  // |u| <= 2^-8: ordered sums as in df_exp
+  df c = df_add_f_ord_u(mk(T3H, T3L), __fmul_rn(uf, c4));  // 1/3 - u/4 + u^2/5 - ...
+  c = df_add_to_f_u(-0.5f, df_mul(u, c));
+  const df l1p = df_add_ord(u, df_mul(df_sqr(u), c));        // log1p(u)
   k += j >= 64 ? 1 : 0;
   const float kf = (float)k;
   // k ln2: k LN1 exact, k LN2 as an exact product, k LN3 rounded
