@@ -55,14 +55,14 @@ LOOSE_TOL = 1e-8  # the served stream's looser tolerance, where MIXED is meant t
 FP64_TRAFFIC_BYTES_PER_LAUNCH = 575.78e6
 # FP32-pipe (FMA heavy + lite) thread instructions per double-float Cash-Karp
 # attempt on the Kerr set: ncu capture of trace_df64_persistent on the 12
-# renders at 256x256 (3.5559e10 FMA-pipe warp instructions x 28.73 active
+# renders at 256x256 (3.3475e10 FMA-pipe warp instructions x 28.71 active
 # lanes over 2.7322e8 attempts), profiles/trace_df64_persistent_kerr12x256_ncu.md.
-DF64_FP32_INST_PER_ATTEMPT = 3739
+DF64_FP32_INST_PER_ATTEMPT = 3518
 # The same for the MIXED kernel (FP32 evaluations in the double-float stepper)
 # at tol 1e-8: ncu capture of trace_mixed_persistent on the 12 renders at
-# 256x256 (8.7459e9 FMA-pipe warp instructions x 26.18 active lanes over
+# 256x256 (8.7710e9 FMA-pipe warp instructions x 26.17 active lanes over
 # 1.4603e8 attempts), profiles/trace_mixed_persistent_kerr12x256_ncu.md.
-MIXED_FP32_INST_PER_ATTEMPT = 1568
+MIXED_FP32_INST_PER_ATTEMPT = 1572
 
 
 # Workloads: the headline Kerr set (default) and the measured "next" rows,
