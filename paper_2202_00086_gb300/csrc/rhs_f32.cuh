@@ -1,26 +1,39 @@
 // Hamilton's equations in FP32 for the MIXED kernels: the separated form of
 // rhs64 (trace_device.cuh, Sec. 2.1 on the metric of Sec. 4.3) with every
-// operation in single precision, evaluated at the df64 stage input of the
-// double-float stepper (step_df.cuh). Two quantities that FP32 would lose to
-// cancellation are formed from both words of that input:
+// operation in single precision, evaluated at a stage input of the MIXED
+// stepper (step_mixed.cuh). A stage input is the df64 state plus an FP32
+// increment; r and theta are passed in that form (PointF32), because two
+// quantities that FP32 would lose to cancellation are formed from the base's
+// two words and the increment without rounding the sum first:
 //   - Delta = (r - r+)(r - r-): the factor r - r+ vanishes at the horizon, so
-//     it is taken as (r.hi - r+.hi) + (r.lo - r+.lo), whose leading difference
-//     is exact there (Sterbenz); Delta keeps FP32 relative accuracy down to
-//     the capture radius, where r^2 - 2r + a^2 in FP32 would keep none;
+//     it is taken as ((r.hi - r+.hi) + dr) + (r.lo - r+.lo), whose leading
+//     difference is exact there (Sterbenz); Delta keeps FP32 relative
+//     accuracy down to the capture radius, where r^2 - 2r + a^2 in FP32 would
+//     keep none;
 //   - the reduced angle t = theta - k pi/2 of sin and cos: k P1 is subtracted
-//     from the leading word exactly (as in df_sincos), so sin theta keeps its
-//     relative accuracy next to the poles.
-// Every other operation has FP32 relative accuracy (~1e-7), the accuracy of
-// the derivatives this returns. The q-metric evaluation (rhs_q_f32, Appendix
-// A) does the same with r - 2, the factor of f = 1 - 2/r that vanishes at its
-// inner surface, and takes the powers f^q and X^k from the FP32 exp and log
-// intrinsics. Like rhs_df it uses no CUDA built-in beyond the FP32
-// intrinsics, so it also compiles as host C++ for the CPU tests.
+//     from the base's leading word exactly (as in df_sincos) before the
+//     increment is added, so sin theta keeps its relative accuracy next to
+//     the poles.
+// p_r and p_theta enter only as FP32 values. Every other operation has FP32
+// relative accuracy (~1e-7), the accuracy of the derivatives this returns.
+// The q-metric evaluation (rhs_q_f32, Appendix A) does the same with r - 2,
+// the factor of f = 1 - 2/r that vanishes at its inner surface, and takes the
+// powers f^q and X^k from the FP32 exp and log intrinsics. Like rhs_df it uses
+// no CUDA built-in beyond the FP32 intrinsics, so it also compiles as host
+// C++ for the CPU tests.
 #pragma once
 
 #include "df64.cuh"
 
 namespace osiris_impl {
+
+// The point of an evaluation: r = r.hi + r.lo + dr and theta = th.hi + th.lo
+// + dth (a df64 base and an FP32 increment, dr = dth = -0 for the base
+// itself), p_r and p_theta in FP32.
+struct PointF32 {
+  df r, th;
+  float dr, dth, pr, pth;
+};
 
 struct RayF32 {
   float a, a2, aE, aL, E, L, twoE;
@@ -29,13 +42,14 @@ struct RayF32 {
   float twoH0;
 };
 
-// sin and cos of a df64 angle in FP32: t = theta - k pi/2, |t| <= pi/4, then
-// the Taylor polynomials of sin t (to t^9) and cos t (to t^10), whose
-// truncation at |t| = pi/4 is below 3e-9 of the result.
-__device__ __forceinline__ void sincos_f32(df th, float& s, float& c) {
+// sin and cos of th + dth (a df64 base and an FP32 increment) in FP32:
+// t = theta - k pi/2, |t| <= pi/4 (k from the rounded sum; th.hi - k P1 is
+// exact, Sterbenz), then the Taylor polynomials of sin t (to t^9) and cos t
+// (to t^10), whose truncation at |t| = pi/4 is below 3e-9 of the result.
+__device__ __forceinline__ void sincos_f32(df th, float dth, float& s, float& c) {
   using namespace dfc;
-  const float k = rintf(__fmul_rn(th.hi, 0.636619772367581343f));
-  const float t = __fadd_rn(fmaf(-k, P1, th.hi), fmaf(-k, P2, th.lo));
+  const float k = rintf(__fmul_rn(__fadd_rn(th.hi, dth), 0.636619772367581343f));
+  const float t = __fadd_rn(__fadd_rn(fmaf(-k, P1, th.hi), dth), fmaf(-k, P2, th.lo));
   const float u = __fmul_rn(t, t);
   const float ps = fmaf(u, fmaf(u, fmaf(u, fmaf(u, I9H, -I7H), I5H), -I3H), 1.0f);
   const float st = __fmul_rn(t, ps);
@@ -57,17 +71,19 @@ __device__ __forceinline__ void sincos_f32(df th, float& s, float& c) {
   }
 }
 
-// The derivatives (r', theta', phi', p_r', p_theta') and 2 (H - H0) at
-// (r, theta, p_r, p_theta), as rhs64 writes them, in FP32.
-__device__ __forceinline__ void rhs_f32(const RayF32& K, df r, df th, df pr, df pth, float& dr,
+// The derivatives (r', theta', phi', p_r', p_theta') and 2 (H - H0) at x,
+// as rhs64 writes them, in FP32.
+__device__ __forceinline__ void rhs_f32(const RayF32& K, const PointF32& x, float& dr,
                                         float& dth, float& dph, float& dpr, float& dpth,
                                         float& twoH) {
   float s, c;
-  sincos_f32(th, s, c);
-  const float rf = __fadd_rn(r.hi, r.lo);
-  const float prf = __fadd_rn(pr.hi, pr.lo);
-  const float ptf = __fadd_rn(pth.hi, pth.lo);
-  const float dp = __fadd_rn(__fsub_rn(r.hi, K.rp.hi), __fsub_rn(r.lo, K.rp.lo));  // r - r+
+  sincos_f32(x.th, x.dth, s, c);
+  const float rf = __fadd_rn(x.r.hi, x.dr);
+  const float prf = x.pr;
+  const float ptf = x.pth;
+  // r - r+ (the differences of the words are exact next to the horizon)
+  const float dp = __fadd_rn(__fadd_rn(__fsub_rn(x.r.hi, K.rp.hi), x.dr),
+                             __fsub_rn(x.r.lo, K.rp.lo));
   const float Delta = __fmul_rn(dp, __fsub_rn(rf, K.rm));
   const float ra2 = fmaf(rf, rf, K.a2);  // r^2 + a^2
   const float a2s = __fmul_rn(K.a2, s);
@@ -106,15 +122,16 @@ struct RayQF32 {
 // (rhs_df.cuh) and rhs_q64, the derivatives from the four terms of 2H and
 // their logarithmic derivatives, with f = (r - 2) / r and X = 1 + sin^2 / D,
 // D = r (r - 2).
-__device__ __forceinline__ void rhs_q_f32(const RayQF32& K, df r, df th, df pr, df pth,
-                                          float& dr, float& dth, float& dph, float& dpr,
-                                          float& dpth, float& twoH) {
+__device__ __forceinline__ void rhs_q_f32(const RayQF32& K, const PointF32& x, float& dr,
+                                          float& dth, float& dph, float& dpr, float& dpth,
+                                          float& twoH) {
   float s, c;
-  sincos_f32(th, s, c);
-  const float rf = __fadd_rn(r.hi, r.lo);
-  const float prf = __fadd_rn(pr.hi, pr.lo);
-  const float ptf = __fadd_rn(pth.hi, pth.lo);
-  const float rm2 = __fadd_rn(__fsub_rn(r.hi, 2.0f), r.lo);  // r - 2, exact next to r = 2
+  sincos_f32(x.th, x.dth, s, c);
+  const float rf = __fadd_rn(x.r.hi, x.dr);
+  const float prf = x.pr;
+  const float ptf = x.pth;
+  // r - 2, exact next to r = 2
+  const float rm2 = __fadd_rn(__fadd_rn(__fsub_rn(x.r.hi, 2.0f), x.dr), x.r.lo);
   const float iD = __fdividef(1.0f, __fmul_rn(rf, rm2));
   const float ir = __fmul_rn(rm2, iD);  // 1/r
   const float f = __fmul_rn(rm2, ir);   // 1 - 2/r

@@ -52,6 +52,7 @@ struct KerrDF {
     rhs_df(K, r, th, pr, pth, dr, dth, dph, dpr, dpth, twoH);
   }
   static constexpr bool kTrackH = true;
+  static constexpr bool kF32Stages = false;
   static constexpr double kLocateRel = 4e-16;
   static __device__ __forceinline__ float end_twoH(const Ray& K, const RayK&, const StateDF& y) {
     df dr, dth, dph, dpr, dpth;
@@ -71,6 +72,7 @@ struct QMetricDF {
     rhs_q_df(K, r, th, pr, pth, dr, dth, dph, dpr, dpth, twoH);
   }
   static constexpr bool kTrackH = true;
+  static constexpr bool kF32Stages = false;
   static constexpr double kLocateRel = 4e-16;
   static __device__ __forceinline__ float end_twoH(const Ray& K, const RayK&, const StateDF& y) {
     df dr, dth, dph, dpr, dpth;

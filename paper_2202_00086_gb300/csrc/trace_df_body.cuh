@@ -1,17 +1,21 @@
 // The lane state machine shared by the double-float (DF64) and mixed (MIXED)
 // trace kernels: a df64 state vector (pairs of FP32, 48-bit significand)
-// integrated by rk_step_df (step_df.cuh) on the FP32 pipe, with the
-// evaluation of Hamilton's equations supplied by a metric policy: double-float
-// for DF64 (trace_df64.cu), FP32 for MIXED (trace_mixed.cu). FP64 is used
-// once per ray (initial data, the terminal state and the observables) and for
-// the step-length bracket of surface location.
+// integrated on the FP32 pipe, with the evaluation of Hamilton's equations
+// supplied by a metric policy: double-float for DF64 (trace_df64.cu, stepper
+// rk_step_df in step_df.cuh), FP32 for MIXED (trace_mixed.cu, stepper
+// rk_step_mixed in step_mixed.cuh). FP64 is used once per ray (initial data,
+// the terminal state and the observables) and for the step-length bracket of
+// surface location.
 #pragma once
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "df64.cuh"
 #include "rhs_df.cuh"
 #include "step_df.cuh"
+#include "step_mixed.cuh"
 #include "trace_kernel.cuh"
 
 namespace osiris_impl {
@@ -81,7 +85,9 @@ __device__ __forceinline__ bool df_not_finite(float x) {
 // no FP64 instruction. Surface location keeps its bracket in FP64.
 //
 // The metric policy Met provides: Ray (its per-ray constants) and ray(K);
-// rhs(), the evaluation of Hamilton's equations at a df64 point; end_twoH(),
+// kF32Stages, which stepper integrates (false: rk_step_df with rhs(), the
+// double-float evaluation of Hamilton's equations at a df64 point; true:
+// rk_step_mixed with rhs_f(), the FP32 evaluation); end_twoH(),
 // 2 (H - H0) at the end point in double-float; kTrackH, whether the |H| of
 // every step start (from rhs) enters the ray's max |H|; kLocateRel, the
 // relative width of the step-length bracket at which surface location stops
@@ -106,7 +112,7 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
   float h_step = 0.0f;                // length of the last accepted step
   float flo = 0.0f, fhi = 0.0f;
   StateDF yF, yE;
-  LaneCacheDF<INTEG> LC;
+  std::conditional_t<Met::kF32Stages, LaneCacheF32<INTEG>, LaneCacheDF<INTEG>> LC;
 
   auto start_ray = [&](int64_t g) {
     State y0;
@@ -228,7 +234,10 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
     StateDF o;
     float d[5];
     float twoH;
-    rk_step_df<Met, INTEG>(KD, LC, y, hd, o, d, twoH);
+    if constexpr (Met::kF32Stages)
+      rk_step_mixed<Met, INTEG>(KD, LC, y, hd, o, d, twoH);
+    else
+      rk_step_df<Met, INTEG>(KD, LC, y, hd, o, d, twoH);
     S.rhs += 6;
 
     if (mode == MODE_INTEGRATE) {

@@ -1,12 +1,13 @@
 // Mixed-precision trace kernels (OSIRIS_MIXED), Kerr and the q-metric: the
-// lane state machine and the double-float stepper of the DF64 kernels
-// (trace_df_body.cuh, step_df.cuh) with the six evaluations of Hamilton's
-// equations of every attempt in FP32 (rhs_f32.cuh). The state, the stage inputs, the increment,
-// the error estimate and the controller keep df64 precision (FP32 with
-// compensated sums); only the stage derivatives carry FP32 rounding, ~1e-7 of
-// |k|. No step of the integration runs on the FP64 pipe: FP64 only sets up
-// each ray, keeps the step-length bracket of surface location and forms the
-// outputs.
+// lane state machine of the DF64 kernels (trace_df_body.cuh) with the six
+// evaluations of Hamilton's equations of every attempt in FP32 (rhs_f32.cuh)
+// and a stepper that sums their derivatives in FP32 (step_mixed.cuh). The
+// state and the stage inputs keep df64 precision (FP32 with compensated
+// sums), so adding a small increment to the state loses nothing; the
+// derivatives carry FP32 rounding, ~1e-7 of |k|, and the sums over stages
+// (increments, error estimate) add roundings of the same relative size. No
+// step of the integration runs on the FP64 pipe: FP64 only sets up each ray,
+// keeps the step-length bracket of surface location and forms the outputs.
 //
 // Tolerance range. The embedded error estimate h sum_s (b_s - b*_s)(k_s - k_1)
 // then carries a noise of ~1e-8 h |k| ~ 1e-8 (h/tau) |y| (tau: time scale of
@@ -31,20 +32,26 @@
 
 namespace osiris_impl {
 
-// Registers capped at 96 so that five blocks of 128 threads (20 warps) are
-// resident per SM: the FP32 evaluations leave the same double-float stepper
-// state as DF64 but fewer live temporaries, and the extra warps hide more of
-// the dependent FP32 chains than the added spills (L1 hits) cost. Measured on
-// the 12 x 1024^2 Kerr set at tol 1e-8 (Mrays/s, Cash-Karp): 192 registers
-// 46.7, 160: 52.6, 128: 59.9, 112: 60.7, 96: 64.7.
+// Registers capped so that more blocks of 128 threads are resident per SM
+// than the code's natural ~190 registers allow: the FP32 stepper keeps only
+// the df64 state, the stage inputs and FP32 sums live, and the extra warps
+// hide more of the dependent FP32 chains than the added spills (L1 hits)
+// cost. Measured on the 12 x 1024^2 Kerr set at tol 1e-8 (Mrays/s, Cash-Karp,
+// refill at 32 idle lanes): 112 registers 93.5, 96: 101.9, 88: 101.2,
+// 80 (6 blocks): 106.3, 72: 104.6, 64: 103.5; on the six q-metric renders:
+// 96: 88.2, 80: 93.2, 72: 96.9, 64 (8 blocks): 97.3.
 #ifndef OSIRIS_MIXED_MAXREGS
-#define OSIRIS_MIXED_MAXREGS 96
+#define OSIRIS_MIXED_MAXREGS 80
+#endif
+#ifndef OSIRIS_MIXED_Q_MAXREGS
+#define OSIRIS_MIXED_Q_MAXREGS 64
 #endif
 
 struct KerrMixed {
   using Ray = RayF32;
   static constexpr int kMaxRegs = OSIRIS_MIXED_MAXREGS;
   static constexpr bool kTrackH = false;
+  static constexpr bool kF32Stages = true;
   static constexpr double kLocateRel = 2e-7;
   static __device__ __forceinline__ Ray ray(const RayK& K) {
     Ray k;
@@ -61,16 +68,10 @@ struct KerrMixed {
     k.twoH0 = 0.0f;
     return k;
   }
-  static __device__ __forceinline__ void rhs(const Ray& K, df r, df th, df pr, df pth, df& dr,
-                                             df& dth, df& dph, df& dpr, df& dpth,
-                                             float& twoH) {
-    float fr, ft, fp, fpr, fpt;
-    rhs_f32(K, r, th, pr, pth, fr, ft, fp, fpr, fpt, twoH);
-    dr = mk(fr, 0.0f);
-    dth = mk(ft, 0.0f);
-    dph = mk(fp, 0.0f);
-    dpr = mk(fpr, 0.0f);
-    dpth = mk(fpt, 0.0f);
+  static __device__ __forceinline__ void rhs_f(const Ray& K, const PointF32& x, float& dr,
+                                               float& dth, float& dph, float& dpr, float& dpth,
+                                               float& twoH) {
+    rhs_f32(K, x, dr, dth, dph, dpr, dpth, twoH);
   }
   // 2 (H - H0) at the end point with the double-float equations of DF64.
   static __device__ __forceinline__ float end_twoH(const Ray& KD, const RayK& K,
@@ -88,8 +89,9 @@ struct KerrMixed {
 // the double-float q-metric equations (rhs_q_df).
 struct QMetricMixed {
   using Ray = RayQF32;
-  static constexpr int kMaxRegs = OSIRIS_MIXED_MAXREGS;
+  static constexpr int kMaxRegs = OSIRIS_MIXED_Q_MAXREGS;
   static constexpr bool kTrackH = false;
+  static constexpr bool kF32Stages = true;
   static constexpr double kLocateRel = 2e-7;
   static __device__ __forceinline__ Ray ray(const RayK& K) {
     Ray k;
@@ -102,16 +104,10 @@ struct QMetricMixed {
     k.twoH0 = 0.0f;
     return k;
   }
-  static __device__ __forceinline__ void rhs(const Ray& K, df r, df th, df pr, df pth, df& dr,
-                                             df& dth, df& dph, df& dpr, df& dpth,
-                                             float& twoH) {
-    float fr, ft, fp, fpr, fpt;
-    rhs_q_f32(K, r, th, pr, pth, fr, ft, fp, fpr, fpt, twoH);
-    dr = mk(fr, 0.0f);
-    dth = mk(ft, 0.0f);
-    dph = mk(fp, 0.0f);
-    dpr = mk(fpr, 0.0f);
-    dpth = mk(fpt, 0.0f);
+  static __device__ __forceinline__ void rhs_f(const Ray& K, const PointF32& x, float& dr,
+                                               float& dth, float& dph, float& dpr, float& dpth,
+                                               float& twoH) {
+    rhs_q_f32(K, x, dr, dth, dph, dpr, dpth, twoH);
   }
   static __device__ __forceinline__ float end_twoH(const Ray& KD, const RayK& K,
                                                    const StateDF& y) {

@@ -28,14 +28,27 @@ HARNESS = r"""
 #include <cstdlib>
 #include "rhs_f32.cuh"
 using namespace osiris_impl;
+// The point (r, theta, p_r, p_theta) as a stage input of the MIXED stepper:
+// df64 bases r - dr and theta - dth plus the FP32 increments dr, dth (both
+// exact floats, -0 for a point given by its base alone).
+static PointF32 point(const double* v, double dr, double dth) {
+  PointF32 x;
+  x.r = df_from_double(v[0] - dr);
+  x.th = df_from_double(v[1] - dth);
+  x.dr = (float)dr;
+  x.dth = (float)dth;
+  x.pr = (float)v[2];
+  x.pth = (float)v[3];
+  return x;
+}
 int main(int argc, char** argv) {
   const char op = argv[1][0];
-  double in[9];  // 'e': a, E, L, r, theta, p_r, p_theta; 's': theta
-  const int n = op == 'e' ? 7 : 1;
+  double in[9];  // 'e': a, E, L, r, theta, p_r, p_theta, dr, dth; 's': theta, dth
+  const int n = op == 'e' ? 9 : 2;
   while (std::fread(in, sizeof(double) * n, 1, stdin) == 1) {
     if (op == 's') {
       float s, c;
-      sincos_f32(df_from_double(in[0]), s, c);
+      sincos_f32(df_from_double(in[0] - in[1]), (float)in[1], s, c);
       const double out[2] = {s, c};
       std::fwrite(out, sizeof out, 1, stdout);
       continue;
@@ -54,14 +67,28 @@ int main(int argc, char** argv) {
     k.rm = (float)(1.0 - sq);
     k.twoH0 = 0.0f;
     float d[5], twoH;
-    rhs_f32(k, df_from_double(in[3]), df_from_double(in[4]), df_from_double(in[5]),
-            df_from_double(in[6]), d[0], d[1], d[2], d[3], d[4], twoH);
+    rhs_f32(k, point(in + 3, in[7], in[8]), d[0], d[1], d[2], d[3], d[4], twoH);
     const double out[6] = {d[0], d[1], d[2], d[3], d[4], twoH};
     std::fwrite(out, sizeof out, 1, stdout);
   }
   return 0;
 }
 """
+
+
+def _split(rows, seed):
+    """Append the increments (dr, dth) of the stage-input form: a quarter of
+    the points given by their base alone (-0), the rest split into a base and
+    an FP32 increment of up to 5 % of r and 0.3 rad."""
+    rng = np.random.default_rng(seed)
+    rows = np.asarray(rows, dtype=np.float64)
+    n = len(rows)
+    dr = np.float32(rows[:, 3] * rng.uniform(-0.05, 0.05, n)).astype(np.float64)
+    dth = np.float32(rng.uniform(-0.3, 0.3, n)).astype(np.float64)
+    base = rng.uniform(size=n) < 0.25
+    dr[base] = -0.0
+    dth[base] = -0.0
+    return np.column_stack([rows, dr, dth])
 
 
 @pytest.fixture(scope="module")
@@ -105,7 +132,7 @@ def _errors(rows, out):
 
 def test_kerr_rhs_f32_against_oracle(dev):
     rows = _points(150, 11)
-    worst_terms, worst_rel = _errors(rows, dev("e", rows, 6))
+    worst_terms, worst_rel = _errors(rows, dev("e", _split(rows, 21), 6))
     assert worst_terms <= 2e-6 and worst_rel <= 2e-6, (worst_terms, worst_rel)
 
 
@@ -119,7 +146,7 @@ def test_kerr_rhs_f32_next_to_the_horizon(dev):
                 rows.append([a, 1.0, rng.uniform(-4.0, 4.0), f * r_h, rng.uniform(0.3, 2.8),
                              rng.normal(), 3.0 * rng.normal()])
     rows = np.array(rows)
-    worst_terms, worst_rel = _errors(rows, dev("e", rows, 6))
+    worst_terms, worst_rel = _errors(rows, dev("e", _split(rows, 22), 6))
     assert worst_terms <= 2e-6 and worst_rel <= 2e-6, (worst_terms, worst_rel)
 
 
@@ -129,7 +156,9 @@ def test_sincos_f32_next_to_poles_and_equator(dev):
     th = np.concatenate([c + np.exp(rng.uniform(np.log(1e-8), np.log(1e-5), 60))
                          * rng.choice([-1.0, 1.0], 60) for c in centres])
     th = np.concatenate([th, rng.uniform(-np.pi, 2.0 * np.pi, 300)])
-    out = dev("s", th[:, None], 2)
+    dth = np.float32(rng.uniform(-0.3, 0.3, len(th))).astype(np.float64)
+    dth[::4] = -0.0
+    out = dev("s", np.column_stack([th, dth]), 2)
     rel_s = np.abs(out[:, 0] - np.sin(th)) / np.abs(np.sin(th))
     rel_c = np.abs(out[:, 1] - np.cos(th)) / np.abs(np.cos(th))
     assert rel_s.max() <= 1e-6 and rel_c.max() <= 1e-6, (rel_s.max(), rel_c.max())
@@ -139,7 +168,7 @@ QHARNESS = r"""
 #include "rhs_f32.cuh"
 using namespace osiris_impl;
 int main() {
-  double in[7];  // q, E, L, r, theta, p_r, p_theta
+  double in[9];  // q, E, L, r, theta, p_r, p_theta, dr, dth (as in HARNESS)
   while (std::fread(in, sizeof in, 1, stdin) == 1) {
     const double q = in[0], E = in[1], L = in[2];
     RayQF32 k;  // ray constants formed as the MIXED kernels form them
@@ -151,8 +180,14 @@ int main() {
     k.E2 = (float)(E * E);
     k.twoH0 = 0.0f;
     float d[5], twoH;
-    rhs_q_f32(k, df_from_double(in[3]), df_from_double(in[4]), df_from_double(in[5]),
-              df_from_double(in[6]), d[0], d[1], d[2], d[3], d[4], twoH);
+    PointF32 x;
+    x.r = df_from_double(in[3] - in[7]);
+    x.th = df_from_double(in[4] - in[8]);
+    x.dr = (float)in[7];
+    x.dth = (float)in[8];
+    x.pr = (float)in[5];
+    x.pth = (float)in[6];
+    rhs_q_f32(k, x, d[0], d[1], d[2], d[3], d[4], twoH);
     const double out[6] = {d[0], d[1], d[2], d[3], d[4], twoH};
     std::fwrite(out, sizeof out, 1, stdout);
   }
@@ -176,7 +211,7 @@ def test_qmetric_rhs_q_f32_against_oracle(tmp_path_factory):
                          np.exp(rng.uniform(np.log(2.02), np.log(1000.0))),
                          rng.uniform(0.05, np.pi - 0.05), 2.0 * rng.normal(), 5.0 * rng.normal()])
     rows = np.array(rows)
-    p = subprocess.run([str(exe)], input=np.ascontiguousarray(rows).tobytes(),
+    p = subprocess.run([str(exe)], input=np.ascontiguousarray(_split(rows, 23)).tobytes(),
                        capture_output=True, check=True)
     out = np.frombuffer(p.stdout, dtype=np.float64).reshape(-1, 6)
     worst_terms = worst_rel = 0.0
