@@ -53,16 +53,36 @@ LOOSE_TOL = 1e-8  # the served stream's looser tolerance, where MIXED is meant t
 # + 528.18 MB written (profiles/trace_fp64_persistent_kerr12x1024_dram.md);
 # the outputs alone are 528.5 MB (42 B per ray).
 FP64_TRAFFIC_BYTES_PER_LAUNCH = 575.78e6
-# FP32-pipe (FMA heavy + lite) thread instructions per double-float Cash-Karp
-# attempt on the Kerr set: ncu capture of trace_df64_persistent on the 12
-# renders at 256x256 (3.3475e10 FMA-pipe warp instructions x 28.71 active
-# lanes over 2.7322e8 attempts), profiles/trace_df64_persistent_kerr12x256_ncu.md.
+# FP32-pipe (FMA heavy + lite) thread instructions, and warp instructions of
+# every pipe, per double-float Cash-Karp attempt on the Kerr set: ncu capture
+# of trace_df64_persistent on the 12 renders at 256x256 (3.3475e10 FMA-pipe
+# warp instructions x 28.71 active lanes, and 4.050e10 warp instructions, over
+# 2.7322e8 attempts), profiles/trace_df64_persistent_kerr12x256_ncu.md.
 DF64_FP32_INST_PER_ATTEMPT = 3518
-# The same for the MIXED kernel (FP32 evaluations in the double-float stepper)
-# at tol 1e-8: ncu capture of trace_mixed_persistent on the 12 renders at
-# 256x256 (8.7710e9 FMA-pipe warp instructions x 26.17 active lanes over
-# 1.4603e8 attempts), profiles/trace_mixed_persistent_kerr12x256_ncu.md.
-MIXED_FP32_INST_PER_ATTEMPT = 1572
+DF64_WARP_INST_PER_ATTEMPT = 148.2
+# The same for the MIXED kernel (FP32 evaluations, FP32 stage sums) at tol
+# 1e-8: ncu capture of trace_mixed_persistent on the 12 renders at 256x256
+# (3.6500e9 FMA-pipe warp instructions x 25.19 active lanes, and 5.5962e9 warp
+# instructions, over 1.4642e8 attempts),
+# profiles/trace_mixed_persistent_kerr12x256_ncu.md.
+MIXED_FP32_INST_PER_ATTEMPT = 628
+MIXED_WARP_INST_PER_ATTEMPT = 38.22
+
+
+def fp32_roofline(probe, inst_per_attempt, warp_inst_per_attempt, attempts, seconds):
+    """Roofline of a kernel on the FP32 pipe (DF64, MIXED): its FMA-pipe thread
+    instructions per attempt (ncu) x attempts/s over the FP32 probe's thread
+    instruction rate, and, as `issue_frac`, its warp instructions of all pipes
+    per attempt x attempts/s over the issue rate of one warp instruction per
+    cycle per SM sub-partition, which the FP32 probe reaches."""
+    rate = attempts * inst_per_attempt / seconds
+    warp_peak = probe["fp32_fma"]["warp_inst_per_s"]
+    return {"bound": "alu", "pipe": "FP32 (FMA heavy + lite)", "achieved": rate / 1e12,
+            "peak": warp_peak * 32 / 1e12, "unit": "T thread-instructions/s",
+            "frac": rate / (warp_peak * 32), "inst_per_attempt": inst_per_attempt,
+            "issue_frac": attempts * warp_inst_per_attempt / seconds / warp_peak,
+            "warp_inst_per_attempt": warp_inst_per_attempt,
+            "peak_source": "FP32 pipe probe measured in this process"}
 
 
 # Workloads: the headline Kerr set (default) and the measured "next" rows,
@@ -807,18 +827,9 @@ def main():
             "dtype": "f64+df64",
             "fp64_equivalent_tflops": vflops / (vms * 1e-3) / 1e12,
             "fp64_equivalent_frac_of_fp64_peak": vflops / (vms * 1e-3) / 1e12 / peaks["fp64"],
-            # the pipe the double-float kernel runs on: FP32-pipe thread
-            # instructions per attempt (ncu) x attempts/s over the FP32 probe's
-            # thread-instruction rate
-            "roofline": ({
-                "bound": "alu", "pipe": "FP32 (FMA heavy + lite)",
-                "achieved": vatt * DF64_FP32_INST_PER_ATTEMPT / (vms * 1e-3) / 1e12,
-                "peak": probe["fp32_fma"]["warp_inst_per_s"] * 32 / 1e12,
-                "unit": "T thread-instructions/s",
-                "frac": (vatt * DF64_FP32_INST_PER_ATTEMPT / (vms * 1e-3)) /
-                        (probe["fp32_fma"]["warp_inst_per_s"] * 32),
-                "inst_per_attempt": DF64_FP32_INST_PER_ATTEMPT,
-                "peak_source": "FP32 pipe probe measured in this process"}
+            # the pipe the double-float kernel runs on (see fp32_roofline)
+            "roofline": (fp32_roofline(probe, DF64_FP32_INST_PER_ATTEMPT,
+                                       DF64_WARP_INST_PER_ATTEMPT, vatt, vms * 1e-3)
                 if args.workload == "kerr" else None),
             "max_abs_H": vs["max_abs_H"],
             "steps_per_ray": {"accepted": vs["accepted"] / (n_rays * args.steps),
@@ -840,16 +851,11 @@ def main():
                            "rejected_per_ray": ls["rejected"] / (n_rays * args.steps)}
             if prec in (osr.DF64, osr.MIXED) and args.workload == "kerr":
                 # against the FP32 pipe the double-float stepper runs on, as variants.df64
-                ipa = (MIXED_FP32_INST_PER_ATTEMPT if prec == osr.MIXED
-                       else DF64_FP32_INST_PER_ATTEMPT)
-                latt = ls["accepted"] + ls["rejected"] + ls["root_steps"]
-                rate = latt * ipa / (lms * 1e-3)
-                peak32 = probe["fp32_fma"]["warp_inst_per_s"] * 32
-                loose[name]["roofline"] = {
-                    "bound": "alu", "pipe": "FP32 (FMA heavy + lite)", "achieved": rate / 1e12,
-                    "peak": peak32 / 1e12, "unit": "T thread-instructions/s",
-                    "frac": rate / peak32, "inst_per_attempt": ipa,
-                    "peak_source": "FP32 pipe probe measured in this process"}
+                mixed = prec == osr.MIXED
+                loose[name]["roofline"] = fp32_roofline(
+                    probe, MIXED_FP32_INST_PER_ATTEMPT if mixed else DF64_FP32_INST_PER_ATTEMPT,
+                    MIXED_WARP_INST_PER_ATTEMPT if mixed else DF64_WARP_INST_PER_ATTEMPT,
+                    ls["accepted"] + ls["rejected"] + ls["root_steps"], lms * 1e-3)
         loose["mixed_vs_df64"] = loose["mixed"]["value"] / loose["df64"]["value"]
         variants["tol_%g" % LOOSE_TOL] = loose
 
@@ -915,6 +921,28 @@ def main():
     per_launch_ms = ms / max(1, kernel_launches)
     achieved = flops / max(1, kernel_launches) / (per_launch_ms * 1e-3) / 1e12
     peak = peaks["fp64"] if precision == osr.FP64 else peaks["fp32"]
+    # The headline roofline: FP64 operations against the FP64 pipe for the FP64
+    # kernels; for DF64 and MIXED, the FP32 pipe and the issue slots they run
+    # on, from instruction counts measured on the Kerr set (else none).
+    if precision == osr.FP64:
+        roofline_main = {
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "traffic": (FP64_TRAFFIC_BYTES_PER_LAUNCH
+                        if args.side == 1024 and args.kernel == "batch"
+                        and args.workload == "kerr" else None),
+            "peak_source": ("pipe probe measured in this process: FP64 fused "
+                            "multiply-add, 16 chains per thread, every SM full"),
+            "flops_per_launch": flops / max(1, kernel_launches),
+            "f_rhs": f_rhs, "f_step": F_STEP}
+    elif args.workload == "kerr":
+        mixed = precision == osr.MIXED
+        roofline_main = fp32_roofline(
+            probe, MIXED_FP32_INST_PER_ATTEMPT if mixed else DF64_FP32_INST_PER_ATTEMPT,
+            MIXED_WARP_INST_PER_ATTEMPT if mixed else DF64_WARP_INST_PER_ATTEMPT,
+            attempts / max(1, kernel_launches), per_launch_ms * 1e-3)
+    else:
+        roofline_main = None
     line = {
         "metric": WORKLOADS[args.workload][1], "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -934,19 +962,7 @@ def main():
                                    ("status_captured", "status_escaped", "status_maxstep",
                                     "status_disk", "status_error")},
         "max_abs_H": s["max_abs_H"],
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak,
-                     "traffic": (FP64_TRAFFIC_BYTES_PER_LAUNCH
-                                 if precision == osr.FP64 and args.side == 1024
-                                 and args.kernel == "batch" and args.workload == "kerr"
-                                 else None),
-                     "peak_source": ("pipe probe measured in this process: FP64 fused "
-                                     "multiply-add, 16 chains per thread, every SM full"
-                                     if precision == osr.FP64 else
-                                     "pipe probe measured in this process: FP32 fused "
-                                     "multiply-add, 16 chains per thread, every SM full"),
-                     "flops_per_launch": flops / max(1, kernel_launches),
-                     "f_rhs": f_rhs, "f_step": F_STEP},
+        "roofline": roofline_main,
         "fma_probe_tflops": peaks,
         "pipe_probes": probe,
         "variants": variants,

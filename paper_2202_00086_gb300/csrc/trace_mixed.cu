@@ -37,14 +37,14 @@ namespace osiris_impl {
 // the df64 state, the stage inputs and FP32 sums live, and the extra warps
 // hide more of the dependent FP32 chains than the added spills (L1 hits)
 // cost. Measured on the 12 x 1024^2 Kerr set at tol 1e-8 (Mrays/s, Cash-Karp,
-// refill at 32 idle lanes): 112 registers 93.5, 96: 101.9, 88: 101.2,
-// 80 (6 blocks): 106.3, 72: 104.6, 64: 103.5; on the six q-metric renders:
-// 96: 88.2, 80: 93.2, 72: 96.9, 64 (8 blocks): 97.3.
+// refill at 32 idle lanes): 96 registers 160.9, 80 (6 blocks): 162.3, 72:
+// 154.7, 64: 153.0; on the six q-metric renders: 80: 117.6, 72: 118.9, 64:
+// 123.3, 56 (9 blocks): 127.1.
 #ifndef OSIRIS_MIXED_MAXREGS
 #define OSIRIS_MIXED_MAXREGS 80
 #endif
 #ifndef OSIRIS_MIXED_Q_MAXREGS
-#define OSIRIS_MIXED_Q_MAXREGS 64
+#define OSIRIS_MIXED_Q_MAXREGS 56
 #endif
 
 struct KerrMixed {
