@@ -389,8 +389,8 @@ STREAM_LABEL = ("Poisson %g renders/s for %g s (PCG64 seed 5), side log-uniform 
                 "tol 1e-8/1e-10 50/50")
 
 
-SERVED_FORM = ("DF64 for the renders at tol 1e-10, MIXED (FP32 stage evaluations in the "
-               "double-float stepper) for those at tol 1e-8")
+SERVED_FORM = ("DF64 for the renders at tol 1e-10, MIXED (FP32 stage evaluations and stage "
+               "sums, df64 state) for those at tol 1e-8")
 
 
 def serve_stream(osr, torch, dist, rank, world, barrier, rate, seconds, phase):
@@ -850,7 +850,7 @@ def main():
                            "accepted_per_ray": ls["accepted"] / (n_rays * args.steps),
                            "rejected_per_ray": ls["rejected"] / (n_rays * args.steps)}
             if prec in (osr.DF64, osr.MIXED) and args.workload == "kerr":
-                # against the FP32 pipe the double-float stepper runs on, as variants.df64
+                # against the FP32 pipe DF64 and MIXED run on, as variants.df64
                 mixed = prec == osr.MIXED
                 loose[name]["roofline"] = fp32_roofline(
                     probe, MIXED_FP32_INST_PER_ATTEMPT if mixed else DF64_FP32_INST_PER_ATTEMPT,

@@ -1,7 +1,7 @@
 """Parity of the reduced-precision paths with the FP64 oracle.
 
 DF64 (double-float stage evaluations, df64 state) is held to the same bar as
-the FP64 kernels. MIXED (FP32 stage evaluations inside the df64 stepper) is
+the FP64 kernels. MIXED (FP32 stage evaluations and sums around a df64 state) is
 held to its stated error bound: flags identical outside the oracle's band,
 redshift g within 1e-5 and coordinates within 1e-5 (relative) of the oracle
 at 1e-10, when MIXED runs at tolerances of 1e-7 to 1e-8.
