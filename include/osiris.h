@@ -47,10 +47,11 @@ extern "C" {
 
 /* ---- precision of the integrator -------------------------------------- */
 #define OSIRIS_FP64 0  /* every operation in double precision */
-#define OSIRIS_MIXED 1 /* stage evaluations of Hamilton's equations in FP32,
-                          inside the DF64 stepper: double-float state, stage
-                          sums, error estimate and controller, end-point |H|
-                          in double-float; for tolerances of 1e-8 and looser
+#define OSIRIS_MIXED 1 /* stage evaluations of Hamilton's equations and the
+                          sums over stages in FP32 around a double-float
+                          state (each stage input is the state plus an FP32
+                          increment); FP32 controller, end-point |H| in
+                          double-float; for tolerances of 1e-8 and looser
                           (FP32 rounding of the stages swamps the error
                           estimate of tighter ones) */
 #define OSIRIS_DF64 2  /* every operation of the integration in double-float

@@ -176,10 +176,11 @@ int persistent_shape(const osiris_trace_opts* o, int spacetime, int* block,
 // in MIXED once all 32 are). Measured on the 12 x 1024^2 Kerr set, refill
 // granularity 1 / 4 / 8 / 16 / 32: DF64 16.2 / 18.5-19.0 / 18.1 / 18.5 / 18.9
 // Mrays/s, FP64 3.59 / 3.79 / 3.69 / 3.70 / 3.75; MIXED at tol 1e-8 49.0 /
-// 65.3 / 65.5 / 67.5 / 70.2. A MIXED ray takes about half the attempts of a
-// DF64 ray at tol 1e-10, so its start and end (FP64 work, one warp instruction
-// however many lanes share it) weigh more, and starting a warp's rays together
-// also keeps neighbouring pixels in one warp.
+// 65.3 / 65.5 / 67.5 / 70.2 (double-float stepper), refill 4 / 8 / 16 / 32:
+// 94.7 / 96.7 / 100.7 / 106.1 (FP32 stage sums). A MIXED ray takes about half
+// the attempts of a DF64 ray at tol 1e-10, so its start and end (FP64 work,
+// one warp instruction however many lanes share it) weigh more, and starting
+// a warp's rays together also keeps neighbouring pixels in one warp.
 constexpr int kDefaultRaysPerLane = 1;
 constexpr int kDefaultRefillLanes = 4;
 constexpr int kDefaultRefillLanesMixed = 32;

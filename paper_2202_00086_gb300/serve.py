@@ -23,7 +23,7 @@ Renders (camera set-ups) arrive over time. The server:
 Round composition: a batched launch holds one space-time and one precision,
 so each render has a kind: Kerr renders run at the server's precision, or at
 `loose_precision` when one is given and the render's tolerance is at least
-`loose_tol` (e.g. MIXED, FP32 stage evaluations, for the renders at 1e-8);
+`loose_tol` (e.g. MIXED, FP32 stage evaluations and sums, for the renders at 1e-8);
 q-metric renders (shadow and lensing; Appendix A) likewise. A round serves one
 kind: that of the oldest render with rays left, or the next kind in that
 order when the previous round served it, so kinds alternate while several
