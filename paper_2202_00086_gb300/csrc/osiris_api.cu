@@ -177,7 +177,8 @@ int persistent_shape(const osiris_trace_opts* o, int spacetime, int* block,
 // granularity 1 / 4 / 8 / 16 / 32: DF64 16.2 / 18.5-19.0 / 18.1 / 18.5 / 18.9
 // Mrays/s, FP64 3.59 / 3.79 / 3.69 / 3.70 / 3.75; MIXED at tol 1e-8 49.0 /
 // 65.3 / 65.5 / 67.5 / 70.2 (double-float stepper), refill 4 / 8 / 16 / 32:
-// 94.7 / 96.7 / 100.7 / 106.1 (FP32 stage sums). A MIXED ray takes about half
+// 94.7 / 96.7 / 100.7 / 106.1 (FP32 stage sums, rolled), 16 / 32: 148.5 /
+// 162.2 (the current stepper). A MIXED ray takes about half
 // the attempts of a DF64 ray at tol 1e-10, so its start and end (FP64 work,
 // one warp instruction however many lanes share it) weigh more, and starting
 // a warp's rays together also keeps neighbouring pixels in one warp.

@@ -76,8 +76,16 @@ __device__ __forceinline__ float df_side(df th) {
   return t.hi != 0.0f ? t.hi : t.lo;
 }
 
-__device__ __forceinline__ bool df_not_finite(float x) {
-  return ((__float_as_uint(x) >> 23) & 0xffu) == 0xffu;
+// True when any of the values is infinite or NaN: 0 * x is NaN exactly for
+// those, and one NaN term makes the sum NaN. One FMA per value on the FP32
+// pipe, where a test of the exponent bits takes two or three integer
+// instructions and an OR per value.
+template <int N>
+__device__ __forceinline__ bool any_not_finite(const float (&v)[N]) {
+  float z = 0.0f;
+#pragma unroll
+  for (int i = 0; i < N; ++i) z = fmaf(0.0f, v[i], z);
+  return z != z;
 }
 
 // The lane state machine of trace_body (trace_kernel.cuh) with a df64 state:
@@ -244,11 +252,12 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
       if (Met::kTrackH) max_abs_H = fmaxf(max_abs_H, fabsf(0.5f * twoH));  // 2 (H - H0) at y
       const float ys[5] = {y.r.hi, y.th.hi, y.ph.hi, y.pr.hi, y.pth.hi};
       const float os[5] = {o.r.hi, o.th.hi, o.ph.hi, o.pr.hi, o.pth.hi};
-      bool bad = false, ok = true;
+      const float od[10] = {os[0], os[1], os[2], os[3], os[4], d[0], d[1], d[2], d[3], d[4]};
+      const bool bad = any_not_finite(od);
+      bool ok = true;
       float err = 0.0f;
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
-        bad |= df_not_finite(os[c]) | df_not_finite(d[c]);
         const float scale = tol * (1.0f + fmaxf(fabsf(ys[c]), fabsf(os[c])));
         const float ad = fabsf(d[c]);
         ok = ok && (ad <= scale);
@@ -278,8 +287,8 @@ __device__ __forceinline__ void trace_body_df(const KernelArgs& A) {
     } else {  // MODE_LOCATE: Illinois-modified regula falsi on the step length
       S.root += 1;
       ++iters;
-      if (df_not_finite(o.r.hi) | df_not_finite(o.th.hi) | df_not_finite(o.ph.hi) |
-          df_not_finite(o.pr.hi) | df_not_finite(o.pth.hi)) {
+      const float os[5] = {o.r.hi, o.th.hi, o.ph.hi, o.pr.hi, o.pth.hi};
+      if (any_not_finite(os)) {
         finish(OSIRIS_STATUS_ERROR, y);
         continue;
       }

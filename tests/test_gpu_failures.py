@@ -38,7 +38,7 @@ BAD = [(1, 4, float("nan")), (4, "E", float("inf")), (6, 2, float("nan")), (9, 1
        (12, "L", float("nan"))]
 
 
-@pytest.mark.parametrize("precision", [osr.FP64, osr.DF64])
+@pytest.mark.parametrize("precision", [osr.FP64, osr.DF64, osr.MIXED])
 @pytest.mark.parametrize("q", [None, 0.5])
 @pytest.mark.parametrize("persistent", [False, True])
 def test_non_finite_initial_data_end_in_error(precision, q, persistent):
@@ -56,6 +56,8 @@ def test_non_finite_initial_data_end_in_error(precision, q, persistent):
     bad_rows = sorted({r for r, _, _ in BAD})
     good = np.setdiff1d(np.arange(16), bad_rows)
     kw = dict(a=a, q=q, precision=precision)
+    if precision == osr.MIXED:
+        kw["tol"] = 1e-8  # the tolerances MIXED is meant for
     ws = None
     if persistent:
         ws = torch.empty(osr.workspace_bytes(1), dtype=torch.uint8, device="cuda")
