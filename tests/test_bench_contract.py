@@ -149,6 +149,25 @@ def test_reference_arm_under_torchrun_two_ranks():
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
 
 
+def test_fp32_roofline_arithmetic():
+    """The FP32-pipe roofline of DF64 and MIXED: FMA-pipe thread instructions
+    per attempt x attempts/s over 32 x the probe's warp-instruction rate, and
+    the issue fraction: warp instructions per attempt x attempts/s over the
+    probe's warp-instruction rate (one per cycle per SM sub-partition)."""
+    import bench
+    probe = {"fp32_fma": {"warp_inst_per_s": 1.25e12}}
+    r = bench.fp32_roofline(probe, 600, 40.0, attempts=3.0e9, seconds=0.1)
+    assert r["peak"] == pytest.approx(1.25e12 * 32 / 1e12)
+    assert r["achieved"] == pytest.approx(3.0e10 * 600 / 1e12)
+    assert r["frac"] == pytest.approx(3.0e10 * 600 / (1.25e12 * 32))
+    assert r["issue_frac"] == pytest.approx(3.0e10 * 40.0 / 1.25e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    # the constants in use: FMA-pipe instructions are a part of all those issued
+    for ipa, wpa in ((bench.DF64_FP32_INST_PER_ATTEMPT, bench.DF64_WARP_INST_PER_ATTEMPT),
+                     (bench.MIXED_FP32_INST_PER_ATTEMPT, bench.MIXED_WARP_INST_PER_ATTEMPT)):
+        assert 0 < ipa < 32 * wpa
+
+
 def test_workload_inputs():
     """Each workload's inputs: render counts and sizes, and the time-like
     particles on the mass shell H = -1/2 (the oracle's Kerr Hamiltonian),
